@@ -1,0 +1,26 @@
+"""Seeded synthetic inputs shared by the CUDA path and the CPU oracle.
+
+This package holds problem definitions only: grid sizes, which degrees of
+freedom are supported, the nodal load vector, the initial density field and
+seeded random vectors.  It performs none of the method's arithmetic (no
+stiffness, no filtering, no solves), so both sides can import it without
+sharing any computation.
+"""
+
+from .problems import (  # noqa: F401
+    Problem,
+    Job,
+    config1_mbb2d,
+    config2_cantilever3d,
+    config3_cantilever3d,
+    config4_bridge3d,
+    config5_jobs,
+    cantilever3d,
+    bridge3d,
+    mbb2d,
+    cantilever2d,
+    small_problem,
+    rand_vector,
+    rand_density,
+    grid_counts,
+)
