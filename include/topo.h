@@ -1,0 +1,200 @@
+/*
+ * topo.h -- C ABI of the GB300 (sm_103a) AARMR topology-optimisation library.
+ *
+ * The library solves the equilibrium equation K(rho~) u = f of minimum-
+ * compliance topology optimisation (Eq. 3) on a regular grid of unit Q4
+ * (plane stress) or hex8 elements with the modified SIMP law (Eq. 1), by
+ *   - MGCG: conjugate gradients preconditioned by a Galerkin V-cycle
+ *     (Algorithm 2), which also maintains the PARM (Eq. 27-28), and
+ *   - the CARM reduced model built from the PARM (Eq. 15-29),
+ * and provides the compliance sensitivity (Eq. 6, 34), the density filter
+ * and its transpose (Eq. 31-33) and the optimality-criteria update (Eq. 3
+ * constraint, update rule of the paper's ref. [31]).  Algorithm 1 (the
+ * choice between CARM and MGCG) is driven by the caller from these calls.
+ *
+ * Conventions (all sizes in elements of the stated type):
+ *   nel  = nelx*nely (2D) or nelx*nely*nelz (3D)        -- elements
+ *   nn   = (nelx+1)*(nely+1)(*(nelz+1))                  -- nodes
+ *   n    = dim*nn                                         -- DOFs
+ *   node (i,j,k) = i + (nelx+1)*(j + (nely+1)*k); DOF c of a node = dim*node+c;
+ *   element (ex,ey,ez) = ex + nelx*(ey + nely*ez).
+ *   Vectors are float64, contiguous, in that DOF order.  Multi-vector blocks
+ *   are column-major (column i starts at i*n).
+ *
+ * Ownership: the caller owns every buffer.  Device memory for the solver
+ * state is one caller-allocated workspace whose size to_workspace_bytes()
+ * reports; the library never allocates device memory.  Pointer arguments
+ * marked (dev) are device pointers borrowed for the duration of the call;
+ * (host) are host pointers.  Every call is enqueued on the CUDA stream given
+ * to to_mesh_init and returns without synchronising unless stated.
+ *
+ * Errors: every call returns a to_status.  Invalid sizes, null pointers or
+ * non-finite scalars return TO_E_INVALID before any launch.  A failed CUDA
+ * launch returns TO_E_CUDA.  to_last_error() gives a message.  No call
+ * aborts the process.
+ */
+#ifndef TOPO_H_
+#define TOPO_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t to_status;
+
+enum {
+  TO_OK = 0,
+  TO_E_INVALID = 1,        /* bad argument; nothing launched */
+  TO_E_STATE = 2,          /* call out of order (e.g. CARM before the PARM is full) */
+  TO_E_OOM = 3,            /* workspace smaller than to_workspace_bytes() */
+  TO_E_CUDA = 4,           /* a CUDA runtime call or launch failed */
+  TO_E_NOT_CONVERGED = 5,  /* iteration limit reached; result still written */
+  TO_E_SINGULAR = 6,       /* a factorisation met a non-positive pivot */
+  TO_E_TIMEOUT = 7         /* a bounded device wait expired */
+};
+
+enum { TO_FP64 = 0, TO_MIXED = 1 };
+enum { TO_FILTER_DENSITY = 0, TO_FILTER_SENS = 1 };
+enum { TO_SOLVE_WARM_START = 1, TO_SOLVE_PUSH_PARM = 2 };
+enum { TO_OP_K = 0, TO_OP_KREF = 1, TO_OP_DK = 2 };
+enum { TO_PREC_NATIVE = 0, TO_PREC_FP64 = 1, TO_PREC_FP32 = 2 };
+
+typedef struct to_ctx to_ctx;
+
+/* Problem description.  dim is 2 (Q4, plane stress) or 3 (hex8); nel[2] is
+ * ignored in 2D.  E0, Emin, penal: SIMP law of Eq. 1; nu: Poisson ratio;
+ * rmin: density-filter radius of Eq. 32 in element lengths.  mg_levels
+ * counts all grids including the finest; every nel[i] must be divisible by
+ * 2^(mg_levels-1).  precision: TO_FP64 (all arithmetic in float64) or
+ * TO_MIXED (stiffness apply, V-cycle and smoother in float32; CG vectors,
+ * dot products, reduced solves, Gram-Schmidt, compliance and OC in
+ * float64).  n_parm = N_s columns of the PARM, n_carm = N_m columns of the
+ * CARM (each 1..16). */
+typedef struct to_mesh_desc {
+  int32_t dim;
+  int32_t nel[3];
+  double E0, Emin, nu, penal, rmin;
+  int32_t mg_levels;
+  int32_t precision;
+  int32_t n_parm, n_carm;
+} to_mesh_desc;
+
+/* Bytes of device workspace needed for a problem (host-only query). */
+to_status to_workspace_bytes(const to_mesh_desc* desc, int64_t* bytes);
+
+/* Create a solver context.
+ * fixed_mask (dev, uint8, n): 1 = the DOF is prescribed zero (copied).
+ * f (dev, float64, n): nodal load vector (copied); f must be zero on fixed
+ *   DOFs and not identically zero.
+ * workspace (dev), ws_bytes: caller allocation of to_workspace_bytes() bytes,
+ *   256-byte aligned; owned by the caller and used until to_destroy.
+ * stream: cudaStream_t (as void*) on which every call of this context runs.
+ * Supports must be closed under coarse-grid interpolation (every fixed fine
+ * DOF is interpolated only from fixed coarse DOFs); otherwise TO_E_INVALID.
+ * The Galerkin coarse operators rely on it. */
+to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, const double* f,
+                       void* workspace, int64_t ws_bytes, void* stream, to_ctx** out);
+
+/* Set the physical densities rho~ (dev, float64, nel) of this design
+ * iteration: E_e = Emin + (E0-Emin) rho~_e^penal (Eq. 1).  The previous E
+ * becomes the reference stiffness K_ref of the reanalysis (Eq. 8); the first
+ * call sets both.  Invalidates the multigrid hierarchy (rebuilt lazily). */
+to_status to_set_density(to_ctx* ctx, const double* rho_phys);
+
+/* MGCG (Algorithm 2 as preconditioner of CG) for K(E) u = f.
+ * u (dev, float64, n): in: initial guess if flags has TO_SOLVE_WARM_START
+ *   (else ignored and zero is used); out: the solution.
+ * rtol: stop when ||f - K u|| / ||f|| < rtol (recursive residual);
+ * maxit: CG iteration cap (>= 1).  On the cap the last iterate is returned
+ *   with TO_E_NOT_CONVERGED.
+ * flags & TO_SOLVE_PUSH_PARM: append u/||u|| to the PARM (Eq. 28), dropping
+ *   the oldest column when full (Sec. 3.1).
+ * iters (host, may be NULL): CG iterations taken; relres (host, may be
+ *   NULL): final relative residual.  This call synchronises the stream. */
+to_status to_mgcg_solve(to_ctx* ctx, double rtol, int32_t maxit, int32_t flags, double* u,
+                        int32_t* iters, double* relres);
+
+/* Append u/||u|| (u: dev, float64, n) to the PARM, FIFO (Eq. 27-28). */
+to_status to_parm_push(to_ctx* ctx, const double* u);
+/* Number of PARM columns currently held (host query, no sync). */
+to_status to_parm_count(to_ctx* ctx, int32_t* count);
+/* Remove all PARM columns. */
+to_status to_parm_reset(to_ctx* ctx);
+
+/* Build the CARM basis R~ from u_last (dev, float64, n): K_Phi = Phi^T K_ref
+ * Phi (Eq. 15), r_1 = u_last, r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}
+ * (Eq. 18-20, 26), orthonormalised by modified Gram-Schmidt with
+ * re-orthogonalisation (the basis-orthogonalisation step of Eq. 21); a
+ * column whose norm after two passes is <= 1e-10 of its norm before is
+ * dropped.  Needs a full PARM (else TO_E_STATE). */
+to_status to_carm_build(to_ctx* ctx, const double* u_last);
+
+/* Reduced solve on the last CARM basis: K_R = R~^T K R~, f_R = R~^T f,
+ * y = K_R^{-1} f_R (Eq. 23-24), u = R~ y (Eq. 25, dev float64 n, out) and
+ * eps = ||K R~ y - f|| / ||f|| (Eq. 29) written to eps (host, may be NULL;
+ * synchronises when given) and to eps_dev (dev, may be NULL). */
+to_status to_carm_solve(to_ctx* ctx, double* u, double* eps, double* eps_dev);
+
+/* Compliance and its sensitivity for displacement u (dev, n):
+ * C = sum_e E_e u_e^T KE u_e (Eq. 3) -> compliance_dev (dev, 1 double) and
+ * dc_e = -penal (E0-Emin) rho~_e^(penal-1) u_e^T KE u_e (Eq. 6 / 34) -> dc
+ * (dev, nel). */
+to_status to_sensitivity(to_ctx* ctx, const double* u, double* compliance_dev, double* dc);
+
+/* Density filter (Eq. 31-32), mode TO_FILTER_DENSITY: out = (H in) / Hs;
+ * or its transpose for sensitivities (Eq. 33), mode TO_FILTER_SENS:
+ * out = H^T (in / Hs).  in, out: dev float64 nel, must not alias. */
+to_status to_filter(to_ctx* ctx, int32_t mode, const double* in, double* out);
+
+/* Optimality-criteria update of the design rho (dev, float64, nel, in/out):
+ * rho_new = clamp(rho sqrt(max(0, -dc_f/(lam dv_f))), max(0, rho-move),
+ * min(1, rho+move)) with lam chosen by bisection on [0, 1e9] to a relative
+ * bracket of 1e-13 so that sum_e dv_f,e rho_new,e = volfrac*nel (the
+ * filtered volume when dv_f = H^T(1/Hs), Eq. 3).  dc_f, dv_f: dev nel.
+ * change_dev (dev, 1 double, may be NULL): max |rho_new - rho|. */
+to_status to_oc_update(to_ctx* ctx, double volfrac, double move, const double* dc_f,
+                       const double* dv_f, double* rho, double* change_dev);
+
+/* y = op(x) for x, y dev float64 n (no aliasing).  op: TO_OP_K (current
+ * stiffness with BCs, Eq. 7), TO_OP_KREF (reference stiffness, Eq. 8) or
+ * TO_OP_DK (dK = K - K_ref, zero on fixed DOFs).  prec: TO_PREC_NATIVE
+ * (the context's apply precision), TO_PREC_FP64 or TO_PREC_FP32. */
+to_status to_apply(to_ctx* ctx, int32_t op, int32_t prec, const double* x, double* y);
+
+/* One V-cycle of the current hierarchy (Algorithm 2): z ~= K^{-1} r, with
+ * r, z dev float64 n (builds the hierarchy if stale). */
+to_status to_vcycle(to_ctx* ctx, const double* r, double* z);
+
+/* Galerkin operator of level l >= 1 (coarse grid l of the hierarchy):
+ * y = A_l x with x, y dev float64 of that level's DOF count (see
+ * to_level_info).  For tests of the coarse operators. */
+to_status to_level_apply(to_ctx* ctx, int32_t level, const double* x, double* y);
+/* Element counts per axis and DOF count of level l. */
+to_status to_level_info(to_ctx* ctx, int32_t level, int32_t nel_out[3], int64_t* ndof);
+
+/* Profiling: when enabled, every launch of the stiffness operator is
+ * bracketed by CUDA events on the context stream.  kind 0 = finest-grid
+ * operator (all variants: K x, residual, smoother, K_ref, dK), 1 = coarse-
+ * grid Galerkin operator, 2 = whole V-cycle.  to_profile_read synchronises,
+ * returns the number of timed launches, their summed milliseconds and
+ * (bytes, may be NULL) their summed algorithmic DRAM bytes (each input and
+ * output array counted once), and forgets them.  to_launch_count returns
+ * the number of kernels launched by this context since the last reset. */
+to_status to_profile_enable(to_ctx* ctx, int32_t on);
+to_status to_profile_read(to_ctx* ctx, int32_t kind, int64_t* count, double* ms, double* bytes);
+to_status to_launch_count(to_ctx* ctx, int64_t* count, int32_t reset);
+
+/* Message of the last error of ctx (or of the last context-less call when
+ * ctx is NULL).  The string is owned by the library. */
+const char* to_last_error(const to_ctx* ctx);
+
+/* Release host-side state (the workspace stays the caller's). */
+void to_destroy(to_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOPO_H_ */

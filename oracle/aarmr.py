@@ -105,6 +105,7 @@ def run(prob, n_iter: Optional[int] = None, mode: str = "aarmr", snapshot_at=(),
     parm = reanalysis.Parm(p.n_parm)
     u_last = np.zeros(m.grid.ndof)
     E_prev = None
+    rho_phys_prev = None
     traj = Trajectory(rho)
     for k in range(1, n_iter + 1):
         rho_phys = filters.density_filter(m.H, m.Hs, rho)
@@ -113,6 +114,8 @@ def run(prob, n_iter: Optional[int] = None, mode: str = "aarmr", snapshot_at=(),
         if k in snapshot_at:
             traj.snapshots[k] = dict(rho=rho.copy(), rho_phys=rho_phys.copy(), E=E.copy(),
                                      E_prev=None if E_prev is None else E_prev.copy(),
+                                     rho_phys_prev=None if rho_phys_prev is None
+                                     else rho_phys_prev.copy(),
                                      u_last=u_last.copy(),
                                      Phi=parm.matrix() if parm.cols else None)
         eps, iters = None, 0
@@ -143,5 +146,6 @@ def run(prob, n_iter: Optional[int] = None, mode: str = "aarmr", snapshot_at=(),
         rho = rho_new
         u_last = u
         E_prev = E
+        rho_phys_prev = rho_phys
     traj.rho = rho
     return traj

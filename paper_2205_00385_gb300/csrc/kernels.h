@@ -1,0 +1,124 @@
+// Host launchers of the library's kernels (runtime-dispatched templates).
+#pragma once
+
+#include "topo_internal.cuh"
+
+namespace topo {
+
+enum { T_F64 = 0, T_F32 = 1 };
+enum { EPI_APPLY = 0, EPI_RESID = 1, EPI_SMOOTH = 2 };
+
+// Stiffness operator of one grid level,
+//   y = M (sum_e A_e^T Ke_e A_e) M x + dfix (I - M) x      (EPI_APPLY)
+//   y = b - (that)                                         (EPI_RESID)
+//   y = x + omega * dinv * (b - that)                      (EPI_SMOOTH)
+// with Ke_e = coef_e * KE on the finest level (explicit = false) or the
+// stored Galerkin element matrix Kc_e on coarse levels (explicit = true).
+struct ApplyArgs {
+  int dim;
+  GridP g;
+  const uint8_t* mask;
+  int tc;              // arithmetic type (T_F64 / T_F32)
+  int tx, ty;          // storage types of x (and b) and of y
+  bool expl;
+  const void* coef;    // [nel] of type tc (fine level)
+  const void* Kc;      // [ND*ND*nel] of type tc (coarse levels)
+  const void* ke;      // host pointer to the ND*ND element matrix of type tc
+  const void* x;
+  void* y;
+  const void* b;
+  const void* dinv;    // [n] of type tc
+  double omega, dfix;
+  int epi;
+};
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+
+// dinv = 1 / diag(A) (1 on fixed DOFs)
+cudaError_t launch_diag(int dim, const GridP& g, const uint8_t* mask, int tc, bool expl,
+                        const void* coef, const void* Kc, const void* ke, void* dinv,
+                        cudaStream_t s);
+
+// ---- multigrid transfer and Galerkin operators (kernels_mg.cu) ----
+cudaError_t launch_restrict(int dim, int t, const GridP& gf, const uint8_t* maskf,
+                            const GridP& gc, const uint8_t* maskc, const void* rf, void* bc,
+                            cudaStream_t s);
+cudaError_t launch_prolong_add(int dim, int t, const GridP& gf, const uint8_t* maskf,
+                               const GridP& gc, const void* zc, void* zf, cudaStream_t s);
+// z = omega * dinv * b (smoothing from a zero initial guess); if bout != 0 the
+// input (of type tin) is also converted into bout (type t).
+cudaError_t launch_presmooth(int t, int tin, long long n, const void* bin, void* bout,
+                             const void* dinv, double omega, void* z, cudaStream_t s);
+cudaError_t launch_galerkin_fine(int dim, int t, const GridP& gc, const GridP& gf,
+                                 const void* coef, const void* Qc, void* Kc, cudaStream_t s);
+cudaError_t launch_galerkin_coarse(int dim, int t, const GridP& gc, const GridP& gf,
+                                   const void* Kf, void* Kc, cudaStream_t s);
+cudaError_t launch_dense_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
+                                  const void* Kc, void* A, cudaStream_t s);
+cudaError_t launch_cholesky_inverse(int t, int n, void* A, void* Ainv, int* status,
+                                    cudaStream_t s);
+cudaError_t launch_dense_gemv(int t, int n, const void* A, const void* x, void* y,
+                              cudaStream_t s);
+cudaError_t launch_convert(int tin, int tout, long long n, const void* in, void* out,
+                           cudaStream_t s);
+
+// ---- vector kernels (kernels_blas.cu) ----
+cudaError_t launch_dot(long long n, const double* a, const double* b, double* partials,
+                       unsigned* counter, double* out, cudaStream_t s);
+// alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q; scal[rr] = r.r
+cudaError_t launch_cg_xr(long long n, double* x, double* r, const double* p, const double* q,
+                         double* scal, int num, int den, int rr, double* partials,
+                         unsigned* counter, cudaStream_t s);
+// beta = scal[num] / scal[den]; p = z + beta p
+cudaError_t launch_cg_p(long long n, double* p, const double* z, const double* scal, int num,
+                        int den, cudaStream_t s);
+cudaError_t launch_copy(long long n, const double* a, double* b, cudaStream_t s);
+cudaError_t launch_scale_by_inv_sqrt(long long n, double* a, const double* s2, cudaStream_t s);
+// G[i + ldg*j] = sum_k A[k + i*n] B[k + j*n], i < na (na_dev overrides when
+// non-null), j < nb (likewise)
+cudaError_t launch_multidot(long long n, const double* A, int na, const int* na_dev,
+                            const double* B, int nb, const int* nb_dev, double* G, int ldg,
+                            double* partials, unsigned* counters, cudaStream_t s);
+// y = beta*y + sign * sum_i c[i] A[:, i] (i < m, or *m_dev); if rr != 0 also
+// writes |y - w|^2 (w may be null) to *rr
+cudaError_t launch_combine(long long n, const double* A, int m, const int* m_dev,
+                           const double* c, double sign, double beta, double* y,
+                           const double* w, double* rr, double* partials, unsigned* counter,
+                           cudaStream_t s);
+// small dense kernels on one thread block
+cudaError_t launch_small_spd_inverse(int m, const int* m_dev, const double* A, double* Ainv,
+                                     int* status, cudaStream_t s);
+cudaError_t launch_small_matvec(int m, const int* m_dev, const double* A, const double* x,
+                                double* y, double sign, cudaStream_t s);
+cudaError_t launch_small_chol_solve(int m, const int* m_dev, const double* A, const double* b,
+                                    double* x, int* status, cudaStream_t s);
+// Gram-Schmidt step: column src of R (norm^2 before in scal[n0], after in
+// scal[n1]) is appended to the basis at position ints[I_KCOUNT] if it kept
+// more than tol of its length, normalised.
+cudaError_t launch_gs_accept(long long n, double* R, int src, const double* scal, int n0,
+                             int n1, double tol, int* ints, cudaStream_t s);
+cudaError_t launch_eps(const double* scal, int rr, int f2, double* eps_dev, cudaStream_t s);
+
+// ---- design-optimisation kernels (kernels_opt.cu) ----
+cudaError_t launch_simp(long long nel, const double* rho, double E0, double Emin, double penal,
+                        double* E64, float* E32, cudaStream_t s);
+cudaError_t launch_delta(long long nel, const double* E, const double* Eprev, double* dE64,
+                         float* dE32, float* Eprev32, cudaStream_t s);
+cudaError_t launch_filter(int dim, const GridP& g, const StencilP& st, int mode,
+                          const double* Hs, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_filter_norm(int dim, const GridP& g, const StencilP& st, double* Hs,
+                               cudaStream_t s);
+cudaError_t launch_sensitivity(int dim, const GridP& g, const uint8_t* mask, const double* ke,
+                               const double* u, const double* E, const double* rho,
+                               double penal, double E0, double Emin, double* dc,
+                               double* compliance, double* partials, unsigned* counter,
+                               cudaStream_t s);
+cudaError_t launch_oc_prep(long long nel, const double* rho, const double* dc,
+                           const double* dv, double* a, double* scal, cudaStream_t s);
+cudaError_t launch_oc_step(long long nel, const double* rho, const double* a,
+                           const double* dv, double move, double target, double* scal,
+                           double* partials, unsigned* counter, cudaStream_t s);
+cudaError_t launch_oc_final(long long nel, double* rho, const double* a, double move,
+                            double* scal, double* change_dev, double* partials,
+                            unsigned* counter, cudaStream_t s);
+
+}  // namespace topo

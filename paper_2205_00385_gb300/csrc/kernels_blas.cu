@@ -1,0 +1,404 @@
+// Float64 vector kernels of the CG recursion, the CARM/PARM multi-vector
+// products and Gram-Schmidt, and small dense solves run on one block.
+// All reductions use a fixed grid of RED_BLOCKS blocks and a fixed summation
+// tree, so results do not depend on timing or on other work on the GPU.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace topo {
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_dot(long long n, const double* __restrict__ a, const double* __restrict__ b,
+          double* partials, unsigned* counter, double* out) {
+  __shared__ double sh[32];
+  double v[1] = {0.0};
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    v[0] = fma(a[q], b[q], v[0]);
+  block_sum<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) *out = o[0];
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_cg_xr(long long n, double* __restrict__ x, double* __restrict__ r,
+            const double* __restrict__ p, const double* __restrict__ q, double* scal, int num,
+            int den, int rr, double* partials, unsigned* counter) {
+  __shared__ double sh[32];
+  const double alpha = scal[num] / scal[den];
+  double v[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    v[0] = fma(ri, ri, v[0]);
+  }
+  block_sum<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) scal[rr] = o[0];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_cg_p(long long n, double* __restrict__ p, const double* __restrict__ z,
+           const double* __restrict__ scal, int num, int den) {
+  const double beta = scal[num] / scal[den];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void __launch_bounds__(256) k_copy(long long n, const double* __restrict__ a,
+                                              double* __restrict__ b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+__global__ void __launch_bounds__(256) k_scale_inv_sqrt(long long n, double* __restrict__ a,
+                                                        const double* __restrict__ s2) {
+  const double s = (*s2 > 0.0) ? 1.0 / sqrt(*s2) : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    a[i] *= s;
+}
+
+// G[i + ldg*j] = sum_k A[k + i*n] B[k + j*n] for i < na, with j = blockIdx.y.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_multidot(long long n, const double* __restrict__ A, int na, const int* na_dev,
+               const double* __restrict__ B, int nb, const int* nb_dev, double* G, int ldg,
+               double* partials, unsigned* counters) {
+  __shared__ double sh[MAXB * 32];
+  const int j = blockIdx.y;
+  const int ma = na_dev ? min(*na_dev, na) : na;
+  const int mb = nb_dev ? min(*nb_dev, nb) : nb;
+  if (j >= mb) return;   // whole grid-row exits together: no partial published
+  double v[MAXB];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) v[i] = 0.0;
+  const double* bj = B + (size_t)j * n;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double bk = bj[k];
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i)
+      if (i < ma) v[i] = fma(A[k + (size_t)i * n], bk, v[i]);
+  }
+  block_sum<MAXB>(v, sh);
+  double* part = partials + (size_t)j * gridDim.x * MAXB;
+  if (publish_partials<MAXB>(v, part, counters + j)) {
+    double o[MAXB];
+    finish_sum<MAXB>(part, counters + j, o, sh);
+    if (threadIdx.x == 0)
+      for (int i = 0; i < ma; ++i) G[i + (size_t)ldg * j] = o[i];
+  }
+}
+
+// y = beta*y + sign*sum_i c[i] A[:, i]; optional |y - w|^2 -> *rr
+__global__ void __launch_bounds__(RED_THREADS)
+    k_combine(long long n, const double* __restrict__ A, int m, const int* m_dev,
+              const double* __restrict__ c, double sign, double beta, double* __restrict__ y,
+              const double* __restrict__ w, double* rr, double* partials, unsigned* counter) {
+  __shared__ double sh[32];
+  const int mm = m_dev ? min(*m_dev, m) : m;
+  double cc[MAXB];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) cc[i] = (i < mm) ? sign * c[i] : 0.0;
+  double v[1] = {0.0};
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double s = (beta != 0.0) ? beta * y[k] : 0.0;
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i)
+      if (i < mm) s = fma(cc[i], A[k + (size_t)i * n], s);
+    y[k] = s;
+    if (rr) {
+      const double d = w ? s - w[k] : s;
+      v[0] = fma(d, d, v[0]);
+    }
+  }
+  if (!rr) return;
+  block_sum<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) *rr = o[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small dense float64 kernels (m <= 16), one thread does the work.
+// ---------------------------------------------------------------------------
+__device__ bool chol_small(int m, const double* A, double* L) {
+  for (int i = 0; i < m * m; ++i) L[i] = 0.0;
+  for (int j = 0; j < m; ++j) {
+    double d = 0.5 * (A[j + m * j] + A[j + m * j]);
+    for (int k = 0; k < j; ++k) d -= L[j + m * k] * L[j + m * k];
+    if (!(d > 0.0)) return false;
+    const double ljj = sqrt(d);
+    L[j + m * j] = ljj;
+    for (int i = j + 1; i < m; ++i) {
+      double s = 0.5 * (A[i + m * j] + A[j + m * i]);
+      for (int k = 0; k < j; ++k) s -= L[i + m * k] * L[j + m * k];
+      L[i + m * j] = s / ljj;
+    }
+  }
+  return true;
+}
+
+__device__ void chol_solve_small(int m, const double* L, const double* b, double* x) {
+  double y[MAXB];
+  for (int i = 0; i < m; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i + m * k] * y[k];
+    y[i] = s / L[i + m * i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < m; ++k) s -= L[k + m * i] * x[k];
+    x[i] = s / L[i + m * i];
+  }
+}
+
+// Symmetric Jacobi eigen-decomposition (cyclic sweeps) of the m x m matrix
+// A (column-major); eigenvalues in w, eigenvectors in the columns of V.
+__device__ void jacobi_eigen(int m, double* A, double* w, double* V) {
+  for (int i = 0; i < m * m; ++i) V[i] = 0.0;
+  for (int i = 0; i < m; ++i) V[i + m * i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; q < m; ++q) {
+        const double a = A[p + m * q] * A[p + m * q];
+        tot += a;
+        if (p != q) off += a;
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[p + m * q];
+        if (apq == 0.0) continue;
+        const double theta = (A[q + m * q] - A[p + m * p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = A[k + m * p], akq = A[k + m * q];
+          A[k + m * p] = c * akp - s * akq;
+          A[k + m * q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[p + m * k], aqk = A[q + m * k];
+          A[p + m * k] = c * apk - s * aqk;
+          A[q + m * k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[k + m * p], vkq = V[k + m * q];
+          V[k + m * p] = c * vkp - s * vkq;
+          V[k + m * q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < m; ++i) w[i] = A[i + m * i];
+}
+
+// Ainv = A^{-1} for the small SPD K_Phi: Cholesky, else symmetric
+// eigen-pseudo-inverse with relative cutoff 1e-14.
+__global__ void k_small_spd_inverse(int mmax, const int* m_dev, const double* A, double* Ainv,
+                                    int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = m_dev ? min(*m_dev, mmax) : mmax;
+  double L[MAXB * MAXB];
+  if (chol_small(m, A, L)) {
+    double e[MAXB], col[MAXB];
+    for (int j = 0; j < m; ++j) {
+      for (int i = 0; i < m; ++i) e[i] = (i == j) ? 1.0 : 0.0;
+      chol_solve_small(m, L, e, col);
+      for (int i = 0; i < m; ++i) Ainv[i + m * j] = col[i];
+    }
+    return;
+  }
+  double S[MAXB * MAXB], V[MAXB * MAXB], w[MAXB];
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < m; ++i) S[i + m * j] = 0.5 * (A[i + m * j] + A[j + m * i]);
+  jacobi_eigen(m, S, w, V);
+  double wmax = 0.0;
+  for (int i = 0; i < m; ++i) wmax = fmax(wmax, fabs(w[i]));
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k)
+        if (w[k] > 1e-14 * wmax) s += V[i + m * k] * V[j + m * k] / w[k];
+      Ainv[i + m * j] = s;
+    }
+  (void)status;
+}
+
+// y = sign * A x (A column-major m x m)
+__global__ void k_small_matvec(int mmax, const int* m_dev, const double* A, const double* x,
+                               double* y, double sign) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = m_dev ? min(*m_dev, mmax) : mmax;
+  for (int i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += A[i + m * k] * x[k];
+    y[i] = sign * s;
+  }
+}
+
+__global__ void k_small_chol_solve(int mmax, const int* m_dev, const double* A, const double* b,
+                                   double* x, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = m_dev ? min(*m_dev, mmax) : mmax;
+  double L[MAXB * MAXB];
+  if (!chol_small(m, A, L)) {
+    // fall back to the pseudo-inverse so that a result is still produced
+    double S[MAXB * MAXB], V[MAXB * MAXB], w[MAXB];
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < m; ++i) S[i + m * j] = 0.5 * (A[i + m * j] + A[j + m * i]);
+    jacobi_eigen(m, S, w, V);
+    double wmax = 0.0;
+    for (int i = 0; i < m; ++i) wmax = fmax(wmax, fabs(w[i]));
+    for (int i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) {
+        if (!(w[k] > 1e-14 * wmax)) continue;
+        double vb = 0.0;
+        for (int q = 0; q < m; ++q) vb += V[q + m * k] * b[q];
+        s += V[i + m * k] * vb / w[k];
+      }
+      x[i] = s;
+    }
+    if (status) *status = TO_E_SINGULAR;
+    return;
+  }
+  chol_solve_small(m, L, b, x);
+}
+
+// Gram-Schmidt acceptance: column src (already orthogonalised twice) is
+// kept if |r|^2 after > tol^2 |r|^2 before; it is then normalised into
+// column k = ints[I_KCOUNT] and k is incremented.  Runs as a grid.
+__global__ void __launch_bounds__(256)
+    k_gs_accept(long long n, double* R, int src, const double* scal, int n0, int n1,
+                double tol, int* ints) {
+  const double before = scal[n0], after = scal[n1];
+  const bool keep = after > tol * tol * before && after > 0.0;
+  const int k = ints[I_KCOUNT];
+  if (keep) {
+    const double s = 1.0 / sqrt(after);
+    const double* a = R + (size_t)src * n;
+    double* b = R + (size_t)k * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      b[i] = a[i] * s;
+  }
+}
+
+__global__ void k_gs_count(const double* scal, int n0, int n1, double tol, int* ints) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double before = scal[n0], after = scal[n1];
+  if (after > tol * tol * before && after > 0.0) ints[I_KCOUNT] += 1;
+}
+
+__global__ void k_eps(const double* scal, int rr, int f2, double* eps_dev) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *eps_dev = sqrt(scal[rr] / scal[f2]);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static inline int vgrid(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > RED_BLOCKS) b = RED_BLOCKS;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_dot(long long n, const double* a, const double* b, double* partials,
+                       unsigned* counter, double* out, cudaStream_t s) {
+  k_dot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, b, partials, counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_xr(long long n, double* x, double* r, const double* p, const double* q,
+                         double* scal, int num, int den, int rr, double* partials,
+                         unsigned* counter, cudaStream_t s) {
+  k_cg_xr<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, scal, num, den, rr, partials,
+                                             counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p(long long n, double* p, const double* z, const double* scal, int num,
+                        int den, cudaStream_t s) {
+  k_cg_p<<<vgrid(n), 256, 0, s>>>(n, p, z, scal, num, den);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(long long n, const double* a, double* b, cudaStream_t s) {
+  k_copy<<<vgrid(n), 256, 0, s>>>(n, a, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_inv_sqrt(long long n, double* a, const double* s2, cudaStream_t s) {
+  k_scale_inv_sqrt<<<vgrid(n), 256, 0, s>>>(n, a, s2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multidot(long long n, const double* A, int na, const int* na_dev,
+                            const double* B, int nb, const int* nb_dev, double* G, int ldg,
+                            double* partials, unsigned* counters, cudaStream_t s) {
+  if (na > MAXB || nb > MAXB || na < 1 || nb < 1) return cudaErrorInvalidValue;
+  dim3 grid(RED_BLOCKS, nb);
+  k_multidot<<<grid, RED_THREADS, 0, s>>>(n, A, na, na_dev, B, nb, nb_dev, G, ldg, partials,
+                                          counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(long long n, const double* A, int m, const int* m_dev,
+                           const double* c, double sign, double beta, double* y,
+                           const double* w, double* rr, double* partials, unsigned* counter,
+                           cudaStream_t s) {
+  if (m > MAXB) return cudaErrorInvalidValue;
+  k_combine<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, A, m, m_dev, c, sign, beta, y, w, rr,
+                                               partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_spd_inverse(int m, const int* m_dev, const double* A, double* Ainv,
+                                     int* status, cudaStream_t s) {
+  k_small_spd_inverse<<<1, 32, 0, s>>>(m, m_dev, A, Ainv, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_matvec(int m, const int* m_dev, const double* A, const double* x,
+                                double* y, double sign, cudaStream_t s) {
+  k_small_matvec<<<1, 32, 0, s>>>(m, m_dev, A, x, y, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_chol_solve(int m, const int* m_dev, const double* A, const double* b,
+                                    double* x, int* status, cudaStream_t s) {
+  k_small_chol_solve<<<1, 32, 0, s>>>(m, m_dev, A, b, x, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_accept(long long n, double* R, int src, const double* scal, int n0,
+                             int n1, double tol, int* ints, cudaStream_t s) {
+  k_gs_accept<<<vgrid(n), 256, 0, s>>>(n, R, src, scal, n0, n1, tol, ints);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gs_count<<<1, 32, 0, s>>>(scal, n0, n1, tol, ints);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eps(const double* scal, int rr, int f2, double* eps_dev, cudaStream_t s) {
+  k_eps<<<1, 32, 0, s>>>(scal, rr, f2, eps_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

@@ -1,0 +1,228 @@
+// Element-by-element stiffness operator K(E) x of Eq. 7 on a regular grid of
+// unit Q4 / hex8 elements (matrix-free), and its diagonal.
+//
+// Design: owner-computes gather.  One thread owns one node; it loads the
+// 3^DIM neighbourhood of nodal values once into registers and sums, over the
+// 2^DIM elements around the node, the rows of (coef_e KE) or of the stored
+// Galerkin matrix that belong to it.  No atomics, deterministic, and every
+// nodal value / element coefficient is read from DRAM once per launch (the
+// 27-fold reuse is served by L1/L2).  Boundary conditions are applied as
+// M K M + dfix (I - M) with M the mask of free DOFs.
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace topo {
+
+template <int DIM, typename TC, typename TX, typename TY, int EPI, bool EXPL>
+__global__ void __launch_bounds__(128)
+    k_apply(GridP g, const uint8_t* __restrict__ mask, KEP<TC, Geo<DIM>::ND> ke,
+            const TC* __restrict__ coef, const TC* __restrict__ Kc,
+            const TX* __restrict__ x, TY* __restrict__ y, const TX* __restrict__ b,
+            const TC* __restrict__ dinv, TC omega, TC dfix) {
+  constexpr int ND = Geo<DIM>::ND;
+  constexpr int NPE = Geo<DIM>::NPE;
+  constexpr int NB = Geo<DIM>::NB;
+  constexpr int NZ = DIM == 3 ? 2 : 1;
+  using TE = typename std::conditional<(sizeof(TY) > sizeof(TC)), double, TC>::type;
+
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nn) return;
+  const int i = (int)(node % g.nnx);
+  const long long rest = node / g.nnx;
+  const int j = (int)(rest % g.nny);
+  const int k = DIM == 3 ? (int)(rest / g.nny) : 0;
+
+  TC xn[NB][DIM];
+#pragma unroll
+  for (int dz = 0; dz < (DIM == 3 ? 3 : 1); ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int s = dx + 3 * dy + 9 * dz;
+        const int ii = i + dx - 1, jj = j + dy - 1, kk = k + dz - 1;
+        bool in = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
+        if (DIM == 3) in = in && kk >= 0 && kk < g.nnz;
+        if (in) {
+          const long long nb = ii + (long long)g.nnx * (jj + (long long)g.nny * (DIM == 3 ? kk : 0));
+          const unsigned m = mask[nb];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) xn[s][c] = ((m >> c) & 1u) ? TC(0) : TC(x[DIM * nb + c]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) xn[s][c] = TC(0);
+        }
+      }
+
+  TC acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = TC(0);
+
+#pragma unroll
+  for (int ez = 0; ez < NZ; ++ez)
+#pragma unroll
+    for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+      for (int ex = 0; ex < 2; ++ex) {
+        const int ei = i - 1 + ex, ej = j - 1 + ey, ek = k - 1 + ez;
+        bool in = ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
+        if (DIM == 3) in = in && ek >= 0 && ek < g.nz;
+        if (!in) continue;
+        const long long e = ei + (long long)g.nx * (ej + (long long)g.ny * (DIM == 3 ? ek : 0));
+        const int a = (1 - ex) + 2 * (1 - ey) + (DIM == 3 ? 4 * (1 - ez) : 0);
+        const TC ce = EXPL ? TC(1) : coef[e];
+#pragma unroll
+        for (int ci = 0; ci < DIM; ++ci) {
+          const int row = DIM * a + ci;
+          TC s = TC(0);
+#pragma unroll
+          for (int bc = 0; bc < NPE; ++bc) {
+            const int bx = bc & 1, by = (bc >> 1) & 1, bz = (bc >> 2) & 1;
+            const int sidx = (ex + bx) + 3 * (ey + by) + (DIM == 3 ? 9 * (ez + bz) : 0);
+#pragma unroll
+            for (int cj = 0; cj < DIM; ++cj) {
+              const int col = DIM * bc + cj;
+              const TC kv = EXPL ? Kc[(size_t)(row * ND + col) * g.nel + e] : ke.v[row * ND + col];
+              s = fma(kv, xn[sidx][cj], s);
+            }
+          }
+          acc[ci] = fma(ce, s, acc[ci]);
+        }
+      }
+
+  const unsigned mself = mask[node];
+#pragma unroll
+  for (int ci = 0; ci < DIM; ++ci) {
+    const long long d = DIM * node + ci;
+    TE Ax = ((mself >> ci) & 1u) ? TE(dfix) * TE(x[d]) : TE(acc[ci]);
+    if (EPI == EPI_APPLY) {
+      y[d] = TY(Ax);
+    } else if (EPI == EPI_RESID) {
+      y[d] = TY(TE(b[d]) - Ax);
+    } else {
+      y[d] = TY(TE(x[d]) + TE(omega) * TE(dinv[d]) * (TE(b[d]) - Ax));
+    }
+  }
+}
+
+template <int DIM, typename TC, bool EXPL>
+__global__ void __launch_bounds__(256)
+    k_diag(GridP g, const uint8_t* __restrict__ mask, KEP<TC, Geo<DIM>::ND> ke,
+           const TC* __restrict__ coef, const TC* __restrict__ Kc, TC* __restrict__ dinv) {
+  constexpr int ND = Geo<DIM>::ND;
+  constexpr int NZ = DIM == 3 ? 2 : 1;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nn) return;
+  const int i = (int)(node % g.nnx);
+  const long long rest = node / g.nnx;
+  const int j = (int)(rest % g.nny);
+  const int k = DIM == 3 ? (int)(rest / g.nny) : 0;
+  TC d[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) d[c] = TC(0);
+#pragma unroll
+  for (int ez = 0; ez < NZ; ++ez)
+#pragma unroll
+    for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+      for (int ex = 0; ex < 2; ++ex) {
+        const int ei = i - 1 + ex, ej = j - 1 + ey, ek = k - 1 + ez;
+        bool in = ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
+        if (DIM == 3) in = in && ek >= 0 && ek < g.nz;
+        if (!in) continue;
+        const long long e = ei + (long long)g.nx * (ej + (long long)g.ny * (DIM == 3 ? ek : 0));
+        const int a = (1 - ex) + 2 * (1 - ey) + (DIM == 3 ? 4 * (1 - ez) : 0);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          const int row = DIM * a + c;
+          d[c] += EXPL ? Kc[(size_t)(row * ND + row) * g.nel + e] : coef[e] * ke.v[row * ND + row];
+        }
+      }
+  const unsigned m = mask[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+    dinv[DIM * node + c] = ((m >> c) & 1u) ? TC(1) : TC(1) / d[c];
+}
+
+// ---------------------------------------------------------------------------
+// Host dispatch
+// ---------------------------------------------------------------------------
+template <int DIM, typename TC, typename TX, typename TY, int EPI, bool EXPL>
+static cudaError_t run_apply(const ApplyArgs& a, cudaStream_t s) {
+  constexpr int ND = Geo<DIM>::ND;
+  KEP<TC, ND> ke;
+  if (!EXPL) {
+    const TC* src = static_cast<const TC*>(a.ke);
+    for (int q = 0; q < ND * ND; ++q) ke.v[q] = src[q];
+  } else {
+    for (int q = 0; q < ND * ND; ++q) ke.v[q] = TC(0);
+  }
+  const int th = 128;
+  k_apply<DIM, TC, TX, TY, EPI, EXPL><<<nblocks(a.g.nn, th), th, 0, s>>>(
+      a.g, a.mask, ke, static_cast<const TC*>(a.coef), static_cast<const TC*>(a.Kc),
+      static_cast<const TX*>(a.x), static_cast<TY*>(a.y), static_cast<const TX*>(a.b),
+      static_cast<const TC*>(a.dinv), TC(a.omega), TC(a.dfix));
+  return cudaGetLastError();
+}
+
+template <int DIM, typename TC, typename TX, typename TY, bool EXPL>
+static cudaError_t run_apply_epi(const ApplyArgs& a, cudaStream_t s) {
+  switch (a.epi) {
+    case EPI_APPLY: return run_apply<DIM, TC, TX, TY, EPI_APPLY, EXPL>(a, s);
+    case EPI_RESID: return run_apply<DIM, TC, TX, TY, EPI_RESID, EXPL>(a, s);
+    default: return run_apply<DIM, TC, TX, TY, EPI_SMOOTH, EXPL>(a, s);
+  }
+}
+
+template <int DIM>
+static cudaError_t run_apply_dim(const ApplyArgs& a, cudaStream_t s) {
+  if (a.tc == T_F64) {
+    if (a.tx != T_F64 || a.ty != T_F64) return cudaErrorInvalidValue;
+    return a.expl ? run_apply_epi<DIM, double, double, double, true>(a, s)
+                  : run_apply_epi<DIM, double, double, double, false>(a, s);
+  }
+  if (a.expl) {
+    if (a.tx != T_F32 || a.ty != T_F32) return cudaErrorInvalidValue;
+    return run_apply_epi<DIM, float, float, float, true>(a, s);
+  }
+  if (a.tx == T_F64 && a.ty == T_F64) return run_apply_epi<DIM, float, double, double, false>(a, s);
+  if (a.tx == T_F32 && a.ty == T_F32) return run_apply_epi<DIM, float, float, float, false>(a, s);
+  if (a.tx == T_F32 && a.ty == T_F64) return run_apply_epi<DIM, float, float, double, false>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
+  if (a.g.nn <= 0) return cudaSuccess;
+  return a.dim == 2 ? run_apply_dim<2>(a, s) : run_apply_dim<3>(a, s);
+}
+
+template <int DIM, typename TC, bool EXPL>
+static cudaError_t run_diag(const GridP& g, const uint8_t* mask, const void* coef,
+                            const void* Kc, const void* kev, void* dinv, cudaStream_t s) {
+  constexpr int ND = Geo<DIM>::ND;
+  KEP<TC, ND> ke;
+  for (int q = 0; q < ND * ND; ++q) ke.v[q] = EXPL ? TC(0) : static_cast<const TC*>(kev)[q];
+  k_diag<DIM, TC, EXPL><<<nblocks(g.nn, 256), 256, 0, s>>>(
+      g, mask, ke, static_cast<const TC*>(coef), static_cast<const TC*>(Kc),
+      static_cast<TC*>(dinv));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(int dim, const GridP& g, const uint8_t* mask, int tc, bool expl,
+                        const void* coef, const void* Kc, const void* ke, void* dinv,
+                        cudaStream_t s) {
+  if (g.nn <= 0) return cudaSuccess;
+  if (dim == 2) {
+    if (tc == T_F64) return expl ? run_diag<2, double, true>(g, mask, coef, Kc, ke, dinv, s)
+                                 : run_diag<2, double, false>(g, mask, coef, Kc, ke, dinv, s);
+    return expl ? run_diag<2, float, true>(g, mask, coef, Kc, ke, dinv, s)
+                : run_diag<2, float, false>(g, mask, coef, Kc, ke, dinv, s);
+  }
+  if (tc == T_F64) return expl ? run_diag<3, double, true>(g, mask, coef, Kc, ke, dinv, s)
+                               : run_diag<3, double, false>(g, mask, coef, Kc, ke, dinv, s);
+  return expl ? run_diag<3, float, true>(g, mask, coef, Kc, ke, dinv, s)
+              : run_diag<3, float, false>(g, mask, coef, Kc, ke, dinv, s);
+}
+
+}  // namespace topo

@@ -1,0 +1,449 @@
+// Multigrid pieces of Algorithm 2: restriction P^T, interpolation P, Jacobi
+// smoothing from a zero guess, the Galerkin coarse operators P^T K P as
+// per-coarse-element matrices, and the exact coarsest-grid solve.
+//
+// With 2x coarsening and multilinear P, the fine elements inside one coarse
+// element interpolate only from that coarse element's nodes, so P^T K P is
+// again element-by-element on the coarse grid with element matrices
+//   Kc_E = sum_children P_c^T Ke_child P_c,
+// where P_c = W_c (x) I_dim and W_c[a][A] is the product over axes of the
+// linear weights of fine corner a of child c at coarse corner A.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace topo {
+
+// 1D linear weight of coarse corner A at fine corner a of child position c
+// (positions in half coarse-element units: (c + a) / 2).
+__host__ __device__ __forceinline__ double w1d(int c, int a, int A) {
+  const double pos = 0.5 * (double)(c + a);
+  return A ? pos : 1.0 - pos;
+}
+
+template <int DIM>
+__host__ __device__ __forceinline__ double wchild(int c, int a, int A) {
+  double w = 1.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) w *= w1d((c >> d) & 1, (a >> d) & 1, (A >> d) & 1);
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// Restriction b_c = Pm^T r_f (Pm = M_f P M_c): coarse node (I,J,K) gathers
+// the fine nodes around (2I,2J,2K) with weights prod(1 - |d|/2).
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+    k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
+               const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= gc.nn) return;
+  const int I = (int)(node % gc.nnx);
+  const long long rest = node / gc.nnx;
+  const int J = (int)(rest % gc.nny);
+  const int K = DIM == 3 ? (int)(rest / gc.nny) : 0;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+        bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
+        if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
+        if (!in) continue;
+        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+        const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * (DIM == 3 ? k : 0));
+        const unsigned m = maskf[fn];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+          if (!((m >> c) & 1u)) acc[c] += w * rf[DIM * fn + c];
+      }
+  const unsigned mc = maskc[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) bc[DIM * node + c] = ((mc >> c) & 1u) ? T(0) : acc[c];
+}
+
+// z_f += Pm z_c: fine node (i,j,k) interpolates from coarse nodes
+// floor(i/2) .. ceil(i/2) per axis.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+    k_prolong_add(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
+                  const T* __restrict__ zc, T* __restrict__ zf) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= gf.nn) return;
+  const int i = (int)(node % gf.nnx);
+  const long long rest = node / gf.nnx;
+  const int j = (int)(rest % gf.nny);
+  const int k = DIM == 3 ? (int)(rest / gf.nny) : 0;
+  const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (DIM == 3 && (k & 1)) ? 2 : 1;
+  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1),
+          wz = (DIM == 3 && (k & 1)) ? T(0.5) : T(1);
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+  for (int a = 0; a < nk; ++a)
+    for (int bb = 0; bb < nj; ++bb)
+      for (int cc = 0; cc < ni; ++cc) {
+        const long long cn = (i0 + cc) + (long long)gc.nnx * ((j0 + bb) + (long long)gc.nny * (k0 + a));
+        const T w = wx * wy * wz;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += w * zc[DIM * cn + c];
+      }
+  const unsigned m = maskf[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+    if (!((m >> c) & 1u)) zf[DIM * node + c] += acc[c];
+}
+
+template <typename T, typename TIN>
+__global__ void __launch_bounds__(256)
+    k_presmooth(long long n, const TIN* __restrict__ bin, T* __restrict__ bout,
+                const T* __restrict__ dinv, T omega, T* __restrict__ z) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const T bv = T(bin[q]);
+  if (bout) bout[q] = bv;
+  z[q] = omega * dinv[q] * bv;
+}
+
+template <typename TIN, typename TOUT>
+__global__ void __launch_bounds__(256)
+    k_convert(long long n, const TIN* __restrict__ in, TOUT* __restrict__ out) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = TOUT(in[q]);
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin level 1 from the finest grid: Kc_E = sum_c coef_child(E,c) Q_c,
+// Q_c = P_c^T KE P_c (precomputed).  One thread per (entry, coarse element).
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+    k_galerkin_fine(GridP gc, GridP gf, const T* __restrict__ coef, const T* __restrict__ Qc,
+                    T* __restrict__ Kc) {
+  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.nel * ND * ND) return;
+  const long long E = t % gc.nel;
+  const int entry = (int)(t / gc.nel);
+  const int EX = (int)(E % gc.nx);
+  const long long rest = E / gc.nx;
+  const int EY = (int)(rest % gc.ny);
+  const int EZ = DIM == 3 ? (int)(rest / gc.ny) : 0;
+  T acc = T(0);
+#pragma unroll
+  for (int c = 0; c < NPE; ++c) {
+    const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + ((c >> 2) & 1);
+    const long long fe = fx + (long long)gf.nx * (fy + (long long)gf.ny * (DIM == 3 ? fz : 0));
+    acc += coef[fe] * Qc[c * ND * ND + entry];
+  }
+  Kc[(size_t)entry * gc.nel + E] = acc;
+}
+
+// Galerkin level l+1 from stored level-l element matrices.  One block of
+// ND*ND threads per coarse element; T = Kchild W in shared memory, then
+// Kc += W^T T, summed over the 2^DIM children.
+template <int DIM, typename T>
+__global__ void k_galerkin_coarse(GridP gc, GridP gf, const T* __restrict__ Kf,
+                                  T* __restrict__ Kc) {
+  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
+  __shared__ T sK[ND * ND];
+  __shared__ T sT[ND * ND];
+  const long long E = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int EX = (int)(E % gc.nx);
+  const long long rest = E / gc.nx;
+  const int EY = (int)(rest % gc.ny);
+  const int EZ = DIM == 3 ? (int)(rest / gc.ny) : 0;
+  const int I = tid / ND, J = tid % ND;
+  const int AI = I / DIM, ci = I % DIM, AJ = J / DIM, cj = J % DIM;
+  T acc = T(0);
+  for (int c = 0; c < NPE; ++c) {
+    const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + ((c >> 2) & 1);
+    const long long fe = fx + (long long)gf.nx * (fy + (long long)gf.ny * (DIM == 3 ? fz : 0));
+    sK[tid] = Kf[(size_t)tid * gf.nel + fe];
+    __syncthreads();
+    // T[i][J] = sum_b K[i][(b, cj)] W_c[b][AJ]   (i = I here)
+    T tv = T(0);
+#pragma unroll
+    for (int bcn = 0; bcn < NPE; ++bcn) tv += sK[I * ND + DIM * bcn + cj] * T(wchild<DIM>(c, bcn, AJ));
+    sT[tid] = tv;
+    __syncthreads();
+    // acc[I][J] += sum_a W_c[a][AI] T[(a, ci)][J]
+#pragma unroll
+    for (int acn = 0; acn < NPE; ++acn) acc += T(wchild<DIM>(c, acn, AI)) * sT[(DIM * acn + ci) * ND + J];
+    __syncthreads();
+  }
+  Kc[(size_t)tid * gc.nel + E] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest grid: dense matrix with identity rows/columns at fixed DOFs.
+// One thread per matrix entry, summing over the elements shared by both
+// nodes (deterministic).  Row-major n x n.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+    k_dense_assemble(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ Kc,
+                     T* __restrict__ A) {
+  constexpr int ND = Geo<DIM>::ND;
+  const long long n = DIM * g.nn;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const long long row = t / n, col = t % n;
+  const long long nr = row / DIM, nc = col / DIM;
+  const int cr = (int)(row % DIM), cc = (int)(col % DIM);
+  const bool fr = (mask[nr] >> cr) & 1u, fc = (mask[nc] >> cc) & 1u;
+  if (fr || fc) {
+    A[t] = (row == col) ? T(1) : T(0);
+    return;
+  }
+  const int ir = (int)(nr % g.nnx), jr = (int)((nr / g.nnx) % g.nny), kr = DIM == 3 ? (int)(nr / ((long long)g.nnx * g.nny)) : 0;
+  const int ic = (int)(nc % g.nnx), jc = (int)((nc / g.nnx) % g.nny), kc = DIM == 3 ? (int)(nc / ((long long)g.nnx * g.nny)) : 0;
+  T s = T(0);
+  if (abs(ir - ic) <= 1 && abs(jr - jc) <= 1 && abs(kr - kc) <= 1) {
+    const int exlo = max(max(ir, ic) - 1, 0), exhi = min(min(ir, ic), g.nx - 1);
+    const int eylo = max(max(jr, jc) - 1, 0), eyhi = min(min(jr, jc), g.ny - 1);
+    const int ezlo = DIM == 3 ? max(max(kr, kc) - 1, 0) : 0;
+    const int ezhi = DIM == 3 ? min(min(kr, kc), g.nz - 1) : 0;
+    for (int ez = ezlo; ez <= ezhi; ++ez)
+      for (int ey = eylo; ey <= eyhi; ++ey)
+        for (int ex = exlo; ex <= exhi; ++ex) {
+          const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
+          const int ar = (ir - ex) + 2 * (jr - ey) + (DIM == 3 ? 4 * (kr - ez) : 0);
+          const int ac = (ic - ex) + 2 * (jc - ey) + (DIM == 3 ? 4 * (kc - ez) : 0);
+          s += Kc[(size_t)((DIM * ar + cr) * ND + DIM * ac + cc) * g.nel + e];
+        }
+  }
+  A[t] = s;
+}
+
+// In-place Cholesky (lower) of the n x n row-major matrix A by one block,
+// right-looking.  A non-positive pivot sets *status = TO_E_SINGULAR.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_cholesky(int n, T* __restrict__ A, int* status) {
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      T d = A[(size_t)k * n + k];
+      if (!(d > T(0))) {
+        s_bad = 1;
+        d = T(1);
+      }
+      A[(size_t)k * n + k] = sqrt(d);
+    }
+    __syncthreads();
+    const T lkk = A[(size_t)k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + k] /= lkk;
+    __syncthreads();
+    for (int i = k + 1 + ty; i < n; i += nty) {
+      const T lik = A[(size_t)i * n + k];
+      for (int j = k + 1 + tx; j <= i; j += 32) A[(size_t)i * n + j] -= lik * A[(size_t)j * n + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_bad) *status = TO_E_SINGULAR;
+}
+
+// X = L^{-1} by forward substitution, one warp per column (stored in the
+// upper triangle-free buffer Linv, row-major, zero above the diagonal).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_lower_inverse(int n, const T* __restrict__ L, T* __restrict__ X) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int jc = warp;
+  for (int i = lane; i < jc; i += 32) X[(size_t)i * n + jc] = T(0);
+  if (lane == 0) X[(size_t)jc * n + jc] = T(1) / L[(size_t)jc * n + jc];
+  __syncwarp();
+  for (int i = jc + 1; i < n; ++i) {
+    T s = T(0);
+    for (int m = jc + lane; m < i; m += 32) s += L[(size_t)i * n + m] * X[(size_t)m * n + jc];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) X[(size_t)i * n + jc] = -s / L[(size_t)i * n + i];
+    __syncwarp();
+  }
+}
+
+// Ainv = X^T X (X = L^{-1} lower triangular): Ainv[i][j] = sum_{m>=max(i,j)} X[m][i] X[m][j]
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_gram_lower(int n, const T* __restrict__ X, T* __restrict__ Ainv) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  T s = T(0);
+  for (int m = max(i, j); m < n; ++m) s += X[(size_t)m * n + i] * X[(size_t)m * n + j];
+  Ainv[t] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_gemv(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  T s = T(0);
+  for (int m = lane; m < n; m += 32) s += A[(size_t)warp * n + m] * x[m];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[warp] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+static cudaError_t restrict_t(const GridP& gf, const uint8_t* mf, const GridP& gc,
+                              const uint8_t* mc, const void* rf, void* bc, cudaStream_t s) {
+  k_restrict<DIM, T><<<nblocks(gc.nn, 256), 256, 0, s>>>(gf, mf, gc, mc, (const T*)rf, (T*)bc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(int dim, int t, const GridP& gf, const uint8_t* mf, const GridP& gc,
+                            const uint8_t* mc, const void* rf, void* bc, cudaStream_t s) {
+  if (dim == 2) return t == T_F64 ? restrict_t<2, double>(gf, mf, gc, mc, rf, bc, s)
+                                  : restrict_t<2, float>(gf, mf, gc, mc, rf, bc, s);
+  return t == T_F64 ? restrict_t<3, double>(gf, mf, gc, mc, rf, bc, s)
+                    : restrict_t<3, float>(gf, mf, gc, mc, rf, bc, s);
+}
+
+template <int DIM, typename T>
+static cudaError_t prolong_t(const GridP& gf, const uint8_t* mf, const GridP& gc, const void* zc,
+                             void* zf, cudaStream_t s) {
+  k_prolong_add<DIM, T><<<nblocks(gf.nn, 256), 256, 0, s>>>(gf, mf, gc, (const T*)zc, (T*)zf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(int dim, int t, const GridP& gf, const uint8_t* mf,
+                               const GridP& gc, const void* zc, void* zf, cudaStream_t s) {
+  if (dim == 2) return t == T_F64 ? prolong_t<2, double>(gf, mf, gc, zc, zf, s)
+                                  : prolong_t<2, float>(gf, mf, gc, zc, zf, s);
+  return t == T_F64 ? prolong_t<3, double>(gf, mf, gc, zc, zf, s)
+                    : prolong_t<3, float>(gf, mf, gc, zc, zf, s);
+}
+
+cudaError_t launch_presmooth(int t, int tin, long long n, const void* bin, void* bout,
+                             const void* dinv, double omega, void* z, cudaStream_t s) {
+  const int nb = nblocks(n, 256);
+  if (t == T_F64) {
+    if (tin != T_F64) return cudaErrorInvalidValue;
+    k_presmooth<double, double><<<nb, 256, 0, s>>>(n, (const double*)bin, (double*)bout,
+                                                   (const double*)dinv, omega, (double*)z);
+  } else if (tin == T_F64) {
+    k_presmooth<float, double><<<nb, 256, 0, s>>>(n, (const double*)bin, (float*)bout,
+                                                  (const float*)dinv, (float)omega, (float*)z);
+  } else {
+    k_presmooth<float, float><<<nb, 256, 0, s>>>(n, (const float*)bin, (float*)bout,
+                                                 (const float*)dinv, (float)omega, (float*)z);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int tin, int tout, long long n, const void* in, void* out,
+                           cudaStream_t s) {
+  const int nb = nblocks(n, 256);
+  if (tin == T_F64 && tout == T_F32)
+    k_convert<double, float><<<nb, 256, 0, s>>>(n, (const double*)in, (float*)out);
+  else if (tin == T_F32 && tout == T_F64)
+    k_convert<float, double><<<nb, 256, 0, s>>>(n, (const float*)in, (double*)out);
+  else if (tin == T_F64)
+    k_convert<double, double><<<nb, 256, 0, s>>>(n, (const double*)in, (double*)out);
+  else
+    k_convert<float, float><<<nb, 256, 0, s>>>(n, (const float*)in, (float*)out);
+  return cudaGetLastError();
+}
+
+template <int DIM, typename T>
+static cudaError_t gal_fine_t(const GridP& gc, const GridP& gf, const void* coef, const void* Qc,
+                              void* Kc, cudaStream_t s) {
+  constexpr int ND = Geo<DIM>::ND;
+  const long long tot = gc.nel * ND * ND;
+  k_galerkin_fine<DIM, T><<<nblocks(tot, 256), 256, 0, s>>>(gc, gf, (const T*)coef,
+                                                            (const T*)Qc, (T*)Kc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_fine(int dim, int t, const GridP& gc, const GridP& gf,
+                                 const void* coef, const void* Qc, void* Kc, cudaStream_t s) {
+  if (dim == 2) return t == T_F64 ? gal_fine_t<2, double>(gc, gf, coef, Qc, Kc, s)
+                                  : gal_fine_t<2, float>(gc, gf, coef, Qc, Kc, s);
+  return t == T_F64 ? gal_fine_t<3, double>(gc, gf, coef, Qc, Kc, s)
+                    : gal_fine_t<3, float>(gc, gf, coef, Qc, Kc, s);
+}
+
+template <int DIM, typename T>
+static cudaError_t gal_coarse_t(const GridP& gc, const GridP& gf, const void* Kf, void* Kc,
+                                cudaStream_t s) {
+  constexpr int ND = Geo<DIM>::ND;
+  if (gc.nel <= 0) return cudaSuccess;
+  k_galerkin_coarse<DIM, T><<<(unsigned)gc.nel, ND * ND, 0, s>>>(gc, gf, (const T*)Kf, (T*)Kc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_coarse(int dim, int t, const GridP& gc, const GridP& gf,
+                                   const void* Kf, void* Kc, cudaStream_t s) {
+  if (dim == 2) return t == T_F64 ? gal_coarse_t<2, double>(gc, gf, Kf, Kc, s)
+                                  : gal_coarse_t<2, float>(gc, gf, Kf, Kc, s);
+  return t == T_F64 ? gal_coarse_t<3, double>(gc, gf, Kf, Kc, s)
+                    : gal_coarse_t<3, float>(gc, gf, Kf, Kc, s);
+}
+
+template <int DIM, typename T>
+static cudaError_t dense_t(const GridP& g, const uint8_t* mask, const void* Kc, void* A,
+                           cudaStream_t s) {
+  const long long n = DIM * g.nn;
+  k_dense_assemble<DIM, T><<<nblocks(n * n, 256), 256, 0, s>>>(g, mask, (const T*)Kc, (T*)A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
+                                  const void* Kc, void* A, cudaStream_t s) {
+  if (dim == 2) return t == T_F64 ? dense_t<2, double>(g, mask, Kc, A, s)
+                                  : dense_t<2, float>(g, mask, Kc, A, s);
+  return t == T_F64 ? dense_t<3, double>(g, mask, Kc, A, s) : dense_t<3, float>(g, mask, Kc, A, s);
+}
+
+template <typename T>
+static cudaError_t cholinv_t(int n, void* A, void* Ainv, int* status, cudaStream_t s) {
+  k_cholesky<T><<<1, 1024, 0, s>>>(n, (T*)A, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // Ainv is used as scratch for L^{-1} first, then A receives X^T X and
+  // the buffers are swapped by copying back.
+  k_lower_inverse<T><<<nblocks((long long)n * 32, 256), 256, 0, s>>>(n, (const T*)A, (T*)Ainv);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gram_lower<T><<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, (const T*)Ainv, (T*)A);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(Ainv, A, sizeof(T) * (size_t)n * n, cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t launch_cholesky_inverse(int t, int n, void* A, void* Ainv, int* status,
+                                    cudaStream_t s) {
+  return t == T_F64 ? cholinv_t<double>(n, A, Ainv, status, s)
+                    : cholinv_t<float>(n, A, Ainv, status, s);
+}
+
+cudaError_t launch_dense_gemv(int t, int n, const void* A, const void* x, void* y,
+                              cudaStream_t s) {
+  const int nb = nblocks((long long)n * 32, 256);
+  if (t == T_F64)
+    k_gemv<double><<<nb, 256, 0, s>>>(n, (const double*)A, (const double*)x, (double*)y);
+  else
+    k_gemv<float><<<nb, 256, 0, s>>>(n, (const float*)A, (const float*)x, (float*)y);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

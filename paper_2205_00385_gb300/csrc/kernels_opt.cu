@@ -1,0 +1,268 @@
+// Design-side kernels: SIMP modulus (Eq. 1), density filter and its
+// transpose (Eq. 31-33), compliance and sensitivity (Eq. 3, 6, 34) and the
+// optimality-criteria update with a device-side bisection for the volume
+// multiplier.  All float64.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace topo {
+
+__device__ __forceinline__ double ipow(double x, double p) {
+  if (p == 3.0) return x * x * x;
+  if (p == 2.0) return x * x;
+  if (p == 1.0) return x;
+  if (p == 4.0) return (x * x) * (x * x);
+  return pow(x, p);
+}
+
+__global__ void __launch_bounds__(256)
+    k_simp(long long nel, const double* __restrict__ rho, double E0, double Emin, double penal,
+           double* __restrict__ E64, float* __restrict__ E32) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  const double E = Emin + (E0 - Emin) * ipow(rho[e], penal);
+  E64[e] = E;
+  E32[e] = (float)E;
+}
+
+__global__ void __launch_bounds__(256)
+    k_delta(long long nel, const double* __restrict__ E, const double* __restrict__ Ep,
+            double* __restrict__ dE64, float* __restrict__ dE32, float* __restrict__ Ep32) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  const double d = E[e] - Ep[e];
+  dE64[e] = d;
+  dE32[e] = (float)d;
+  Ep32[e] = (float)Ep[e];
+}
+
+// mode 0: out_i = sum_j w_ij in_j / Hs_i ; mode 1: out_e = sum_i w_ie in_i / Hs_i
+// mode 2: Hs_i = sum_j w_ij (in/out ignored)
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    k_filter(GridP g, StencilP st, int mode, const double* __restrict__ Hs,
+             const double* __restrict__ in, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.nel) return;
+  const int ex = (int)(e % g.nx);
+  const long long rest = e / g.nx;
+  const int ey = (int)(rest % g.ny);
+  const int ez = DIM == 3 ? (int)(rest / g.ny) : 0;
+  double acc = 0.0;
+  for (int q = 0; q < st.count; ++q) {
+    const int jx = ex + st.d[q][0], jy = ey + st.d[q][1], jz = ez + st.d[q][2];
+    bool in_range = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny;
+    if (DIM == 3) in_range = in_range && jz >= 0 && jz < g.nz;
+    if (!in_range) continue;
+    const long long j = jx + (long long)g.nx * (jy + (long long)g.ny * (DIM == 3 ? jz : 0));
+    const double w = st.w[q];
+    if (mode == 0)
+      acc = fma(w, in[j], acc);
+    else if (mode == 1)
+      acc = fma(w, in[j] / Hs[j], acc);
+    else
+      acc += w;
+  }
+  if (mode == 0)
+    out[e] = acc / Hs[e];
+  else
+    out[e] = acc;
+}
+
+// ce_e = u_e^T KE u_e; dc_e = -penal (E0-Emin) rho_e^(penal-1) ce_e;
+// compliance = sum_e E_e ce_e (deterministic reduction).
+template <int DIM>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_sensitivity(GridP g, const uint8_t* __restrict__ mask, KEP<double, Geo<DIM>::ND> ke,
+                  const double* __restrict__ u, const double* __restrict__ E,
+                  const double* __restrict__ rho, double penal, double E0, double Emin,
+                  double* __restrict__ dc, double* compliance, double* partials,
+                  unsigned* counter) {
+  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
+  __shared__ double sh[32];
+  double v[1] = {0.0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.nel;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int ex = (int)(e % g.nx);
+    const long long rest = e / g.nx;
+    const int ey = (int)(rest % g.ny);
+    const int ez = DIM == 3 ? (int)(rest / g.ny) : 0;
+    double ue[ND];
+#pragma unroll
+    for (int a = 0; a < NPE; ++a) {
+      const int i = ex + (a & 1), j = ey + ((a >> 1) & 1), k = ez + ((a >> 2) & 1);
+      const long long nd = i + (long long)g.nnx * (j + (long long)g.nny * (DIM == 3 ? k : 0));
+      const unsigned m = mask[nd];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) ue[DIM * a + c] = ((m >> c) & 1u) ? 0.0 : u[DIM * nd + c];
+    }
+    double ce = 0.0;
+#pragma unroll
+    for (int r = 0; r < ND; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int c = 0; c < ND; ++c) s = fma(ke.v[r * ND + c], ue[c], s);
+      ce = fma(ue[r], s, ce);
+    }
+    const double re = rho[e];
+    dc[e] = -penal * (E0 - Emin) * ipow(re, penal - 1.0) * ce;
+    v[0] = fma(E[e], ce, v[0]);
+  }
+  block_sum<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) *compliance = o[0];
+  }
+}
+
+// a_e = rho_e sqrt(max(0, -dc_e / dv_e)); bracket [0, 1e9]
+__global__ void __launch_bounds__(256)
+    k_oc_prep(long long nel, const double* __restrict__ rho, const double* __restrict__ dc,
+              const double* __restrict__ dv, double* __restrict__ a, double* scal) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) {
+    scal[S_OC_L1] = 0.0;
+    scal[S_OC_L2] = 1e9;
+  }
+  if (e >= nel) return;
+  a[e] = rho[e] * sqrt(fmax(0.0, -dc[e] / dv[e]));
+}
+
+__device__ __forceinline__ double oc_new(double a, double s, double r, double move) {
+  const double lo = fmax(0.0, r - move), hi = fmin(1.0, r + move);
+  return fmin(hi, fmax(lo, a * s));
+}
+
+// One bisection step: lmid = (l1+l2)/2; the filtered volume of rho_new(lmid)
+// decides which half is kept (as in the oracle).  No-op once the bracket is
+// within a relative 1e-13.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_oc_step(long long nel, const double* __restrict__ rho, const double* __restrict__ a,
+              const double* __restrict__ dv, double move, double target, double* scal,
+              double* partials, unsigned* counter) {
+  __shared__ double sh[32];
+  const double l1 = scal[S_OC_L1], l2 = scal[S_OC_L2];
+  if (!((l2 - l1) > 1e-13 * (l1 + l2))) return;
+  const double lmid = 0.5 * (l1 + l2);
+  const double s = 1.0 / sqrt(lmid);
+  double v[1] = {0.0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nel;
+       e += (long long)gridDim.x * blockDim.x)
+    v[0] = fma(dv[e], oc_new(a[e], s, rho[e], move), v[0]);
+  block_sum<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) {
+      if (o[0] > target)
+        scal[S_OC_L1] = lmid;
+      else
+        scal[S_OC_L2] = lmid;
+      scal[S_OC_VOL] = o[0];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_oc_final(long long nel, double* __restrict__ rho, const double* __restrict__ a,
+               double move, double* scal, double* change_dev, double* partials,
+               unsigned* counter) {
+  __shared__ double sh[32];
+  const double lam = 0.5 * (scal[S_OC_L1] + scal[S_OC_L2]);
+  const double s = 1.0 / sqrt(lam);
+  double v[1] = {0.0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nel;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double r = rho[e];
+    const double rn = oc_new(a[e], s, r, move);
+    rho[e] = rn;
+    v[0] = fmax(v[0], fabs(rn - r));
+  }
+  block_max<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_max<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) {
+      scal[S_CHANGE] = o[0];
+      if (change_dev) *change_dev = o[0];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_simp(long long nel, const double* rho, double E0, double Emin, double penal,
+                        double* E64, float* E32, cudaStream_t s) {
+  k_simp<<<nblocks(nel, 256), 256, 0, s>>>(nel, rho, E0, Emin, penal, E64, E32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_delta(long long nel, const double* E, const double* Eprev, double* dE64,
+                         float* dE32, float* Eprev32, cudaStream_t s) {
+  k_delta<<<nblocks(nel, 256), 256, 0, s>>>(nel, E, Eprev, dE64, dE32, Eprev32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter(int dim, const GridP& g, const StencilP& st, int mode,
+                          const double* Hs, const double* in, double* out, cudaStream_t s) {
+  if (dim == 2)
+    k_filter<2><<<nblocks(g.nel, 256), 256, 0, s>>>(g, st, mode, Hs, in, out);
+  else
+    k_filter<3><<<nblocks(g.nel, 256), 256, 0, s>>>(g, st, mode, Hs, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_norm(int dim, const GridP& g, const StencilP& st, double* Hs,
+                               cudaStream_t s) {
+  return launch_filter(dim, g, st, 2, nullptr, nullptr, Hs, s);
+}
+
+template <int DIM>
+static cudaError_t sens_t(const GridP& g, const uint8_t* mask, const double* kev, const double* u,
+                          const double* E, const double* rho, double penal, double E0,
+                          double Emin, double* dc, double* compliance, double* partials,
+                          unsigned* counter, cudaStream_t s) {
+  constexpr int ND = Geo<DIM>::ND;
+  KEP<double, ND> ke;
+  for (int q = 0; q < ND * ND; ++q) ke.v[q] = kev[q];
+  k_sensitivity<DIM><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, mask, ke, u, E, rho, penal, E0, Emin,
+                                                        dc, compliance, partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sensitivity(int dim, const GridP& g, const uint8_t* mask, const double* ke,
+                               const double* u, const double* E, const double* rho,
+                               double penal, double E0, double Emin, double* dc,
+                               double* compliance, double* partials, unsigned* counter,
+                               cudaStream_t s) {
+  if (dim == 2)
+    return sens_t<2>(g, mask, ke, u, E, rho, penal, E0, Emin, dc, compliance, partials, counter, s);
+  return sens_t<3>(g, mask, ke, u, E, rho, penal, E0, Emin, dc, compliance, partials, counter, s);
+}
+
+cudaError_t launch_oc_prep(long long nel, const double* rho, const double* dc,
+                           const double* dv, double* a, double* scal, cudaStream_t s) {
+  k_oc_prep<<<nblocks(nel, 256), 256, 0, s>>>(nel, rho, dc, dv, a, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oc_step(long long nel, const double* rho, const double* a,
+                           const double* dv, double move, double target, double* scal,
+                           double* partials, unsigned* counter, cudaStream_t s) {
+  k_oc_step<<<RED_BLOCKS, RED_THREADS, 0, s>>>(nel, rho, a, dv, move, target, scal, partials,
+                                               counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oc_final(long long nel, double* rho, const double* a, double move,
+                            double* scal, double* change_dev, double* partials,
+                            unsigned* counter, cudaStream_t s) {
+  k_oc_final<<<RED_BLOCKS, RED_THREADS, 0, s>>>(nel, rho, a, move, scal, change_dev, partials,
+                                                counter);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

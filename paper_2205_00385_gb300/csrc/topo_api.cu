@@ -1,0 +1,983 @@
+// C-ABI entry points of libtopo.so (declared in include/topo.h).
+//
+// The host side only sequences kernels on the context's stream and keeps
+// bookkeeping (level geometry, PARM ring position, iteration counts); every
+// arithmetic step of the solver path runs in the library's kernels.  Device
+// memory comes exclusively from the caller's workspace.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "kernels.h"
+
+using namespace topo;
+
+static std::string g_last_error;
+
+namespace topo {
+
+void note_launch(to_ctx* c) {
+  if (c) c->launches++;
+}
+
+}  // namespace topo
+
+static to_status fail(to_ctx* c, to_status st, const std::string& msg) {
+  if (c)
+    c->last_error = msg;
+  else
+    g_last_error = msg;
+  return st;
+}
+
+static to_status cuda_fail(to_ctx* c, const char* what, cudaError_t e) {
+  return fail(c, TO_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LAUNCH(c, expr, what)                                   \
+  do {                                                          \
+    cudaError_t _e = (expr);                                    \
+    note_launch(c);                                             \
+    if (_e != cudaSuccess) return cuda_fail((c), (what), _e);   \
+  } while (0)
+
+#define CUDA_TRY(c, expr, what)                                 \
+  do {                                                          \
+    cudaError_t _e = (expr);                                    \
+    if (_e != cudaSuccess) return cuda_fail((c), (what), _e);   \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Profiling with CUDA events on the context stream
+// ---------------------------------------------------------------------------
+enum { PK_FINE = 0, PK_COARSE = 1, PK_VCYCLE = 2, PK_N = 3 };
+
+static cudaEvent_t ev_take(to_ctx* c) {
+  cudaEvent_t e;
+  if (!c->ev_pool.empty()) {
+    e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+struct ProfScope {
+  to_ctx* c;
+  int kind;
+  double bytes;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(to_ctx* c_, int k, double b = 0.0) : c(c_), kind(k), bytes(b) {
+    if (c->prof) {
+      e0 = ev_take(c);
+      if (e0) cudaEventRecord(e0, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof && e0) {
+      cudaEvent_t e1 = ev_take(c);
+      if (e1) {
+        cudaEventRecord(e1, c->stream);
+        c->ev_used.push_back({kind, {e0, e1}});
+        c->ev_bytes.push_back(bytes);
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Element matrices and filter stencil (host tables, computed once per context)
+// ---------------------------------------------------------------------------
+// Unit-modulus element stiffness of a unit cell by 2-point Gauss quadrature,
+// local node a = bx + 2by + 4bz, local DOF dim*a + c.
+static void element_stiffness(int dim, double nu, double* KE) {
+  const int npe = 1 << dim, nd = dim * npe;
+  const double g = 0.5 / sqrt(3.0);
+  const double gp[2] = {0.5 - g, 0.5 + g};
+  const int ns = dim == 2 ? 3 : 6;
+  double D[6][6] = {{0}};
+  if (dim == 2) {
+    const double s = 1.0 / (1.0 - nu * nu);
+    D[0][0] = D[1][1] = s;
+    D[0][1] = D[1][0] = s * nu;
+    D[2][2] = s * (1.0 - nu) / 2.0;
+  } else {
+    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) D[i][j] = lam;
+    for (int i = 0; i < 3; ++i) {
+      D[i][i] = lam + 2.0 * mu;
+      D[3 + i][3 + i] = mu;
+    }
+  }
+  for (int q = 0; q < nd * nd; ++q) KE[q] = 0.0;
+  const int nq = dim == 2 ? 4 : 8;
+  for (int q = 0; q < nq; ++q) {
+    double xi[3] = {gp[q & 1], gp[(q >> 1) & 1], gp[(q >> 2) & 1]};
+    double w = dim == 2 ? 0.25 : 0.125;
+    double B[6][24] = {{0}};
+    for (int a = 0; a < npe; ++a) {
+      double dN[3];
+      for (int d = 0; d < dim; ++d) {
+        double v = 1.0;
+        for (int dd = 0; dd < dim; ++dd) {
+          const int bit = (a >> dd) & 1;
+          if (dd == d)
+            v *= bit ? 1.0 : -1.0;
+          else
+            v *= bit ? xi[dd] : 1.0 - xi[dd];
+        }
+        dN[d] = v;
+      }
+      if (dim == 2) {
+        B[0][2 * a] = dN[0];
+        B[1][2 * a + 1] = dN[1];
+        B[2][2 * a] = dN[1];
+        B[2][2 * a + 1] = dN[0];
+      } else {
+        const int c = 3 * a;
+        B[0][c] = dN[0];
+        B[1][c + 1] = dN[1];
+        B[2][c + 2] = dN[2];
+        B[3][c] = dN[1];
+        B[3][c + 1] = dN[0];
+        B[4][c + 1] = dN[2];
+        B[4][c + 2] = dN[1];
+        B[5][c] = dN[2];
+        B[5][c + 2] = dN[0];
+      }
+    }
+    for (int i = 0; i < nd; ++i)
+      for (int j = 0; j < nd; ++j) {
+        double s = 0.0;
+        for (int p = 0; p < ns; ++p)
+          for (int r = 0; r < ns; ++r) s += B[p][i] * D[p][r] * B[r][j];
+        KE[i * nd + j] += w * s;
+      }
+  }
+}
+
+// Q_c = P_c^T KE P_c for each child position c of a coarse element.
+static void child_galerkin(int dim, const double* KE, double* Qc) {
+  const int npe = 1 << dim, nd = dim * npe;
+  std::vector<double> P(nd * nd), T(nd * nd);
+  for (int c = 0; c < npe; ++c) {
+    for (int a = 0; a < npe; ++a)
+      for (int A = 0; A < npe; ++A) {
+        double w = 1.0;
+        for (int d = 0; d < dim; ++d) {
+          const double pos = 0.5 * (((c >> d) & 1) + ((a >> d) & 1));
+          w *= ((A >> d) & 1) ? pos : 1.0 - pos;
+        }
+        for (int ci = 0; ci < dim; ++ci)
+          for (int cj = 0; cj < dim; ++cj) P[(dim * a + ci) * nd + dim * A + cj] = (ci == cj) ? w : 0.0;
+      }
+    for (int i = 0; i < nd; ++i)
+      for (int J = 0; J < nd; ++J) {
+        double s = 0.0;
+        for (int j = 0; j < nd; ++j) s += KE[i * nd + j] * P[j * nd + J];
+        T[i * nd + J] = s;
+      }
+    for (int I = 0; I < nd; ++I)
+      for (int J = 0; J < nd; ++J) {
+        double s = 0.0;
+        for (int i = 0; i < nd; ++i) s += P[i * nd + I] * T[i * nd + J];
+        Qc[(size_t)c * nd * nd + I * nd + J] = s;
+      }
+  }
+}
+
+static bool make_stencil(int dim, double rmin, StencilP* st) {
+  const int R = (int)ceil(rmin);
+  st->count = 0;
+  for (int dz = (dim == 3 ? -R : 0); dz <= (dim == 3 ? R : 0); ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx) {
+        const double w = rmin - sqrt((double)(dx * dx + dy * dy + dz * dz));
+        if (w <= 0.0) continue;
+        if (st->count >= MAX_STENCIL) return false;
+        st->d[st->count][0] = dx;
+        st->d[st->count][1] = dy;
+        st->d[st->count][2] = dz;
+        st->w[st->count] = w;
+        st->count++;
+      }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Validation and workspace layout
+// ---------------------------------------------------------------------------
+static GridP level_grid(const to_mesh_desc& d, int l) {
+  GridP g;
+  g.nx = d.nel[0] >> l;
+  g.ny = d.nel[1] >> l;
+  g.nz = d.dim == 3 ? (d.nel[2] >> l) : 0;
+  g.nnx = g.nx + 1;
+  g.nny = g.ny + 1;
+  g.nnz = d.dim == 3 ? g.nz + 1 : 1;
+  g.nn = (long long)g.nnx * g.nny * g.nnz;
+  g.nel = (long long)g.nx * g.ny * (d.dim == 3 ? g.nz : 1);
+  return g;
+}
+
+static to_status validate(const to_mesh_desc* d, std::string* why) {
+  if (!d) return *why = "desc is NULL", TO_E_INVALID;
+  if (d->dim != 2 && d->dim != 3) return *why = "dim must be 2 or 3", TO_E_INVALID;
+  if (d->mg_levels < 2 || d->mg_levels > MAXL)
+    return *why = "mg_levels must be in [2, 10]", TO_E_INVALID;
+  for (int i = 0; i < d->dim; ++i) {
+    if (d->nel[i] < 1) return *why = "nel must be positive", TO_E_INVALID;
+    const int f = 1 << (d->mg_levels - 1);
+    if (d->nel[i] % f != 0)
+      return *why = "every nel must be divisible by 2^(mg_levels-1)", TO_E_INVALID;
+  }
+  if (!(isfinite(d->E0) && isfinite(d->Emin) && d->Emin > 0.0 && d->E0 > d->Emin))
+    return *why = "need 0 < Emin < E0", TO_E_INVALID;
+  if (!(isfinite(d->nu) && d->nu > -1.0 && d->nu < 0.5)) return *why = "nu out of range", TO_E_INVALID;
+  if (!(isfinite(d->penal) && d->penal >= 1.0)) return *why = "penal must be >= 1", TO_E_INVALID;
+  if (!(isfinite(d->rmin) && d->rmin > 0.0 && d->rmin < 4.5))
+    return *why = "rmin must be in (0, 4.5)", TO_E_INVALID;
+  if (d->precision != TO_FP64 && d->precision != TO_MIXED)
+    return *why = "precision must be TO_FP64 or TO_MIXED", TO_E_INVALID;
+  if (d->n_parm < 1 || d->n_parm > MAXB || d->n_carm < 1 || d->n_carm > MAXB)
+    return *why = "n_parm and n_carm must be in [1, 16]", TO_E_INVALID;
+  GridP gc = level_grid(*d, d->mg_levels - 1);
+  if (d->dim * gc.nn > 6144) return *why = "coarsest grid too large for the dense solve", TO_E_INVALID;
+  return TO_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    const size_t o = off;
+    off = align256(off + count * sizeof(T));
+    return base ? reinterpret_cast<T*>(base + o) : nullptr;
+  }
+};
+
+static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
+  Carver cv{base};
+  const int dim = d.dim, npe = 1 << dim, nd = dim * npe, L = d.mg_levels;
+  const bool mixed = d.precision == TO_MIXED;
+  const size_t ts = mixed ? 4 : 8;
+  GridP g0 = level_grid(d, 0);
+  const long long nel = g0.nel, n = dim * g0.nn;
+  const int Ns = d.n_parm, Nm = d.n_carm;
+  double *E64 = cv.take<double>(nel), *Ep64 = cv.take<double>(nel), *dE64 = cv.take<double>(nel);
+  double *rho = cv.take<double>(nel), *Hs = cv.take<double>(nel), *oca = cv.take<double>(nel);
+  float *E32 = cv.take<float>(nel), *Ep32 = cv.take<float>(nel), *dE32 = cv.take<float>(nel);
+  double* f = cv.take<double>(n);
+  double *r = cv.take<double>(n), *z = cv.take<double>(n), *p = cv.take<double>(n),
+         *q = cv.take<double>(n);
+  double *Phi = cv.take<double>((size_t)n * Ns), *KPhi = cv.take<double>((size_t)n * Ns);
+  double *R = cv.take<double>((size_t)n * Nm), *Q = cv.take<double>((size_t)n * Nm);
+  double* t = cv.take<double>(n);
+  double* Qc64 = cv.take<double>((size_t)npe * nd * nd);
+  float* Qc32 = cv.take<float>((size_t)npe * nd * nd);
+  double* partials = cv.take<double>((size_t)RED_BLOCKS * MAXB * MAXB);
+  unsigned* counters = cv.take<unsigned>(C_NCOUNTERS);
+  double* scal = cv.take<double>(S_NSLOTS);
+  double* small = cv.take<double>(SM_TOTAL);
+  int* ints = cv.take<int>(I_NINTS);
+  LevelBuf lv[MAXL];
+  for (int l = 0; l < L; ++l) {
+    GridP g = level_grid(d, l);
+    const long long nl = dim * g.nn;
+    lv[l].g = g;
+    lv[l].n = nl;
+    lv[l].mask = cv.take<uint8_t>(g.nn);
+    lv[l].dinv = cv.take<char>(nl * ts);
+    lv[l].b = cv.take<char>(nl * ts);
+    lv[l].z = cv.take<char>(nl * ts);
+    lv[l].z2 = cv.take<char>(nl * ts);
+    lv[l].r = cv.take<char>(nl * ts);
+    lv[l].Kc = l >= 1 ? (void*)cv.take<char>((size_t)nd * nd * g.nel * ts) : nullptr;
+  }
+  const long long nc = lv[L - 1].n;
+  void* Ad = cv.take<char>((size_t)nc * nc * ts);
+  void* Ai = cv.take<char>((size_t)nc * nc * ts);
+  if (c) {
+    c->E64 = E64; c->Eprev64 = Ep64; c->dE64 = dE64; c->rho_phys = rho; c->Hs = Hs; c->oc_a = oca;
+    c->E32 = E32; c->Eprev32 = Ep32; c->dE32 = dE32; c->f = f;
+    c->r = r; c->z = z; c->p = p; c->q = q;
+    c->Phi = Phi; c->KPhi = KPhi; c->R = R; c->Q = Q; c->t = t;
+    c->Qc64 = Qc64; c->Qc32 = Qc32;
+    c->partials = partials; c->counters = counters; c->scal = scal; c->small = small;
+    c->ints = ints;
+    for (int l = 0; l < L; ++l) c->lv[l] = lv[l];
+    c->Adense = Ad; c->Ainv = Ai;
+    c->nc = (int)nc;
+  }
+  return cv.off;
+}
+
+// ---------------------------------------------------------------------------
+// Small device helpers used only at set-up
+// ---------------------------------------------------------------------------
+__global__ void k_node_mask(long long nn, int dim, const uint8_t* fixed, uint8_t* mask) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  unsigned m = 0;
+  for (int c = 0; c < dim; ++c)
+    if (fixed[dim * i + c]) m |= 1u << c;
+  mask[i] = (uint8_t)m;
+}
+
+__global__ void k_coarse_mask(GridP gf, const uint8_t* mf, GridP gc, uint8_t* mc) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= gc.nn) return;
+  const int I = (int)(node % gc.nnx);
+  const long long rest = node / gc.nnx;
+  const int J = (int)(rest % gc.nny);
+  const int K = (int)(rest / gc.nny);
+  mc[node] = mf[2 * I + (long long)gf.nnx * (2 * J + (long long)gf.nny * 2 * K)];
+}
+
+// Flags a fixed fine DOF whose interpolation sources include a free coarse
+// DOF (the Galerkin operators need fixed DOFs closed under interpolation),
+// and loads on fixed DOFs.
+__global__ void k_check_bc(GridP gf, const uint8_t* mf, GridP gc, const uint8_t* mc, int dim,
+                           const double* f, int* flag) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= gf.nn) return;
+  const unsigned m = mf[node];
+  if (!m) return;
+  for (int c = 0; c < dim; ++c)
+    if (((m >> c) & 1u) && f && f[dim * node + c] != 0.0) atomicOr(flag, 2);
+  if (!mc) return;
+  const int i = (int)(node % gf.nnx);
+  const long long rest = node / gf.nnx;
+  const int j = (int)(rest % gf.nny);
+  const int k = (int)(rest / gf.nny);
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+  for (int a = 0; a < nk; ++a)
+    for (int b = 0; b < nj; ++b)
+      for (int cc = 0; cc < ni; ++cc) {
+        const long long cn = ((i >> 1) + cc) + (long long)gc.nnx * (((j >> 1) + b) + (long long)gc.nny * ((k >> 1) + a));
+        const unsigned mcv = mc[cn];
+        for (int c = 0; c < dim; ++c)
+          if (((m >> c) & 1u) && !((mcv >> c) & 1u)) atomicOr(flag, 1);
+      }
+}
+
+// ---------------------------------------------------------------------------
+// Public API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+to_status to_workspace_bytes(const to_mesh_desc* desc, int64_t* bytes) {
+  std::string why;
+  if (!bytes) return fail(nullptr, TO_E_INVALID, "bytes is NULL");
+  to_status st = validate(desc, &why);
+  if (st != TO_OK) return fail(nullptr, st, why);
+  *bytes = (int64_t)carve(*desc, nullptr, nullptr) + 256;
+  return TO_OK;
+}
+
+const char* to_last_error(const to_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_last_error.c_str();
+}
+
+to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, const double* f,
+                       void* workspace, int64_t ws_bytes, void* stream, to_ctx** out) {
+  std::string why;
+  if (!out) return fail(nullptr, TO_E_INVALID, "out is NULL");
+  *out = nullptr;
+  to_status st = validate(desc, &why);
+  if (st != TO_OK) return fail(nullptr, st, why);
+  if (!fixed_mask || !f || !workspace) return fail(nullptr, TO_E_INVALID, "NULL pointer argument");
+  if (((uintptr_t)workspace) & 255) return fail(nullptr, TO_E_INVALID, "workspace not 256-byte aligned");
+  const size_t need = carve(*desc, nullptr, nullptr);
+  if (ws_bytes < (int64_t)need) return fail(nullptr, TO_E_OOM, "workspace too small");
+  to_ctx* c = new to_ctx();
+  c->desc = *desc;
+  c->dim = desc->dim;
+  c->npe = 1 << c->dim;
+  c->nd = c->dim * c->npe;
+  c->L = desc->mg_levels;
+  c->mixed = desc->precision == TO_MIXED;
+  c->stream = (cudaStream_t)stream;
+  carve(*desc, c, (char*)workspace);
+  c->nel = c->lv[0].g.nel;
+  c->nn = c->lv[0].g.nn;
+  c->n = c->lv[0].n;
+  c->parm_count = c->parm_head = c->carm_built = 0;
+  c->have_density = false;
+  c->hier_stale = true;
+  c->launches = 0;
+  c->prof = false;
+  if (!make_stencil(c->dim, desc->rmin, &c->stencil)) {
+    delete c;
+    return fail(nullptr, TO_E_INVALID, "filter stencil too large");
+  }
+  element_stiffness(c->dim, desc->nu, c->KE64);
+  for (int q = 0; q < c->nd * c->nd; ++q) c->KE32[q] = (float)c->KE64[q];
+  std::vector<double> Qc((size_t)c->npe * c->nd * c->nd);
+  child_galerkin(c->dim, c->KE64, Qc.data());
+  std::vector<float> Qc32(Qc.size());
+  for (size_t q = 0; q < Qc.size(); ++q) Qc32[q] = (float)Qc[q];
+  cudaStream_t s = c->stream;
+  auto bad = [&](to_status code, const std::string& m) {
+    g_last_error = m;
+    delete c;
+    return code;
+  };
+#define INIT_TRY(expr, what)                                              \
+  do {                                                                    \
+    cudaError_t _e = (expr);                                              \
+    if (_e != cudaSuccess) return bad(TO_E_CUDA, std::string(what) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+  INIT_TRY(cudaMemcpyAsync(c->Qc64, Qc.data(), Qc.size() * 8, cudaMemcpyHostToDevice, s), "copy Qc");
+  INIT_TRY(cudaMemcpyAsync(c->Qc32, Qc32.data(), Qc32.size() * 4, cudaMemcpyHostToDevice, s), "copy Qc32");
+  INIT_TRY(cudaMemcpyAsync(c->f, f, c->n * 8, cudaMemcpyDeviceToDevice, s), "copy f");
+  INIT_TRY(cudaMemsetAsync(c->counters, 0, C_NCOUNTERS * sizeof(unsigned), s), "memset");
+  INIT_TRY(cudaMemsetAsync(c->scal, 0, S_NSLOTS * 8, s), "memset");
+  INIT_TRY(cudaMemsetAsync(c->ints, 0, I_NINTS * sizeof(int), s), "memset");
+  INIT_TRY(cudaMemsetAsync(c->small, 0, SM_TOTAL * 8, s), "memset");
+  k_node_mask<<<nblocks(c->nn, 256), 256, 0, s>>>(c->nn, c->dim, fixed_mask, c->lv[0].mask);
+  INIT_TRY(cudaGetLastError(), "node mask");
+  for (int l = 1; l < c->L; ++l) {
+    k_coarse_mask<<<nblocks(c->lv[l].g.nn, 256), 256, 0, s>>>(c->lv[l - 1].g, c->lv[l - 1].mask,
+                                                             c->lv[l].g, c->lv[l].mask);
+    INIT_TRY(cudaGetLastError(), "coarse mask");
+  }
+  for (int l = 0; l + 1 < c->L; ++l) {
+    k_check_bc<<<nblocks(c->lv[l].g.nn, 256), 256, 0, s>>>(c->lv[l].g, c->lv[l].mask,
+                                                          c->lv[l + 1].g, c->lv[l + 1].mask,
+                                                          c->dim, l == 0 ? c->f : nullptr,
+                                                          c->ints + I_STATUS);
+    INIT_TRY(cudaGetLastError(), "bc check");
+  }
+  INIT_TRY(launch_filter_norm(c->dim, c->lv[0].g, c->stencil, c->Hs, s), "filter norm");
+  INIT_TRY(launch_dot(c->n, c->f, c->f, c->partials, c->counters + C_DOT, c->scal + S_FNORM2, s),
+           "norm f");
+  double f2 = 0.0;
+  int flag = 0;
+  INIT_TRY(cudaMemcpyAsync(&f2, c->scal + S_FNORM2, 8, cudaMemcpyDeviceToHost, s), "read");
+  INIT_TRY(cudaMemcpyAsync(&flag, c->ints + I_STATUS, 4, cudaMemcpyDeviceToHost, s), "read");
+  INIT_TRY(cudaStreamSynchronize(s), "sync");
+#undef INIT_TRY
+  if (flag & 1) return bad(TO_E_INVALID, "supports not closed under coarse-grid interpolation");
+  if (flag & 2) return bad(TO_E_INVALID, "load vector is nonzero on a fixed DOF");
+  if (!(f2 > 0.0) || !isfinite(f2)) return bad(TO_E_INVALID, "load vector is zero or not finite");
+  c->fnorm = sqrt(f2);
+  cudaMemsetAsync(c->ints, 0, I_NINTS * sizeof(int), s);
+  *out = c;
+  return TO_OK;
+}
+
+void to_destroy(to_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& u : ctx->ev_used) {
+    cudaEventDestroy(u.second.first);
+    cudaEventDestroy(u.second.second);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+to_status to_set_density(to_ctx* c, const double* rho_phys) {
+  if (!c || !rho_phys) return fail(c, TO_E_INVALID, "NULL argument");
+  cudaStream_t s = c->stream;
+  const to_mesh_desc& d = c->desc;
+  CUDA_TRY(c, cudaMemcpyAsync(c->rho_phys, rho_phys, c->nel * 8, cudaMemcpyDeviceToDevice, s),
+           "copy rho");
+  if (c->have_density) std::swap(c->E64, c->Eprev64);
+  LAUNCH(c, launch_simp(c->nel, c->rho_phys, d.E0, d.Emin, d.penal, c->E64, c->E32, s), "simp");
+  if (!c->have_density)
+    CUDA_TRY(c, cudaMemcpyAsync(c->Eprev64, c->E64, c->nel * 8, cudaMemcpyDeviceToDevice, s),
+             "copy E");
+  LAUNCH(c, launch_delta(c->nel, c->E64, c->Eprev64, c->dE64, c->dE32, c->Eprev32, s), "delta");
+  c->have_density = true;
+  c->hier_stale = true;
+  return TO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal solver pieces
+// ---------------------------------------------------------------------------
+static int mg_t(const to_ctx* c) { return c->mixed ? T_F32 : T_F64; }
+
+static const void* coef_for(const to_ctx* c, int op, int tc) {
+  if (tc == T_F64) return op == TO_OP_K ? (const void*)c->E64
+                        : op == TO_OP_KREF ? (const void*)c->Eprev64 : (const void*)c->dE64;
+  return op == TO_OP_K ? (const void*)c->E32
+         : op == TO_OP_KREF ? (const void*)c->Eprev32 : (const void*)c->dE32;
+}
+
+static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, const void* x,
+                           void* y, const void* b, const void* dinv, int epi) {
+  ApplyArgs a;
+  a.dim = c->dim;
+  a.g = c->lv[0].g;
+  a.mask = c->lv[0].mask;
+  a.tc = tc;
+  a.tx = tx;
+  a.ty = ty;
+  a.expl = false;
+  a.coef = coef_for(c, op, tc);
+  a.Kc = nullptr;
+  a.ke = tc == T_F64 ? (const void*)c->KE64 : (const void*)c->KE32;
+  a.x = x;
+  a.y = y;
+  a.b = b;
+  a.dinv = dinv;
+  a.omega = 0.6;
+  a.dfix = op == TO_OP_DK ? 0.0 : 1.0;
+  a.epi = epi;
+  return a;
+}
+
+static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, const void* b,
+                             int epi) {
+  ApplyArgs a;
+  const int t = mg_t(c);
+  a.dim = c->dim;
+  a.g = c->lv[l].g;
+  a.mask = c->lv[l].mask;
+  a.tc = t;
+  a.tx = t;
+  a.ty = t;
+  a.expl = true;
+  a.coef = nullptr;
+  a.Kc = c->lv[l].Kc;
+  a.ke = nullptr;
+  a.x = x;
+  a.y = y;
+  a.b = b;
+  a.dinv = c->lv[l].dinv;
+  a.omega = 0.6;
+  a.dfix = 1.0;
+  a.epi = epi;
+  return a;
+}
+
+// Algorithmic DRAM bytes of one operator launch: every input and output
+// array touched once (the 3^dim neighbourhood reuse is not counted).
+static double apply_bytes(const ApplyArgs& a) {
+  const double sx = a.tx == T_F64 ? 8.0 : 4.0, sy = a.ty == T_F64 ? 8.0 : 4.0;
+  const double sc = a.tc == T_F64 ? 8.0 : 4.0;
+  const double n = (double)a.dim * (double)a.g.nn, nel = (double)a.g.nel;
+  const int nd = a.dim * (1 << a.dim);
+  double b = n * (sx + sy) + (double)a.g.nn;          // x, y, node masks
+  b += a.expl ? (double)nd * nd * nel * sc : nel * sc; // element matrices or coefficients
+  if (a.epi != EPI_APPLY) b += n * sx;                 // right-hand side
+  if (a.epi == EPI_SMOOTH) b += n * sc;                // inverse diagonal
+  return b;
+}
+
+static to_status run_op(to_ctx* c, const ApplyArgs& a, const char* what) {
+  ProfScope ps(c, a.expl ? 1 : 0, apply_bytes(a));
+  LAUNCH(c, launch_apply(a, c->stream), what);
+  return TO_OK;
+}
+
+static to_status build_hierarchy(to_ctx* c) {
+  if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
+  cudaStream_t s = c->stream;
+  const int t = mg_t(c);
+  const void* E = t == T_F64 ? (const void*)c->E64 : (const void*)c->E32;
+  const void* KE = t == T_F64 ? (const void*)c->KE64 : (const void*)c->KE32;
+  const void* Qc = t == T_F64 ? (const void*)c->Qc64 : (const void*)c->Qc32;
+  LAUNCH(c, launch_diag(c->dim, c->lv[0].g, c->lv[0].mask, t, false, E, nullptr, KE,
+                        c->lv[0].dinv, s), "diag 0");
+  LAUNCH(c, launch_galerkin_fine(c->dim, t, c->lv[1].g, c->lv[0].g, E, Qc, c->lv[1].Kc, s),
+         "galerkin 1");
+  for (int l = 2; l < c->L; ++l)
+    LAUNCH(c, launch_galerkin_coarse(c->dim, t, c->lv[l].g, c->lv[l - 1].g, c->lv[l - 1].Kc,
+                                     c->lv[l].Kc, s), "galerkin l");
+  for (int l = 1; l < c->L; ++l)
+    LAUNCH(c, launch_diag(c->dim, c->lv[l].g, c->lv[l].mask, t, true, nullptr, c->lv[l].Kc,
+                          nullptr, c->lv[l].dinv, s), "diag l");
+  const int Lc = c->L - 1;
+  LAUNCH(c, launch_dense_assemble(c->dim, t, c->lv[Lc].g, c->lv[Lc].mask, c->lv[Lc].Kc,
+                                  c->Adense, s), "dense assemble");
+  LAUNCH(c, launch_cholesky_inverse(t, c->nc, c->Adense, c->Ainv, c->ints + I_STATUS, s),
+         "coarse factor");
+  c->hier_stale = false;
+  return TO_OK;
+}
+
+// z (float64, n) = V-cycle applied to r (float64, n)
+static to_status vcycle(to_ctx* c, const double* rin, double* zout) {
+  cudaStream_t s = c->stream;
+  const int t = mg_t(c);
+  const int L = c->L;
+  ProfScope ps(c, PK_VCYCLE);
+  LevelBuf* lv = c->lv;
+  // finest level: smoothing from zero, residual, restriction
+  LAUNCH(c, launch_presmooth(t, T_F64, lv[0].n, rin, lv[0].b, lv[0].dinv, 0.6, lv[0].z, s),
+         "presmooth 0");
+  to_status st;
+  if ((st = run_op(c, fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
+                                EPI_RESID), "resid 0")) != TO_OK)
+    return st;
+  LAUNCH(c, launch_restrict(c->dim, t, lv[0].g, lv[0].mask, lv[1].g, lv[1].mask, lv[0].r,
+                            lv[1].b, s), "restrict 0");
+  for (int l = 1; l < L - 1; ++l) {
+    LAUNCH(c, launch_presmooth(t, t, lv[l].n, lv[l].b, nullptr, lv[l].dinv, 0.6, lv[l].z, s),
+           "presmooth l");
+    if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID), "resid l")) != TO_OK)
+      return st;
+    LAUNCH(c, launch_restrict(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].mask,
+                              lv[l].r, lv[l + 1].b, s), "restrict l");
+  }
+  // coarsest grid: exact solve with the stored inverse
+  LAUNCH(c, launch_dense_gemv(t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s), "coarse solve");
+  // upward: interpolate, post-smooth (result of level l lands in z2)
+  for (int l = L - 2; l >= 1; --l) {
+    LAUNCH(c, launch_prolong_add(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].z2,
+                                 lv[l].z, s), "prolong l");
+    if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH),
+                     "postsmooth l")) != TO_OK)
+      return st;
+  }
+  LAUNCH(c, launch_prolong_add(c->dim, t, lv[0].g, lv[0].mask, lv[1].g, lv[1].z2, lv[0].z, s),
+         "prolong 0");
+  return run_op(c, fine_args(c, TO_OP_K, t, t, T_F64, lv[0].z, zout, lv[0].b, lv[0].dinv,
+                             EPI_SMOOTH), "postsmooth 0");
+}
+
+static to_status read_scalar(to_ctx* c, const double* dev, double* host) {
+  CUDA_TRY(c, cudaMemcpyAsync(host, dev, 8, cudaMemcpyDeviceToHost, c->stream), "read scalar");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  return TO_OK;
+}
+
+static to_status check_status(to_ctx* c) {
+  int st = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&st, c->ints + I_STATUS, 4, cudaMemcpyDeviceToHost, c->stream),
+           "read status");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  if (st) {
+    cudaMemsetAsync(c->ints + I_STATUS, 0, 4, c->stream);
+    return fail(c, TO_E_SINGULAR, "a factorisation met a non-positive pivot");
+  }
+  return TO_OK;
+}
+
+static int apply_tc(const to_ctx* c, int prec) {
+  if (prec == TO_PREC_FP64) return T_F64;
+  if (prec == TO_PREC_FP32) return T_F32;
+  return c->mixed ? T_F32 : T_F64;
+}
+
+static to_status apply_op(to_ctx* c, int op, int prec, const double* x, double* y) {
+  return run_op(c, fine_args(c, op, apply_tc(c, prec), T_F64, T_F64, x, y, nullptr, nullptr,
+                             EPI_APPLY), "apply");
+}
+
+static to_status parm_push(to_ctx* c, const double* u) {
+  cudaStream_t s = c->stream;
+  const int Ns = c->desc.n_parm;
+  const int slot = c->parm_head;
+  double* col = c->Phi + (size_t)slot * c->n;
+  LAUNCH(c, launch_dot(c->n, u, u, c->partials, c->counters + C_DOT, c->scal + S_NRM, s), "norm");
+  LAUNCH(c, launch_copy(c->n, u, col, s), "copy");
+  LAUNCH(c, launch_scale_by_inv_sqrt(c->n, col, c->scal + S_NRM, s), "scale");
+  c->parm_head = (c->parm_head + 1) % Ns;
+  c->parm_count = std::min(c->parm_count + 1, Ns);
+  return TO_OK;
+}
+
+extern "C" {
+
+to_status to_apply(to_ctx* c, int32_t op, int32_t prec, const double* x, double* y) {
+  if (!c || !x || !y || x == y) return fail(c, TO_E_INVALID, "bad arguments");
+  if (op < TO_OP_K || op > TO_OP_DK || prec < 0 || prec > 2) return fail(c, TO_E_INVALID, "bad op");
+  if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
+  return apply_op(c, op, prec, x, y);
+}
+
+to_status to_vcycle(to_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z || r == z) return fail(c, TO_E_INVALID, "bad arguments");
+  if (c->hier_stale) {
+    to_status st = build_hierarchy(c);
+    if (st != TO_OK) return st;
+  }
+  return vcycle(c, r, z);
+}
+
+to_status to_level_info(to_ctx* c, int32_t level, int32_t nel_out[3], int64_t* ndof) {
+  if (!c || level < 0 || level >= c->L || !nel_out || !ndof) return fail(c, TO_E_INVALID, "bad level");
+  nel_out[0] = c->lv[level].g.nx;
+  nel_out[1] = c->lv[level].g.ny;
+  nel_out[2] = c->lv[level].g.nz;
+  *ndof = c->lv[level].n;
+  return TO_OK;
+}
+
+to_status to_level_apply(to_ctx* c, int32_t level, const double* x, double* y) {
+  if (!c || !x || !y || level < 1 || level >= c->L) return fail(c, TO_E_INVALID, "bad arguments");
+  if (c->hier_stale) {
+    to_status st = build_hierarchy(c);
+    if (st != TO_OK) return st;
+  }
+  cudaStream_t s = c->stream;
+  LevelBuf& L = c->lv[level];
+  const int t = mg_t(c);
+  LAUNCH(c, launch_convert(T_F64, t, L.n, x, L.z2, s), "convert");
+  LAUNCH(c, launch_apply(coarse_args(c, level, L.z2, L.r, nullptr, EPI_APPLY), s), "level apply");
+  LAUNCH(c, launch_convert(t, T_F64, L.n, L.r, y, s), "convert");
+  return TO_OK;
+}
+
+to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, double* u,
+                        int32_t* iters, double* relres) {
+  if (!c || !u) return fail(c, TO_E_INVALID, "NULL argument");
+  if (!(rtol >= 0.0) || !isfinite(rtol) || maxit < 1) return fail(c, TO_E_INVALID, "bad rtol/maxit");
+  if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
+  cudaStream_t s = c->stream;
+  to_status st;
+  if (c->hier_stale && (st = build_hierarchy(c)) != TO_OK) return st;
+  const long long n = c->n;
+  const int tc = apply_tc(c, TO_PREC_NATIVE);
+  double* x = u;
+  if (!(flags & TO_SOLVE_WARM_START)) CUDA_TRY(c, cudaMemsetAsync(x, 0, n * 8, s), "zero u");
+  if ((st = run_op(c, fine_args(c, TO_OP_K, tc, T_F64, T_F64, x, c->r, c->f, nullptr,
+                                EPI_RESID), "initial residual")) != TO_OK)
+    return st;
+  LAUNCH(c, launch_dot(n, c->r, c->r, c->partials, c->counters + C_DOT, c->scal + S_RR, s), "rr");
+  double rr = 0.0;
+  if ((st = read_scalar(c, c->scal + S_RR, &rr)) != TO_OK) return st;
+  double rel = sqrt(rr) / c->fnorm;
+  int it = 0;
+  bool conv = rel < rtol;
+  if (!conv) {
+    if ((st = vcycle(c, c->r, c->z)) != TO_OK) return st;
+    LAUNCH(c, launch_dot(n, c->r, c->z, c->partials, c->counters + C_DOT, c->scal + S_RZ0, s), "rz");
+    LAUNCH(c, launch_copy(n, c->z, c->p, s), "p = z");
+    int cur = S_RZ0, nxt = S_RZ1;
+    for (it = 1; it <= maxit; ++it) {
+      if ((st = run_op(c, fine_args(c, TO_OP_K, tc, T_F64, T_F64, c->p, c->q, nullptr, nullptr,
+                                    EPI_APPLY), "q = K p")) != TO_OK)
+        return st;
+      LAUNCH(c, launch_dot(n, c->p, c->q, c->partials, c->counters + C_DOT, c->scal + S_PQ, s),
+             "pq");
+      LAUNCH(c, launch_cg_xr(n, x, c->r, c->p, c->q, c->scal, cur, S_PQ, S_RR, c->partials,
+                             c->counters + C_UPD, s), "x, r update");
+      if ((st = read_scalar(c, c->scal + S_RR, &rr)) != TO_OK) return st;
+      rel = sqrt(rr) / c->fnorm;
+      if (!isfinite(rel)) return fail(c, TO_E_SINGULAR, "CG breakdown (non-finite residual)");
+      if (rel < rtol) {
+        conv = true;
+        break;
+      }
+      if (it == maxit) break;
+      if ((st = vcycle(c, c->r, c->z)) != TO_OK) return st;
+      LAUNCH(c, launch_dot(n, c->r, c->z, c->partials, c->counters + C_DOT, c->scal + nxt, s),
+             "rz");
+      LAUNCH(c, launch_cg_p(n, c->p, c->z, c->scal, nxt, cur, s), "p update");
+      std::swap(cur, nxt);
+    }
+    if (it > maxit) it = maxit;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  if ((st = check_status(c)) != TO_OK) return st;
+  if (flags & TO_SOLVE_PUSH_PARM) {
+    if ((st = parm_push(c, x)) != TO_OK) return st;
+  }
+  if (!conv) return fail(c, TO_E_NOT_CONVERGED, "MGCG reached maxit");
+  return TO_OK;
+}
+
+to_status to_parm_push(to_ctx* c, const double* u) {
+  if (!c || !u) return fail(c, TO_E_INVALID, "NULL argument");
+  return parm_push(c, u);
+}
+
+to_status to_parm_count(to_ctx* c, int32_t* count) {
+  if (!c || !count) return fail(c, TO_E_INVALID, "NULL argument");
+  *count = c->parm_count;
+  return TO_OK;
+}
+
+to_status to_parm_reset(to_ctx* c) {
+  if (!c) return fail(c, TO_E_INVALID, "NULL argument");
+  c->parm_count = c->parm_head = 0;
+  return TO_OK;
+}
+
+to_status to_carm_build(to_ctx* c, const double* u_last) {
+  if (!c || !u_last) return fail(c, TO_E_INVALID, "NULL argument");
+  if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
+  if (c->parm_count < c->desc.n_parm) return fail(c, TO_E_STATE, "PARM is not full");
+  cudaStream_t s = c->stream;
+  const long long n = c->n;
+  const int Ns = c->desc.n_parm, m = c->desc.n_carm;
+  to_status st;
+  double* small = c->small;
+  // K_Phi = Phi^T K_ref Phi  (Eq. 15)
+  for (int i = 0; i < Ns; ++i)
+    if ((st = apply_op(c, TO_OP_KREF, TO_PREC_NATIVE, c->Phi + (size_t)i * n,
+                       c->KPhi + (size_t)i * n)) != TO_OK)
+      return st;
+  LAUNCH(c, launch_multidot(n, c->Phi, Ns, nullptr, c->KPhi, Ns, nullptr, small + SM_KPHI, Ns,
+                            c->partials, c->counters + C_MULTI, s), "K_Phi");
+  LAUNCH(c, launch_small_spd_inverse(Ns, nullptr, small + SM_KPHI, small + SM_KPHI_INV,
+                                     c->ints + I_STATUS, s), "K_Phi inverse");
+  // r_1 = u_last; r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}  (Eq. 18-20, 26)
+  LAUNCH(c, launch_copy(n, u_last, c->R, s), "r1");
+  for (int i = 1; i < m; ++i) {
+    if ((st = apply_op(c, TO_OP_DK, TO_PREC_NATIVE, c->R + (size_t)(i - 1) * n, c->t)) != TO_OK)
+      return st;
+    LAUNCH(c, launch_multidot(n, c->Phi, Ns, nullptr, c->t, 1, nullptr, small + SM_Z, Ns,
+                              c->partials, c->counters + C_MULTI, s), "Phi^T t");
+    LAUNCH(c, launch_small_matvec(Ns, nullptr, small + SM_KPHI_INV, small + SM_Z, small + SM_W,
+                                  -1.0, s), "K_Phi^-1 z");
+    LAUNCH(c, launch_combine(n, c->Phi, Ns, nullptr, small + SM_W, 1.0, 0.0,
+                             c->R + (size_t)i * n, nullptr, nullptr, c->partials,
+                             c->counters + C_UPD, s), "r_i");
+  }
+  // modified Gram-Schmidt with re-orthogonalisation, in place
+  CUDA_TRY(c, cudaMemsetAsync(c->ints + I_KCOUNT, 0, sizeof(int), s), "reset k");
+  for (int i = 0; i < m; ++i) {
+    double* ri = c->R + (size_t)i * n;
+    LAUNCH(c, launch_dot(n, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM0, s), "|r|");
+    for (int pass = 0; pass < 2; ++pass) {
+      LAUNCH(c, launch_multidot(n, c->R, MAXB, c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
+                                MAXB, c->partials, c->counters + C_MULTI, s), "GS dots");
+      LAUNCH(c, launch_combine(n, c->R, MAXB, c->ints + I_KCOUNT, small + SM_H, -1.0, 1.0, ri,
+                               nullptr, nullptr, c->partials, c->counters + C_UPD, s), "GS axpy");
+    }
+    LAUNCH(c, launch_dot(n, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM1, s), "|r|");
+    LAUNCH(c, launch_gs_accept(n, c->R, i, c->scal, S_NRM0, S_NRM1, 1e-10, c->ints, s),
+           "GS accept");
+  }
+  int k = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&k, c->ints + I_KCOUNT, 4, cudaMemcpyDeviceToHost, s), "read k");
+  CUDA_TRY(c, cudaStreamSynchronize(s), "sync");
+  c->carm_built = k;
+  if (k < 1) return fail(c, TO_E_SINGULAR, "CARM basis is empty");
+  return TO_OK;
+}
+
+to_status to_carm_solve(to_ctx* c, double* u, double* eps, double* eps_dev) {
+  if (!c || !u) return fail(c, TO_E_INVALID, "NULL argument");
+  if (c->carm_built < 1) return fail(c, TO_E_STATE, "to_carm_build has not been called");
+  cudaStream_t s = c->stream;
+  const long long n = c->n;
+  const int k = c->carm_built;
+  to_status st;
+  double* small = c->small;
+  for (int j = 0; j < k; ++j)
+    if ((st = apply_op(c, TO_OP_K, TO_PREC_NATIVE, c->R + (size_t)j * n, c->Q + (size_t)j * n)) != TO_OK)
+      return st;
+  LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->Q, k, nullptr, small + SM_KR, k, c->partials,
+                            c->counters + C_MULTI, s), "K_R");
+  LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->f, 1, nullptr, small + SM_FR, k, c->partials,
+                            c->counters + C_MULTI, s), "f_R");
+  LAUNCH(c, launch_small_chol_solve(k, nullptr, small + SM_KR, small + SM_FR, small + SM_Y,
+                                    c->ints + I_STATUS, s), "K_R y = f_R");
+  LAUNCH(c, launch_combine(n, c->R, k, nullptr, small + SM_Y, 1.0, 0.0, u, nullptr, nullptr,
+                           c->partials, c->counters + C_UPD, s), "u = R y");
+  LAUNCH(c, launch_combine(n, c->Q, k, nullptr, small + SM_Y, 1.0, 0.0, c->t, c->f,
+                           c->scal + S_RR, c->partials, c->counters + C_UPD, s), "K R y - f");
+  LAUNCH(c, launch_eps(c->scal, S_RR, S_FNORM2, c->scal + S_EPS, s), "eps");
+  if (eps_dev)
+    CUDA_TRY(c, cudaMemcpyAsync(eps_dev, c->scal + S_EPS, 8, cudaMemcpyDeviceToDevice, s), "eps");
+  if (eps) {
+    if ((st = read_scalar(c, c->scal + S_EPS, eps)) != TO_OK) return st;
+  }
+  return TO_OK;
+}
+
+to_status to_sensitivity(to_ctx* c, const double* u, double* compliance_dev, double* dc) {
+  if (!c || !u || !compliance_dev || !dc) return fail(c, TO_E_INVALID, "NULL argument");
+  if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
+  const to_mesh_desc& d = c->desc;
+  LAUNCH(c, launch_sensitivity(c->dim, c->lv[0].g, c->lv[0].mask, c->KE64, u, c->E64,
+                               c->rho_phys, d.penal, d.E0, d.Emin, dc, compliance_dev,
+                               c->partials, c->counters + C_SENS, c->stream), "sensitivity");
+  return TO_OK;
+}
+
+to_status to_filter(to_ctx* c, int32_t mode, const double* in, double* out) {
+  if (!c || !in || !out || in == out) return fail(c, TO_E_INVALID, "bad arguments");
+  if (mode != TO_FILTER_DENSITY && mode != TO_FILTER_SENS) return fail(c, TO_E_INVALID, "bad mode");
+  LAUNCH(c, launch_filter(c->dim, c->lv[0].g, c->stencil, mode, c->Hs, in, out, c->stream),
+         "filter");
+  return TO_OK;
+}
+
+to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_f,
+                       const double* dv_f, double* rho, double* change_dev) {
+  if (!c || !dc_f || !dv_f || !rho) return fail(c, TO_E_INVALID, "NULL argument");
+  if (!(volfrac > 0.0 && volfrac <= 1.0) || !(move > 0.0 && move <= 1.0))
+    return fail(c, TO_E_INVALID, "bad volfrac/move");
+  cudaStream_t s = c->stream;
+  const long long nel = c->nel;
+  const double target = volfrac * (double)nel;
+  LAUNCH(c, launch_oc_prep(nel, rho, dc_f, dv_f, c->oc_a, c->scal, s), "oc prep");
+  // bisection steps run on the device; a step is a no-op once converged
+  for (int chunk = 0; chunk < 8; ++chunk) {
+    for (int q = 0; q < 32; ++q)
+      LAUNCH(c, launch_oc_step(nel, rho, c->oc_a, dv_f, move, target, c->scal, c->partials,
+                               c->counters + C_OC, s), "oc step");
+    double lr[2];
+    CUDA_TRY(c, cudaMemcpyAsync(lr, c->scal + S_OC_L1, 16, cudaMemcpyDeviceToHost, s), "read");
+    CUDA_TRY(c, cudaStreamSynchronize(s), "sync");
+    if (!((lr[1] - lr[0]) > 1e-13 * (lr[0] + lr[1]))) break;
+  }
+  LAUNCH(c, launch_oc_final(nel, rho, c->oc_a, move, c->scal, change_dev, c->partials,
+                            c->counters + C_MAX, s), "oc final");
+  return TO_OK;
+}
+
+to_status to_profile_enable(to_ctx* c, int32_t on) {
+  if (!c) return fail(c, TO_E_INVALID, "NULL ctx");
+  c->prof = on != 0;
+  return TO_OK;
+}
+
+to_status to_profile_read(to_ctx* c, int32_t kind, int64_t* count, double* ms, double* bytes) {
+  if (!c || !count || !ms || kind < 0 || kind >= PK_N) return fail(c, TO_E_INVALID, "bad arguments");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  int64_t cnt = 0;
+  double tot = 0.0, byt = 0.0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> keep;
+  std::vector<double> keep_b;
+  for (size_t q = 0; q < c->ev_used.size(); ++q) {
+    auto& u = c->ev_used[q];
+    if (u.first == kind) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, u.second.first, u.second.second) == cudaSuccess) {
+        tot += t;
+        byt += c->ev_bytes[q];
+        cnt++;
+      }
+      c->ev_pool.push_back(u.second.first);
+      c->ev_pool.push_back(u.second.second);
+    } else {
+      keep.push_back(u);
+      keep_b.push_back(c->ev_bytes[q]);
+    }
+  }
+  c->ev_used.swap(keep);
+  c->ev_bytes.swap(keep_b);
+  *count = cnt;
+  *ms = tot;
+  if (bytes) *bytes = byt;
+  return TO_OK;
+}
+
+to_status to_launch_count(to_ctx* c, int64_t* count, int32_t reset) {
+  if (!c || !count) return fail(c, TO_E_INVALID, "bad arguments");
+  *count = c->launches;
+  if (reset) c->launches = 0;
+  return TO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,250 @@
+// Internal definitions shared by the translation units of libtopo.so.
+// Nothing here is part of the public ABI (include/topo.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/topo.h"
+
+namespace topo {
+
+constexpr int MAXL = 10;        // multigrid levels
+constexpr int MAXB = 16;        // PARM / CARM columns
+constexpr int RED_BLOCKS = 608; // fixed grid of deterministic reductions (4 x 152 SMs)
+constexpr int RED_THREADS = 256;
+constexpr int MAX_STENCIL = 128;
+
+// ---------------------------------------------------------------------------
+// Geometry of one grid level.  2D grids have nz = 0 elements and nnz = 1.
+// ---------------------------------------------------------------------------
+struct GridP {
+  int nx, ny, nz;      // elements per axis
+  int nnx, nny, nnz;   // nodes per axis
+  long long nn, nel;   // node and element counts
+};
+
+template <int DIM>
+struct Geo {
+  static constexpr int NPE = 1 << DIM;            // nodes per element
+  static constexpr int ND = DIM * NPE;            // DOFs per element
+  static constexpr int NB = (DIM == 2) ? 9 : 27;  // nodes in a 3^DIM neighbourhood
+};
+
+template <typename T, int ND>
+struct KEP {
+  T v[ND * ND];
+};
+
+struct StencilP {
+  int count;
+  int d[MAX_STENCIL][3];
+  double w[MAX_STENCIL];
+};
+
+// Scalar slots in ctx->scal (float64, device)
+enum Slot {
+  S_RR = 0, S_PQ = 1, S_RZ0 = 2, S_RZ1 = 3, S_NRM = 4, S_TMP = 5, S_COMPL = 6,
+  S_OC_L1 = 7, S_OC_L2 = 8, S_OC_VOL = 9, S_OC_DONE = 10, S_CHANGE = 11, S_EPS = 12,
+  S_NRM0 = 13, S_NRM1 = 14, S_FNORM2 = 15, S_FLAG = 16,
+  S_NSLOTS = 64
+};
+
+// Small-matrix area layout in ctx->small (float64, device), offsets in doubles
+enum SmallOff {
+  SM_KPHI = 0,                      // N_s x N_s
+  SM_KPHI_INV = SM_KPHI + 256,      // N_s x N_s
+  SM_Z = SM_KPHI_INV + 256,         // N_s (Phi^T t)
+  SM_W = SM_Z + 16,                 // N_s (K_Phi^{-1} z), negated
+  SM_H = SM_W + 16,                 // GS coefficients
+  SM_KR = SM_H + 16,                // m x m
+  SM_FR = SM_KR + 256,              // m
+  SM_Y = SM_FR + 16,                // m
+  SM_TOTAL = SM_Y + 16 + 64
+};
+
+enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_NINTS = 16 };
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction of NV float64 values, finished by the last
+// block of the grid, which sums the per-block partials in block order.
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* >= NV*32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[q * 32 + warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = lane < nw ? sh[q * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      v[q] = s;  // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+template <int NV>
+__device__ __forceinline__ void block_max(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+    if (lane == 0) sh[q * 32 + warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = lane < nw ? sh[q * 32 + lane] : -1e308;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+      v[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Writes this block's partials; returns true in all threads of the last block
+// to arrive (which may then read all partials).  counter is reset by it.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(const double (&v)[NV], double* partials,
+                                                 unsigned* counter) {
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) partials[(size_t)blockIdx.x * NV + q] = v[q];
+    __threadfence();
+    unsigned ticket = atomicAdd(counter, 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+// In the last block: out[q] = sum over blocks (in order) of partial q.
+template <int NV>
+__device__ __forceinline__ void finish_sum(const double* partials, unsigned* counter,
+                                           double (&out)[NV], double* sh) {
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  // each thread sums a fixed, strided subset of blocks; then a fixed tree
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] += partials[(size_t)b * NV + q];
+  }
+  block_sum<NV>(acc, sh);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = acc[q];
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <int NV>
+__device__ __forceinline__ void finish_max(const double* partials, unsigned* counter,
+                                           double (&out)[NV], double* sh) {
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = -1e308;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = fmax(acc[q], partials[(size_t)b * NV + q]);
+  }
+  block_max<NV>(acc, sh);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = acc[q];
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+}  // namespace topo
+
+// ---------------------------------------------------------------------------
+// Host-side context
+// ---------------------------------------------------------------------------
+struct LevelBuf {
+  topo::GridP g;
+  long long n;           // DOFs
+  uint8_t* mask;         // per node: bit c set = DOF c fixed
+  void* dinv;            // T[n]
+  void* b;               // T[n]
+  void* z;               // T[n]
+  void* z2;              // T[n]
+  void* r;               // T[n]
+  void* Kc;              // T[ND*ND*nel], entry-major (levels >= 1)
+};
+
+struct to_ctx {
+  to_mesh_desc desc;
+  int dim, nd, npe, L;
+  bool mixed;
+  cudaStream_t stream;
+  LevelBuf lv[topo::MAXL];
+  long long n, nel, nn;
+  int nc;                // DOFs of the coarsest level
+  // fine-level coefficient arrays
+  double *E64, *Eprev64, *dE64, *rho_phys;
+  float *E32, *Eprev32, *dE32;
+  double *f, *Hs, *oc_a;
+  // CG
+  double *r, *z, *p, *q;
+  // PARM / CARM
+  double *Phi, *KPhi, *R, *Q, *t;
+  int parm_count, parm_head, carm_built;
+  // Galerkin tables (level-1 child matrices Q_c), float64 and float32
+  double* Qc64;
+  float* Qc32;
+  // coarsest level
+  void* Adense;
+  void* Ainv;
+  // reductions and scalars
+  double* partials;
+  unsigned* counters;
+  double* scal;
+  double* small;
+  int* ints;
+  // host state
+  double fnorm;
+  bool have_density, hier_stale;
+  double KE64[576];
+  float KE32[576];
+  topo::StencilP stencil;
+  std::string last_error;
+  long long launches;
+  bool prof;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  std::vector<double> ev_bytes;
+};
+
+namespace topo {
+
+// Counter slots (ctx->counters, one per reduction site in flight)
+enum Counter { C_DOT = 0, C_MULTI = 1 /* .. +16 */, C_UPD = 20, C_OC = 21, C_SENS = 22,
+               C_MAX = 23, C_NCOUNTERS = 32 };
+
+// --- launch helpers (host) ---
+void note_launch(to_ctx* c);
+cudaError_t check_launch(to_ctx* c, const char* what);
+void prof_begin(to_ctx* c, int kind, cudaEvent_t* e0);
+void prof_end(to_ctx* c, int kind, cudaEvent_t e0);
+
+inline int nblocks(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace topo

@@ -1,0 +1,142 @@
+"""Design loop of AARMR topology optimisation (Fig. 1, Algorithm 1) driven
+through the C ABI.
+
+The host decides which branch runs (MGCG or CARM) from scalars the device
+returns (the CG residual, eps of Eq. 29); every arithmetic step runs in
+libtopo.so kernels.  PyTorch only provides device memory and the stream.
+
+Readings (shared with the oracle): MGCG for design iterations k <= N_on,
+whose last N_s solutions fill the PARM; from k = N_on + 1 the CARM is
+built from u_last and accepted when eps < eps_tol, otherwise MGCG is
+warm-started from the reduced solution and its result pushed into the PARM.
+"""
+
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from . import binding as B
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@dataclass
+class IterLog:
+    k: int
+    branch: str
+    compliance: float
+    eps: Optional[float]
+    cg_iters: int
+    change: float
+    seconds: float
+
+
+class TopoSolver:
+    """One optimisation job resident on the GPU."""
+
+    def __init__(self, prob, device="cuda", stream=None, precision: Optional[str] = None):
+        torch = _torch()
+        self.prob = prob
+        self.device = torch.device(device)
+        prec = (precision or prob.precision)
+        self.precision = prec
+        self.desc = B.make_desc(prob.dim, (prob.nelx, prob.nely, prob.nelz), prob.E0, prob.Emin,
+                                prob.nu, prob.penal, prob.rmin, prob.mg_levels,
+                                B.TO_MIXED if prec == "mixed" else B.TO_FP64, prob.n_parm,
+                                prob.n_carm)
+        self.ws_bytes = B.to_workspace_bytes(self.desc)
+        raw = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-raw.data_ptr()) % 256
+        self._ws_raw = raw
+        self.ws = raw[off:off + self.ws_bytes]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):
+            fixed = torch.from_numpy(prob.fixed.astype(np.uint8)).to(self.device)
+            f = torch.from_numpy(prob.f.astype(np.float64)).to(self.device)
+            self.ctx = B.to_mesh_init(self.desc, fixed, f, self.ws, self.stream.cuda_stream)
+            self._keep = (fixed, f)
+            nel, n = prob.nel, prob.ndof
+            self.rho = torch.from_numpy(prob.rho0.astype(np.float64)).to(self.device)
+            self.rho_phys = torch.empty(nel, **f64)
+            self.dc = torch.empty(nel, **f64)
+            self.dc_f = torch.empty(nel, **f64)
+            self.dv_f = torch.empty(nel, **f64)
+            self.u = torch.zeros(n, **f64)
+            self.scalars = torch.zeros(4, **f64)       # compliance, change, eps, spare
+            ones = torch.ones(nel, **f64)
+            B.to_filter(self.ctx, B.TO_FILTER_SENS, ones, self.dv_f)
+        self.k = 0
+        self.history: List[IterLog] = []
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            B.to_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- one design iteration -------------------------------------------------
+    def step(self, read_compliance: bool = True) -> IterLog:
+        p = self.prob
+        ctx = self.ctx
+        self.k += 1
+        k = self.k
+        t0 = time.perf_counter()
+        B.to_filter(ctx, B.TO_FILTER_DENSITY, self.rho, self.rho_phys)
+        B.to_set_density(ctx, self.rho_phys)
+        eps = None
+        iters = 0
+        if k <= p.n_on or B.to_parm_count(ctx) < p.n_parm:
+            flags = (B.TO_SOLVE_WARM_START if k > 1 else 0)
+            if k > p.n_on - p.n_parm:
+                flags |= B.TO_SOLVE_PUSH_PARM
+            iters, _, _ = B.to_mgcg_solve(ctx, p.rtol, p.maxit, flags, self.u)
+            branch = "mgcg"
+        else:
+            B.to_carm_build(ctx, self.u)
+            eps = B.to_carm_solve(ctx, self.u, self.scalars[2:3])
+            if eps < p.eps_tol:
+                branch = "carm"
+            else:
+                iters, _, _ = B.to_mgcg_solve(ctx, p.rtol, p.maxit,
+                                              B.TO_SOLVE_WARM_START | B.TO_SOLVE_PUSH_PARM,
+                                              self.u)
+                branch = "mgcg-fallback"
+        B.to_sensitivity(ctx, self.u, self.scalars[0:1], self.dc)
+        B.to_filter(ctx, B.TO_FILTER_SENS, self.dc, self.dc_f)
+        B.to_oc_update(ctx, p.volfrac, p.move, self.dc_f, self.dv_f, self.rho,
+                       self.scalars[1:2])
+        C = change = float("nan")
+        if read_compliance:
+            vals = self.scalars[:2].cpu().numpy()
+            C, change = float(vals[0]), float(vals[1])
+        log = IterLog(k, branch, C, eps, iters, change, time.perf_counter() - t0)
+        self.history.append(log)
+        return log
+
+    def run(self, n_iter: Optional[int] = None) -> List[IterLog]:
+        for _ in range(n_iter if n_iter is not None else self.prob.n_iter):
+            self.step()
+        return self.history
+
+
+def run_job(prob, n_iter=None, device="cuda", precision=None):
+    s = TopoSolver(prob, device=device, precision=precision)
+    try:
+        hist = s.run(n_iter)
+        rho = s.rho.cpu().numpy()
+    finally:
+        s.close()
+    return rho, hist
