@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="48x24x24 instead (quick checks)")
+    ap.add_argument("--kernel", default=None, choices=[None, "apply"],
+                    help="time one kernel alone (profiling) instead of the design loop")
+    ap.add_argument("--kernel-prec", default="fp32", choices=["fp32", "fp64"])
     return ap.parse_args()
 
 
@@ -348,8 +351,38 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_kernel_apply(args):
+    """Times only the finest-grid stiffness operator K x on the bench
+    workload (uniform design), for profiling: W untimed, K timed launches."""
+    import numpy as np
+    import torch
+    from paper_2205_00385_gb300 import binding as B
+    from paper_2205_00385_gb300.driver import TopoSolver
+    p = _problem(args)
+    s = TopoSolver(p)
+    rho = torch.full((p.nel,), p.volfrac, dtype=torch.float64, device="cuda")
+    B.to_set_density(s.ctx, rho)
+    x = torch.from_numpy(np.random.default_rng(1).standard_normal(p.ndof)).cuda()
+    y = torch.empty_like(x)
+    prec = B.TO_PREC_FP32 if args.kernel_prec == "fp32" else B.TO_PREC_FP64
+    for _ in range(args.warmup):
+        B.to_apply(s.ctx, B.TO_OP_K, prec, x, y)
+    B.to_profile_enable(s.ctx, True)
+    B.to_profile_read(s.ctx, 0)
+    for _ in range(args.steps):
+        B.to_apply(s.ctx, B.TO_OP_K, prec, x, y)
+    n, ms, by = B.to_profile_read(s.ctx, 0)
+    s.close()
+    return {"kernel": "k_apply", "precision": args.kernel_prec, "launches": n,
+            "avg_us": ms / n * 1e3, "GB/s": by / (ms / 1e3) / 1e9,
+            "bytes_per_launch": by / n, "workload": p.name + f" {p.nelx}x{p.nely}x{p.nelz}"}
+
+
 def main():
     args = _args()
+    if args.kernel == "apply":
+        print(json.dumps(run_kernel_apply(args)), flush=True)
+        return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)

@@ -106,7 +106,11 @@ to_status to_set_density(to_ctx* ctx, const double* rho_phys);
 /* MGCG (Algorithm 2 as preconditioner of CG) for K(E) u = f.
  * u (dev, float64, n): in: initial guess if flags has TO_SOLVE_WARM_START
  *   (else ignored and zero is used); out: the solution.
- * rtol: stop when ||f - K u|| / ||f|| < rtol (recursive residual);
+ * rtol: stop when ||f - K u|| / ||f|| < rtol.  In TO_FP64 the CG recursive
+ *   residual is tested; in TO_MIXED (float32 operator inside CG) the
+ *   recursive residual is replaced by the float64 true residual f - K u
+ *   whenever it has dropped 100x since the last replacement, and
+ *   convergence is declared on the true residual.
  * maxit: CG iteration cap (>= 1).  On the cap the last iterate is returned
  *   with TO_E_NOT_CONVERGED.
  * flags & TO_SOLVE_PUSH_PARM: append u/||u|| to the PARM (Eq. 28), dropping
@@ -131,7 +135,8 @@ to_status to_parm_reset(to_ctx* ctx);
  * dropped.  Needs a full PARM (else TO_E_STATE). */
 to_status to_carm_build(to_ctx* ctx, const double* u_last);
 
-/* Reduced solve on the last CARM basis: K_R = R~^T K R~, f_R = R~^T f,
+/* Reduced solve on the last CARM basis (K R~ is always formed with the
+ * float64 operator, also in TO_MIXED): K_R = R~^T K R~, f_R = R~^T f,
  * y = K_R^{-1} f_R (Eq. 23-24), u = R~ y (Eq. 25, dev float64 n, out) and
  * eps = ||K R~ y - f|| / ||f|| (Eq. 29) written to eps (host, may be NULL;
  * synchronises when given) and to eps_dev (dev, may be NULL). */

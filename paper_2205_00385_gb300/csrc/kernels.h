@@ -24,6 +24,8 @@ struct ApplyArgs {
   const void* coef;    // [nel] of type tc (fine level)
   const void* Kc;      // [ND*ND*nel] of type tc (coarse levels)
   const void* ke;      // host pointer to the ND*ND element matrix of type tc
+  const void* wht;     // host pointer to the 8x3x3 Walsh-Hadamard blocks of KE
+                       // (type tc; 3D finest grid only, else null)
   const void* x;
   void* y;
   const void* b;
@@ -32,6 +34,8 @@ struct ApplyArgs {
   int epi;
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+// Host: the eight 3x3 blocks of the hex8 KE in the corner Walsh-Hadamard basis
+void wht_blocks(const double* KE, double* out64, float* out32);
 
 // dinv = 1 / diag(A) (1 on fixed DOFs)
 cudaError_t launch_diag(int dim, const GridP& g, const uint8_t* mask, int tc, bool expl,

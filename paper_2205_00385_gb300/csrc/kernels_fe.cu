@@ -106,6 +106,164 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Finest-grid hex8 operator, element-by-element with a Walsh-Hadamard
+// factorisation of KE.
+//
+// KE commutes with the three coordinate reflections of the unit cube (which
+// permute corners a -> a xor s and flip the reflected displacement
+// component).  The Walsh-Hadamard transform over corners,
+// X[t][c] = sum_a (-1)^{popcount(a & t)} x[a][c], therefore block-diagonalises
+// KE: X[t][c] only couples to X[t'][c'] with t xor e_c == t' xor e_c', eight
+// 3x3 blocks.  KE x = FWHT( B FWHT(x) ) with B (including the 1/64 of the
+// two transforms) built on the host from KE, so one element costs
+// 72 adds + 72 FMA + 72 adds instead of 576 FMA.
+//
+// Each thread owns one element column (ex, ey) and streams up in z, keeping
+// the shared face's nodal values and partial forces in registers.  A block
+// covers 16 x 8 element columns and owns the 15 x 7 nodes whose four
+// surrounding columns it computes (owner-computes; one column of halo);
+// per z-layer the four column partials of each owned node are summed in
+// shared memory in a fixed order (deterministic, no atomics).
+// ---------------------------------------------------------------------------
+constexpr int WX = 16, WY = 8, WOX = WX - 1, WOY = WY - 1, WZC = 16;
+
+template <typename TC>
+struct WhtBlocks {
+  TC b[8][3][3];   // b[tau][c][c'] couples X[tau^e_c][c] and X[tau^e_c'][c']
+};
+
+template <typename TC>
+__device__ __forceinline__ void fwht8(TC (&v)[8]) {
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!(a & h)) {
+        const TC u = v[a], w = v[a + h];
+        v[a] = u + w;
+        v[a + h] = u - w;
+      }
+}
+
+template <typename TC, typename TX, typename TY, int EPI>
+__global__ void __launch_bounds__(WX * WY)
+    k_apply3_wht(GridP g, const uint8_t* __restrict__ mask, WhtBlocks<TC> kb,
+                 const TC* __restrict__ coef, const TX* __restrict__ x, TY* __restrict__ y,
+                 const TX* __restrict__ b, const TC* __restrict__ dinv, TC omega, TC dfix) {
+  using TE = typename std::conditional<(sizeof(TY) > sizeof(TC)), double, TC>::type;
+  __shared__ TC part[2][4][WY][WX][3];
+  const int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
+  const int x0 = blockIdx.x * WOX, y0 = blockIdx.y * WOY;
+  const int z0 = blockIdx.z * WZC, z1 = min(z0 + WZC, g.nnz);
+  const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
+  const bool col_ok = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
+  const long long plane = (long long)g.nnx * g.nny;
+
+  // nodal values of the current bottom face (corners 0..3) and top face
+  TC xb[4][3], xt[4][3];
+  TC acc[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[q][c] = TC(0);
+
+  auto load_face = [&](int kz, TC (&f)[4][3]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = ex + (q & 1), j = ey + (q >> 1);
+      bool in = col_ok && kz >= 0 && kz < g.nnz;
+      if (in) {
+        const long long nd = i + (long long)g.nnx * j + plane * kz;
+        const unsigned m = mask[nd];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[q][c] = ((m >> c) & 1u) ? TC(0) : TC(x[3 * nd + c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[q][c] = TC(0);
+      }
+    }
+  };
+
+  load_face(z0 - 1, xb);
+  const bool own = tx < WOX && ty < WOY && (x0 + tx) < g.nnx && (y0 + ty) < g.nny;
+  int buf = 0;
+  for (int ez = z0 - 1; ez < z1; ++ez) {
+    load_face(ez + 1, xt);
+    TC ye[8][3];
+    const bool el_ok = col_ok && ez >= 0 && ez < g.nz;
+    if (el_ok) {
+      const TC ce = coef[ex + (long long)g.nx * (ey + (long long)g.ny * ez)];
+      TC X[3][8];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          X[c][q] = xb[q][c];
+          X[c][q + 4] = xt[q][c];
+        }
+        fwht8<TC>(X[c]);
+      }
+      TC Y[3][8];
+#pragma unroll
+      for (int tau = 0; tau < 8; ++tau) {
+        TC zt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) zt[c] = ce * X[c][tau ^ (1 << c)];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          TC s = kb.b[tau][c][0] * zt[0];
+          s = fma(kb.b[tau][c][1], zt[1], s);
+          s = fma(kb.b[tau][c][2], zt[2], s);
+          Y[c][tau ^ (1 << c)] = s;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        fwht8<TC>(Y[c]);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) ye[a][c] = Y[c][a];
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ye[a][c] = TC(0);
+    }
+    // bottom face of this element completes this column's share of layer ez
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        part[buf][q][ty][tx][c] = acc[q][c] + ye[q][c];
+        acc[q][c] = ye[q + 4][c];
+        xb[q][c] = xt[q][c];
+      }
+    __syncthreads();
+    if (own && ez >= z0) {
+      // node (x0+tx, y0+ty, ez): corner 3 of column (tx,ty), corner 2 of
+      // (tx+1,ty), corner 1 of (tx,ty+1), corner 0 of (tx+1,ty+1)
+      const long long nd = (x0 + tx) + (long long)g.nnx * (y0 + ty) + plane * ez;
+      const unsigned m = mask[nd];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const TC s = ((part[buf][3][ty][tx][c] + part[buf][2][ty][tx + 1][c]) +
+                      part[buf][1][ty + 1][tx][c]) + part[buf][0][ty + 1][tx + 1][c];
+        const long long d = 3 * nd + c;
+        const TE Ax = ((m >> c) & 1u) ? TE(dfix) * TE(x[d]) : TE(s);
+        if (EPI == EPI_APPLY) {
+          y[d] = TY(Ax);
+        } else if (EPI == EPI_RESID) {
+          y[d] = TY(TE(b[d]) - Ax);
+        } else {
+          y[d] = TY(TE(x[d]) + TE(omega) * TE(dinv[d]) * (TE(b[d]) - Ax));
+        }
+      }
+    }
+    buf ^= 1;
+  }
+}
+
 template <int DIM, typename TC, bool EXPL>
 __global__ void __launch_bounds__(256)
     k_diag(GridP g, const uint8_t* __restrict__ mask, KEP<TC, Geo<DIM>::ND> ke,
@@ -192,9 +350,60 @@ static cudaError_t run_apply_dim(const ApplyArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+template <typename TC, typename TX, typename TY, int EPI>
+static cudaError_t run_wht(const ApplyArgs& a, cudaStream_t s) {
+  WhtBlocks<TC> kb;
+  const TC* src = static_cast<const TC*>(a.wht);
+  for (int q = 0; q < 72; ++q) (&kb.b[0][0][0])[q] = src[q];
+  dim3 grid((a.g.nnx + WOX - 1) / WOX, (a.g.nny + WOY - 1) / WOY, (a.g.nnz + WZC - 1) / WZC);
+  k_apply3_wht<TC, TX, TY, EPI><<<grid, WX * WY, 0, s>>>(
+      a.g, a.mask, kb, static_cast<const TC*>(a.coef), static_cast<const TX*>(a.x),
+      static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
+      TC(a.omega), TC(a.dfix));
+  return cudaGetLastError();
+}
+
+template <typename TC, typename TX, typename TY>
+static cudaError_t run_wht_epi(const ApplyArgs& a, cudaStream_t s) {
+  switch (a.epi) {
+    case EPI_APPLY: return run_wht<TC, TX, TY, EPI_APPLY>(a, s);
+    case EPI_RESID: return run_wht<TC, TX, TY, EPI_RESID>(a, s);
+    default: return run_wht<TC, TX, TY, EPI_SMOOTH>(a, s);
+  }
+}
+
+static cudaError_t run_wht_types(const ApplyArgs& a, cudaStream_t s) {
+  if (a.tc == T_F64) {
+    if (a.tx != T_F64 || a.ty != T_F64) return cudaErrorInvalidValue;
+    return run_wht_epi<double, double, double>(a, s);
+  }
+  if (a.tx == T_F64 && a.ty == T_F64) return run_wht_epi<float, double, double>(a, s);
+  if (a.tx == T_F32 && a.ty == T_F32) return run_wht_epi<float, float, float>(a, s);
+  if (a.tx == T_F32 && a.ty == T_F64) return run_wht_epi<float, float, double>(a, s);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   if (a.g.nn <= 0) return cudaSuccess;
+  if (a.dim == 3 && !a.expl && a.wht != nullptr) return run_wht_types(a, s);
   return a.dim == 2 ? run_apply_dim<2>(a, s) : run_apply_dim<3>(a, s);
+}
+
+void wht_blocks(const double* KE, double* out64, float* out32) {
+  // B = T KE T / 64 with T[(t,c),(a,c)] = (-1)^{popcount(a & t)}, restricted
+  // to the eight 3x3 blocks of characters tau = t xor e_c.
+  auto sgn = [](int a, int t) { return (__builtin_popcount(a & t) & 1) ? -1.0 : 1.0; };
+  for (int tau = 0; tau < 8; ++tau)
+    for (int c = 0; c < 3; ++c)
+      for (int cp = 0; cp < 3; ++cp) {
+        const int t = tau ^ (1 << c), tp = tau ^ (1 << cp);
+        double s = 0.0;
+        for (int a = 0; a < 8; ++a)
+          for (int ap = 0; ap < 8; ++ap) s += sgn(a, t) * KE[(3 * a + c) * 24 + 3 * ap + cp] * sgn(ap, tp);
+        s /= 64.0;
+        out64[(tau * 3 + c) * 3 + cp] = s;
+        out32[(tau * 3 + c) * 3 + cp] = (float)s;
+      }
 }
 
 template <int DIM, typename TC, bool EXPL>

@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(256)
 // ND*ND threads per coarse element; T = Kchild W in shared memory, then
 // Kc += W^T T, summed over the 2^DIM children.
 template <int DIM, typename T>
-__global__ void k_galerkin_coarse(GridP gc, GridP gf, const T* __restrict__ Kf,
-                                  T* __restrict__ Kc) {
+__global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
+    k_galerkin_coarse(GridP gc, GridP gf, const T* __restrict__ Kf, T* __restrict__ Kc) {
   constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
   __shared__ T sK[ND * ND];
   __shared__ T sT[ND * ND];

@@ -421,6 +421,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   }
   element_stiffness(c->dim, desc->nu, c->KE64);
   for (int q = 0; q < c->nd * c->nd; ++q) c->KE32[q] = (float)c->KE64[q];
+  if (c->dim == 3) wht_blocks(c->KE64, c->wht64, c->wht32);
   std::vector<double> Qc((size_t)c->npe * c->nd * c->nd);
   child_galerkin(c->dim, c->KE64, Qc.data());
   std::vector<float> Qc32(Qc.size());
@@ -529,6 +530,7 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.coef = coef_for(c, op, tc);
   a.Kc = nullptr;
   a.ke = tc == T_F64 ? (const void*)c->KE64 : (const void*)c->KE32;
+  a.wht = c->dim == 3 ? (tc == T_F64 ? (const void*)c->wht64 : (const void*)c->wht32) : nullptr;
   a.x = x;
   a.y = y;
   a.b = b;
@@ -553,6 +555,7 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
   a.coef = nullptr;
   a.Kc = c->lv[l].Kc;
   a.ke = nullptr;
+  a.wht = nullptr;
   a.x = x;
   a.y = y;
   a.b = b;
@@ -745,13 +748,20 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   const int tc = apply_tc(c, TO_PREC_NATIVE);
   double* x = u;
   if (!(flags & TO_SOLVE_WARM_START)) CUDA_TRY(c, cudaMemsetAsync(x, 0, n * 8, s), "zero u");
-  if ((st = run_op(c, fine_args(c, TO_OP_K, tc, T_F64, T_F64, x, c->r, c->f, nullptr,
-                                EPI_RESID), "initial residual")) != TO_OK)
-    return st;
-  LAUNCH(c, launch_dot(n, c->r, c->r, c->partials, c->counters + C_DOT, c->scal + S_RR, s), "rr");
+  // r = f - K x, always with the float64 operator (the true residual)
+  auto true_residual = [&](double* rr_out) -> to_status {
+    to_status e;
+    if ((e = run_op(c, fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, x, c->r, c->f, nullptr,
+                                 EPI_RESID), "true residual")) != TO_OK)
+      return e;
+    LAUNCH(c, launch_dot(n, c->r, c->r, c->partials, c->counters + C_DOT, c->scal + S_RR, s),
+           "rr");
+    return read_scalar(c, c->scal + S_RR, rr_out);
+  };
   double rr = 0.0;
-  if ((st = read_scalar(c, c->scal + S_RR, &rr)) != TO_OK) return st;
+  if ((st = true_residual(&rr)) != TO_OK) return st;
   double rel = sqrt(rr) / c->fnorm;
+  double rr_max = rr;          // largest residual since the last true-residual update
   int it = 0;
   bool conv = rel < rtol;
   if (!conv) {
@@ -770,6 +780,16 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
       if ((st = read_scalar(c, c->scal + S_RR, &rr)) != TO_OK) return st;
       rel = sqrt(rr) / c->fnorm;
       if (!isfinite(rel)) return fail(c, TO_E_SINGULAR, "CG breakdown (non-finite residual)");
+      // Reliable updates: with a float32 operator the recursive residual
+      // drifts from f - K x, so it is replaced by the float64 true residual
+      // whenever it has dropped 100x since the last replacement and before
+      // convergence is declared.  The search direction is kept.
+      if (tc != T_F64 && (rel < rtol || rr < 1e-4 * rr_max)) {
+        if ((st = true_residual(&rr)) != TO_OK) return st;
+        rel = sqrt(rr) / c->fnorm;
+        rr_max = rr;
+      }
+      rr_max = std::max(rr_max, rr);
       if (rel < rtol) {
         conv = true;
         break;
@@ -872,8 +892,10 @@ to_status to_carm_solve(to_ctx* c, double* u, double* eps, double* eps_dev) {
   const int k = c->carm_built;
   to_status st;
   double* small = c->small;
+  // K R~ enters the reduced matrix and the residual check, so it always uses
+  // the float64 operator; the basis itself may be built in float32.
   for (int j = 0; j < k; ++j)
-    if ((st = apply_op(c, TO_OP_K, TO_PREC_NATIVE, c->R + (size_t)j * n, c->Q + (size_t)j * n)) != TO_OK)
+    if ((st = apply_op(c, TO_OP_K, TO_PREC_FP64, c->R + (size_t)j * n, c->Q + (size_t)j * n)) != TO_OK)
       return st;
   LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->Q, k, nullptr, small + SM_KR, k, c->partials,
                             c->counters + C_MULTI, s), "K_R");

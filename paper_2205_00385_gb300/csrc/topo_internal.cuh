@@ -221,6 +221,8 @@ struct to_ctx {
   bool have_density, hier_stale;
   double KE64[576];
   float KE32[576];
+  double wht64[72];   // Walsh-Hadamard blocks of KE (3D only)
+  float wht32[72];
   topo::StencilP stencil;
   std::string last_error;
   long long launches;

@@ -6,11 +6,15 @@ Tolerances (relative unless stated):
   largest entry -- only summation order differs (<= ~30 terms per entry);
 * float32 apply: 1e-5 in norm (float32 rounding of KE, E and x, 24-term sums);
 * float64 V-cycle: 1e-10 (a few thousand operations per entry, the dense
-  coarse inverse is formed explicitly);
+  coarse inverse is formed explicitly); float32 V-cycle: 2e-3 (the coarsest
+  grid's explicit inverse is formed in float32 from a matrix of condition
+  ~1e4, so its relative error is ~1e-3);
 * MGCG solutions: compliance within 1e-10 (float64 path, rtol 1e-12) and
   1e-6 (mixed path) of the exact solve -- the stated per-solve targets;
-* filter, sensitivity, OC: 1e-12 (OC: 1e-10 absolute on rho, the bisection
-  bracket is 1e-13 relative).
+* filter, sensitivity filter: 1e-12; compliance and sensitivity: 1e-10
+  (u_e^T KE u_e cancels for elements in near-rigid motion: the rounding
+  error is relative to |u_e|^2 |KE|, up to ~1e3 times the element energy);
+  OC: 1e-10 absolute on rho (the bisection bracket is 1e-13 relative).
 """
 
 import numpy as np
@@ -120,7 +124,7 @@ def test_vcycle_parity(kind, kw):
         z = dev(np.zeros(g.ndof))
         B.to_vcycle(c.ctx, dev(r), z)
         z = host(z)
-    assert np.linalg.norm(z - z_ref) <= 1e-4 * np.linalg.norm(z_ref)
+    assert np.linalg.norm(z - z_ref) <= 2e-3 * np.linalg.norm(z_ref)
 
 
 def _snapshot_density(p, k):
@@ -180,8 +184,8 @@ def test_filter_sensitivity_oc_parity(kind, kw):
         Cd = dev(np.zeros(1))
         dcd = dev(np.zeros(g.nel))
         B.to_sensitivity(c.ctx, dev(u), Cd, dcd)
-        assert abs(host(Cd)[0] - C_ref) <= 1e-12 * C_ref
-        assert np.max(np.abs(host(dcd) - dc_ref)) <= 1e-12 * np.max(np.abs(dc_ref))
+        assert abs(host(Cd)[0] - C_ref) <= 1e-10 * C_ref
+        assert np.max(np.abs(host(dcd) - dc_ref)) <= 1e-10 * np.max(np.abs(dc_ref))
         dcf = dev(np.zeros(g.nel))
         B.to_filter(c.ctx, B.TO_FILTER_SENS, dev(dc_ref), dcf)
         assert np.max(np.abs(host(dcf) - dcf_ref)) <= 1e-12 * np.max(np.abs(dcf_ref))
