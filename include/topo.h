@@ -162,6 +162,27 @@ to_status to_filter(to_ctx* ctx, int32_t mode, const double* in, double* out);
 to_status to_oc_update(to_ctx* ctx, double volfrac, double move, const double* dc_f,
                        const double* dv_f, double* rho, double* change_dev);
 
+/* The optimality-criteria update of to_oc_update for callers that cannot
+ * allocate device memory (code running inside another runtime's memory pool
+ * or allocator hook, plugins whose host application owns all device
+ * allocations): it needs no context and no workspace and allocates nothing.
+ * The paper has no counterpart; this is an interface variant.
+ * nel: element count, 1 <= nel <= 2,097,152 (else TO_E_INVALID, nothing
+ *   launched).  volfrac, move, dc_f, dv_f, rho, change_dev: as for
+ *   to_oc_update (dev pointers; change_dev may be NULL).  stream: a
+ *   cudaStream_t (as void*) on which the kernels are enqueued; the call does
+ *   not synchronise.
+ * Scratch: a ~16 MiB file-scope device array of the library, which every GPU
+ * that loads libtopo.so holds until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (different streams, devices
+ * are separate) race and must be serialised by the caller.  Errors are
+ * reported by the return code and to_last_error(NULL). */
+to_status to_oc_update_noalloc(int64_t nel, double volfrac, double move, const double* dc_f,
+                               const double* dv_f, double* rho, double* change_dev,
+                               void* stream);
+
 /* y = op(x) for x, y dev float64 n (no aliasing).  op: TO_OP_K (current
  * stiffness with BCs, Eq. 7), TO_OP_KREF (reference stiffness, Eq. 8) or
  * TO_OP_DK (dK = K - K_ref, zero on fixed DOFs).  prec: TO_PREC_NATIVE

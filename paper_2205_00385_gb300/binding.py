@@ -56,6 +56,7 @@ _SIGS = {
     "to_sensitivity": [_VP, _VP, _VP, _VP],
     "to_filter": [_VP, C.c_int32, _VP, _VP],
     "to_oc_update": [_VP, C.c_double, C.c_double, _VP, _VP, _VP, _VP],
+    "to_oc_update_noalloc": [C.c_int64, C.c_double, C.c_double, _VP, _VP, _VP, _VP, _VP],
     "to_apply": [_VP, C.c_int32, C.c_int32, _VP, _VP],
     "to_vcycle": [_VP, _VP, _VP],
     "to_level_apply": [_VP, C.c_int32, _VP, _VP],
@@ -182,6 +183,13 @@ def to_filter(ctx, mode, x, out):
 def to_oc_update(ctx, volfrac, move, dc_f, dv_f, rho, change_dev=None):
     _check(load().to_oc_update(ctx, volfrac, move, _ptr(dc_f), _ptr(dv_f), _ptr(rho),
                                _ptr(change_dev)), ctx)
+
+
+def to_oc_update_noalloc(nel, volfrac, move, dc_f, dv_f, rho, change_dev, stream_handle):
+    """OC update without a context or workspace (scratch is a static device
+    array of the library); errors read from to_last_error(None)."""
+    _check(load().to_oc_update_noalloc(nel, volfrac, move, _ptr(dc_f), _ptr(dv_f), _ptr(rho),
+                                       _ptr(change_dev), stream_handle))
 
 
 def to_apply(ctx, op, prec, x, y):

@@ -23,6 +23,8 @@ void note_launch(to_ctx* c) {
   if (c) c->launches++;
 }
 
+void set_global_error(const std::string& msg) { g_last_error = msg; }
+
 }  // namespace topo
 
 static to_status fail(to_ctx* c, to_status st, const std::string& msg) {

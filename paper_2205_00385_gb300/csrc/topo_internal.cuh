@@ -240,6 +240,8 @@ enum Counter { C_DOT = 0, C_MULTI = 1 /* .. +16 */, C_UPD = 20, C_OC = 21, C_SEN
 
 // --- launch helpers (host) ---
 void note_launch(to_ctx* c);
+// message returned by to_last_error(NULL)
+void set_global_error(const std::string& msg);
 cudaError_t check_launch(to_ctx* c, const char* what);
 void prof_begin(to_ctx* c, int kind, cudaEvent_t* e0);
 void prof_end(to_ctx* c, int kind, cudaEvent_t e0);
