@@ -75,6 +75,15 @@ cudaError_t launch_cg_xr(long long n, double* x, double* r, const double* p, con
 // beta = scal[num] / scal[den]; p = z + beta p
 cudaError_t launch_cg_p(long long n, double* p, const double* z, const double* scal, int num,
                         int den, cudaStream_t s);
+// mixed-precision CG: float32 operator input/output shadows
+cudaError_t launch_dot_df(long long n, const double* a, const float* b, double* partials,
+                          unsigned* counter, double* out, cudaStream_t s);
+cudaError_t launch_cg_xr_f(long long n, double* x, double* r, const double* p, const float* q,
+                           double* scal, int num, int den, int rr, double* partials,
+                           unsigned* counter, cudaStream_t s);
+// p = z + beta p (num < 0: p = z); p32 = float(p)
+cudaError_t launch_cg_p_f(long long n, double* p, float* p32, const float* z, const double* scal,
+                          int num, int den, cudaStream_t s);
 cudaError_t launch_copy(long long n, const double* a, double* b, cudaStream_t s);
 cudaError_t launch_scale_by_inv_sqrt(long long n, double* a, const double* s2, cudaStream_t s);
 // G[i + ldg*j] = sum_k A[k + i*n] B[k + j*n], i < na (na_dev overrides when
@@ -108,8 +117,8 @@ cudaError_t launch_simp(long long nel, const double* rho, double E0, double Emin
 cudaError_t launch_delta(long long nel, const double* E, const double* Eprev, double* dE64,
                          float* dE32, float* Eprev32, cudaStream_t s);
 cudaError_t launch_filter(int dim, const GridP& g, const StencilP& st, int mode,
-                          const double* Hs, const double* in, double* out, cudaStream_t s);
-cudaError_t launch_filter_norm(int dim, const GridP& g, const StencilP& st, double* Hs,
+                          const double* invHs, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_filter_norm(int dim, const GridP& g, const StencilP& st, double* invHs,
                                cudaStream_t s);
 cudaError_t launch_sensitivity(int dim, const GridP& g, const uint8_t* mask, const double* ke,
                                const double* u, const double* E, const double* rho,

@@ -55,6 +55,60 @@ __global__ void __launch_bounds__(256)
     p[i] = fma(beta, p[i], z[i]);
 }
 
+// Mixed-precision CG kernels: p, x, r stay float64; the operator works on the
+// float32 shadows p32 -> q32 and the V-cycle returns z32.  Each float32
+// value is widened once per pass here, not inside the operator.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_dot_df(long long n, const double* __restrict__ a, const float* __restrict__ b,
+             double* partials, unsigned* counter, double* out) {
+  __shared__ double sh[32];
+  double v[1] = {0.0};
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    v[0] = fma(a[q], (double)b[q], v[0]);
+  block_sum<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) *out = o[0];
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_cg_xr_f(long long n, double* __restrict__ x, double* __restrict__ r,
+              const double* __restrict__ p, const float* __restrict__ q, double* scal, int num,
+              int den, int rr, double* partials, unsigned* counter) {
+  __shared__ double sh[32];
+  const double alpha = scal[num] / scal[den];
+  double v[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, (double)q[i], r[i]);
+    r[i] = ri;
+    v[0] = fma(ri, ri, v[0]);
+  }
+  block_sum<1>(v, sh);
+  if (publish_partials<1>(v, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) scal[rr] = o[0];
+  }
+}
+
+// p = z + beta p (beta = scal[num]/scal[den], or 0 when num < 0); p32 = p
+__global__ void __launch_bounds__(256)
+    k_cg_p_f(long long n, double* __restrict__ p, float* __restrict__ p32,
+             const float* __restrict__ z, const double* __restrict__ scal, int num, int den) {
+  const double beta = num >= 0 ? scal[num] / scal[den] : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double pi = num >= 0 ? fma(beta, p[i], (double)z[i]) : (double)z[i];
+    p[i] = pi;
+    p32[i] = (float)pi;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_copy(long long n, const double* __restrict__ a,
                                               double* __restrict__ b) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -336,6 +390,26 @@ cudaError_t launch_cg_xr(long long n, double* x, double* r, const double* p, con
 cudaError_t launch_cg_p(long long n, double* p, const double* z, const double* scal, int num,
                         int den, cudaStream_t s) {
   k_cg_p<<<vgrid(n), 256, 0, s>>>(n, p, z, scal, num, den);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_df(long long n, const double* a, const float* b, double* partials,
+                          unsigned* counter, double* out, cudaStream_t s) {
+  k_dot_df<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, b, partials, counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_xr_f(long long n, double* x, double* r, const double* p, const float* q,
+                           double* scal, int num, int den, int rr, double* partials,
+                           unsigned* counter, cudaStream_t s) {
+  k_cg_xr_f<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, scal, num, den, rr, partials,
+                                               counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p_f(long long n, double* p, float* p32, const float* z, const double* scal,
+                          int num, int den, cudaStream_t s) {
+  k_cg_p_f<<<vgrid(n), 256, 0, s>>>(n, p, p32, z, scal, num, den);
   return cudaGetLastError();
 }
 

@@ -37,11 +37,12 @@ __global__ void __launch_bounds__(256)
   Ep32[e] = (float)Ep[e];
 }
 
-// mode 0: out_i = sum_j w_ij in_j / Hs_i ; mode 1: out_e = sum_i w_ie in_i / Hs_i
-// mode 2: Hs_i = sum_j w_ij (in/out ignored)
+// invHs_i = 1 / sum_j w_ij (precomputed, so no float64 division per term)
+// mode 0: out_i = invHs_i sum_j w_ij in_j ; mode 1: out_e = sum_i w_ie in_i invHs_i
+// mode 2: out_i = invHs_i (in ignored)
 template <int DIM>
 __global__ void __launch_bounds__(256)
-    k_filter(GridP g, StencilP st, int mode, const double* __restrict__ Hs,
+    k_filter(GridP g, StencilP st, int mode, const double* __restrict__ invHs,
              const double* __restrict__ in, double* __restrict__ out) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.nel) return;
@@ -60,14 +61,16 @@ __global__ void __launch_bounds__(256)
     if (mode == 0)
       acc = fma(w, in[j], acc);
     else if (mode == 1)
-      acc = fma(w, in[j] / Hs[j], acc);
+      acc = fma(w, in[j] * invHs[j], acc);
     else
       acc += w;
   }
   if (mode == 0)
-    out[e] = acc / Hs[e];
-  else
+    out[e] = acc * invHs[e];
+  else if (mode == 1)
     out[e] = acc;
+  else
+    out[e] = 1.0 / acc;
 }
 
 // ce_e = u_e^T KE u_e; dc_e = -penal (E0-Emin) rho_e^(penal-1) ce_e;

@@ -275,11 +275,12 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   const long long nel = g0.nel, n = dim * g0.nn;
   const int Ns = d.n_parm, Nm = d.n_carm;
   double *E64 = cv.take<double>(nel), *Ep64 = cv.take<double>(nel), *dE64 = cv.take<double>(nel);
-  double *rho = cv.take<double>(nel), *Hs = cv.take<double>(nel), *oca = cv.take<double>(nel);
+  double *rho = cv.take<double>(nel), *invHs = cv.take<double>(nel), *oca = cv.take<double>(nel);
   float *E32 = cv.take<float>(nel), *Ep32 = cv.take<float>(nel), *dE32 = cv.take<float>(nel);
   double* f = cv.take<double>(n);
   double *r = cv.take<double>(n), *z = cv.take<double>(n), *p = cv.take<double>(n),
          *q = cv.take<double>(n);
+  float *p32 = cv.take<float>(n), *q32 = cv.take<float>(n);
   double *Phi = cv.take<double>((size_t)n * Ns), *KPhi = cv.take<double>((size_t)n * Ns);
   double *R = cv.take<double>((size_t)n * Nm), *Q = cv.take<double>((size_t)n * Nm);
   double* t = cv.take<double>(n);
@@ -308,9 +309,9 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   void* Ad = cv.take<char>((size_t)nc * nc * ts);
   void* Ai = cv.take<char>((size_t)nc * nc * ts);
   if (c) {
-    c->E64 = E64; c->Eprev64 = Ep64; c->dE64 = dE64; c->rho_phys = rho; c->Hs = Hs; c->oc_a = oca;
+    c->E64 = E64; c->Eprev64 = Ep64; c->dE64 = dE64; c->rho_phys = rho; c->invHs = invHs; c->oc_a = oca;
     c->E32 = E32; c->Eprev32 = Ep32; c->dE32 = dE32; c->f = f;
-    c->r = r; c->z = z; c->p = p; c->q = q;
+    c->r = r; c->z = z; c->p = p; c->q = q; c->p32 = p32; c->q32 = q32;
     c->Phi = Phi; c->KPhi = KPhi; c->R = R; c->Q = Q; c->t = t;
     c->Qc64 = Qc64; c->Qc32 = Qc32;
     c->partials = partials; c->counters = counters; c->scal = scal; c->small = small;
@@ -460,7 +461,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
                                                           c->ints + I_STATUS);
     INIT_TRY(cudaGetLastError(), "bc check");
   }
-  INIT_TRY(launch_filter_norm(c->dim, c->lv[0].g, c->stencil, c->Hs, s), "filter norm");
+  INIT_TRY(launch_filter_norm(c->dim, c->lv[0].g, c->stencil, c->invHs, s), "filter norm");
   INIT_TRY(launch_dot(c->n, c->f, c->f, c->partials, c->counters + C_DOT, c->scal + S_FNORM2, s),
            "norm f");
   double f2 = 0.0;
@@ -614,8 +615,9 @@ static to_status build_hierarchy(to_ctx* c) {
   return TO_OK;
 }
 
-// z (float64, n) = V-cycle applied to r (float64, n)
-static to_status vcycle(to_ctx* c, const double* rin, double* zout) {
+// zout (type zt: float64, or float32 in the mixed path) = V-cycle applied to
+// r (float64, n)
+static to_status vcycle(to_ctx* c, const double* rin, void* zout, int zt) {
   cudaStream_t s = c->stream;
   const int t = mg_t(c);
   const int L = c->L;
@@ -650,7 +652,7 @@ static to_status vcycle(to_ctx* c, const double* rin, double* zout) {
   }
   LAUNCH(c, launch_prolong_add(c->dim, t, lv[0].g, lv[0].mask, lv[1].g, lv[1].z2, lv[0].z, s),
          "prolong 0");
-  return run_op(c, fine_args(c, TO_OP_K, t, t, T_F64, lv[0].z, zout, lv[0].b, lv[0].dinv,
+  return run_op(c, fine_args(c, TO_OP_K, t, t, zt, lv[0].z, zout, lv[0].b, lv[0].dinv,
                              EPI_SMOOTH), "postsmooth 0");
 }
 
@@ -711,7 +713,11 @@ to_status to_vcycle(to_ctx* c, const double* r, double* z) {
     to_status st = build_hierarchy(c);
     if (st != TO_OK) return st;
   }
-  return vcycle(c, r, z);
+  if (!c->mixed) return vcycle(c, r, z, T_F64);
+  to_status st = vcycle(c, r, c->lv[0].z2, T_F32);
+  if (st != TO_OK) return st;
+  LAUNCH(c, launch_convert(T_F32, T_F64, c->n, c->lv[0].z2, z, c->stream), "convert");
+  return TO_OK;
 }
 
 to_status to_level_info(to_ctx* c, int32_t level, int32_t nel_out[3], int64_t* ndof) {
@@ -766,19 +772,48 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   double rr_max = rr;          // largest residual since the last true-residual update
   int it = 0;
   bool conv = rel < rtol;
+  // In the mixed path the operator and the V-cycle work on float32 shadows
+  // (p32 -> q32, z32); x, r, p and all dot products stay float64.
+  const bool f32 = tc != T_F64;
+  float* z32 = static_cast<float*>(c->lv[0].z2);
+  auto precondition = [&](int slot) -> to_status {
+    to_status e;
+    if (f32) {
+      if ((e = vcycle(c, c->r, z32, T_F32)) != TO_OK) return e;
+      LAUNCH(c, launch_dot_df(n, c->r, z32, c->partials, c->counters + C_DOT, c->scal + slot, s),
+             "rz");
+    } else {
+      if ((e = vcycle(c, c->r, c->z, T_F64)) != TO_OK) return e;
+      LAUNCH(c, launch_dot(n, c->r, c->z, c->partials, c->counters + C_DOT, c->scal + slot, s),
+             "rz");
+    }
+    return TO_OK;
+  };
   if (!conv) {
-    if ((st = vcycle(c, c->r, c->z)) != TO_OK) return st;
-    LAUNCH(c, launch_dot(n, c->r, c->z, c->partials, c->counters + C_DOT, c->scal + S_RZ0, s), "rz");
-    LAUNCH(c, launch_copy(n, c->z, c->p, s), "p = z");
+    if ((st = precondition(S_RZ0)) != TO_OK) return st;
+    if (f32)
+      LAUNCH(c, launch_cg_p_f(n, c->p, c->p32, z32, c->scal, -1, 0, s), "p = z");
+    else
+      LAUNCH(c, launch_copy(n, c->z, c->p, s), "p = z");
     int cur = S_RZ0, nxt = S_RZ1;
     for (it = 1; it <= maxit; ++it) {
-      if ((st = run_op(c, fine_args(c, TO_OP_K, tc, T_F64, T_F64, c->p, c->q, nullptr, nullptr,
-                                    EPI_APPLY), "q = K p")) != TO_OK)
-        return st;
-      LAUNCH(c, launch_dot(n, c->p, c->q, c->partials, c->counters + C_DOT, c->scal + S_PQ, s),
-             "pq");
-      LAUNCH(c, launch_cg_xr(n, x, c->r, c->p, c->q, c->scal, cur, S_PQ, S_RR, c->partials,
-                             c->counters + C_UPD, s), "x, r update");
+      if (f32) {
+        if ((st = run_op(c, fine_args(c, TO_OP_K, T_F32, T_F32, T_F32, c->p32, c->q32, nullptr,
+                                      nullptr, EPI_APPLY), "q = K p")) != TO_OK)
+          return st;
+        LAUNCH(c, launch_dot_df(n, c->p, c->q32, c->partials, c->counters + C_DOT,
+                                c->scal + S_PQ, s), "pq");
+        LAUNCH(c, launch_cg_xr_f(n, x, c->r, c->p, c->q32, c->scal, cur, S_PQ, S_RR, c->partials,
+                                 c->counters + C_UPD, s), "x, r update");
+      } else {
+        if ((st = run_op(c, fine_args(c, TO_OP_K, tc, T_F64, T_F64, c->p, c->q, nullptr, nullptr,
+                                      EPI_APPLY), "q = K p")) != TO_OK)
+          return st;
+        LAUNCH(c, launch_dot(n, c->p, c->q, c->partials, c->counters + C_DOT, c->scal + S_PQ, s),
+               "pq");
+        LAUNCH(c, launch_cg_xr(n, x, c->r, c->p, c->q, c->scal, cur, S_PQ, S_RR, c->partials,
+                               c->counters + C_UPD, s), "x, r update");
+      }
       if ((st = read_scalar(c, c->scal + S_RR, &rr)) != TO_OK) return st;
       rel = sqrt(rr) / c->fnorm;
       if (!isfinite(rel)) return fail(c, TO_E_SINGULAR, "CG breakdown (non-finite residual)");
@@ -797,10 +832,11 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
         break;
       }
       if (it == maxit) break;
-      if ((st = vcycle(c, c->r, c->z)) != TO_OK) return st;
-      LAUNCH(c, launch_dot(n, c->r, c->z, c->partials, c->counters + C_DOT, c->scal + nxt, s),
-             "rz");
-      LAUNCH(c, launch_cg_p(n, c->p, c->z, c->scal, nxt, cur, s), "p update");
+      if ((st = precondition(nxt)) != TO_OK) return st;
+      if (f32)
+        LAUNCH(c, launch_cg_p_f(n, c->p, c->p32, z32, c->scal, nxt, cur, s), "p update");
+      else
+        LAUNCH(c, launch_cg_p(n, c->p, c->z, c->scal, nxt, cur, s), "p update");
       std::swap(cur, nxt);
     }
     if (it > maxit) it = maxit;
@@ -931,7 +967,7 @@ to_status to_sensitivity(to_ctx* c, const double* u, double* compliance_dev, dou
 to_status to_filter(to_ctx* c, int32_t mode, const double* in, double* out) {
   if (!c || !in || !out || in == out) return fail(c, TO_E_INVALID, "bad arguments");
   if (mode != TO_FILTER_DENSITY && mode != TO_FILTER_SENS) return fail(c, TO_E_INVALID, "bad mode");
-  LAUNCH(c, launch_filter(c->dim, c->lv[0].g, c->stencil, mode, c->Hs, in, out, c->stream),
+  LAUNCH(c, launch_filter(c->dim, c->lv[0].g, c->stencil, mode, c->invHs, in, out, c->stream),
          "filter");
   return TO_OK;
 }

@@ -198,9 +198,10 @@ struct to_ctx {
   // fine-level coefficient arrays
   double *E64, *Eprev64, *dE64, *rho_phys;
   float *E32, *Eprev32, *dE32;
-  double *f, *Hs, *oc_a;
+  double *f, *invHs, *oc_a;   // invHs: 1 / row sums of the filter weights
   // CG
   double *r, *z, *p, *q;
+  float *p32, *q32;     // float32 shadows of p and K p (mixed path)
   // PARM / CARM
   double *Phi, *KPhi, *R, *Q, *t;
   int parm_count, parm_head, carm_built;
