@@ -26,6 +26,8 @@ struct ApplyArgs {
   const void* ke;      // host pointer to the ND*ND element matrix of type tc
   const void* wht;     // host pointer to the 8x3x3 Walsh-Hadamard blocks of KE
                        // (type tc; 3D finest grid only, else null)
+  bool gal1;           // 3D level 1 without stored matrices: coef holds the
+  GridP gf;            // finest-grid moduli, gf the finest grid
   const void* x;
   void* y;
   const void* b;
@@ -56,6 +58,13 @@ cudaError_t launch_galerkin_fine(int dim, int t, const GridP& gc, const GridP& g
                                  const void* coef, const void* Qc, void* Kc, cudaStream_t s);
 cudaError_t launch_galerkin_coarse(int dim, int t, const GridP& gc, const GridP& gf,
                                    const void* Kf, void* Kc, cudaStream_t s);
+// 3D level 1 kept implicit: its diagonal from the finest moduli (qdiag: host
+// table [8 children][8 corners][3] of diag(Q_ch)), and level-2 element
+// matrices from the finest moduli with 64 tables R (device, [64][576]).
+cudaError_t launch_diag_l1(int t, const GridP& g1, const GridP& gf, const uint8_t* mask,
+                           const double* qdiag, const void* coef, void* dinv, cudaStream_t s);
+cudaError_t launch_galerkin_l2(int t, const GridP& g2, const GridP& gf, const void* coef,
+                               const void* R, void* Kc, cudaStream_t s);
 cudaError_t launch_dense_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
                                   const void* Kc, void* A, cudaStream_t s);
 cudaError_t launch_cholesky_inverse(int t, int n, void* A, void* Ainv, int* status,

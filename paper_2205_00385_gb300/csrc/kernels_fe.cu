@@ -146,9 +146,103 @@ __device__ __forceinline__ void fwht8(TC (&v)[8]) {
       }
 }
 
-template <typename TC, typename TX, typename TY, int EPI>
+// Level-1 Galerkin operator in the Walsh basis.  With 2x coarsening, the
+// fine element at child position ch of a coarse element sees the nodal
+// vector W_ch x (multilinear interpolation), so the coarse element operator is
+// sum_ch E_ch W_ch^T KE W_ch = T (sum_ch E_ch M_ch^T B M_ch) T with
+// M_ch = T W_ch T / 8.  M_ch is the tensor product over the axes of the 2x2
+// factor [[1, +-1/2], [0, 1/2]] (Walsh index 0 = sum, 1 = difference; the
+// sign is + for the lower child position and - for the upper), so it only
+// couples X[t] with X[t'] for t a subset of t'.
+__host__ __device__ constexpr float wmix(int ch, int t, int tp) {
+  return ((t & 1) ? ((tp & 1) ? 0.5f : 0.0f) : ((tp & 1) ? ((ch & 1) ? -0.5f : 0.5f) : 1.0f)) *
+         ((t & 2) ? ((tp & 2) ? 0.5f : 0.0f) : ((tp & 2) ? ((ch & 2) ? -0.5f : 0.5f) : 1.0f)) *
+         ((t & 4) ? ((tp & 4) ? 0.5f : 0.0f) : ((tp & 4) ? ((ch & 4) ? -0.5f : 0.5f) : 1.0f));
+}
+
+// ye = element operator applied to the element's nodal values (bottom face
+// xb = corners 0..3, top face xt = corners 4..7).  GAL1 = false: E_e KE; true:
+// the level-1 Galerkin composite with the eight child moduli ce[].
+template <typename TC, bool GAL1>
+__device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&ce)[GAL1 ? 8 : 1],
+                                            const TC (&xb)[4][3], const TC (&xt)[4][3],
+                                            TC (&ye)[8][3]) {
+  TC X[3][8];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      X[c][q] = xb[q][c];
+      X[c][q + 4] = xt[q][c];
+    }
+    fwht8<TC>(X[c]);
+  }
+  TC Y[3][8];
+  if (!GAL1) {
+#pragma unroll
+    for (int tau = 0; tau < 8; ++tau) {
+      TC zt[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) zt[c] = ce[0] * X[c][tau ^ (1 << c)];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        TC s = kb.b[tau][c][0] * zt[0];
+        s = fma(kb.b[tau][c][1], zt[1], s);
+        s = fma(kb.b[tau][c][2], zt[2], s);
+        Y[c][tau ^ (1 << c)] = s;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int t = 0; t < 8; ++t) Y[c][t] = TC(0);
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      TC Xf[3][8], Zf[3][8];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          TC s = TC(0);
+#pragma unroll
+          for (int tp = 0; tp < 8; ++tp)
+            if ((t & ~tp) == 0) s = fma(TC(wmix(ch, t, tp)), X[c][tp], s);
+          Xf[c][t] = s;
+        }
+#pragma unroll
+      for (int tau = 0; tau < 8; ++tau) {
+        TC zt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) zt[c] = ce[ch] * Xf[c][tau ^ (1 << c)];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          TC s = kb.b[tau][c][0] * zt[0];
+          s = fma(kb.b[tau][c][1], zt[1], s);
+          s = fma(kb.b[tau][c][2], zt[2], s);
+          Zf[c][tau ^ (1 << c)] = s;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int tp = 0; tp < 8; ++tp)
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if ((t & ~tp) == 0) Y[c][tp] = fma(TC(wmix(ch, t, tp)), Zf[c][t], Y[c][tp]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    fwht8<TC>(Y[c]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) ye[a][c] = Y[c][a];
+  }
+}
+
+template <typename TC, typename TX, typename TY, int EPI, bool GAL1>
 __global__ void __launch_bounds__(WX * WY)
-    k_apply3_wht(GridP g, const uint8_t* __restrict__ mask, WhtBlocks<TC> kb,
+    k_apply3_wht(GridP g, GridP gf, const uint8_t* __restrict__ mask, WhtBlocks<TC> kb,
                  const TC* __restrict__ coef, const TX* __restrict__ x, TY* __restrict__ y,
                  const TX* __restrict__ b, const TC* __restrict__ dinv, TC omega, TC dfix) {
   using TE = typename std::conditional<(sizeof(TY) > sizeof(TC)), double, TC>::type;
@@ -193,37 +287,17 @@ __global__ void __launch_bounds__(WX * WY)
     TC ye[8][3];
     const bool el_ok = col_ok && ez >= 0 && ez < g.nz;
     if (el_ok) {
-      const TC ce = coef[ex + (long long)g.nx * (ey + (long long)g.ny * ez)];
-      TC X[3][8];
+      TC ce[GAL1 ? 8 : 1];
+      if (!GAL1) {
+        ce[0] = coef[ex + (long long)g.nx * (ey + (long long)g.ny * ez)];
+      } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          X[c][q] = xb[q][c];
-          X[c][q + 4] = xt[q][c];
-        }
-        fwht8<TC>(X[c]);
+        for (int ch = 0; ch < (GAL1 ? 8 : 1); ++ch)
+          ce[ch] = coef[(2 * ex + (ch & 1)) +
+                        (long long)gf.nx * ((2 * ey + ((ch >> 1) & 1)) +
+                                            (long long)gf.ny * (2 * ez + ((ch >> 2) & 1)))];
       }
-      TC Y[3][8];
-#pragma unroll
-      for (int tau = 0; tau < 8; ++tau) {
-        TC zt[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) zt[c] = ce * X[c][tau ^ (1 << c)];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          TC s = kb.b[tau][c][0] * zt[0];
-          s = fma(kb.b[tau][c][1], zt[1], s);
-          s = fma(kb.b[tau][c][2], zt[2], s);
-          Y[c][tau ^ (1 << c)] = s;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        fwht8<TC>(Y[c]);
-#pragma unroll
-        for (int a = 0; a < 8; ++a) ye[a][c] = Y[c][a];
-      }
+      wht_element<TC, GAL1>(kb, ce, xb, xt, ye);
     } else {
 #pragma unroll
       for (int a = 0; a < 8; ++a)
@@ -356,10 +430,16 @@ static cudaError_t run_wht(const ApplyArgs& a, cudaStream_t s) {
   const TC* src = static_cast<const TC*>(a.wht);
   for (int q = 0; q < 72; ++q) (&kb.b[0][0][0])[q] = src[q];
   dim3 grid((a.g.nnx + WOX - 1) / WOX, (a.g.nny + WOY - 1) / WOY, (a.g.nnz + WZC - 1) / WZC);
-  k_apply3_wht<TC, TX, TY, EPI><<<grid, WX * WY, 0, s>>>(
-      a.g, a.mask, kb, static_cast<const TC*>(a.coef), static_cast<const TX*>(a.x),
-      static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
-      TC(a.omega), TC(a.dfix));
+  if (a.gal1)
+    k_apply3_wht<TC, TX, TY, EPI, true><<<grid, WX * WY, 0, s>>>(
+        a.g, a.gf, a.mask, kb, static_cast<const TC*>(a.coef), static_cast<const TX*>(a.x),
+        static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
+        TC(a.omega), TC(a.dfix));
+  else
+    k_apply3_wht<TC, TX, TY, EPI, false><<<grid, WX * WY, 0, s>>>(
+        a.g, a.gf, a.mask, kb, static_cast<const TC*>(a.coef), static_cast<const TX*>(a.x),
+        static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
+        TC(a.omega), TC(a.dfix));
   return cudaGetLastError();
 }
 

@@ -145,6 +145,75 @@ __global__ void __launch_bounds__(256)
   Kc[(size_t)entry * gc.nel + E] = acc;
 }
 
+// Level-1 diagonal without stored matrices (3D): node I of level 1 sums, over
+// its coarse elements E and their children ch, E_child * diag(Q_ch) at I's
+// corner a.  qd.v[(ch * 8 + a) * 3 + c] = Q_ch[(3a+c),(3a+c)].
+template <typename T>
+struct QDiagP {
+  T v[8 * 8 * 3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_diag_l1(GridP g1, GridP gf, const uint8_t* __restrict__ mask, QDiagP<T> qd,
+              const T* __restrict__ coef, T* __restrict__ dinv) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1.nn) return;
+  const int i = (int)(node % g1.nnx);
+  const long long rest = node / g1.nnx;
+  const int j = (int)(rest % g1.nny);
+  const int k = (int)(rest / g1.nny);
+  T d[3] = {T(0), T(0), T(0)};
+  for (int ez = 0; ez < 2; ++ez)
+    for (int ey = 0; ey < 2; ++ey)
+      for (int ex = 0; ex < 2; ++ex) {
+        const int EX = i - 1 + ex, EY = j - 1 + ey, EZ = k - 1 + ez;
+        if (EX < 0 || EX >= g1.nx || EY < 0 || EY >= g1.ny || EZ < 0 || EZ >= g1.nz) continue;
+        const int a = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          const long long fe = (2 * EX + (ch & 1)) +
+                               (long long)gf.nx * ((2 * EY + ((ch >> 1) & 1)) +
+                                                   (long long)gf.ny * (2 * EZ + ((ch >> 2) & 1)));
+          const T e = coef[fe];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) d[c] += e * qd.v[(ch * 8 + a) * 3 + c];
+        }
+      }
+  const unsigned m = mask[node];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dinv[3 * node + c] = ((m >> c) & 1u) ? T(1) : T(1) / d[c];
+}
+
+// Level-2 element matrices straight from the finest moduli (3D): a level-2
+// element covers 4x4x4 finest elements f, and
+// Kc_E = sum_f E_f R_f with R_f = W_c1^T (W_c0^T KE W_c0) W_c1 for the
+// finest element's position c0 inside its level-1 parent and that parent's
+// position c1 inside E (64 precomputed tables, R[f * 576 + entry]).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_galerkin_l2(GridP g2, GridP gf, const T* __restrict__ coef, const T* __restrict__ R,
+                  T* __restrict__ Kc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g2.nel * 576) return;
+  const long long E = t % g2.nel;
+  const int entry = (int)(t / g2.nel);
+  const int EX = (int)(E % g2.nx);
+  const long long rest = E / g2.nx;
+  const int EY = (int)(rest % g2.ny);
+  const int EZ = (int)(rest / g2.ny);
+  T acc = T(0);
+#pragma unroll 8
+  for (int f = 0; f < 64; ++f) {
+    const int c1 = f >> 3, c0 = f & 7;
+    const int fx = 4 * EX + 2 * (c1 & 1) + (c0 & 1);
+    const int fy = 4 * EY + 2 * ((c1 >> 1) & 1) + ((c0 >> 1) & 1);
+    const int fz = 4 * EZ + 2 * ((c1 >> 2) & 1) + ((c0 >> 2) & 1);
+    acc += coef[fx + (long long)gf.nx * (fy + (long long)gf.ny * fz)] * R[f * 576 + entry];
+  }
+  Kc[(size_t)entry * g2.nel + E] = acc;
+}
+
 // Galerkin level l+1 from stored level-l element matrices.  One block of
 // ND*ND threads per coarse element; T = Kchild W in shared memory, then
 // Kc += W^T T, summed over the 2^DIM children.
@@ -380,6 +449,33 @@ cudaError_t launch_galerkin_fine(int dim, int t, const GridP& gc, const GridP& g
                                   : gal_fine_t<2, float>(gc, gf, coef, Qc, Kc, s);
   return t == T_F64 ? gal_fine_t<3, double>(gc, gf, coef, Qc, Kc, s)
                     : gal_fine_t<3, float>(gc, gf, coef, Qc, Kc, s);
+}
+
+template <typename T>
+static cudaError_t diag_l1_t(const GridP& g1, const GridP& gf, const uint8_t* mask,
+                             const double* qdiag, const void* coef, void* dinv, cudaStream_t s) {
+  QDiagP<T> qd;
+  for (int q = 0; q < 192; ++q) qd.v[q] = T(qdiag[q]);
+  k_diag_l1<T><<<nblocks(g1.nn, 256), 256, 0, s>>>(g1, gf, mask, qd, (const T*)coef, (T*)dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_l1(int t, const GridP& g1, const GridP& gf, const uint8_t* mask,
+                           const double* qdiag, const void* coef, void* dinv, cudaStream_t s) {
+  return t == T_F64 ? diag_l1_t<double>(g1, gf, mask, qdiag, coef, dinv, s)
+                    : diag_l1_t<float>(g1, gf, mask, qdiag, coef, dinv, s);
+}
+
+cudaError_t launch_galerkin_l2(int t, const GridP& g2, const GridP& gf, const void* coef,
+                               const void* R, void* Kc, cudaStream_t s) {
+  const long long tot = g2.nel * 576;
+  if (t == T_F64)
+    k_galerkin_l2<double><<<nblocks(tot, 256), 256, 0, s>>>(g2, gf, (const double*)coef,
+                                                             (const double*)R, (double*)Kc);
+  else
+    k_galerkin_l2<float><<<nblocks(tot, 256), 256, 0, s>>>(g2, gf, (const float*)coef,
+                                                           (const float*)R, (float*)Kc);
+  return cudaGetLastError();
 }
 
 template <int DIM, typename T>

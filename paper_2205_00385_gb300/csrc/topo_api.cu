@@ -163,33 +163,56 @@ static void element_stiffness(int dim, double nu, double* KE) {
   }
 }
 
+// P_c: nodal values of child c's corners from its parent's corners
+// (multilinear interpolation, per displacement component), nd x nd.
+static void child_interp(int dim, int c, double* P) {
+  const int npe = 1 << dim, nd = dim * npe;
+  for (int a = 0; a < npe; ++a)
+    for (int A = 0; A < npe; ++A) {
+      double w = 1.0;
+      for (int d = 0; d < dim; ++d) {
+        const double pos = 0.5 * (((c >> d) & 1) + ((a >> d) & 1));
+        w *= ((A >> d) & 1) ? pos : 1.0 - pos;
+      }
+      for (int ci = 0; ci < dim; ++ci)
+        for (int cj = 0; cj < dim; ++cj) P[(dim * a + ci) * nd + dim * A + cj] = (ci == cj) ? w : 0.0;
+    }
+}
+
+// out = P^T A P for nd x nd row-major matrices
+static void triple(int nd, const double* P, const double* A, double* out) {
+  std::vector<double> T(nd * nd);
+  for (int i = 0; i < nd; ++i)
+    for (int J = 0; J < nd; ++J) {
+      double s = 0.0;
+      for (int j = 0; j < nd; ++j) s += A[i * nd + j] * P[j * nd + J];
+      T[i * nd + J] = s;
+    }
+  for (int I = 0; I < nd; ++I)
+    for (int J = 0; J < nd; ++J) {
+      double s = 0.0;
+      for (int i = 0; i < nd; ++i) s += P[i * nd + I] * T[i * nd + J];
+      out[I * nd + J] = s;
+    }
+}
+
 // Q_c = P_c^T KE P_c for each child position c of a coarse element.
 static void child_galerkin(int dim, const double* KE, double* Qc) {
   const int npe = 1 << dim, nd = dim * npe;
-  std::vector<double> P(nd * nd), T(nd * nd);
+  std::vector<double> P(nd * nd);
   for (int c = 0; c < npe; ++c) {
-    for (int a = 0; a < npe; ++a)
-      for (int A = 0; A < npe; ++A) {
-        double w = 1.0;
-        for (int d = 0; d < dim; ++d) {
-          const double pos = 0.5 * (((c >> d) & 1) + ((a >> d) & 1));
-          w *= ((A >> d) & 1) ? pos : 1.0 - pos;
-        }
-        for (int ci = 0; ci < dim; ++ci)
-          for (int cj = 0; cj < dim; ++cj) P[(dim * a + ci) * nd + dim * A + cj] = (ci == cj) ? w : 0.0;
-      }
-    for (int i = 0; i < nd; ++i)
-      for (int J = 0; J < nd; ++J) {
-        double s = 0.0;
-        for (int j = 0; j < nd; ++j) s += KE[i * nd + j] * P[j * nd + J];
-        T[i * nd + J] = s;
-      }
-    for (int I = 0; I < nd; ++I)
-      for (int J = 0; J < nd; ++J) {
-        double s = 0.0;
-        for (int i = 0; i < nd; ++i) s += P[i * nd + I] * T[i * nd + J];
-        Qc[(size_t)c * nd * nd + I * nd + J] = s;
-      }
+    child_interp(dim, c, P.data());
+    triple(nd, P.data(), KE, Qc + (size_t)c * nd * nd);
+  }
+}
+
+// 3D: R_f = P_c1^T Q_c0 P_c1 for the 64 finest elements f = 8 c1 + c0 of a
+// level-2 element (c1: level-1 parent inside it, c0: position in the parent).
+static void grandchild_galerkin(const double* Qc, double* R) {
+  std::vector<double> P(576);
+  for (int c1 = 0; c1 < 8; ++c1) {
+    child_interp(3, c1, P.data());
+    for (int c0 = 0; c0 < 8; ++c0) triple(24, P.data(), Qc + (size_t)c0 * 576, R + (size_t)(8 * c1 + c0) * 576);
   }
 }
 
@@ -286,6 +309,11 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   double* t = cv.take<double>(n);
   double* Qc64 = cv.take<double>((size_t)npe * nd * nd);
   float* Qc32 = cv.take<float>((size_t)npe * nd * nd);
+  // 3D with >= 3 levels: level 1 is applied without stored matrices and
+  // level 2 is formed from 64 grandchild tables
+  const bool l1_implicit = dim == 3 && L >= 3;
+  double* R2_64 = l1_implicit ? cv.take<double>((size_t)64 * 576) : nullptr;
+  float* R2_32 = l1_implicit ? cv.take<float>((size_t)64 * 576) : nullptr;
   double* partials = cv.take<double>((size_t)RED_BLOCKS * MAXB * MAXB);
   unsigned* counters = cv.take<unsigned>(C_NCOUNTERS);
   double* scal = cv.take<double>(S_NSLOTS);
@@ -303,7 +331,8 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
     lv[l].z = cv.take<char>(nl * ts);
     lv[l].z2 = cv.take<char>(nl * ts);
     lv[l].r = cv.take<char>(nl * ts);
-    lv[l].Kc = l >= 1 ? (void*)cv.take<char>((size_t)nd * nd * g.nel * ts) : nullptr;
+    const bool stored = l >= 2 || (l == 1 && !l1_implicit);
+    lv[l].Kc = stored ? (void*)cv.take<char>((size_t)nd * nd * g.nel * ts) : nullptr;
   }
   const long long nc = lv[L - 1].n;
   void* Ad = cv.take<char>((size_t)nc * nc * ts);
@@ -314,6 +343,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
     c->r = r; c->z = z; c->p = p; c->q = q; c->p32 = p32; c->q32 = q32;
     c->Phi = Phi; c->KPhi = KPhi; c->R = R; c->Q = Q; c->t = t;
     c->Qc64 = Qc64; c->Qc32 = Qc32;
+    c->l1_implicit = l1_implicit; c->R2_64 = R2_64; c->R2_32 = R2_32;
     c->partials = partials; c->counters = counters; c->scal = scal; c->small = small;
     c->ints = ints;
     for (int l = 0; l < L; ++l) c->lv[l] = lv[l];
@@ -442,6 +472,19 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   } while (0)
   INIT_TRY(cudaMemcpyAsync(c->Qc64, Qc.data(), Qc.size() * 8, cudaMemcpyHostToDevice, s), "copy Qc");
   INIT_TRY(cudaMemcpyAsync(c->Qc32, Qc32.data(), Qc32.size() * 4, cudaMemcpyHostToDevice, s), "copy Qc32");
+  if (c->l1_implicit) {
+    std::vector<double> R2((size_t)64 * 576);
+    grandchild_galerkin(Qc.data(), R2.data());
+    std::vector<float> R2f(R2.size());
+    for (size_t q = 0; q < R2.size(); ++q) R2f[q] = (float)R2[q];
+    INIT_TRY(cudaMemcpyAsync(c->R2_64, R2.data(), R2.size() * 8, cudaMemcpyHostToDevice, s), "copy R2");
+    INIT_TRY(cudaMemcpyAsync(c->R2_32, R2f.data(), R2f.size() * 4, cudaMemcpyHostToDevice, s), "copy R2");
+    INIT_TRY(cudaStreamSynchronize(s), "sync");
+    for (int ch = 0; ch < 8; ++ch)
+      for (int a = 0; a < 8; ++a)
+        for (int cc = 0; cc < 3; ++cc)
+          c->qdiag[(ch * 8 + a) * 3 + cc] = Qc[(size_t)ch * 576 + (3 * a + cc) * 24 + 3 * a + cc];
+  }
   INIT_TRY(cudaMemcpyAsync(c->f, f, c->n * 8, cudaMemcpyDeviceToDevice, s), "copy f");
   INIT_TRY(cudaMemsetAsync(c->counters, 0, C_NCOUNTERS * sizeof(unsigned), s), "memset");
   INIT_TRY(cudaMemsetAsync(c->scal, 0, S_NSLOTS * 8, s), "memset");
@@ -534,6 +577,8 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.Kc = nullptr;
   a.ke = tc == T_F64 ? (const void*)c->KE64 : (const void*)c->KE32;
   a.wht = c->dim == 3 ? (tc == T_F64 ? (const void*)c->wht64 : (const void*)c->wht32) : nullptr;
+  a.gal1 = false;
+  a.gf = c->lv[0].g;
   a.x = x;
   a.y = y;
   a.b = b;
@@ -559,6 +604,16 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
   a.Kc = c->lv[l].Kc;
   a.ke = nullptr;
   a.wht = nullptr;
+  a.gal1 = false;
+  a.gf = c->lv[0].g;
+  if (l == 1 && c->l1_implicit) {
+    // level-1 Galerkin operator evaluated from the finest moduli
+    a.expl = false;
+    a.gal1 = true;
+    a.coef = t == T_F64 ? (const void*)c->E64 : (const void*)c->E32;
+    a.Kc = nullptr;
+    a.wht = t == T_F64 ? (const void*)c->wht64 : (const void*)c->wht32;
+  }
   a.x = x;
   a.y = y;
   a.b = b;
@@ -577,14 +632,15 @@ static double apply_bytes(const ApplyArgs& a) {
   const double n = (double)a.dim * (double)a.g.nn, nel = (double)a.g.nel;
   const int nd = a.dim * (1 << a.dim);
   double b = n * (sx + sy) + (double)a.g.nn;          // x, y, node masks
-  b += a.expl ? (double)nd * nd * nel * sc : nel * sc; // element matrices or coefficients
+  b += a.expl ? (double)nd * nd * nel * sc             // element matrices,
+              : (a.gal1 ? 8.0 : 1.0) * nel * sc;       // or (child) moduli
   if (a.epi != EPI_APPLY) b += n * sx;                 // right-hand side
   if (a.epi == EPI_SMOOTH) b += n * sc;                // inverse diagonal
   return b;
 }
 
 static to_status run_op(to_ctx* c, const ApplyArgs& a, const char* what) {
-  ProfScope ps(c, a.expl ? 1 : 0, apply_bytes(a));
+  ProfScope ps(c, (a.expl || a.gal1) ? 1 : 0, apply_bytes(a));
   LAUNCH(c, launch_apply(a, c->stream), what);
   return TO_OK;
 }
@@ -598,12 +654,21 @@ static to_status build_hierarchy(to_ctx* c) {
   const void* Qc = t == T_F64 ? (const void*)c->Qc64 : (const void*)c->Qc32;
   LAUNCH(c, launch_diag(c->dim, c->lv[0].g, c->lv[0].mask, t, false, E, nullptr, KE,
                         c->lv[0].dinv, s), "diag 0");
-  LAUNCH(c, launch_galerkin_fine(c->dim, t, c->lv[1].g, c->lv[0].g, E, Qc, c->lv[1].Kc, s),
-         "galerkin 1");
-  for (int l = 2; l < c->L; ++l)
+  if (c->l1_implicit) {
+    // level 1 stays implicit; level 2 straight from the finest moduli
+    const void* R2 = t == T_F64 ? (const void*)c->R2_64 : (const void*)c->R2_32;
+    LAUNCH(c, launch_diag_l1(t, c->lv[1].g, c->lv[0].g, c->lv[1].mask, c->qdiag, E,
+                             c->lv[1].dinv, s), "diag 1");
+    LAUNCH(c, launch_galerkin_l2(t, c->lv[2].g, c->lv[0].g, E, R2, c->lv[2].Kc, s), "galerkin 2");
+  } else {
+    LAUNCH(c, launch_galerkin_fine(c->dim, t, c->lv[1].g, c->lv[0].g, E, Qc, c->lv[1].Kc, s),
+           "galerkin 1");
+  }
+  const int lfirst = c->l1_implicit ? 3 : 2;
+  for (int l = lfirst; l < c->L; ++l)
     LAUNCH(c, launch_galerkin_coarse(c->dim, t, c->lv[l].g, c->lv[l - 1].g, c->lv[l - 1].Kc,
                                      c->lv[l].Kc, s), "galerkin l");
-  for (int l = 1; l < c->L; ++l)
+  for (int l = c->l1_implicit ? 2 : 1; l < c->L; ++l)
     LAUNCH(c, launch_diag(c->dim, c->lv[l].g, c->lv[l].mask, t, true, nullptr, c->lv[l].Kc,
                           nullptr, c->lv[l].dinv, s), "diag l");
   const int Lc = c->L - 1;

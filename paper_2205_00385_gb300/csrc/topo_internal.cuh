@@ -208,6 +208,12 @@ struct to_ctx {
   // Galerkin tables (level-1 child matrices Q_c), float64 and float32
   double* Qc64;
   float* Qc32;
+  // 3D, >= 3 levels: level 1 applied from the finest moduli (no stored
+  // matrices); level 2 formed with the 64 grandchild tables R2
+  bool l1_implicit;
+  double* R2_64;
+  float* R2_32;
+  double qdiag[192];   // diag(Q_ch) per child and corner, for the level-1 diagonal
   // coarsest level
   void* Adense;
   void* Ainv;
