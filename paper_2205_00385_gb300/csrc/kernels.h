@@ -14,6 +14,7 @@ enum { EPI_APPLY = 0, EPI_RESID = 1, EPI_SMOOTH = 2 };
 //   y = x + omega * dinv * (b - that)                      (EPI_SMOOTH)
 // with Ke_e = coef_e * KE on the finest level (explicit = false) or the
 // stored Galerkin element matrix Kc_e on coarse levels (explicit = true).
+// Stored element matrices are element-major, row-major: Kc[e*ND*ND + r*ND + c].
 struct ApplyArgs {
   int dim;
   GridP g;
@@ -34,6 +35,7 @@ struct ApplyArgs {
   const void* dinv;    // [n] of type tc
   double omega, dfix;
   int epi;
+  void* eo;            // explicit levels: per-element output rows [nel * ND] of type tc
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 // Host: the eight 3x3 blocks of the hex8 KE in the corner Walsh-Hadamard basis
@@ -129,16 +131,24 @@ cudaError_t launch_filter(int dim, const GridP& g, const StencilP& st, int mode,
                           const double* invHs, const double* in, double* out, cudaStream_t s);
 cudaError_t launch_filter_norm(int dim, const GridP& g, const StencilP& st, double* invHs,
                                cudaStream_t s);
+// wht: host pointer to the float64 Walsh blocks of KE (3D), else null
 cudaError_t launch_sensitivity(int dim, const GridP& g, const uint8_t* mask, const double* ke,
-                               const double* u, const double* E, const double* rho,
-                               double penal, double E0, double Emin, double* dc,
-                               double* compliance, double* partials, unsigned* counter,
-                               cudaStream_t s);
+                               const double* wht, const double* u, const double* E,
+                               const double* rho, double penal, double E0, double Emin,
+                               double* dc, double* compliance, double* partials,
+                               unsigned* counter, cudaStream_t s);
 cudaError_t launch_oc_prep(long long nel, const double* rho, const double* dc,
                            const double* dv, double* a, double* scal, cudaStream_t s);
 cudaError_t launch_oc_step(long long nel, const double* rho, const double* a,
                            const double* dv, double move, double target, double* scal,
                            double* partials, unsigned* counter, cudaStream_t s);
+// bisection with stored move-limit bounds lo/hi (context path)
+cudaError_t launch_oc_prep_b(long long nel, const double* rho, const double* dc,
+                             const double* dv, double move, double* a, double* lo, double* hi,
+                             double* scal, cudaStream_t s);
+cudaError_t launch_oc_step_b(long long nel, const double* a, const double* lo, const double* hi,
+                             const double* dv, double target, double* scal, double* partials,
+                             unsigned* counter, cudaStream_t s);
 cudaError_t launch_oc_final(long long nel, double* rho, const double* a, double move,
                             double* scal, double* change_dev, double* partials,
                             unsigned* counter, cudaStream_t s);

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int cj = 0; cj < DIM; ++cj) {
               const int col = DIM * bc + cj;
-              const TC kv = EXPL ? Kc[(size_t)(row * ND + col) * g.nel + e] : ke.v[row * ND + col];
+              const TC kv = EXPL ? Kc[(size_t)e * ND * ND + row * ND + col] : ke.v[row * ND + col];
               s = fma(kv, xn[sidx][cj], s);
             }
           }
@@ -127,24 +127,6 @@ __global__ void __launch_bounds__(128)
 // shared memory in a fixed order (deterministic, no atomics).
 // ---------------------------------------------------------------------------
 constexpr int WX = 16, WY = 8, WOX = WX - 1, WOY = WY - 1, WZC = 16;
-
-template <typename TC>
-struct WhtBlocks {
-  TC b[8][3][3];   // b[tau][c][c'] couples X[tau^e_c][c] and X[tau^e_c'][c']
-};
-
-template <typename TC>
-__device__ __forceinline__ void fwht8(TC (&v)[8]) {
-#pragma unroll
-  for (int h = 1; h < 8; h <<= 1)
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-      if (!(a & h)) {
-        const TC u = v[a], w = v[a + h];
-        v[a] = u + w;
-        v[a + h] = u - w;
-      }
-}
 
 // Level-1 Galerkin operator in the Walsh basis.  With 2x coarsening, the
 // fine element at child position ch of a coarse element sees the nodal
@@ -240,16 +222,159 @@ __device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&
   }
 }
 
-template <typename TC, typename TX, typename TY, int EPI, bool GAL1>
+// ---------------------------------------------------------------------------
+// Coarse levels with stored Galerkin element matrices (element-major,
+// row-major 24x24 or 8x8 per element): one warp per element computes
+// eo_e = Kc_e x_e (lane r owns row r and loads it with 16-byte vector loads,
+// so all of an element's matrix is in flight at once); a node-centric gather
+// then sums the element rows belonging to each node in a fixed order.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__device__ __forceinline__ void load_row16(const T* __restrict__ p, T (&v)[N]) {
+  static_assert((N * sizeof(T)) % 16 == 0, "row must be a multiple of 16 bytes");
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const float4 w = __ldg(q + k);
+      v[4 * k] = w.x;
+      v[4 * k + 1] = w.y;
+      v[4 * k + 2] = w.z;
+      v[4 * k + 3] = w.w;
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const double2 w = __ldg(q + k);
+      v[2 * k] = w.x;
+      v[2 * k + 1] = w.y;
+    }
+  }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+    k_elem_gemv(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ Kc,
+                const T* __restrict__ x, T* __restrict__ eo) {
+  constexpr int ND = Geo<DIM>::ND;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long e = warp; e < g.nel; e += nwarps) {
+    const int ex = (int)(e % g.nx);
+    const long long rest = e / g.nx;
+    const int ey = (int)(rest % g.ny);
+    const int ez = DIM == 3 ? (int)(rest / g.ny) : 0;
+    T xv = T(0);
+    T row[ND];
+    if (lane < ND) {
+      const int a = lane / DIM, c = lane % DIM;
+      const long long nd = (ex + (a & 1)) +
+                           (long long)g.nnx * ((ey + ((a >> 1) & 1)) +
+                                               (long long)g.nny * (DIM == 3 ? ez + ((a >> 2) & 1) : 0));
+      xv = ((mask[nd] >> c) & 1u) ? T(0) : x[DIM * nd + c];
+      load_row16<T, ND>(Kc + (size_t)e * ND * ND + lane * ND, row);
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < ND; ++c) {
+      const T xc = __shfl_sync(0xffffffffu, xv, c);
+      if (lane < ND) acc = fma(row[c], xc, acc);
+    }
+    if (lane < ND) eo[(size_t)e * ND + lane] = acc;
+  }
+}
+
+template <int DIM, typename T, int EPI>
+__global__ void __launch_bounds__(256)
+    k_elem_gather(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ eo,
+                  const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ b,
+                  const T* __restrict__ dinv, T omega, T dfix) {
+  constexpr int ND = Geo<DIM>::ND;
+  constexpr int NZ = DIM == 3 ? 2 : 1;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nn) return;
+  const int i = (int)(node % g.nnx);
+  const long long rest = node / g.nnx;
+  const int j = (int)(rest % g.nny);
+  const int k = DIM == 3 ? (int)(rest / g.nny) : 0;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int ez = 0; ez < NZ; ++ez)
+#pragma unroll
+    for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+      for (int ex = 0; ex < 2; ++ex) {
+        const int ei = i - 1 + ex, ej = j - 1 + ey, ek = k - 1 + ez;
+        bool in = ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
+        if (DIM == 3) in = in && ek >= 0 && ek < g.nz;
+        if (!in) continue;
+        const long long e = ei + (long long)g.nx * (ej + (long long)g.ny * (DIM == 3 ? ek : 0));
+        const int a = (1 - ex) + 2 * (1 - ey) + (DIM == 3 ? 4 * (1 - ez) : 0);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += eo[(size_t)e * ND + DIM * a + c];
+      }
+  const unsigned m = mask[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long d = DIM * node + c;
+    const T Ax = ((m >> c) & 1u) ? dfix * x[d] : acc[c];
+    if (EPI == EPI_APPLY)
+      y[d] = Ax;
+    else if (EPI == EPI_RESID)
+      y[d] = b[d] - Ax;
+    else
+      y[d] = x[d] + omega * dinv[d] * (b[d] - Ax);
+  }
+}
+
+template <int DIM, typename T, int EPI>
+static cudaError_t run_expl(const ApplyArgs& a, cudaStream_t s) {
+  const long long warps = a.g.nel < 152LL * 64 ? a.g.nel : 152LL * 64;
+  k_elem_gemv<DIM, T><<<nblocks(warps * 32, 256), 256, 0, s>>>(
+      a.g, a.mask, static_cast<const T*>(a.Kc), static_cast<const T*>(a.x), static_cast<T*>(a.eo));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_elem_gather<DIM, T, EPI><<<nblocks(a.g.nn, 256), 256, 0, s>>>(
+      a.g, a.mask, static_cast<const T*>(a.eo), static_cast<const T*>(a.x), static_cast<T*>(a.y),
+      static_cast<const T*>(a.b), static_cast<const T*>(a.dinv), T(a.omega), T(a.dfix));
+  return cudaGetLastError();
+}
+
+template <int DIM, typename T>
+static cudaError_t run_expl_epi(const ApplyArgs& a, cudaStream_t s) {
+  switch (a.epi) {
+    case EPI_APPLY: return run_expl<DIM, T, EPI_APPLY>(a, s);
+    case EPI_RESID: return run_expl<DIM, T, EPI_RESID>(a, s);
+    default: return run_expl<DIM, T, EPI_SMOOTH>(a, s);
+  }
+}
+
+static cudaError_t run_expl_any(const ApplyArgs& a, cudaStream_t s) {
+  if (a.tx != a.tc || a.ty != a.tc || a.eo == nullptr) return cudaErrorInvalidValue;
+  if (a.dim == 2)
+    return a.tc == T_F64 ? run_expl_epi<2, double>(a, s) : run_expl_epi<2, float>(a, s);
+  return a.tc == T_F64 ? run_expl_epi<3, double>(a, s) : run_expl_epi<3, float>(a, s);
+}
+
+// Element operator of the column-streaming kernel
+enum { OPK_FINE = 0, OPK_GAL1 = 1 };
+
+template <typename TC, typename TX, typename TY, int EPI, int OP>
 __global__ void __launch_bounds__(WX * WY)
-    k_apply3_wht(GridP g, GridP gf, const uint8_t* __restrict__ mask, WhtBlocks<TC> kb,
-                 const TC* __restrict__ coef, const TX* __restrict__ x, TY* __restrict__ y,
-                 const TX* __restrict__ b, const TC* __restrict__ dinv, TC omega, TC dfix) {
+    k_apply3_col(GridP g, GridP gf, const uint8_t* __restrict__ mask, WhtBlocks<TC> kb,
+                 const TC* __restrict__ coef, int zc, const TX* __restrict__ x,
+                 TY* __restrict__ y, const TX* __restrict__ b, const TC* __restrict__ dinv,
+                 TC omega, TC dfix) {
   using TE = typename std::conditional<(sizeof(TY) > sizeof(TC)), double, TC>::type;
+  constexpr bool GAL1 = OP == OPK_GAL1;
   __shared__ TC part[2][4][WY][WX][3];
   const int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
   const int x0 = blockIdx.x * WOX, y0 = blockIdx.y * WOY;
-  const int z0 = blockIdx.z * WZC, z1 = min(z0 + WZC, g.nnz);
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nnz);
   const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
   const bool col_ok = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
   const long long plane = (long long)g.nnx * g.nny;
@@ -368,7 +493,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
           const int row = DIM * a + c;
-          d[c] += EXPL ? Kc[(size_t)(row * ND + row) * g.nel + e] : coef[e] * ke.v[row * ND + row];
+          d[c] += EXPL ? Kc[(size_t)e * ND * ND + row * ND + row] : coef[e] * ke.v[row * ND + row];
         }
       }
   const unsigned m = mask[node];
@@ -407,16 +532,13 @@ static cudaError_t run_apply_epi(const ApplyArgs& a, cudaStream_t s) {
   }
 }
 
+// node-centric gather kernel: finest grid in 2D (and 3D without Walsh blocks)
 template <int DIM>
 static cudaError_t run_apply_dim(const ApplyArgs& a, cudaStream_t s) {
+  if (a.expl) return cudaErrorInvalidValue;
   if (a.tc == T_F64) {
     if (a.tx != T_F64 || a.ty != T_F64) return cudaErrorInvalidValue;
-    return a.expl ? run_apply_epi<DIM, double, double, double, true>(a, s)
-                  : run_apply_epi<DIM, double, double, double, false>(a, s);
-  }
-  if (a.expl) {
-    if (a.tx != T_F32 || a.ty != T_F32) return cudaErrorInvalidValue;
-    return run_apply_epi<DIM, float, float, float, true>(a, s);
+    return run_apply_epi<DIM, double, double, double, false>(a, s);
   }
   if (a.tx == T_F64 && a.ty == T_F64) return run_apply_epi<DIM, float, double, double, false>(a, s);
   if (a.tx == T_F32 && a.ty == T_F32) return run_apply_epi<DIM, float, float, float, false>(a, s);
@@ -424,48 +546,54 @@ static cudaError_t run_apply_dim(const ApplyArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-template <typename TC, typename TX, typename TY, int EPI>
-static cudaError_t run_wht(const ApplyArgs& a, cudaStream_t s) {
+template <typename TC, typename TX, typename TY, int EPI, int OP>
+static cudaError_t run_col(const ApplyArgs& a, cudaStream_t s) {
   WhtBlocks<TC> kb;
   const TC* src = static_cast<const TC*>(a.wht);
-  for (int q = 0; q < 72; ++q) (&kb.b[0][0][0])[q] = src[q];
-  dim3 grid((a.g.nnx + WOX - 1) / WOX, (a.g.nny + WOY - 1) / WOY, (a.g.nnz + WZC - 1) / WZC);
-  if (a.gal1)
-    k_apply3_wht<TC, TX, TY, EPI, true><<<grid, WX * WY, 0, s>>>(
-        a.g, a.gf, a.mask, kb, static_cast<const TC*>(a.coef), static_cast<const TX*>(a.x),
-        static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
-        TC(a.omega), TC(a.dfix));
-  else
-    k_apply3_wht<TC, TX, TY, EPI, false><<<grid, WX * WY, 0, s>>>(
-        a.g, a.gf, a.mask, kb, static_cast<const TC*>(a.coef), static_cast<const TX*>(a.x),
-        static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
-        TC(a.omega), TC(a.dfix));
+  for (int q = 0; q < 72; ++q) (&kb.b[0][0][0])[q] = src ? src[q] : TC(0);
+  const int gx = (a.g.nnx + WOX - 1) / WOX, gy = (a.g.nny + WOY - 1) / WOY;
+  // z-chunk: the standard 16 layers, shortened on small grids so that the
+  // launch still covers the GPU (each chunk recomputes one element layer)
+  int zc = WZC;
+  while (zc > 2 && (long long)gx * gy * ((a.g.nnz + zc - 1) / zc) < 2 * 152) zc /= 2;
+  dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
+  k_apply3_col<TC, TX, TY, EPI, OP><<<grid, WX * WY, 0, s>>>(
+      a.g, a.gf, a.mask, kb, static_cast<const TC*>(a.coef), zc, static_cast<const TX*>(a.x),
+      static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
+      TC(a.omega), TC(a.dfix));
   return cudaGetLastError();
 }
 
-template <typename TC, typename TX, typename TY>
-static cudaError_t run_wht_epi(const ApplyArgs& a, cudaStream_t s) {
+template <typename TC, typename TX, typename TY, int OP>
+static cudaError_t run_col_epi(const ApplyArgs& a, cudaStream_t s) {
   switch (a.epi) {
-    case EPI_APPLY: return run_wht<TC, TX, TY, EPI_APPLY>(a, s);
-    case EPI_RESID: return run_wht<TC, TX, TY, EPI_RESID>(a, s);
-    default: return run_wht<TC, TX, TY, EPI_SMOOTH>(a, s);
+    case EPI_APPLY: return run_col<TC, TX, TY, EPI_APPLY, OP>(a, s);
+    case EPI_RESID: return run_col<TC, TX, TY, EPI_RESID, OP>(a, s);
+    default: return run_col<TC, TX, TY, EPI_SMOOTH, OP>(a, s);
   }
 }
 
-static cudaError_t run_wht_types(const ApplyArgs& a, cudaStream_t s) {
+template <int OP>
+static cudaError_t run_col_types(const ApplyArgs& a, cudaStream_t s) {
   if (a.tc == T_F64) {
     if (a.tx != T_F64 || a.ty != T_F64) return cudaErrorInvalidValue;
-    return run_wht_epi<double, double, double>(a, s);
+    return run_col_epi<double, double, double, OP>(a, s);
   }
-  if (a.tx == T_F64 && a.ty == T_F64) return run_wht_epi<float, double, double>(a, s);
-  if (a.tx == T_F32 && a.ty == T_F32) return run_wht_epi<float, float, float>(a, s);
-  if (a.tx == T_F32 && a.ty == T_F64) return run_wht_epi<float, float, double>(a, s);
+  if (a.tx == T_F32 && a.ty == T_F32) return run_col_epi<float, float, float, OP>(a, s);
+  if (OP == OPK_FINE) {
+    if (a.tx == T_F64 && a.ty == T_F64) return run_col_epi<float, double, double, OPK_FINE>(a, s);
+    if (a.tx == T_F32 && a.ty == T_F64) return run_col_epi<float, float, double, OPK_FINE>(a, s);
+  }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   if (a.g.nn <= 0) return cudaSuccess;
-  if (a.dim == 3 && !a.expl && a.wht != nullptr) return run_wht_types(a, s);
+  if (a.expl) return run_expl_any(a, s);
+  if (a.dim == 3) {
+    if (a.gal1) return run_col_types<OPK_GAL1>(a, s);
+    if (a.wht != nullptr) return run_col_types<OPK_FINE>(a, s);
+  }
   return a.dim == 2 ? run_apply_dim<2>(a, s) : run_apply_dim<3>(a, s);
 }
 

@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(256)
   constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gc.nel * ND * ND) return;
-  const long long E = t % gc.nel;
-  const int entry = (int)(t / gc.nel);
+  const long long E = t / (ND * ND);
+  const int entry = (int)(t % (ND * ND));
   const int EX = (int)(E % gc.nx);
   const long long rest = E / gc.nx;
   const int EY = (int)(rest % gc.ny);
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256)
     const long long fe = fx + (long long)gf.nx * (fy + (long long)gf.ny * (DIM == 3 ? fz : 0));
     acc += coef[fe] * Qc[c * ND * ND + entry];
   }
-  Kc[(size_t)entry * gc.nel + E] = acc;
+  Kc[(size_t)E * ND * ND + entry] = acc;
 }
 
 // Level-1 diagonal without stored matrices (3D): node I of level 1 sums, over
@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(256)
                   T* __restrict__ Kc) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g2.nel * 576) return;
-  const long long E = t % g2.nel;
-  const int entry = (int)(t / g2.nel);
+  const long long E = t / 576;
+  const int entry = (int)(t % 576);
   const int EX = (int)(E % g2.nx);
   const long long rest = E / g2.nx;
   const int EY = (int)(rest % g2.ny);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256)
     const int fz = 4 * EZ + 2 * ((c1 >> 2) & 1) + ((c0 >> 2) & 1);
     acc += coef[fx + (long long)gf.nx * (fy + (long long)gf.ny * fz)] * R[f * 576 + entry];
   }
-  Kc[(size_t)entry * g2.nel + E] = acc;
+  Kc[(size_t)E * 576 + entry] = acc;
 }
 
 // Galerkin level l+1 from stored level-l element matrices.  One block of
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
   for (int c = 0; c < NPE; ++c) {
     const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + ((c >> 2) & 1);
     const long long fe = fx + (long long)gf.nx * (fy + (long long)gf.ny * (DIM == 3 ? fz : 0));
-    sK[tid] = Kf[(size_t)tid * gf.nel + fe];
+    sK[tid] = Kf[(size_t)fe * ND * ND + tid];
     __syncthreads();
     // T[i][J] = sum_b K[i][(b, cj)] W_c[b][AJ]   (i = I here)
     T tv = T(0);
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
     for (int acn = 0; acn < NPE; ++acn) acc += T(wchild<DIM>(c, acn, AI)) * sT[(DIM * acn + ci) * ND + J];
     __syncthreads();
   }
-  Kc[(size_t)tid * gc.nel + E] = acc;
+  Kc[(size_t)E * ND * ND + tid] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256)
           const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
           const int ar = (ir - ex) + 2 * (jr - ey) + (DIM == 3 ? 4 * (kr - ez) : 0);
           const int ac = (ic - ex) + 2 * (jc - ey) + (DIM == 3 ? 4 * (kc - ez) : 0);
-          s += Kc[(size_t)((DIM * ar + cr) * ND + DIM * ac + cc) * g.nel + e];
+          s += Kc[(size_t)e * ND * ND + (DIM * ar + cr) * ND + DIM * ac + cc];
         }
   }
   A[t] = s;

@@ -299,6 +299,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   const int Ns = d.n_parm, Nm = d.n_carm;
   double *E64 = cv.take<double>(nel), *Ep64 = cv.take<double>(nel), *dE64 = cv.take<double>(nel);
   double *rho = cv.take<double>(nel), *invHs = cv.take<double>(nel), *oca = cv.take<double>(nel);
+  double *oclo = cv.take<double>(nel), *ochi = cv.take<double>(nel);
   float *E32 = cv.take<float>(nel), *Ep32 = cv.take<float>(nel), *dE32 = cv.take<float>(nel);
   double* f = cv.take<double>(n);
   double *r = cv.take<double>(n), *z = cv.take<double>(n), *p = cv.take<double>(n),
@@ -333,12 +334,14 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
     lv[l].r = cv.take<char>(nl * ts);
     const bool stored = l >= 2 || (l == 1 && !l1_implicit);
     lv[l].Kc = stored ? (void*)cv.take<char>((size_t)nd * nd * g.nel * ts) : nullptr;
+    lv[l].eo = stored ? (void*)cv.take<char>((size_t)nd * g.nel * ts) : nullptr;
   }
   const long long nc = lv[L - 1].n;
   void* Ad = cv.take<char>((size_t)nc * nc * ts);
   void* Ai = cv.take<char>((size_t)nc * nc * ts);
   if (c) {
     c->E64 = E64; c->Eprev64 = Ep64; c->dE64 = dE64; c->rho_phys = rho; c->invHs = invHs; c->oc_a = oca;
+    c->oc_lo = oclo; c->oc_hi = ochi;
     c->E32 = E32; c->Eprev32 = Ep32; c->dE32 = dE32; c->f = f;
     c->r = r; c->z = z; c->p = p; c->q = q; c->p32 = p32; c->q32 = q32;
     c->Phi = Phi; c->KPhi = KPhi; c->R = R; c->Q = Q; c->t = t;
@@ -579,6 +582,7 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.wht = c->dim == 3 ? (tc == T_F64 ? (const void*)c->wht64 : (const void*)c->wht32) : nullptr;
   a.gal1 = false;
   a.gf = c->lv[0].g;
+  a.eo = nullptr;
   a.x = x;
   a.y = y;
   a.b = b;
@@ -606,6 +610,7 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
   a.wht = nullptr;
   a.gal1 = false;
   a.gf = c->lv[0].g;
+  a.eo = c->lv[l].eo;
   if (l == 1 && c->l1_implicit) {
     // level-1 Galerkin operator evaluated from the finest moduli
     a.expl = false;
@@ -1023,7 +1028,8 @@ to_status to_sensitivity(to_ctx* c, const double* u, double* compliance_dev, dou
   if (!c || !u || !compliance_dev || !dc) return fail(c, TO_E_INVALID, "NULL argument");
   if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
   const to_mesh_desc& d = c->desc;
-  LAUNCH(c, launch_sensitivity(c->dim, c->lv[0].g, c->lv[0].mask, c->KE64, u, c->E64,
+  LAUNCH(c, launch_sensitivity(c->dim, c->lv[0].g, c->lv[0].mask, c->KE64,
+                               c->dim == 3 ? c->wht64 : nullptr, u, c->E64,
                                c->rho_phys, d.penal, d.E0, d.Emin, dc, compliance_dev,
                                c->partials, c->counters + C_SENS, c->stream), "sensitivity");
   return TO_OK;
@@ -1045,12 +1051,13 @@ to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_
   cudaStream_t s = c->stream;
   const long long nel = c->nel;
   const double target = volfrac * (double)nel;
-  LAUNCH(c, launch_oc_prep(nel, rho, dc_f, dv_f, c->oc_a, c->scal, s), "oc prep");
+  LAUNCH(c, launch_oc_prep_b(nel, rho, dc_f, dv_f, move, c->oc_a, c->oc_lo, c->oc_hi, c->scal, s),
+         "oc prep");
   // bisection steps run on the device; a step is a no-op once converged
   for (int chunk = 0; chunk < 8; ++chunk) {
     for (int q = 0; q < 32; ++q)
-      LAUNCH(c, launch_oc_step(nel, rho, c->oc_a, dv_f, move, target, c->scal, c->partials,
-                               c->counters + C_OC, s), "oc step");
+      LAUNCH(c, launch_oc_step_b(nel, c->oc_a, c->oc_lo, c->oc_hi, dv_f, target, c->scal,
+                                 c->partials, c->counters + C_OC, s), "oc step");
     double lr[2];
     CUDA_TRY(c, cudaMemcpyAsync(lr, c->scal + S_OC_L1, 16, cudaMemcpyDeviceToHost, s), "read");
     CUDA_TRY(c, cudaStreamSynchronize(s), "sync");

@@ -39,6 +39,28 @@ struct KEP {
   T v[ND * ND];
 };
 
+// The hex8 KE in the Walsh-Hadamard basis over element corners: eight 3x3
+// blocks, b[tau][c][c'] couples X[tau^e_c][c] and X[tau^e_c'][c'], with
+// KE = T B T and T the unnormalised transform (see kernels_fe.cu).
+template <typename TC>
+struct WhtBlocks {
+  TC b[8][3][3];
+};
+
+// in-place unnormalised Walsh-Hadamard transform of 8 corner values
+template <typename TC>
+__device__ __forceinline__ void fwht8(TC (&v)[8]) {
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!(a & h)) {
+        const TC u = v[a], w = v[a + h];
+        v[a] = u + w;
+        v[a + h] = u - w;
+      }
+}
+
 struct StencilP {
   int count;
   int d[MAX_STENCIL][3];
@@ -184,7 +206,8 @@ struct LevelBuf {
   void* z;               // T[n]
   void* z2;              // T[n]
   void* r;               // T[n]
-  void* Kc;              // T[ND*ND*nel], entry-major (levels >= 1)
+  void* Kc;              // T[nel*ND*ND], element-major (stored coarse levels)
+  void* eo;              // T[nel*ND]: per-element operator rows (stored levels)
 };
 
 struct to_ctx {
@@ -199,6 +222,7 @@ struct to_ctx {
   double *E64, *Eprev64, *dE64, *rho_phys;
   float *E32, *Eprev32, *dE32;
   double *f, *invHs, *oc_a;   // invHs: 1 / row sums of the filter weights
+  double *oc_lo, *oc_hi;      // OC move-limit bounds of the current update
   // CG
   double *r, *z, *p, *q;
   float *p32, *q32;     // float32 shadows of p and K p (mixed path)
