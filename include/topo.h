@@ -59,7 +59,7 @@ enum { TO_FP64 = 0, TO_MIXED = 1 };
 enum { TO_FILTER_DENSITY = 0, TO_FILTER_SENS = 1 };
 enum { TO_SOLVE_WARM_START = 1, TO_SOLVE_PUSH_PARM = 2 };
 enum { TO_OP_K = 0, TO_OP_KREF = 1, TO_OP_DK = 2 };
-enum { TO_PREC_NATIVE = 0, TO_PREC_FP64 = 1, TO_PREC_FP32 = 2 };
+enum { TO_PREC_NATIVE = 0, TO_PREC_FP64 = 1, TO_PREC_FP32 = 2, TO_PREC_DF = 3 };
 
 typedef struct to_ctx to_ctx;
 
@@ -186,7 +186,10 @@ to_status to_oc_update_noalloc(int64_t nel, double volfrac, double move, const d
 /* y = op(x) for x, y dev float64 n (no aliasing).  op: TO_OP_K (current
  * stiffness with BCs, Eq. 7), TO_OP_KREF (reference stiffness, Eq. 8) or
  * TO_OP_DK (dK = K - K_ref, zero on fixed DOFs).  prec: TO_PREC_NATIVE
- * (the context's apply precision), TO_PREC_FP64 or TO_PREC_FP32. */
+ * (the context's apply precision), TO_PREC_FP64, TO_PREC_FP32 or
+ * TO_PREC_DF (3D: double-float arithmetic on the FP32 pipe, ~2^-48
+ * relative; elsewhere float64).  TO_MIXED uses TO_PREC_DF for the products
+ * that must be float64-accurate (true CG residuals, K R~). */
 to_status to_apply(to_ctx* ctx, int32_t op, int32_t prec, const double* x, double* y);
 
 /* One V-cycle of the current hierarchy (Algorithm 2): z ~= K^{-1} r, with

@@ -22,7 +22,7 @@ TO_FP64, TO_MIXED = 0, 1
 TO_FILTER_DENSITY, TO_FILTER_SENS = 0, 1
 TO_SOLVE_WARM_START, TO_SOLVE_PUSH_PARM = 1, 2
 TO_OP_K, TO_OP_KREF, TO_OP_DK = 0, 1, 2
-TO_PREC_NATIVE, TO_PREC_FP64, TO_PREC_FP32 = 0, 1, 2
+TO_PREC_NATIVE, TO_PREC_FP64, TO_PREC_FP32, TO_PREC_DF = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "TO_OK", 1: "TO_E_INVALID", 2: "TO_E_STATE", 3: "TO_E_OOM", 4: "TO_E_CUDA",
                 5: "TO_E_NOT_CONVERGED", 6: "TO_E_SINGULAR", 7: "TO_E_TIMEOUT"}

@@ -5,7 +5,9 @@
 
 namespace topo {
 
-enum { T_F64 = 0, T_F32 = 1 };
+// arithmetic / storage types; T_DF = float64 storage with double-float
+// arithmetic on the FP32 pipe (finest 3D grid only)
+enum { T_F64 = 0, T_F32 = 1, T_DF = 2 };
 enum { EPI_APPLY = 0, EPI_RESID = 1, EPI_SMOOTH = 2 };
 
 // Stiffness operator of one grid level,
@@ -38,6 +40,11 @@ struct ApplyArgs {
   void* eo;            // explicit levels: per-element output rows [nel * ND] of type tc
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+// Double-float finest-grid operator (kernels_df.cu): float64 x/b/y, float64
+// moduli in coef, float64 Walsh blocks in wht; EPI_APPLY or EPI_RESID.
+cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s);
+// true if the Walsh blocks have the structural zeros the double-float kernel skips
+bool df_blocks_ok(const double* wht64);
 // Host: the eight 3x3 blocks of the hex8 KE in the corner Walsh-Hadamard basis
 void wht_blocks(const double* KE, double* out64, float* out32);
 

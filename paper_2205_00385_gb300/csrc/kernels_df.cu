@@ -1,0 +1,261 @@
+// Float64-accurate hex8 stiffness operator in double-float arithmetic.
+//
+// GB300 runs float64 at ~1/64 of the float32 rate, so the float64 Walsh
+// kernel (k_apply3_col<double>) is bound by the FP64 pipe at ~1.3 ms per
+// 5.4M-DOF apply.  Here every value is an unevaluated sum hi + lo of two
+// floats (48-bit significand) and all arithmetic runs on the FP32 pipe with
+// error-free transformations (TwoSum, FMA-based TwoProduct).  float64 inputs
+// are split into (hi, lo) and results widened back with integer bit
+// operations, so the FP64 pipe only sees the final additions of the
+// epilogue.  The structure (element columns streamed in z, owner-computes
+// node sums in shared memory, Walsh blocks) is that of k_apply3_col.
+#include "kernels.h"
+
+namespace topo {
+
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float h = p + e;
+  return {h, e - (h - p)};
+}
+
+// double -> (hi, lo) with integer operations: hi keeps the leading 24
+// significant bits (truncated), lo the next 24 of the remaining 29.  Values
+// outside [2^-100, 2^100] (zero, or far outside the data's range) take the
+// conversion instructions instead.
+__device__ __forceinline__ dfl split_d(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  if (e < 1023 - 100 || e > 1023 + 100) {
+    if (e == 0) return {0.f, 0.f};
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+  }
+  const unsigned s = (unsigned)(u >> 63) << 31;
+  const float h = __uint_as_float(s | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
+  const unsigned L = (unsigned)(u & 0x1FFFFFFFu);
+  if (L == 0u) return {h, 0.f};
+  const int sh = __clz((int)L) - 8;                  // puts the leading one at bit 23
+  const unsigned m = sh >= 0 ? (L << sh) : (L >> (-sh));
+  const int ef = e - 925 - sh;                       // float exponent field of lo
+  if (ef <= 0) return {h, 0.f};                      // below 2^-126: negligible
+  return {h, __uint_as_float(s | ((unsigned)ef << 23) | (m & 0x7FFFFFu))};
+}
+
+// exact float -> double with integer operations (zero and normal floats)
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xFFu;
+  if (ef == 0u) return 0.0;
+  if (ef == 0xFFu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(ef + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+__device__ __forceinline__ void fwht8_df(dfl (&v)[8]) {
+#pragma unroll
+  for (int hh = 1; hh < 8; hh <<= 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!(a & hh)) {
+        const dfl u = v[a], w = v[a + hh];
+        v[a] = df_add(u, w);
+        v[a + hh] = df_add(u, df_neg(w));
+      }
+}
+
+// Structural zeros of the Walsh blocks of an isotropic hex8 KE: for a
+// single-bit character tau = e_k the translation component k decouples
+// (row and column zero); for a two-bit character the third component
+// decouples from the other two.
+__host__ __device__ constexpr bool wht_zero(int tau, int c, int cp) {
+  return (tau == 1 || tau == 2 || tau == 4)
+             ? (tau == (1 << c) || tau == (1 << cp))
+             : ((tau == 3 || tau == 5 || tau == 6) && c != cp &&
+                ((7 ^ tau) == (1 << c) || (7 ^ tau) == (1 << cp)));
+}
+
+struct DfBlocks {
+  float h[8][3][3], l[8][3][3];
+};
+
+constexpr int DX = 16, DY = 8, DOX = DX - 1, DOY = DY - 1;
+
+template <int EPI>
+__global__ void __launch_bounds__(DX * DY)
+    k_apply3_df(GridP g, const uint8_t* __restrict__ mask, DfBlocks kb,
+                const double* __restrict__ coef, int zc, const double* __restrict__ x,
+                double* __restrict__ y, const double* __restrict__ b, double dfix) {
+  __shared__ dfl part[2][4][DY][DX][3];
+  const int tx = threadIdx.x % DX, ty = threadIdx.x / DX;
+  const int x0 = blockIdx.x * DOX, y0 = blockIdx.y * DOY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nnz);
+  const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
+  const bool col_ok = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
+  const long long plane = (long long)g.nnx * g.nny;
+
+  dfl xb[4][3], xt[4][3], acc[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[q][c] = {0.f, 0.f};
+
+  auto load_face = [&](int kz, dfl (&f)[4][3]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = ex + (q & 1), j = ey + (q >> 1);
+      if (col_ok && kz >= 0 && kz < g.nnz) {
+        const long long nd = i + (long long)g.nnx * j + plane * kz;
+        const unsigned m = mask[nd];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          f[q][c] = ((m >> c) & 1u) ? dfl{0.f, 0.f} : split_d(x[3 * nd + c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[q][c] = {0.f, 0.f};
+      }
+    }
+  };
+
+  load_face(z0 - 1, xb);
+  const bool own = tx < DOX && ty < DOY && (x0 + tx) < g.nnx && (y0 + ty) < g.nny;
+  int buf = 0;
+  for (int ez = z0 - 1; ez < z1; ++ez) {
+    load_face(ez + 1, xt);
+    dfl ye[8][3];
+    if (col_ok && ez >= 0 && ez < g.nz) {
+      const dfl ce = split_d(coef[ex + (long long)g.nx * (ey + (long long)g.ny * ez)]);
+      dfl X[3][8];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          X[c][q] = xb[q][c];
+          X[c][q + 4] = xt[q][c];
+        }
+        fwht8_df(X[c]);
+      }
+      dfl Y[3][8];
+#pragma unroll
+      for (int tau = 0; tau < 8; ++tau) {
+        dfl zt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) zt[c] = df_mul(ce, X[c][tau ^ (1 << c)]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dfl s = {0.f, 0.f};
+          bool first = true;
+#pragma unroll
+          for (int cp = 0; cp < 3; ++cp) {
+            if (wht_zero(tau, c, cp)) continue;
+            const dfl t = df_mul(dfl{kb.h[tau][c][cp], kb.l[tau][c][cp]}, zt[cp]);
+            s = first ? t : df_add(s, t);
+            first = false;
+          }
+          Y[c][tau ^ (1 << c)] = s;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        fwht8_df(Y[c]);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) ye[a][c] = Y[c][a];
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ye[a][c] = {0.f, 0.f};
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        part[buf][q][ty][tx][c] = df_add(acc[q][c], ye[q][c]);
+        acc[q][c] = ye[q + 4][c];
+        xb[q][c] = xt[q][c];
+      }
+    __syncthreads();
+    if (own && ez >= z0) {
+      const long long nd = (x0 + tx) + (long long)g.nnx * (y0 + ty) + plane * ez;
+      const unsigned m = mask[nd];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const dfl s = df_add(df_add(df_add(part[buf][3][ty][tx][c], part[buf][2][ty][tx + 1][c]),
+                                    part[buf][1][ty + 1][tx][c]),
+                             part[buf][0][ty + 1][tx + 1][c]);
+        const long long d = 3 * nd + c;
+        if ((m >> c) & 1u) {
+          const double Ax = dfix * x[d];
+          y[d] = EPI == EPI_RESID ? b[d] - Ax : Ax;
+        } else if (EPI == EPI_RESID) {
+          // b and K x nearly cancel near convergence: subtract the leading
+          // part first (exact when close), then the trailing part
+          y[d] = (b[d] - f2d(s.h)) - f2d(s.l);
+        } else {
+          y[d] = f2d(s.h) + f2d(s.l);
+        }
+      }
+    }
+    buf ^= 1;
+  }
+}
+
+bool df_blocks_ok(const double* wht64) {
+  double mx = 0.0;
+  for (int q = 0; q < 72; ++q) mx = fmax(mx, fabs(wht64[q]));
+  for (int tau = 0; tau < 8; ++tau)
+    for (int c = 0; c < 3; ++c)
+      for (int cp = 0; cp < 3; ++cp)
+        if (wht_zero(tau, c, cp) && fabs(wht64[(tau * 3 + c) * 3 + cp]) > 1e-14 * mx) return false;
+  return true;
+}
+
+cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s) {
+  if (a.dim != 3 || a.expl || a.gal1 || a.tx != T_F64 || a.ty != T_F64 || !a.wht ||
+      a.epi == EPI_SMOOTH)
+    return cudaErrorInvalidValue;
+  if (a.g.nn <= 0) return cudaSuccess;
+  const double* w = static_cast<const double*>(a.wht);
+  DfBlocks kb;
+  for (int q = 0; q < 72; ++q) {
+    const float h = (float)w[q];
+    (&kb.h[0][0][0])[q] = h;
+    (&kb.l[0][0][0])[q] = (float)(w[q] - (double)h);
+  }
+  const int gx = (a.g.nnx + DOX - 1) / DOX, gy = (a.g.nny + DOY - 1) / DOY;
+  int zc = 16;
+  while (zc > 2 && (long long)gx * gy * ((a.g.nnz + zc - 1) / zc) < 2 * 152) zc /= 2;
+  dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
+  if (a.epi == EPI_RESID)
+    k_apply3_df<EPI_RESID><<<grid, DX * DY, 0, s>>>(
+        a.g, a.mask, kb, static_cast<const double*>(a.coef), zc, static_cast<const double*>(a.x),
+        static_cast<double*>(a.y), static_cast<const double*>(a.b), a.dfix);
+  else
+    k_apply3_df<EPI_APPLY><<<grid, DX * DY, 0, s>>>(
+        a.g, a.mask, kb, static_cast<const double*>(a.coef), zc, static_cast<const double*>(a.x),
+        static_cast<double*>(a.y), static_cast<const double*>(a.b), a.dfix);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

@@ -589,6 +589,7 @@ static cudaError_t run_col_types(const ApplyArgs& a, cudaStream_t s) {
 
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   if (a.g.nn <= 0) return cudaSuccess;
+  if (a.tc == T_DF) return launch_apply_df(a, s);
   if (a.expl) return run_expl_any(a, s);
   if (a.dim == 3) {
     if (a.gal1) return run_col_types<OPK_GAL1>(a, s);

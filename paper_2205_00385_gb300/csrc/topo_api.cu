@@ -458,6 +458,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   element_stiffness(c->dim, desc->nu, c->KE64);
   for (int q = 0; q < c->nd * c->nd; ++q) c->KE32[q] = (float)c->KE64[q];
   if (c->dim == 3) wht_blocks(c->KE64, c->wht64, c->wht32);
+  c->df_ok = c->dim == 3 && df_blocks_ok(c->wht64);
   std::vector<double> Qc((size_t)c->npe * c->nd * c->nd);
   child_galerkin(c->dim, c->KE64, Qc.data());
   std::vector<float> Qc32(Qc.size());
@@ -560,7 +561,7 @@ to_status to_set_density(to_ctx* c, const double* rho_phys) {
 static int mg_t(const to_ctx* c) { return c->mixed ? T_F32 : T_F64; }
 
 static const void* coef_for(const to_ctx* c, int op, int tc) {
-  if (tc == T_F64) return op == TO_OP_K ? (const void*)c->E64
+  if (tc == T_F64 || tc == T_DF) return op == TO_OP_K ? (const void*)c->E64
                         : op == TO_OP_KREF ? (const void*)c->Eprev64 : (const void*)c->dE64;
   return op == TO_OP_K ? (const void*)c->E32
          : op == TO_OP_KREF ? (const void*)c->Eprev32 : (const void*)c->dE32;
@@ -578,8 +579,9 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.expl = false;
   a.coef = coef_for(c, op, tc);
   a.Kc = nullptr;
-  a.ke = tc == T_F64 ? (const void*)c->KE64 : (const void*)c->KE32;
-  a.wht = c->dim == 3 ? (tc == T_F64 ? (const void*)c->wht64 : (const void*)c->wht32) : nullptr;
+  const bool wide = tc == T_F64 || tc == T_DF;
+  a.ke = wide ? (const void*)c->KE64 : (const void*)c->KE32;
+  a.wht = c->dim == 3 ? (wide ? (const void*)c->wht64 : (const void*)c->wht32) : nullptr;
   a.gal1 = false;
   a.gf = c->lv[0].g;
   a.eo = nullptr;
@@ -633,7 +635,7 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
 // array touched once (the 3^dim neighbourhood reuse is not counted).
 static double apply_bytes(const ApplyArgs& a) {
   const double sx = a.tx == T_F64 ? 8.0 : 4.0, sy = a.ty == T_F64 ? 8.0 : 4.0;
-  const double sc = a.tc == T_F64 ? 8.0 : 4.0;
+  const double sc = a.tc == T_F32 ? 4.0 : 8.0;
   const double n = (double)a.dim * (double)a.g.nn, nel = (double)a.g.nel;
   const int nd = a.dim * (1 << a.dim);
   double b = n * (sx + sy) + (double)a.g.nn;          // x, y, node masks
@@ -747,8 +749,13 @@ static to_status check_status(to_ctx* c) {
 static int apply_tc(const to_ctx* c, int prec) {
   if (prec == TO_PREC_FP64) return T_F64;
   if (prec == TO_PREC_FP32) return T_F32;
+  if (prec == TO_PREC_DF) return c->df_ok ? T_DF : T_F64;
   return c->mixed ? T_F32 : T_F64;
 }
+
+// Arithmetic of the float64-accurate products (true residuals, K R~): the
+// FP64 path uses float64; the mixed path double-float where available.
+static int accurate_tc(const to_ctx* c) { return (c->mixed && c->df_ok) ? T_DF : T_F64; }
 
 static to_status apply_op(to_ctx* c, int op, int prec, const double* x, double* y) {
   return run_op(c, fine_args(c, op, apply_tc(c, prec), T_F64, T_F64, x, y, nullptr, nullptr,
@@ -772,7 +779,7 @@ extern "C" {
 
 to_status to_apply(to_ctx* c, int32_t op, int32_t prec, const double* x, double* y) {
   if (!c || !x || !y || x == y) return fail(c, TO_E_INVALID, "bad arguments");
-  if (op < TO_OP_K || op > TO_OP_DK || prec < 0 || prec > 2) return fail(c, TO_E_INVALID, "bad op");
+  if (op < TO_OP_K || op > TO_OP_DK || prec < 0 || prec > 3) return fail(c, TO_E_INVALID, "bad op");
   if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
   return apply_op(c, op, prec, x, y);
 }
@@ -829,7 +836,7 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   // r = f - K x, always with the float64 operator (the true residual)
   auto true_residual = [&](double* rr_out) -> to_status {
     to_status e;
-    if ((e = run_op(c, fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, x, c->r, c->f, nullptr,
+    if ((e = run_op(c, fine_args(c, TO_OP_K, accurate_tc(c), T_F64, T_F64, x, c->r, c->f, nullptr,
                                  EPI_RESID), "true residual")) != TO_OK)
       return e;
     LAUNCH(c, launch_dot(n, c->r, c->r, c->partials, c->counters + C_DOT, c->scal + S_RR, s),
@@ -1003,7 +1010,9 @@ to_status to_carm_solve(to_ctx* c, double* u, double* eps, double* eps_dev) {
   // K R~ enters the reduced matrix and the residual check, so it always uses
   // the float64 operator; the basis itself may be built in float32.
   for (int j = 0; j < k; ++j)
-    if ((st = apply_op(c, TO_OP_K, TO_PREC_FP64, c->R + (size_t)j * n, c->Q + (size_t)j * n)) != TO_OK)
+    if ((st = run_op(c, fine_args(c, TO_OP_K, accurate_tc(c), T_F64, T_F64, c->R + (size_t)j * n,
+                                  c->Q + (size_t)j * n, nullptr, nullptr, EPI_APPLY),
+                     "K R")) != TO_OK)
       return st;
   LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->Q, k, nullptr, small + SM_KR, k, c->partials,
                             c->counters + C_MULTI, s), "K_R");

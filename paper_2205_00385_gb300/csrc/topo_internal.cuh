@@ -235,6 +235,7 @@ struct to_ctx {
   // 3D, >= 3 levels: level 1 applied from the finest moduli (no stored
   // matrices); level 2 formed with the 64 grandchild tables R2
   bool l1_implicit;
+  bool df_ok;          // double-float finest-grid operator available (3D)
   double* R2_64;
   float* R2_32;
   double qdiag[192];   // diag(Q_ch) per child and corner, for the level-1 diagonal

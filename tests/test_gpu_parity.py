@@ -66,12 +66,17 @@ def test_apply_parity(kind, kw, op):
         xd = dev(x)
         y64 = dev(np.zeros(g.ndof))
         y32 = dev(np.zeros(g.ndof))
+        ydf = dev(np.zeros(g.ndof))
         B.to_apply(c.ctx, op, B.TO_PREC_FP64, xd, y64)
         B.to_apply(c.ctx, op, B.TO_PREC_FP32, xd, y32)
-        y64, y32 = host(y64), host(y32)
+        B.to_apply(c.ctx, op, B.TO_PREC_DF, xd, ydf)
+        y64, y32, ydf = host(y64), host(y32), host(ydf)
     scale = np.max(np.abs(y_ref))
     assert np.max(np.abs(y64 - y_ref)) <= 1e-13 * scale
     assert np.linalg.norm(y32 - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+    # double-float: 48-bit significands, errors relative to |KE| |x_e| summed
+    # over ~30 terms per entry -> 1e-12 of the largest entry
+    assert np.max(np.abs(ydf - y_ref)) <= 1e-12 * scale
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
