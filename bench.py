@@ -49,6 +49,10 @@ def _args():
     ap.add_argument("--kernel", default=None, choices=[None, "apply"],
                     help="time one kernel alone (profiling) instead of the design loop")
     ap.add_argument("--kernel-prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--serve-jobs", type=int, default=24,
+                    help="jobs of the served stream replayed for p50/p99 (0: skip)")
+    ap.add_argument("--serve-iters", type=int, default=6)
+    ap.add_argument("--serve-time-scale", type=float, default=0.25)
     return ap.parse_args()
 
 
@@ -318,6 +322,22 @@ def run_ours(args):
         "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         "wall_s": round(wall, 3),
     }
+    if args.serve_jobs > 0 and ws == 1:
+        from paper_2205_00385_gb300.serve import Server
+        from workloads import config5_jobs
+        jobs = config5_jobs()[:args.serve_jobs]
+        rep = Server(int(120 * 2 ** 30), max_active=16).run(jobs, args.serve_iters,
+                                                          args.serve_time_scale)
+        line["serving"] = {
+            "stream": (f"first {args.serve_jobs} jobs of the 256-job Poisson stream (4 jobs/s, "
+                       f"arrivals x{args.serve_time_scale}), {args.serve_iters} design iterations "
+                       "each, mixed precision, HBM budget 120 GiB, up to 16 concurrent jobs"),
+            "throughput_iters_per_s": round(rep["throughput_iters_per_s"], 2),
+            "iter_latency_ms_p50": round(rep["iter_latency_ms"]["p50"], 2),
+            "iter_latency_ms_p99": round(rep["iter_latency_ms"]["p99"], 2),
+            "job_latency_s_p50": round(rep["job_latency_s"]["p50"], 3),
+            "job_latency_s_p99": round(rep["job_latency_s"]["p99"], 3),
+            "peak_active_jobs": rep["peak_active_jobs"], "jobs_done": rep["jobs_done"]}
     if not args.no_cpu_baseline and ws == 1:
         try:
             line["cpu_baseline"] = cpu_baseline(2, p.precision)

@@ -322,6 +322,93 @@ __global__ void __launch_bounds__(1024) k_cholesky(int n, T* __restrict__ A, int
   if (threadIdx.x == 0 && s_bad) *status = TO_E_SINGULAR;
 }
 
+// Blocked right-looking Cholesky (lower, in place) by one block of 1024
+// threads: per 32-column block, the diagonal block is factored by one warp
+// in shared memory, the panel below it is solved row by row, staged in
+// shared memory, and the trailing lower triangle is updated by all threads.
+constexpr int CB = 32, CBP = 33;
+
+__device__ __forceinline__ void tri_index(long long p, int& ii, int& jj) {
+  // float estimate (GB300's FP64 pipe is slow), corrected in integers
+  int r = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  while ((long long)r * (r + 1) / 2 > p) --r;
+  while ((long long)(r + 1) * (r + 2) / 2 <= p) ++r;
+  ii = r;
+  jj = (int)(p - (long long)r * (r + 1) / 2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_cholesky_blocked(int n, T* __restrict__ A, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Dg = reinterpret_cast<T*>(smem_raw);   // CB x CBP
+  T* Pn = Dg + CB * CBP;                    // (n) x CBP panel rows
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_bad = 0;
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    const int kb = min(CB, n - k0);
+    for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+      const int r = idx / kb, cc = idx % kb;
+      Dg[r * CBP + cc] = A[(size_t)(k0 + r) * n + k0 + cc];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int j = 0; j < kb; ++j) {
+        if (lane == 0) {
+          T d = Dg[j * CBP + j];
+          if (!(d > T(0))) {
+            s_bad = 1;
+            d = T(1);
+          }
+          Dg[j * CBP + j] = sqrt(d);
+        }
+        __syncwarp();
+        const T ljj = Dg[j * CBP + j];
+        if (lane > j && lane < kb) Dg[lane * CBP + j] /= ljj;
+        __syncwarp();
+        if (lane > j && lane < kb) {
+          const T lij = Dg[lane * CBP + j];
+          for (int jj = j + 1; jj <= lane; ++jj) Dg[lane * CBP + jj] -= lij * Dg[jj * CBP + j];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+      const int r = idx / kb, cc = idx % kb;
+      if (cc <= r) A[(size_t)(k0 + r) * n + k0 + cc] = Dg[r * CBP + cc];
+    }
+    const int m = n - k0 - kb;
+    for (int r = tid; r < m; r += blockDim.x) {
+      const size_t row = (size_t)(k0 + kb + r) * n + k0;
+      T xr[CB];
+#pragma unroll
+      for (int cc = 0; cc < CB; ++cc) {
+        if (cc < kb) {
+          T s = A[row + cc];
+#pragma unroll
+          for (int t = 0; t < CB; ++t)
+            if (t < cc) s -= xr[t] * Dg[cc * CBP + t];
+          xr[cc] = s / Dg[cc * CBP + cc];
+          A[row + cc] = xr[cc];
+          Pn[r * CBP + cc] = xr[cc];
+        }
+      }
+    }
+    __syncthreads();
+    const long long total = (long long)m * (m + 1) / 2;
+    for (long long p = tid; p < total; p += blockDim.x) {
+      int ii, jj;
+      tri_index(p, ii, jj);
+      T s = T(0);
+      for (int t = 0; t < kb; ++t) s += Pn[ii * CBP + t] * Pn[jj * CBP + t];
+      A[(size_t)(k0 + kb + ii) * n + k0 + kb + jj] -= s;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad) *status = TO_E_SINGULAR;
+}
+
 // X = L^{-1} by forward substitution, one warp per column (stored in the
 // upper triangle-free buffer Linv, row-major, zero above the diagonal).
 template <typename T>
@@ -512,8 +599,17 @@ cudaError_t launch_dense_assemble(int dim, int t, const GridP& g, const uint8_t*
 
 template <typename T>
 static cudaError_t cholinv_t(int n, void* A, void* Ainv, int* status, cudaStream_t s) {
-  k_cholesky<T><<<1, 1024, 0, s>>>(n, (T*)A, status);
-  cudaError_t e = cudaGetLastError();
+  const size_t smem = (size_t)(CB * CBP + (size_t)n * CBP) * sizeof(T);
+  cudaError_t e;
+  if (smem <= 227 * 1024) {
+    e = cudaFuncSetAttribute(k_cholesky_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_cholesky_blocked<T><<<1, 1024, smem, s>>>(n, (T*)A, status);
+  } else {
+    k_cholesky<T><<<1, 1024, 0, s>>>(n, (T*)A, status);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // Ainv is used as scratch for L^{-1} first, then A receives X^T X and
   // the buffers are swapped by copying back.

@@ -120,7 +120,9 @@ class TopoSolver:
                        self.scalars[1:2])
         C = change = float("nan")
         if read_compliance:
-            vals = self.scalars[:2].cpu().numpy()
+            torch = _torch()
+            with torch.cuda.stream(self.stream):
+                vals = self.scalars[:2].cpu().numpy()
             C, change = float(vals[0]), float(vals[1])
         log = IterLog(k, branch, C, eps, iters, change, time.perf_counter() - t0)
         self.history.append(log)
