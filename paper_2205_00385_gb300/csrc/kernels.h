@@ -43,10 +43,12 @@ cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 // Double-float finest-grid operator (kernels_df.cu): float64 x/b/y, float64
 // moduli in coef, float64 Walsh blocks in wht; EPI_APPLY or EPI_RESID.
 cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s);
-// true if the Walsh blocks have the structural zeros the double-float kernel skips
+// true if the Walsh blocks have the structural zeros (wht_zero) to rounding
 bool df_blocks_ok(const double* wht64);
 // Host: the eight 3x3 blocks of the hex8 KE in the corner Walsh-Hadamard basis
-void wht_blocks(const double* KE, double* out64, float* out32);
+void wht_blocks(const double* KE, double* out64);
+// Host: store the verified structural zeros exactly and round to float32
+void wht_blocks_pin_zeros(double* w64, float* w32);
 
 // dinv = 1 / diag(A) (1 on fixed DOFs)
 cudaError_t launch_diag(int dim, const GridP& g, const uint8_t* mask, int tc, bool expl,

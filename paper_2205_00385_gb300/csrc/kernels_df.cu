@@ -84,17 +84,6 @@ __device__ __forceinline__ void fwht8_df(dfl (&v)[8]) {
       }
 }
 
-// Structural zeros of the Walsh blocks of an isotropic hex8 KE: for a
-// single-bit character tau = e_k the translation component k decouples
-// (row and column zero); for a two-bit character the third component
-// decouples from the other two.
-__host__ __device__ constexpr bool wht_zero(int tau, int c, int cp) {
-  return (tau == 1 || tau == 2 || tau == 4)
-             ? (tau == (1 << c) || tau == (1 << cp))
-             : ((tau == 3 || tau == 5 || tau == 6) && c != cp &&
-                ((7 ^ tau) == (1 << c) || (7 ^ tau) == (1 << cp)));
-}
-
 struct DfBlocks {
   float h[8][3][3], l[8][3][3];
 };

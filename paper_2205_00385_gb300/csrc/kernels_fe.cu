@@ -142,6 +142,21 @@ __host__ __device__ constexpr float wmix(int ch, int t, int tp) {
          ((t & 4) ? ((tp & 4) ? 0.5f : 0.0f) : ((tp & 4) ? ((ch & 4) ? -0.5f : 0.5f) : 1.0f));
 }
 
+// Row c of Walsh block tau times zt, skipping the block's structural zeros
+// (27 of the 72 entries; their indices are compile-time after unrolling).
+template <typename TC>
+__device__ __forceinline__ TC wht_row(const WhtBlocks<TC>& kb, int tau, int c, const TC (&zt)[3]) {
+  TC s = TC(0);
+  bool first = true;
+#pragma unroll
+  for (int cp = 0; cp < 3; ++cp) {
+    if (wht_zero(tau, c, cp)) continue;
+    s = first ? kb.b[tau][c][cp] * zt[cp] : fma(kb.b[tau][c][cp], zt[cp], s);
+    first = false;
+  }
+  return s;
+}
+
 // ye = element operator applied to the element's nodal values (bottom face
 // xb = corners 0..3, top face xt = corners 4..7).  GAL1 = false: E_e KE; true:
 // the level-1 Galerkin composite with the eight child moduli ce[].
@@ -167,12 +182,7 @@ __device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&
 #pragma unroll
       for (int c = 0; c < 3; ++c) zt[c] = ce[0] * X[c][tau ^ (1 << c)];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        TC s = kb.b[tau][c][0] * zt[0];
-        s = fma(kb.b[tau][c][1], zt[1], s);
-        s = fma(kb.b[tau][c][2], zt[2], s);
-        Y[c][tau ^ (1 << c)] = s;
-      }
+      for (int c = 0; c < 3; ++c) Y[c][tau ^ (1 << c)] = wht_row(kb, tau, c, zt);
     }
   } else {
 #pragma unroll
@@ -198,12 +208,7 @@ __device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&
 #pragma unroll
         for (int c = 0; c < 3; ++c) zt[c] = ce[ch] * Xf[c][tau ^ (1 << c)];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          TC s = kb.b[tau][c][0] * zt[0];
-          s = fma(kb.b[tau][c][1], zt[1], s);
-          s = fma(kb.b[tau][c][2], zt[2], s);
-          Zf[c][tau ^ (1 << c)] = s;
-        }
+        for (int c = 0; c < 3; ++c) Zf[c][tau ^ (1 << c)] = wht_row(kb, tau, c, zt);
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -387,28 +392,43 @@ __global__ void __launch_bounds__(WX * WY)
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[q][c] = TC(0);
 
-  auto load_face = [&](int kz, TC (&f)[4][3]) {
+  // Face loads are software-pipelined: the raw values and masks of the next
+  // top face are requested before the current element is computed, so their
+  // latency overlaps the arithmetic.
+  TX raw[4][3];
+  unsigned rmask = 0u;   // 3 bits per corner; all set = out of range
+  auto issue_face = [&](int kz) {
+    rmask = 0u;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = ex + (q & 1), j = ey + (q >> 1);
-      bool in = col_ok && kz >= 0 && kz < g.nnz;
-      if (in) {
+      if (col_ok && kz >= 0 && kz < g.nnz) {
         const long long nd = i + (long long)g.nnx * j + plane * kz;
-        const unsigned m = mask[nd];
+        rmask |= ((unsigned)mask[nd] & 7u) << (3 * q);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) f[q][c] = ((m >> c) & 1u) ? TC(0) : TC(x[3 * nd + c]);
+        for (int c = 0; c < 3; ++c) raw[q][c] = x[3 * nd + c];
       } else {
+        rmask |= 7u << (3 * q);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) f[q][c] = TC(0);
+        for (int c = 0; c < 3; ++c) raw[q][c] = TX(0);
       }
     }
   };
+  auto consume_face = [&](TC (&f)[4][3]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) f[q][c] = ((rmask >> (3 * q + c)) & 1u) ? TC(0) : TC(raw[q][c]);
+  };
 
-  load_face(z0 - 1, xb);
+  issue_face(z0 - 1);
+  consume_face(xb);
+  issue_face(z0);
   const bool own = tx < WOX && ty < WOY && (x0 + tx) < g.nnx && (y0 + ty) < g.nny;
   int buf = 0;
   for (int ez = z0 - 1; ez < z1; ++ez) {
-    load_face(ez + 1, xt);
+    consume_face(xt);
+    if (ez + 2 <= z1) issue_face(ez + 2);
     TC ye[8][3];
     const bool el_ok = col_ok && ez >= 0 && ez < g.nz;
     if (el_ok) {
@@ -598,7 +618,7 @@ cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   return a.dim == 2 ? run_apply_dim<2>(a, s) : run_apply_dim<3>(a, s);
 }
 
-void wht_blocks(const double* KE, double* out64, float* out32) {
+void wht_blocks(const double* KE, double* out64) {
   // B = T KE T / 64 with T[(t,c),(a,c)] = (-1)^{popcount(a & t)}, restricted
   // to the eight 3x3 blocks of characters tau = t xor e_c.
   auto sgn = [](int a, int t) { return (__builtin_popcount(a & t) & 1) ? -1.0 : 1.0; };
@@ -611,7 +631,16 @@ void wht_blocks(const double* KE, double* out64, float* out32) {
           for (int ap = 0; ap < 8; ++ap) s += sgn(a, t) * KE[(3 * a + c) * 24 + 3 * ap + cp] * sgn(ap, tp);
         s /= 64.0;
         out64[(tau * 3 + c) * 3 + cp] = s;
-        out32[(tau * 3 + c) * 3 + cp] = (float)s;
+      }
+}
+
+void wht_blocks_pin_zeros(double* w64, float* w32) {
+  for (int tau = 0; tau < 8; ++tau)
+    for (int c = 0; c < 3; ++c)
+      for (int cp = 0; cp < 3; ++cp) {
+        const int q = (tau * 3 + c) * 3 + cp;
+        if (wht_zero(tau, c, cp)) w64[q] = 0.0;
+        w32[q] = (float)w64[q];
       }
 }
 

@@ -457,8 +457,15 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   }
   element_stiffness(c->dim, desc->nu, c->KE64);
   for (int q = 0; q < c->nd * c->nd; ++q) c->KE32[q] = (float)c->KE64[q];
-  if (c->dim == 3) wht_blocks(c->KE64, c->wht64, c->wht32);
-  c->df_ok = c->dim == 3 && df_blocks_ok(c->wht64);
+  if (c->dim == 3) {
+    wht_blocks(c->KE64, c->wht64);
+    if (!df_blocks_ok(c->wht64)) {
+      delete c;
+      return fail(nullptr, TO_E_INVALID, "element Walsh blocks lack their structural zeros");
+    }
+    wht_blocks_pin_zeros(c->wht64, c->wht32);
+  }
+  c->df_ok = c->dim == 3;
   std::vector<double> Qc((size_t)c->npe * c->nd * c->nd);
   child_galerkin(c->dim, c->KE64, Qc.data());
   std::vector<float> Qc32(Qc.size());

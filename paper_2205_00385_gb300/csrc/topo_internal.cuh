@@ -47,6 +47,18 @@ struct WhtBlocks {
   TC b[8][3][3];
 };
 
+// Structural zeros of the Walsh blocks of an isotropic hex8 KE: for a
+// single-bit character tau = e_k the translation component k decouples
+// (row and column zero); for a two-bit character the third component
+// decouples from the other two.  The host verifies these entries vanish
+// to rounding and stores them as exact zeros; kernels skip them.
+__host__ __device__ constexpr bool wht_zero(int tau, int c, int cp) {
+  return (tau == 1 || tau == 2 || tau == 4)
+             ? (tau == (1 << c) || tau == (1 << cp))
+             : ((tau == 3 || tau == 5 || tau == 6) && c != cp &&
+                ((7 ^ tau) == (1 << c) || (7 ^ tau) == (1 << cp)));
+}
+
 // in-place unnormalised Walsh-Hadamard transform of 8 corner values
 template <typename TC>
 __device__ __forceinline__ void fwht8(TC (&v)[8]) {
