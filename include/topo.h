@@ -186,7 +186,9 @@ to_status to_oc_update_noalloc(int64_t nel, double volfrac, double move, const d
 /* y = op(x) for x, y dev float64 n (no aliasing).  op: TO_OP_K (current
  * stiffness with BCs, Eq. 7), TO_OP_KREF (reference stiffness, Eq. 8) or
  * TO_OP_DK (dK = K - K_ref, zero on fixed DOFs).  prec: TO_PREC_NATIVE
- * (the context's apply precision), TO_PREC_FP64, TO_PREC_FP32 or
+ * (the context's apply precision), TO_PREC_FP64, TO_PREC_FP32 (3D: x is
+ * rounded to float32 and the float32-storage operator of the mixed solver
+ * runs; y is its result widened) or
  * TO_PREC_DF (3D: double-float arithmetic on the FP32 pipe, ~2^-48
  * relative; elsewhere float64).  TO_MIXED uses TO_PREC_DF for the products
  * that must be float64-accurate (true CG residuals, K R~). */
@@ -203,15 +205,19 @@ to_status to_level_apply(to_ctx* ctx, int32_t level, const double* x, double* y)
 /* Element counts per axis and DOF count of level l. */
 to_status to_level_info(to_ctx* ctx, int32_t level, int32_t nel_out[3], int64_t* ndof);
 
-/* Profiling: when enabled, every launch of the stiffness operator is
- * bracketed by CUDA events on the context stream.  kind 0 = finest-grid
- * operator (all variants: K x, residual, smoother, K_ref, dK), 1 = coarse-
- * grid Galerkin operator, 2 = whole V-cycle.  to_profile_read synchronises,
+/* Profiling: launches of the kinds selected by the bit mask `kinds` (bit k
+ * = kind k; 0 turns profiling off) are bracketed by CUDA events on the
+ * context stream.  kind 0 = finest-grid operator with float32 storage and
+ * arithmetic (the operator of the mixed solver), 1 = coarse-grid Galerkin
+ * operator, 2 = whole V-cycle, 3 = finest-grid operator in the other
+ * precisions (float64, double-float, float32 arithmetic on float64 storage).
+ * Inside MGCG the V-cycle runs as a captured CUDA graph: its inner launches
+ * are timed only through kind 2.  to_profile_read synchronises,
  * returns the number of timed launches, their summed milliseconds and
  * (bytes, may be NULL) their summed algorithmic DRAM bytes (each input and
  * output array counted once), and forgets them.  to_launch_count returns
  * the number of kernels launched by this context since the last reset. */
-to_status to_profile_enable(to_ctx* ctx, int32_t on);
+to_status to_profile_enable(to_ctx* ctx, int32_t kinds);
 to_status to_profile_read(to_ctx* ctx, int32_t kind, int64_t* count, double* ms, double* bytes);
 to_status to_launch_count(to_ctx* ctx, int64_t* count, int32_t reset);
 

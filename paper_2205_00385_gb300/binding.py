@@ -211,8 +211,15 @@ def to_level_info(ctx, level):
     return tuple(nel), n.value
 
 
-def to_profile_enable(ctx, on: bool):
-    _check(load().to_profile_enable(ctx, int(on)), ctx)
+# profiling kinds (to_profile_read) and their bits in to_profile_enable
+PK_FINE32, PK_COARSE, PK_VCYCLE, PK_FINE_OTHER = 0, 1, 2, 3
+
+
+def to_profile_enable(ctx, kinds):
+    """kinds: bit mask of profiling kinds (bit k = kind k); True = all, False = off."""
+    if isinstance(kinds, bool):
+        kinds = 0xF if kinds else 0
+    _check(load().to_profile_enable(ctx, int(kinds)), ctx)
 
 
 def to_profile_read(ctx, kind: int):

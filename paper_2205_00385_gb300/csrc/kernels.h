@@ -38,8 +38,18 @@ struct ApplyArgs {
   double omega, dfix;
   int epi;
   void* eo;            // explicit levels: per-element output rows [nel * ND] of type tc
+  const uint8_t* colfix = nullptr;   // per node column (i, j): 1 if any DOF of the
+                                     // column is fixed (null: mask every node)
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+// Float32 3D finest-grid operator, two element columns per thread with packed
+// f32x2 arithmetic (kernels_pair.cu); pair_apply_ok tells whether it applies.
+bool pair_apply_ok(const ApplyArgs& a);
+cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s);
+// caches the pair kernel's resident-block counts for the current device
+void pair_prepare();
+// colfix[i + nnx j] = 1 if any node (i, j, k) of the grid has a fixed DOF
+cudaError_t launch_colfix(const GridP& g, const uint8_t* mask, uint8_t* colfix, cudaStream_t s);
 // Double-float finest-grid operator (kernels_df.cu): float64 x/b/y, float64
 // moduli in coef, float64 Walsh blocks in wht; EPI_APPLY or EPI_RESID.
 cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s);

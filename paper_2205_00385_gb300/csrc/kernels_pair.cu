@@ -1,0 +1,460 @@
+// Finest-grid 3D stiffness operator in float32, two element columns per
+// thread with packed f32x2 arithmetic (Sec. 2 / Eq. 1: K(rho) x assembled
+// element by element from E_e KE; fixed DOFs enter as M K M + dfix (I - M)).
+//
+// The element operator is applied in the corner Walsh-Hadamard basis
+// (KE = T B T with B eight 3x3 blocks, 45 non-zero entries).  Compared with
+// the one-column kernel in kernels_fe.cu:
+//  * each thread owns the element pair (i, i+1) of one x-row of columns and
+//    streams it up in z; the pair's two elements are the two lanes of every
+//    f32x2 add / mul / fma, so one instruction serves both elements;
+//  * the transform is separable, T = T_z (x) T_xy: the xy part of each
+//    horizontal face is computed once and serves the element below and the
+//    element above; on the way back, the two elements' contributions to a
+//    shared face are added in the xy-Walsh domain and transformed once;
+//  * one face row (three nodes) is loaded per thread and row, the middle
+//    node serving both elements;
+//  * fixed-DOF masking runs only in warps that touch a node column holding a
+//    fixed DOF (a per-column flag computed once at mesh set-up).
+// A block of 16 x 8 threads covers 32 x 8 element columns and owns the
+// 30 x 7 nodes whose surrounding columns it computes; per z-layer the
+// column partials of each owned node are summed in shared memory in a fixed
+// order (deterministic, no atomics).
+#include "kernels.h"
+#include "topo_internal.cuh"
+
+namespace topo {
+namespace {
+
+constexpr int PX = 16, PY = 8, POX = 2 * (PX - 1), POY = PY - 1, PZC = 16;
+
+struct WhtPair {
+  float2 b[8][3][3];   // Walsh blocks with each entry in both lanes
+};
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
+// 4-point Walsh-Hadamard transform over the corners q = bx + 2 by of a face
+// (self-inverse up to the factor 4, which is folded into B).
+__device__ __forceinline__ void wht4(const float2 (&v)[4], float2 (&w)[4]) {
+  const float2 s0 = padd(v[0], v[1]), d0 = psub(v[0], v[1]);
+  const float2 s1 = padd(v[2], v[3]), d1 = psub(v[2], v[3]);
+  w[0] = padd(s0, s1);
+  w[1] = padd(d0, d1);
+  w[2] = psub(s0, s1);
+  w[3] = psub(d0, d1);
+}
+
+// true if column cp of Walsh block tau is structurally zero
+__host__ __device__ constexpr bool wht_col_zero(int tau, int cp) {
+  return wht_zero(tau, 0, cp) && wht_zero(tau, 1, cp) && wht_zero(tau, 2, cp);
+}
+
+// Element pair: bottom and top face transforms Wb, Wt (xy-Walsh, per
+// component), moduli ce = (E_A, E_B).  Returns the xy-Walsh coefficients of
+// the pair's contributions to its bottom face (Ub) and top face (Ut).
+__device__ __forceinline__ void pair_element(const WhtPair& kb, float2 ce,
+                                             const float2 (&Wb)[3][4], const float2 (&Wt)[3][4],
+                                             float2 (&Ub)[3][4], float2 (&Ut)[3][4]) {
+  float2 X[3][8];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      X[c][t] = padd(Wb[c][t], Wt[c][t]);
+      X[c][t + 4] = psub(Wb[c][t], Wt[c][t]);
+    }
+  float2 Y[3][8];
+#pragma unroll
+  for (int tau = 0; tau < 8; ++tau) {
+    float2 zt[3];
+#pragma unroll
+    for (int cp = 0; cp < 3; ++cp)
+      zt[cp] = wht_col_zero(tau, cp) ? make_float2(0.f, 0.f) : pmul(ce, X[cp][tau ^ (1 << cp)]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 s = make_float2(0.f, 0.f);
+      bool first = true;
+#pragma unroll
+      for (int cp = 0; cp < 3; ++cp) {
+        if (wht_zero(tau, c, cp)) continue;
+        s = first ? pmul(kb.b[tau][c][cp], zt[cp]) : pfma(kb.b[tau][c][cp], zt[cp], s);
+        first = false;
+      }
+      Y[c][tau ^ (1 << c)] = s;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      Ub[c][t] = padd(Y[c][t], Y[c][t + 4]);
+      Ut[c][t] = psub(Y[c][t], Y[c][t + 4]);
+    }
+}
+
+struct PairArgs {
+  GridP g;
+  const uint8_t* mask;
+  const uint8_t* colfix;   // per node column (i, j): any DOF fixed at any k
+  const float* coef;
+  int zc;
+  const float* x;
+  float* y;
+  const float* b;
+  const float* dinv;
+  float omega, dfix;
+};
+
+// Face tile of a block: (2 PX + 1) x (PY + 1) nodes, three floats per node,
+// rows of FROW floats (odd, so the two half-warps' rows hit disjoint banks)
+constexpr int FNX = 2 * PX + 1, FNY = PY + 1, FROW = 3 * FNX, FTILE = FROW * FNY;
+constexpr int NSTAGE = 4;                                   // faces in flight
+constexpr int FCOPY = (FTILE + PX * PY - 1) / (PX * PY);    // 4-byte copies per thread
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+struct PairSmem {
+  float face[NSTAGE][FTILE];
+  float4 pub[2][4][PY][PX];
+};
+
+template <int EPI, bool MASKED>
+__device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, PairSmem& sm) {
+  const GridP& g = a.g;
+  const int tid = threadIdx.x;
+  const int tx = tid % PX, ty = tid / PX;
+  const int X0 = blockIdx.x * POX, Y0 = blockIdx.y * POY;
+  const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, g.nnz);
+  const int i = X0 - 1 + 2 * tx, j = Y0 - 1 + ty;   // corner 0 of element A
+  const long long plane = (long long)g.nnx * g.nny;
+  const bool eA = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  const bool eB = i + 1 >= 0 && i + 1 < g.nx && j >= 0 && j < g.ny;
+
+  // copies of this thread: tile floats f = tid + k * blockDim, f = row * FROW + col
+  int coff[FCOPY];
+  unsigned cvalid = 0u;
+#pragma unroll
+  for (int k = 0; k < FCOPY; ++k) {
+    const int f = tid + k * PX * PY;
+    const int row = f / FROW, col = f % FROW;
+    const int ni = X0 - 1 + col / 3, nj = Y0 - 1 + row;
+    const bool ok = f < FTILE && ni >= 0 && ni < g.nnx && nj >= 0 && nj < g.nny;
+    cvalid |= (ok ? 1u : 0u) << k;
+    coff[k] = ok ? 3 * (ni + g.nnx * nj) + col % 3 : 0;
+  }
+  const int fbase = z0 - 1;   // face index of stage 0
+  auto issue_face = [&](int kz) {
+    if (kz >= 0 && kz < g.nnz && kz <= z1) {
+      float* dst = sm.face[(kz - fbase) % NSTAGE];
+      const float* src = a.x + 3 * plane * kz;
+#pragma unroll
+      for (int k = 0; k < FCOPY; ++k) {
+        const int f = tid + k * PX * PY;
+        if (f < FTILE) {
+          const bool ok = (cvalid >> k) & 1u;
+          cp_async4(dst + f, ok ? src + coff[k] : a.x, ok);
+        }
+      }
+    } else if (kz >= z0 - 1 && kz <= z1) {
+      // face outside the grid: zeros
+      float* dst = sm.face[(kz - fbase) % NSTAGE];
+#pragma unroll
+      for (int k = 0; k < FCOPY; ++k) {
+        const int f = tid + k * PX * PY;
+        if (f < FTILE) dst[f] = 0.f;
+      }
+    }
+    cp_commit();
+  };
+  // node masks of a face (MASKED): 3 bits per (r, n)
+  auto face_mask = [&](int kz) -> unsigned {
+    unsigned m = 0u;
+    if (kz < 0 || kz >= g.nnz) return m;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int n = 0; n < 3; ++n) {
+        const bool ok = i + n >= 0 && i + n < g.nnx && j + r >= 0 && j + r < g.nny;
+        const long long nd = (long long)(i + n) + (long long)g.nnx * (j + r) + plane * kz;
+        m |= (ok ? (unsigned)a.mask[nd] & 7u : 0u) << (3 * (3 * r + n));
+      }
+    return m;
+  };
+  // face -> xy-Walsh coefficients of the pair, per component
+  auto face_wht = [&](int kz, unsigned fm, float2 (&W)[3][4]) {
+    const float* fs = sm.face[(kz - fbase) % NSTAGE] + ty * FROW + 6 * tx;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float v[2][3];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+          const float u = fs[r * FROW + 3 * n + c];
+          v[r][n] = (MASKED && ((fm >> (3 * (3 * r + n) + c)) & 1u)) ? 0.f : u;
+        }
+      float2 P[4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        P[2 * r] = make_float2(v[r][0], v[r][1]);
+        P[2 * r + 1] = make_float2(v[r][1], v[r][2]);
+      }
+      wht4(P, W[c]);
+    }
+  };
+  auto coef_pair = [&](int ez) -> float2 {
+    const bool zin = ez >= 0 && ez < g.nz;
+    const long long eo = (long long)(eA ? i : i + 1) + (long long)g.nx * (j + (long long)g.ny * ez);
+    return make_float2(zin && eA ? a.coef[eo] : 0.f, zin && eB ? a.coef[eo + (eA ? 1 : 0)] : 0.f);
+  };
+
+  const bool own = tx < PX - 1 && ty < PY - 1 && i + 1 < g.nnx && j + 1 < g.nny;
+  const bool own2 = own && i + 2 < g.nnx;
+
+  // prologue: faces z0-1 .. z0+NSTAGE-2 in flight, z0-1 and z0 complete
+#pragma unroll
+  for (int s = 0; s < NSTAGE; ++s) issue_face(z0 - 1 + s);
+  cp_wait<NSTAGE - 2>();
+  __syncthreads();
+  float2 Wb[3][4], Wt[3][4], Up[3][4];
+  unsigned mb = MASKED ? face_mask(z0 - 1) : 0u, mt = MASKED ? face_mask(z0) : 0u;
+  face_wht(z0 - 1, mb, Wb);
+  __syncthreads();
+  issue_face(z0 - 1 + NSTAGE);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) Up[c][t] = make_float2(0.f, 0.f);
+  float2 ce = coef_pair(z0 - 1);
+  int buf = 0;
+  // invariant at the top of step ez: the stages hold faces ez+1 .. ez+NSTAGE,
+  // face ez+1 complete and visible to the block
+  for (int ez = z0 - 1; ez < z1; ++ez) {
+    // epilogue operands of the owned nodes of layer ez, requested before the
+    // element compute so that their latency overlaps it
+    const long long nd0 = (long long)(i + 1) + (long long)g.nnx * (j + 1) + plane * ez;
+    const bool ep = own && ez >= z0;
+    float eb[2][3], ex[2][3], ed[2][3];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const bool ok = ep && (m == 0 || own2);
+        const long long d = 3 * (nd0 + m) + c;
+        eb[m][c] = (EPI != EPI_APPLY && ok) ? a.b[d] : 0.f;
+        ex[m][c] = (EPI == EPI_SMOOTH && ok) ? a.x[d] : 0.f;
+        ed[m][c] = (EPI == EPI_SMOOTH && ok) ? a.dinv[d] : 0.f;
+      }
+    face_wht(ez + 1, mt, Wt);
+    const float2 ce_next = coef_pair(ez + 1);
+    if (MASKED) mt = face_mask(ez + 2);
+    float2 Ub[3][4], Ut[3][4];
+    pair_element(kb, ce, Wb, Wt, Ub, Ut);
+    ce = ce_next;
+    float part[2][3][3];   // nodal partials of layer ez: row r, node i+n, component
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 acc[4], o[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        acc[t] = padd(Up[c][t], Ub[c][t]);
+        Up[c][t] = Ut[c][t];
+        Wb[c][t] = Wt[c][t];
+      }
+      wht4(acc, o);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        part[r][0][c] = o[2 * r].x;
+        part[r][1][c] = o[2 * r + 1].x + o[2 * r].y;
+        part[r][2][c] = o[2 * r + 1].y;
+      }
+    }
+    sm.pub[buf][0][ty][tx] = make_float4(part[0][0][0], part[0][0][1], part[0][0][2], 0.f);
+    sm.pub[buf][1][ty][tx] = make_float4(part[0][1][0], part[0][1][1], part[0][1][2], 0.f);
+    sm.pub[buf][2][ty][tx] = make_float4(part[0][2][0], part[0][2][1], part[0][2][2], 0.f);
+    sm.pub[buf][3][ty][tx] = make_float4(part[1][0][0], part[1][0][1], part[1][0][2], 0.f);
+    cp_wait<NSTAGE - 2>();   // this thread's copies of face ez+2 have landed
+    __syncthreads();
+    issue_face(ez + 1 + NSTAGE);   // into the stage of face ez+1, read above
+    if (ep) {
+      const float4 m1 = sm.pub[buf][1][ty + 1][tx];
+      const float4 q3 = sm.pub[buf][3][ty][tx + 1];
+      const float4 q2 = sm.pub[buf][2][ty + 1][tx];
+      const float4 q0 = sm.pub[buf][0][ty + 1][tx + 1];
+      float s[2][3];
+      s[0][0] = part[1][1][0] + m1.x;
+      s[0][1] = part[1][1][1] + m1.y;
+      s[0][2] = part[1][1][2] + m1.z;
+      s[1][0] = ((part[1][2][0] + q3.x) + q2.x) + q0.x;
+      s[1][1] = ((part[1][2][1] + q3.y) + q2.y) + q0.y;
+      s[1][2] = ((part[1][2][2] + q3.z) + q2.z) + q0.z;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        if (m == 1 && !own2) break;
+        const long long nd = nd0 + m;
+        const unsigned mk = MASKED ? (unsigned)a.mask[nd] : 0u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long d = 3 * nd + c;
+          const float Ax = (MASKED && ((mk >> c) & 1u)) ? a.dfix * a.x[d] : s[m][c];
+          if (EPI == EPI_APPLY) {
+            a.y[d] = Ax;
+          } else if (EPI == EPI_RESID) {
+            a.y[d] = eb[m][c] - Ax;
+          } else {
+            a.y[d] = ex[m][c] + a.omega * ed[m][c] * (eb[m][c] - Ax);
+          }
+        }
+      }
+    }
+    buf ^= 1;
+  }
+  cp_wait<0>();
+}
+
+#ifndef PAIR_MIN_BLOCKS
+#define PAIR_MIN_BLOCKS 3
+#endif
+
+template <int EPI>
+__global__ void __launch_bounds__(PX * PY, PAIR_MIN_BLOCKS) k_apply3_pair(PairArgs a, WhtPair kb) {
+  __shared__ PairSmem sm;
+  const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
+  const int i = blockIdx.x * POX - 1 + 2 * tx, j = blockIdx.y * POY - 1 + ty;
+  bool flag = a.colfix == nullptr;
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int n = 0; n < 3; ++n)
+      if (a.colfix && i + n >= 0 && i + n < a.g.nnx && j + r >= 0 && j + r < a.g.nny)
+        flag |= a.colfix[(i + n) + (long long)a.g.nnx * (j + r)] != 0;
+  // all threads of a block must take the same branch (both contain
+  // __syncthreads), so the decision is block-wide
+  if (__syncthreads_or(flag))
+    pair_loop<EPI, true>(a, kb, sm);
+  else
+    pair_loop<EPI, false>(a, kb, sm);
+}
+
+__global__ void k_colfix(GridP g, const uint8_t* __restrict__ mask, uint8_t* __restrict__ colfix) {
+  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ncol = (long long)g.nnx * g.nny;
+  if (col >= ncol) return;
+  unsigned any = 0u;
+  for (int k = 0; k < g.nnz; ++k) any |= mask[col + ncol * k];
+  colfix[col] = any ? 1 : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_colfix(const GridP& g, const uint8_t* mask, uint8_t* colfix, cudaStream_t s) {
+  const long long ncol = (long long)g.nnx * g.nny;
+  if (ncol <= 0) return cudaSuccess;
+  k_colfix<<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(g, mask, colfix);
+  return cudaGetLastError();
+}
+
+// resident blocks of the pair kernel on the current device (cached per device)
+static long long pair_slots(int epi) {
+  static long long cache[3][64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  const int e = epi == EPI_APPLY ? 0 : epi == EPI_RESID ? 1 : 2;
+  if (cache[e][dev] > 0) return cache[e][dev];
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t err;
+  if (e == 0)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply3_pair<EPI_APPLY>, PX * PY, 0);
+  else if (e == 1)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply3_pair<EPI_RESID>, PX * PY, 0);
+  else
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply3_pair<EPI_SMOOTH>, PX * PY, 0);
+  if (err != cudaSuccess || sms <= 0 || per_sm <= 0) return 2 * 152;
+  cache[e][dev] = (long long)sms * per_sm;
+  return cache[e][dev];
+}
+
+void pair_prepare() {
+  // occupancy queries happen here, outside any stream capture
+  pair_slots(EPI_APPLY);
+  pair_slots(EPI_RESID);
+  pair_slots(EPI_SMOOTH);
+}
+
+bool pair_apply_ok(const ApplyArgs& a) {
+  return a.dim == 3 && !a.expl && !a.gal1 && a.wht != nullptr && a.tc == T_F32 &&
+         a.tx == T_F32 && a.ty == T_F32 && 3LL * a.g.nn < (1LL << 40);
+}
+
+cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
+  if (!pair_apply_ok(a)) return cudaErrorInvalidValue;
+  if (a.g.nn <= 0) return cudaSuccess;
+  WhtPair kb;
+  const float* src = static_cast<const float*>(a.wht);
+  for (int q = 0; q < 72; ++q) {
+    const float v = src[q];
+    (&kb.b[0][0][0])[q] = make_float2(v, v);
+  }
+  PairArgs p;
+  p.g = a.g;
+  p.mask = a.mask;
+  p.colfix = a.colfix;
+  p.coef = static_cast<const float*>(a.coef);
+  p.x = static_cast<const float*>(a.x);
+  p.y = static_cast<float*>(a.y);
+  p.b = static_cast<const float*>(a.b);
+  p.dinv = static_cast<const float*>(a.dinv);
+  p.omega = (float)a.omega;
+  p.dfix = (float)a.dfix;
+  const int gx = (a.g.nnx + POX - 1) / POX, gy = (a.g.nny + POY - 1) / POY;
+  // z-chunks: each chunk streams its layers and recomputes one element layer
+  // below it; the count is chosen to minimise waves x layers per chunk for
+  // the resident-block capacity of the device
+  const long long slots = pair_slots(a.epi);
+  const long long nxy = (long long)gx * gy;
+  int best = 1;
+  long long best_cost = -1;
+  for (int nzc = 1; nzc <= a.g.nnz; ++nzc) {
+    const int zc = (a.g.nnz + nzc - 1) / nzc;
+    if ((a.g.nnz + zc - 1) / zc != nzc) continue;
+    const long long waves = (nxy * nzc + slots - 1) / slots;
+    const long long cost = waves * (zc + 1);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = nzc;
+    }
+  }
+  p.zc = (a.g.nnz + best - 1) / best;
+  dim3 grid(gx, gy, best);
+  switch (a.epi) {
+    case EPI_APPLY: k_apply3_pair<EPI_APPLY><<<grid, PX * PY, 0, s>>>(p, kb); break;
+    case EPI_RESID: k_apply3_pair<EPI_RESID><<<grid, PX * PY, 0, s>>>(p, kb); break;
+    default: k_apply3_pair<EPI_SMOOTH><<<grid, PX * PY, 0, s>>>(p, kb); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace topo

@@ -55,7 +55,7 @@ static to_status cuda_fail(to_ctx* c, const char* what, cudaError_t e) {
 // ---------------------------------------------------------------------------
 // Profiling with CUDA events on the context stream
 // ---------------------------------------------------------------------------
-enum { PK_FINE = 0, PK_COARSE = 1, PK_VCYCLE = 2, PK_N = 3 };
+enum { PK_FINE32 = 0, PK_COARSE = 1, PK_VCYCLE = 2, PK_FINE_OTHER = 3, PK_N = 4 };
 
 static cudaEvent_t ev_take(to_ctx* c) {
   cudaEvent_t e;
@@ -74,13 +74,13 @@ struct ProfScope {
   double bytes;
   cudaEvent_t e0 = nullptr;
   ProfScope(to_ctx* c_, int k, double b = 0.0) : c(c_), kind(k), bytes(b) {
-    if (c->prof) {
+    if ((c->prof_mask >> kind) & 1u) {
       e0 = ev_take(c);
       if (e0) cudaEventRecord(e0, c->stream);
     }
   }
   ~ProfScope() {
-    if (c->prof && e0) {
+    if (e0) {
       cudaEvent_t e1 = ev_take(c);
       if (e1) {
         cudaEventRecord(e1, c->stream);
@@ -327,6 +327,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
     lv[l].g = g;
     lv[l].n = nl;
     lv[l].mask = cv.take<uint8_t>(g.nn);
+    lv[l].colfix = cv.take<uint8_t>((size_t)g.nnx * g.nny);
     lv[l].dinv = cv.take<char>(nl * ts);
     lv[l].b = cv.take<char>(nl * ts);
     lv[l].z = cv.take<char>(nl * ts);
@@ -450,7 +451,9 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->have_density = false;
   c->hier_stale = true;
   c->launches = 0;
-  c->prof = false;
+  c->prof_mask = 0u;
+  c->n_vgraph = 0;
+  c->cap_stream = nullptr;
   if (!make_stencil(c->dim, desc->rmin, &c->stencil)) {
     delete c;
     return fail(nullptr, TO_E_INVALID, "filter stencil too large");
@@ -508,6 +511,9 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
                                                              c->lv[l].g, c->lv[l].mask);
     INIT_TRY(cudaGetLastError(), "coarse mask");
   }
+  if (c->dim == 3) pair_prepare();
+  for (int l = 0; l < c->L; ++l)
+    INIT_TRY(launch_colfix(c->lv[l].g, c->lv[l].mask, c->lv[l].colfix, s), "column flags");
   for (int l = 0; l + 1 < c->L; ++l) {
     k_check_bc<<<nblocks(c->lv[l].g.nn, 256), 256, 0, s>>>(c->lv[l].g, c->lv[l].mask,
                                                           c->lv[l + 1].g, c->lv[l + 1].mask,
@@ -540,6 +546,8 @@ void to_destroy(to_ctx* ctx) {
     cudaEventDestroy(u.second.second);
   }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (int q = 0; q < ctx->n_vgraph; ++q) cudaGraphExecDestroy(ctx->vgraph[q].exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -592,6 +600,7 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.gal1 = false;
   a.gf = c->lv[0].g;
   a.eo = nullptr;
+  a.colfix = c->lv[0].colfix;
   a.x = x;
   a.y = y;
   a.b = b;
@@ -620,6 +629,7 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
   a.gal1 = false;
   a.gf = c->lv[0].g;
   a.eo = c->lv[l].eo;
+  a.colfix = c->lv[l].colfix;
   if (l == 1 && c->l1_implicit) {
     // level-1 Galerkin operator evaluated from the finest moduli
     a.expl = false;
@@ -654,7 +664,9 @@ static double apply_bytes(const ApplyArgs& a) {
 }
 
 static to_status run_op(to_ctx* c, const ApplyArgs& a, const char* what) {
-  ProfScope ps(c, (a.expl || a.gal1) ? 1 : 0, apply_bytes(a));
+  const bool fine32 = a.tc == T_F32 && a.tx == T_F32 && a.ty == T_F32;
+  ProfScope ps(c, (a.expl || a.gal1) ? PK_COARSE : fine32 ? PK_FINE32 : PK_FINE_OTHER,
+               apply_bytes(a));
   LAUNCH(c, launch_apply(a, c->stream), what);
   return TO_OK;
 }
@@ -735,6 +747,58 @@ static to_status vcycle(to_ctx* c, const double* rin, void* zout, int zt) {
                              EPI_SMOOTH), "postsmooth 0");
 }
 
+// The V-cycle's launch sequence depends only on buffer addresses fixed at
+// set-up and on the coefficient array (which alternates between two buffers
+// in float64), so it is captured once per (input, output, precision,
+// coefficients) as a CUDA graph and replayed: one launch per preconditioner
+// application instead of one per kernel, with no host gaps between kernels.
+static to_status vcycle_graphed(to_ctx* c, const double* rin, void* zout, int zt) {
+  const void* coef = mg_t(c) == T_F64 ? (const void*)c->E64 : (const void*)c->E32;
+  to_ctx::VGraph* vg = nullptr;
+  for (int q = 0; q < c->n_vgraph; ++q) {
+    to_ctx::VGraph& v = c->vgraph[q];
+    if (v.rin == rin && v.zout == zout && v.zt == zt && v.coef == coef) vg = &v;
+  }
+  if (!vg) {
+    if (!c->cap_stream)
+      CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking),
+               "capture stream");
+    const cudaStream_t keep_stream = c->stream;
+    const unsigned keep_prof = c->prof_mask;
+    const long long keep_launches = c->launches;
+    c->stream = c->cap_stream;
+    c->prof_mask = 0u;
+    cudaGraph_t graph = nullptr;
+    to_status st = TO_OK;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      st = vcycle(c, rin, zout, zt);
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+      if (e == cudaSuccess) e = e2;
+    }
+    const long long captured = c->launches - keep_launches;
+    c->stream = keep_stream;
+    c->prof_mask = keep_prof;
+    c->launches = keep_launches;
+    cudaGraphExec_t exec = nullptr;
+    if (st == TO_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st != TO_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(c, "V-cycle graph", e);
+    if (c->n_vgraph == 4) {
+      cudaGraphExecDestroy(c->vgraph[0].exec);
+      for (int q = 1; q < 4; ++q) c->vgraph[q - 1] = c->vgraph[q];
+      c->n_vgraph = 3;
+    }
+    vg = &c->vgraph[c->n_vgraph++];
+    *vg = to_ctx::VGraph{rin, zout, coef, zt, exec, captured};
+  }
+  ProfScope ps(c, PK_VCYCLE);
+  CUDA_TRY(c, cudaGraphLaunch(vg->exec, c->stream), "V-cycle graph launch");
+  c->launches += vg->launches;
+  return TO_OK;
+}
+
 static to_status read_scalar(to_ctx* c, const double* dev, double* host) {
   CUDA_TRY(c, cudaMemcpyAsync(host, dev, 8, cudaMemcpyDeviceToHost, c->stream), "read scalar");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
@@ -765,8 +829,19 @@ static int apply_tc(const to_ctx* c, int prec) {
 static int accurate_tc(const to_ctx* c) { return (c->mixed && c->df_ok) ? T_DF : T_F64; }
 
 static to_status apply_op(to_ctx* c, int op, int prec, const double* x, double* y) {
-  return run_op(c, fine_args(c, op, apply_tc(c, prec), T_F64, T_F64, x, y, nullptr, nullptr,
-                             EPI_APPLY), "apply");
+  const int tc = apply_tc(c, prec);
+  const ApplyArgs a32 = fine_args(c, op, tc, T_F32, T_F32, c->p32, c->q32, nullptr, nullptr,
+                                  EPI_APPLY);
+  if (prec == TO_PREC_FP32 && pair_apply_ok(a32)) {
+    // float32 storage end to end: the operator that runs inside the mixed solver
+    LAUNCH(c, launch_convert(T_F64, T_F32, c->n, x, c->p32, c->stream), "convert x");
+    to_status st = run_op(c, a32, "apply");
+    if (st != TO_OK) return st;
+    LAUNCH(c, launch_convert(T_F32, T_F64, c->n, c->q32, y, c->stream), "convert y");
+    return TO_OK;
+  }
+  return run_op(c, fine_args(c, op, tc, T_F64, T_F64, x, y, nullptr, nullptr, EPI_APPLY),
+                "apply");
 }
 
 static to_status parm_push(to_ctx* c, const double* u) {
@@ -863,11 +938,11 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   auto precondition = [&](int slot) -> to_status {
     to_status e;
     if (f32) {
-      if ((e = vcycle(c, c->r, z32, T_F32)) != TO_OK) return e;
+      if ((e = vcycle_graphed(c, c->r, z32, T_F32)) != TO_OK) return e;
       LAUNCH(c, launch_dot_df(n, c->r, z32, c->partials, c->counters + C_DOT, c->scal + slot, s),
              "rz");
     } else {
-      if ((e = vcycle(c, c->r, c->z, T_F64)) != TO_OK) return e;
+      if ((e = vcycle_graphed(c, c->r, c->z, T_F64)) != TO_OK) return e;
       LAUNCH(c, launch_dot(n, c->r, c->z, c->partials, c->counters + C_DOT, c->scal + slot, s),
              "rz");
     }
@@ -1084,9 +1159,10 @@ to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_
   return TO_OK;
 }
 
-to_status to_profile_enable(to_ctx* c, int32_t on) {
+to_status to_profile_enable(to_ctx* c, int32_t kinds) {
   if (!c) return fail(c, TO_E_INVALID, "NULL ctx");
-  c->prof = on != 0;
+  if (kinds < 0 || kinds >= (1 << PK_N)) return fail(c, TO_E_INVALID, "bad kind mask");
+  c->prof_mask = (unsigned)kinds;
   return TO_OK;
 }
 

@@ -213,6 +213,7 @@ struct LevelBuf {
   topo::GridP g;
   long long n;           // DOFs
   uint8_t* mask;         // per node: bit c set = DOF c fixed
+  uint8_t* colfix;       // per node column (i, j): 1 if any of its DOFs is fixed
   void* dinv;            // T[n]
   void* b;               // T[n]
   void* z;               // T[n]
@@ -270,7 +271,19 @@ struct to_ctx {
   topo::StencilP stencil;
   std::string last_error;
   long long launches;
-  bool prof;
+  unsigned prof_mask;   // bit k: time launches of profiling kind k
+  // V-cycles captured as CUDA graphs, keyed by their buffers and precision
+  struct VGraph {
+    const void* rin;
+    const void* zout;
+    const void* coef;
+    int zt;
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  VGraph vgraph[4];
+  int n_vgraph;
+  cudaStream_t cap_stream;   // private stream used only for graph capture
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   std::vector<double> ev_bytes;
