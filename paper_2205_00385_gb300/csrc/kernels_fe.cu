@@ -298,12 +298,11 @@ __global__ void __launch_bounds__(256)
                   const T* __restrict__ dinv, T omega, T dfix) {
   constexpr int ND = Geo<DIM>::ND;
   constexpr int NZ = DIM == 3 ? 2 : 1;
-  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= g.nn) return;
-  const int i = (int)(node % g.nnx);
-  const long long rest = node / g.nnx;
-  const int j = (int)(rest % g.nny);
-  const int k = DIM == 3 ? (int)(rest / g.nny) : 0;
+  // threads on the node grid: x lanes along i, block rows along j, z = k
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y;
+  const int k = DIM == 3 ? (int)blockIdx.z : 0;
+  if (i >= g.nnx || j >= g.nny) return;
+  const long long node = i + (long long)g.nnx * (j + (long long)g.nny * k);
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
@@ -343,7 +342,8 @@ static cudaError_t run_expl(const ApplyArgs& a, cudaStream_t s) {
       a.g, a.mask, static_cast<const T*>(a.Kc), static_cast<const T*>(a.x), static_cast<T*>(a.eo));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_elem_gather<DIM, T, EPI><<<nblocks(a.g.nn, 256), 256, 0, s>>>(
+  const dim3 ggrid((a.g.nnx + 31) / 32, (a.g.nny + 3) / 4, DIM == 3 ? a.g.nnz : 1);
+  k_elem_gather<DIM, T, EPI><<<ggrid, dim3(32, 4), 0, s>>>(
       a.g, a.mask, static_cast<const T*>(a.eo), static_cast<const T*>(a.x), static_cast<T*>(a.y),
       static_cast<const T*>(a.b), static_cast<const T*>(a.dinv), T(a.omega), T(a.dfix));
   return cudaGetLastError();

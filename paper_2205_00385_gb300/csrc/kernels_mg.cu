@@ -31,21 +31,24 @@ __host__ __device__ __forceinline__ double wchild(int c, int a, int A) {
 
 // ---------------------------------------------------------------------------
 // Restriction b_c = Pm^T r_f (Pm = M_f P M_c): coarse node (I,J,K) gathers
-// the fine nodes around (2I,2J,2K) with weights prod(1 - |d|/2).
+// the fine nodes around (2I,2J,2K) with weights prod(1 - |d|/2).  Threads
+// are laid out on the node grid (x lanes along I, block rows along J,
+// blockIdx.z = K), so no index division is needed; the 3^DIM gathers are
+// independent loads summed in a fixed order.
 // ---------------------------------------------------------------------------
+constexpr int TBX = 32, TBY = 4;
+
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(TBX * TBY, 8)
     k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
                const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc) {
-  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= gc.nn) return;
-  const int I = (int)(node % gc.nnx);
-  const long long rest = node / gc.nnx;
-  const int J = (int)(rest % gc.nny);
-  const int K = DIM == 3 ? (int)(rest / gc.nny) : 0;
+  const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
+  const int K = DIM == 3 ? (int)blockIdx.z : 0;
+  if (I >= gc.nnx || J >= gc.nny) return;
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
   for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
@@ -54,46 +57,48 @@ __global__ void __launch_bounds__(256)
         const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
         bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
         if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
-        if (!in) continue;
         const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
         const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * (DIM == 3 ? k : 0));
-        const unsigned m = maskf[fn];
+        const unsigned m = in ? (unsigned)maskf[fn] : 7u;
 #pragma unroll
         for (int c = 0; c < DIM; ++c)
           if (!((m >> c) & 1u)) acc[c] += w * rf[DIM * fn + c];
       }
+  const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
   const unsigned mc = maskc[node];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) bc[DIM * node + c] = ((mc >> c) & 1u) ? T(0) : acc[c];
 }
 
 // z_f += Pm z_c: fine node (i,j,k) interpolates from coarse nodes
-// floor(i/2) .. ceil(i/2) per axis.
+// floor(i/2) .. ceil(i/2) per axis (threads on the fine node grid).
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(TBX * TBY)
     k_prolong_add(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
                   const T* __restrict__ zc, T* __restrict__ zf) {
-  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= gf.nn) return;
-  const int i = (int)(node % gf.nnx);
-  const long long rest = node / gf.nnx;
-  const int j = (int)(rest % gf.nny);
-  const int k = DIM == 3 ? (int)(rest / gf.nny) : 0;
+  const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+  const int k = DIM == 3 ? (int)blockIdx.z : 0;
+  if (i >= gf.nnx || j >= gf.nny) return;
   const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
   const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (DIM == 3 && (k & 1)) ? 2 : 1;
   const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1),
           wz = (DIM == 3 && (k & 1)) ? T(0.5) : T(1);
+  const T w = wx * wy * wz;
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-  for (int a = 0; a < nk; ++a)
-    for (int bb = 0; bb < nj; ++bb)
-      for (int cc = 0; cc < ni; ++cc) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        if (a >= nk || bb >= nj || cc >= ni) continue;
         const long long cn = (i0 + cc) + (long long)gc.nnx * ((j0 + bb) + (long long)gc.nny * (k0 + a));
-        const T w = wx * wy * wz;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) acc[c] += w * zc[DIM * cn + c];
       }
+  const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
   const unsigned m = maskf[node];
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
@@ -462,7 +467,9 @@ __global__ void __launch_bounds__(256)
 template <int DIM, typename T>
 static cudaError_t restrict_t(const GridP& gf, const uint8_t* mf, const GridP& gc,
                               const uint8_t* mc, const void* rf, void* bc, cudaStream_t s) {
-  k_restrict<DIM, T><<<nblocks(gc.nn, 256), 256, 0, s>>>(gf, mf, gc, mc, (const T*)rf, (T*)bc);
+  if (gc.nn <= 0) return cudaSuccess;
+  dim3 grid((gc.nnx + TBX - 1) / TBX, (gc.nny + TBY - 1) / TBY, DIM == 3 ? gc.nnz : 1);
+  k_restrict<DIM, T><<<grid, dim3(TBX, TBY), 0, s>>>(gf, mf, gc, mc, (const T*)rf, (T*)bc);
   return cudaGetLastError();
 }
 
@@ -477,7 +484,9 @@ cudaError_t launch_restrict(int dim, int t, const GridP& gf, const uint8_t* mf, 
 template <int DIM, typename T>
 static cudaError_t prolong_t(const GridP& gf, const uint8_t* mf, const GridP& gc, const void* zc,
                              void* zf, cudaStream_t s) {
-  k_prolong_add<DIM, T><<<nblocks(gf.nn, 256), 256, 0, s>>>(gf, mf, gc, (const T*)zc, (T*)zf);
+  if (gf.nn <= 0) return cudaSuccess;
+  dim3 grid((gf.nnx + TBX - 1) / TBX, (gf.nny + TBY - 1) / TBY, DIM == 3 ? gf.nnz : 1);
+  k_prolong_add<DIM, T><<<grid, dim3(TBX, TBY), 0, s>>>(gf, mf, gc, (const T*)zc, (T*)zf);
   return cudaGetLastError();
 }
 
