@@ -1,0 +1,77 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// floats (48-bit significand), and every operation runs on the FP32 pipe
+// with error-free transformations (TwoSum, FMA-based TwoProduct).  GB300
+// executes one float64 FMA per clock per SM against 128 float32 FMAs, so
+// float64-accurate arithmetic on long vectors is done this way; float64
+// values are split into (hi, lo) and widened back with integer operations.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace topo {
+
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float h = p + e;
+  return {h, e - (h - p)};
+}
+
+// double -> (hi, lo) with integer operations: hi keeps the leading 24
+// significant bits (truncated), lo the next 24 of the remaining 29.  Values
+// outside [2^-100, 2^100] (zero, or far outside the data's range) take the
+// conversion instructions instead.
+__device__ __forceinline__ dfl split_d(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  if (e < 1023 - 100 || e > 1023 + 100) {
+    if (e == 0) return {0.f, 0.f};
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+  }
+  const unsigned s = (unsigned)(u >> 63) << 31;
+  const float h = __uint_as_float(s | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
+  const unsigned L = (unsigned)(u & 0x1FFFFFFFu);
+  if (L == 0u) return {h, 0.f};
+  const int sh = __clz((int)L) - 8;                  // puts the leading one at bit 23
+  const unsigned m = sh >= 0 ? (L << sh) : (L >> (-sh));
+  const int ef = e - 925 - sh;                       // float exponent field of lo
+  if (ef <= 0) return {h, 0.f};                      // below 2^-126: negligible
+  return {h, __uint_as_float(s | ((unsigned)ef << 23) | (m & 0x7FFFFFu))};
+}
+
+// exact float -> double with integer operations (zero and normal floats)
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xFFu;
+  if (ef == 0u) return 0.0;
+  if (ef == 0xFFu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(ef + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// a * b + c
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }
+
+// (hi + lo) rounded to float64: the halves widen exactly, one float64 add
+__device__ __forceinline__ double df_to_d(dfl a) { return f2d(a.h) + f2d(a.l); }
+
+}  // namespace topo

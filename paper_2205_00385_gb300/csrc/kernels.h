@@ -117,16 +117,18 @@ cudaError_t launch_cg_p_f(long long n, double* p, float* p32, const float* z, co
 cudaError_t launch_copy(long long n, const double* a, double* b, cudaStream_t s);
 cudaError_t launch_scale_by_inv_sqrt(long long n, double* a, const double* s2, cudaStream_t s);
 // G[i + ldg*j] = sum_k A[k + i*n] B[k + j*n], i < na (na_dev overrides when
-// non-null), j < nb (likewise)
+// non-null), j < nb (likewise); one pass over the data.  df: double-float
+// arithmetic on the FP32 pipe (~2^-48 relative), else float64.  Uses one
+// counter.
 cudaError_t launch_multidot(long long n, const double* A, int na, const int* na_dev,
                             const double* B, int nb, const int* nb_dev, double* G, int ldg,
-                            double* partials, unsigned* counters, cudaStream_t s);
+                            double* partials, unsigned* counters, bool df, cudaStream_t s);
 // y = beta*y + sign * sum_i c[i] A[:, i] (i < m, or *m_dev); if rr != 0 also
-// writes |y - w|^2 (w may be null) to *rr
+// writes |y - w|^2 (w may be null) to *rr; df as for launch_multidot
 cudaError_t launch_combine(long long n, const double* A, int m, const int* m_dev,
                            const double* c, double sign, double beta, double* y,
                            const double* w, double* rr, double* partials, unsigned* counter,
-                           cudaStream_t s);
+                           bool df, cudaStream_t s);
 // small dense kernels on one thread block
 cudaError_t launch_small_spd_inverse(int m, const int* m_dev, const double* A, double* Ainv,
                                      int* status, cudaStream_t s);

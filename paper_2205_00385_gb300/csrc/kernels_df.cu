@@ -1,76 +1,18 @@
 // Float64-accurate hex8 stiffness operator in double-float arithmetic.
 //
-// GB300 runs float64 at ~1/64 of the float32 rate, so the float64 Walsh
-// kernel (k_apply3_col<double>) is bound by the FP64 pipe at ~1.3 ms per
-// 5.4M-DOF apply.  Here every value is an unevaluated sum hi + lo of two
+// GB300 runs float64 at one FMA per clock per SM, 1/128 of the float32
+// rate, so the float64 Walsh kernel (k_apply3_col<double>) is bound by the
+// FP64 pipe at ~1.3 ms per 5.4M-DOF apply.  Here every value is an unevaluated sum hi + lo of two
 // floats (48-bit significand) and all arithmetic runs on the FP32 pipe with
 // error-free transformations (TwoSum, FMA-based TwoProduct).  float64 inputs
 // are split into (hi, lo) and results widened back with integer bit
 // operations, so the FP64 pipe only sees the final additions of the
 // epilogue.  The structure (element columns streamed in z, owner-computes
 // node sums in shared memory, Walsh blocks) is that of k_apply3_col.
+#include "dfmath.cuh"
 #include "kernels.h"
 
 namespace topo {
-
-struct dfl {
-  float h, l;
-};
-
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  const float s = a.h + b.h;
-  const float bb = s - a.h;
-  float e = (a.h - (s - bb)) + (b.h - bb);
-  e += a.l + b.l;
-  const float h = s + e;
-  return {h, e - (h - s)};
-}
-
-__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
-
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  const float h = p + e;
-  return {h, e - (h - p)};
-}
-
-// double -> (hi, lo) with integer operations: hi keeps the leading 24
-// significant bits (truncated), lo the next 24 of the remaining 29.  Values
-// outside [2^-100, 2^100] (zero, or far outside the data's range) take the
-// conversion instructions instead.
-__device__ __forceinline__ dfl split_d(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((u >> 52) & 0x7FF);
-  if (e < 1023 - 100 || e > 1023 + 100) {
-    if (e == 0) return {0.f, 0.f};
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
-  }
-  const unsigned s = (unsigned)(u >> 63) << 31;
-  const float h = __uint_as_float(s | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
-  const unsigned L = (unsigned)(u & 0x1FFFFFFFu);
-  if (L == 0u) return {h, 0.f};
-  const int sh = __clz((int)L) - 8;                  // puts the leading one at bit 23
-  const unsigned m = sh >= 0 ? (L << sh) : (L >> (-sh));
-  const int ef = e - 925 - sh;                       // float exponent field of lo
-  if (ef <= 0) return {h, 0.f};                      // below 2^-126: negligible
-  return {h, __uint_as_float(s | ((unsigned)ef << 23) | (m & 0x7FFFFFu))};
-}
-
-// exact float -> double with integer operations (zero and normal floats)
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ef = (u >> 23) & 0xFFu;
-  if (ef == 0u) return 0.0;
-  if (ef == 0xFFu) return (double)f;
-  const unsigned long long d = ((unsigned long long)(u >> 31) << 63) |
-                               ((unsigned long long)(ef + 896u) << 52) |
-                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)d);
-}
 
 __device__ __forceinline__ void fwht8_df(dfl (&v)[8]) {
 #pragma unroll

@@ -1042,7 +1042,7 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
                        c->KPhi + (size_t)i * n)) != TO_OK)
       return st;
   LAUNCH(c, launch_multidot(n, c->Phi, Ns, nullptr, c->KPhi, Ns, nullptr, small + SM_KPHI, Ns,
-                            c->partials, c->counters + C_MULTI, s), "K_Phi");
+                            c->partials, c->counters + C_MULTI, c->mixed, s), "K_Phi");
   LAUNCH(c, launch_small_spd_inverse(Ns, nullptr, small + SM_KPHI, small + SM_KPHI_INV,
                                      c->ints + I_STATUS, s), "K_Phi inverse");
   // r_1 = u_last; r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}  (Eq. 18-20, 26)
@@ -1051,12 +1051,12 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
     if ((st = apply_op(c, TO_OP_DK, TO_PREC_NATIVE, c->R + (size_t)(i - 1) * n, c->t)) != TO_OK)
       return st;
     LAUNCH(c, launch_multidot(n, c->Phi, Ns, nullptr, c->t, 1, nullptr, small + SM_Z, Ns,
-                              c->partials, c->counters + C_MULTI, s), "Phi^T t");
+                              c->partials, c->counters + C_MULTI, c->mixed, s), "Phi^T t");
     LAUNCH(c, launch_small_matvec(Ns, nullptr, small + SM_KPHI_INV, small + SM_Z, small + SM_W,
                                   -1.0, s), "K_Phi^-1 z");
     LAUNCH(c, launch_combine(n, c->Phi, Ns, nullptr, small + SM_W, 1.0, 0.0,
                              c->R + (size_t)i * n, nullptr, nullptr, c->partials,
-                             c->counters + C_UPD, s), "r_i");
+                             c->counters + C_UPD, c->mixed, s), "r_i");
   }
   // modified Gram-Schmidt with re-orthogonalisation, in place
   CUDA_TRY(c, cudaMemsetAsync(c->ints + I_KCOUNT, 0, sizeof(int), s), "reset k");
@@ -1064,10 +1064,10 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
     double* ri = c->R + (size_t)i * n;
     LAUNCH(c, launch_dot(n, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM0, s), "|r|");
     for (int pass = 0; pass < 2; ++pass) {
-      LAUNCH(c, launch_multidot(n, c->R, MAXB, c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
-                                MAXB, c->partials, c->counters + C_MULTI, s), "GS dots");
-      LAUNCH(c, launch_combine(n, c->R, MAXB, c->ints + I_KCOUNT, small + SM_H, -1.0, 1.0, ri,
-                               nullptr, nullptr, c->partials, c->counters + C_UPD, s), "GS axpy");
+      LAUNCH(c, launch_multidot(n, c->R, std::max(i, 1), c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
+                                MAXB, c->partials, c->counters + C_MULTI, c->mixed, s), "GS dots");
+      LAUNCH(c, launch_combine(n, c->R, std::max(i, 1), c->ints + I_KCOUNT, small + SM_H, -1.0, 1.0, ri,
+                               nullptr, nullptr, c->partials, c->counters + C_UPD, c->mixed, s), "GS axpy");
     }
     LAUNCH(c, launch_dot(n, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM1, s), "|r|");
     LAUNCH(c, launch_gs_accept(n, c->R, i, c->scal, S_NRM0, S_NRM1, 1e-10, c->ints, s),
@@ -1097,15 +1097,15 @@ to_status to_carm_solve(to_ctx* c, double* u, double* eps, double* eps_dev) {
                      "K R")) != TO_OK)
       return st;
   LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->Q, k, nullptr, small + SM_KR, k, c->partials,
-                            c->counters + C_MULTI, s), "K_R");
+                            c->counters + C_MULTI, c->mixed, s), "K_R");
   LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->f, 1, nullptr, small + SM_FR, k, c->partials,
-                            c->counters + C_MULTI, s), "f_R");
+                            c->counters + C_MULTI, c->mixed, s), "f_R");
   LAUNCH(c, launch_small_chol_solve(k, nullptr, small + SM_KR, small + SM_FR, small + SM_Y,
                                     c->ints + I_STATUS, s), "K_R y = f_R");
   LAUNCH(c, launch_combine(n, c->R, k, nullptr, small + SM_Y, 1.0, 0.0, u, nullptr, nullptr,
-                           c->partials, c->counters + C_UPD, s), "u = R y");
+                           c->partials, c->counters + C_UPD, c->mixed, s), "u = R y");
   LAUNCH(c, launch_combine(n, c->Q, k, nullptr, small + SM_Y, 1.0, 0.0, c->t, c->f,
-                           c->scal + S_RR, c->partials, c->counters + C_UPD, s), "K R y - f");
+                           c->scal + S_RR, c->partials, c->counters + C_UPD, c->mixed, s), "K R y - f");
   LAUNCH(c, launch_eps(c->scal, S_RR, S_FNORM2, c->scal + S_EPS, s), "eps");
   if (eps_dev)
     CUDA_TRY(c, cudaMemcpyAsync(eps_dev, c->scal + S_EPS, 8, cudaMemcpyDeviceToDevice, s), "eps");
