@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libtopo.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["kernels_fe.cu", "kernels_pair.cu", "kernels_df.cu", "kernels_mg.cu", "kernels_blas.cu", "kernels_opt.cu",
+SOURCES = ["kernels_fe.cu", "kernels_pair.cu", "kernels_df.cu", "kernels_mg.cu", "kernels_blas.cu", "kernels_vec.cu", "kernels_opt.cu",
            "topo_api.cu", "noalloc.cu"]
 
 
@@ -72,7 +72,7 @@ def build(verbose: bool = False, extra_flags=None) -> str:
             list(ex.map(run, jobs))
     if jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC", "-Xlinker", "--no-undefined"])
         os.replace(tmp, LIB)
     return LIB
 

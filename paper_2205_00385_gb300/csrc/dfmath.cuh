@@ -74,4 +74,29 @@ __device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mu
 // (hi + lo) rounded to float64: the halves widen exactly, one float64 add
 __device__ __forceinline__ double df_to_d(dfl a) { return f2d(a.h) + f2d(a.l); }
 
+// storage access for float64-accurate values held as float64 or as pairs
+__device__ __forceinline__ dfl ld_df(const double* p, long long i) { return split_d(p[i]); }
+__device__ __forceinline__ dfl ld_df(const float2* p, long long i) {
+  const float2 v = p[i];
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st_df(double* p, long long i, dfl v) { p[i] = df_to_d(v); }
+__device__ __forceinline__ void st_df(float2* p, long long i, dfl v) {
+  p[i] = make_float2(v.h, v.l);
+}
+
+// value conversions between storage types (pairs round to float32 once)
+template <typename TO, typename TI>
+__device__ __forceinline__ TO cvt(TI v) {
+  return TO(v);
+}
+template <>
+__device__ __forceinline__ float cvt<float, float2>(float2 v) {
+  return __fadd_rn(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ float2 cvt<float2, float>(float v) {
+  return make_float2(v, 0.f);
+}
+
 }  // namespace topo

@@ -7,7 +7,9 @@ namespace topo {
 
 // arithmetic / storage types; T_DF = float64 storage with double-float
 // arithmetic on the FP32 pipe (finest 3D grid only)
-enum { T_F64 = 0, T_F32 = 1, T_DF = 2 };
+// Arithmetic / storage codes.  T_DF: double-float arithmetic (float64
+// storage or pairs); T_D2: storage as double-float pairs float2 {hi, lo}.
+enum { T_F64 = 0, T_F32 = 1, T_DF = 2, T_D2 = 3 };
 enum { EPI_APPLY = 0, EPI_RESID = 1, EPI_SMOOTH = 2 };
 
 // Stiffness operator of one grid level,
@@ -105,30 +107,48 @@ cudaError_t launch_cg_xr(long long n, double* x, double* r, const double* p, con
 // beta = scal[num] / scal[den]; p = z + beta p
 cudaError_t launch_cg_p(long long n, double* p, const double* z, const double* scal, int num,
                         int den, cudaStream_t s);
-// mixed-precision CG: float32 operator input/output shadows
-cudaError_t launch_dot_df(long long n, const double* a, const float* b, double* partials,
-                          unsigned* counter, double* out, cudaStream_t s);
-cudaError_t launch_cg_xr_f(long long n, double* x, double* r, const double* p, const float* q,
-                           double* scal, int num, int den, int rr, double* partials,
-                           unsigned* counter, cudaStream_t s);
-// p = z + beta p (num < 0: p = z); p32 = float(p)
-cudaError_t launch_cg_p_f(long long n, double* p, float* p32, const float* z, const double* scal,
-                          int num, int den, cudaStream_t s);
 cudaError_t launch_copy(long long n, const double* a, double* b, cudaStream_t s);
 cudaError_t launch_scale_by_inv_sqrt(long long n, double* a, const double* s2, cudaStream_t s);
+// ---- float64-accurate long vectors (kernels_vec.cu) ----
+// Storage: V_F64 = float64 with float64 arithmetic (FP64 path); V_DF2 =
+// float2 {hi, lo} double-float pairs with double-float arithmetic on the
+// FP32 pipe (mixed path), 8 bytes per entry either way.
+enum VecT { V_F64 = 0, V_DF2 = 1 };
+cudaError_t launch_vdot(long long n, int vt, const void* a, const void* b, double* partials,
+                        unsigned* counter, double* out, cudaStream_t s);
+// out = in with a change of storage (split, widen or copy)
+cudaError_t launch_vconvert(long long n, int tin, const void* in, int tout, void* out,
+                            cudaStream_t s);
+// a *= 1/sqrt(*s2)
+cudaError_t launch_vscale_inv_sqrt(long long n, int vt, void* a, const double* s2,
+                                   cudaStream_t s);
 // G[i + ldg*j] = sum_k A[k + i*n] B[k + j*n], i < na (na_dev overrides when
-// non-null), j < nb (likewise); one pass over the data.  df: double-float
-// arithmetic on the FP32 pipe (~2^-48 relative), else float64.  Uses one
-// counter.
-cudaError_t launch_multidot(long long n, const double* A, int na, const int* na_dev,
-                            const double* B, int nb, const int* nb_dev, double* G, int ldg,
-                            double* partials, unsigned* counters, bool df, cudaStream_t s);
+// non-null), j < nb (likewise); one pass over the data; one counter
+cudaError_t launch_gram(long long n, int vt, const void* A, int na, const int* na_dev,
+                        const void* B, int nb, const int* nb_dev, double* G, int ldg,
+                        double* partials, unsigned* counter, cudaStream_t s);
 // y = beta*y + sign * sum_i c[i] A[:, i] (i < m, or *m_dev); if rr != 0 also
-// writes |y - w|^2 (w may be null) to *rr; df as for launch_multidot
-cudaError_t launch_combine(long long n, const double* A, int m, const int* m_dev,
-                           const double* c, double sign, double beta, double* y,
-                           const double* w, double* rr, double* partials, unsigned* counter,
-                           bool df, cudaStream_t s);
+// writes |y - w|^2 (w may be null) to *rr.  A and w have storage vt, y has
+// storage yt (yt = vt, or V_F64 with vt = V_DF2).
+cudaError_t launch_combine(long long n, int vt, const void* A, int m, const int* m_dev,
+                           const double* c, double sign, double beta, void* y, int yt,
+                           const void* w, double* rr, double* partials, unsigned* counter,
+                           cudaStream_t s);
+// Gram-Schmidt step: column src of R (norm^2 before in scal[n0], after in
+// scal[n1]) is appended to the basis at position ints[I_KCOUNT] if it kept
+// more than tol of its length, normalised.
+cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double* scal, int n0,
+                             int n1, double tol, int* ints, cudaStream_t s);
+// mixed-path CG (pairs x, r, p; float32 shadows p32 -> q32 and z32)
+cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* partials,
+                           unsigned* counter, double* out, cudaStream_t s);
+// x += alpha p, r -= alpha q, scal[rr] = |r|^2 with alpha = scal[num]/scal[den]
+cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const float* q,
+                            double* scal, int num, int den, int rr, double* partials,
+                            unsigned* counter, cudaStream_t s);
+// p = z + beta p (num < 0: p = z), beta = scal[num]/scal[den]; p32 = float(p)
+cudaError_t launch_cg_p_d2(long long n, void* p, float* p32, const float* z, const double* scal,
+                           int num, int den, cudaStream_t s);
 // small dense kernels on one thread block
 cudaError_t launch_small_spd_inverse(int m, const int* m_dev, const double* A, double* Ainv,
                                      int* status, cudaStream_t s);
@@ -136,11 +156,6 @@ cudaError_t launch_small_matvec(int m, const int* m_dev, const double* A, const 
                                 double* y, double sign, cudaStream_t s);
 cudaError_t launch_small_chol_solve(int m, const int* m_dev, const double* A, const double* b,
                                     double* x, int* status, cudaStream_t s);
-// Gram-Schmidt step: column src of R (norm^2 before in scal[n0], after in
-// scal[n1]) is appended to the basis at position ints[I_KCOUNT] if it kept
-// more than tol of its length, normalised.
-cudaError_t launch_gs_accept(long long n, double* R, int src, const double* scal, int n0,
-                             int n1, double tol, int* ints, cudaStream_t s);
 cudaError_t launch_eps(const double* scal, int rr, int f2, double* eps_dev, cudaStream_t s);
 
 // ---- design-optimisation kernels (kernels_opt.cu) ----

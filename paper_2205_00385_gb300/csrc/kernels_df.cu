@@ -9,6 +9,8 @@
 // operations, so the FP64 pipe only sees the final additions of the
 // epilogue.  The structure (element columns streamed in z, owner-computes
 // node sums in shared memory, Walsh blocks) is that of k_apply3_col.
+#include <type_traits>
+
 #include "dfmath.cuh"
 #include "kernels.h"
 
@@ -32,11 +34,13 @@ struct DfBlocks {
 
 constexpr int DX = 16, DY = 8, DOX = DX - 1, DOY = DY - 1;
 
-template <int EPI>
+// S: storage of x, b and y -- float64 (split on load, widened on store) or
+// double-float pairs float2 (used as they are)
+template <int EPI, typename S>
 __global__ void __launch_bounds__(DX * DY)
     k_apply3_df(GridP g, const uint8_t* __restrict__ mask, DfBlocks kb,
-                const double* __restrict__ coef, int zc, const double* __restrict__ x,
-                double* __restrict__ y, const double* __restrict__ b, double dfix) {
+                const double* __restrict__ coef, int zc, const S* __restrict__ x,
+                S* __restrict__ y, const S* __restrict__ b, double dfix) {
   __shared__ dfl part[2][4][DY][DX][3];
   const int tx = threadIdx.x % DX, ty = threadIdx.x / DX;
   const int x0 = blockIdx.x * DOX, y0 = blockIdx.y * DOY;
@@ -60,7 +64,7 @@ __global__ void __launch_bounds__(DX * DY)
         const unsigned m = mask[nd];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          f[q][c] = ((m >> c) & 1u) ? dfl{0.f, 0.f} : split_d(x[3 * nd + c]);
+          f[q][c] = ((m >> c) & 1u) ? dfl{0.f, 0.f} : ld_df(x, 3 * nd + c);
       } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[q][c] = {0.f, 0.f};
@@ -136,15 +140,21 @@ __global__ void __launch_bounds__(DX * DY)
                                     part[buf][1][ty + 1][tx][c]),
                              part[buf][0][ty + 1][tx + 1][c]);
         const long long d = 3 * nd + c;
-        if ((m >> c) & 1u) {
-          const double Ax = dfix * x[d];
-          y[d] = EPI == EPI_RESID ? b[d] - Ax : Ax;
-        } else if (EPI == EPI_RESID) {
-          // b and K x nearly cancel near convergence: subtract the leading
-          // part first (exact when close), then the trailing part
-          y[d] = (b[d] - f2d(s.h)) - f2d(s.l);
+        if constexpr (std::is_same<S, double>::value) {
+          if ((m >> c) & 1u) {
+            const double Ax = dfix * x[d];
+            y[d] = EPI == EPI_RESID ? b[d] - Ax : Ax;
+          } else if (EPI == EPI_RESID) {
+            // b and K x nearly cancel near convergence: subtract the leading
+            // part first (exact when close), then the trailing part
+            y[d] = (b[d] - f2d(s.h)) - f2d(s.l);
+          } else {
+            y[d] = f2d(s.h) + f2d(s.l);
+          }
         } else {
-          y[d] = f2d(s.h) + f2d(s.l);
+          // dfix is 0 or 1, so dfix * x is exact in the pair format
+          const dfl Ax = ((m >> c) & 1u) ? (dfix != 0.0 ? ld_df(x, d) : dfl{0.f, 0.f}) : s;
+          st_df(y, d, EPI == EPI_RESID ? df_add(ld_df(b, d), df_neg(Ax)) : Ax);
         }
       }
     }
@@ -162,9 +172,21 @@ bool df_blocks_ok(const double* wht64) {
   return true;
 }
 
+template <typename S>
+static void run_df(const ApplyArgs& a, const DfBlocks& kb, dim3 grid, int zc, cudaStream_t s) {
+  if (a.epi == EPI_RESID)
+    k_apply3_df<EPI_RESID, S><<<grid, DX * DY, 0, s>>>(
+        a.g, a.mask, kb, static_cast<const double*>(a.coef), zc, static_cast<const S*>(a.x),
+        static_cast<S*>(a.y), static_cast<const S*>(a.b), a.dfix);
+  else
+    k_apply3_df<EPI_APPLY, S><<<grid, DX * DY, 0, s>>>(
+        a.g, a.mask, kb, static_cast<const double*>(a.coef), zc, static_cast<const S*>(a.x),
+        static_cast<S*>(a.y), static_cast<const S*>(a.b), a.dfix);
+}
+
 cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s) {
-  if (a.dim != 3 || a.expl || a.gal1 || a.tx != T_F64 || a.ty != T_F64 || !a.wht ||
-      a.epi == EPI_SMOOTH)
+  if (a.dim != 3 || a.expl || a.gal1 || a.tx != a.ty || (a.tx != T_F64 && a.tx != T_D2) ||
+      !a.wht || a.epi == EPI_SMOOTH || (a.tx == T_D2 && a.dfix != 0.0 && a.dfix != 1.0))
     return cudaErrorInvalidValue;
   if (a.g.nn <= 0) return cudaSuccess;
   const double* w = static_cast<const double*>(a.wht);
@@ -178,14 +200,10 @@ cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s) {
   int zc = 16;
   while (zc > 2 && (long long)gx * gy * ((a.g.nnz + zc - 1) / zc) < 2 * 152) zc /= 2;
   dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
-  if (a.epi == EPI_RESID)
-    k_apply3_df<EPI_RESID><<<grid, DX * DY, 0, s>>>(
-        a.g, a.mask, kb, static_cast<const double*>(a.coef), zc, static_cast<const double*>(a.x),
-        static_cast<double*>(a.y), static_cast<const double*>(a.b), a.dfix);
+  if (a.tx == T_D2)
+    run_df<float2>(a, kb, grid, zc, s);
   else
-    k_apply3_df<EPI_APPLY><<<grid, DX * DY, 0, s>>>(
-        a.g, a.mask, kb, static_cast<const double*>(a.coef), zc, static_cast<const double*>(a.x),
-        static_cast<double*>(a.y), static_cast<const double*>(a.b), a.dfix);
+    run_df<double>(a, kb, grid, zc, s);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 // linear weights of fine corner a of child c at coarse corner A.
 #include <math.h>
 
+#include "dfmath.cuh"
 #include "kernels.h"
 
 namespace topo {
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(256)
                 const T* __restrict__ dinv, T omega, T* __restrict__ z) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  const T bv = T(bin[q]);
+  const T bv = cvt<T>(bin[q]);
   if (bout) bout[q] = bv;
   z[q] = omega * dinv[q] * bv;
 }
@@ -120,7 +121,7 @@ template <typename TIN, typename TOUT>
 __global__ void __launch_bounds__(256)
     k_convert(long long n, const TIN* __restrict__ in, TOUT* __restrict__ out) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) out[q] = TOUT(in[q]);
+  if (q < n) out[q] = cvt<TOUT>(in[q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -508,6 +509,9 @@ cudaError_t launch_presmooth(int t, int tin, long long n, const void* bin, void*
   } else if (tin == T_F64) {
     k_presmooth<float, double><<<nb, 256, 0, s>>>(n, (const double*)bin, (float*)bout,
                                                   (const float*)dinv, (float)omega, (float*)z);
+  } else if (tin == T_D2) {
+    k_presmooth<float, float2><<<nb, 256, 0, s>>>(n, (const float2*)bin, (float*)bout,
+                                                  (const float*)dinv, (float)omega, (float*)z);
   } else {
     k_presmooth<float, float><<<nb, 256, 0, s>>>(n, (const float*)bin, (float*)bout,
                                                  (const float*)dinv, (float)omega, (float*)z);
@@ -518,7 +522,11 @@ cudaError_t launch_presmooth(int t, int tin, long long n, const void* bin, void*
 cudaError_t launch_convert(int tin, int tout, long long n, const void* in, void* out,
                            cudaStream_t s) {
   const int nb = nblocks(n, 256);
-  if (tin == T_F64 && tout == T_F32)
+  if (tin == T_D2 && tout == T_F32)
+    k_convert<float2, float><<<nb, 256, 0, s>>>(n, (const float2*)in, (float*)out);
+  else if (tin == T_F32 && tout == T_D2)
+    k_convert<float, float2><<<nb, 256, 0, s>>>(n, (const float*)in, (float2*)out);
+  else if (tin == T_F64 && tout == T_F32)
     k_convert<double, float><<<nb, 256, 0, s>>>(n, (const double*)in, (float*)out);
   else if (tin == T_F32 && tout == T_F64)
     k_convert<float, double><<<nb, 256, 0, s>>>(n, (const float*)in, (double*)out);

@@ -1,0 +1,566 @@
+// Float64-accurate long-vector kernels: the CG recursion of the mixed path,
+// the PARM/CARM Gram matrices and combinations, and Gram-Schmidt.
+//
+// A vector is stored either as float64 (the FP64 path: float64 arithmetic)
+// or as double-float pairs float2 {hi, lo} (the mixed path: every operation
+// in double-float on the FP32 pipe, ~2^-48 relative).  GB300 executes one
+// float64 FMA per clock per SM against 128 float32 FMAs, so the mixed path
+// keeps its float64-accurate vectors in the pair format: loads and stores
+// need no conversion and the FP64 pipe is left idle.  Reductions use a
+// fixed grid and fixed summation orders, so results do not depend on
+// scheduling.
+#include <type_traits>
+
+#include "dfmath.cuh"
+#include "kernels.h"
+
+namespace topo {
+
+// Arithmetic of a storage type: T is the register type.
+template <typename S>
+struct Ar;
+template <>
+struct Ar<double> {
+  using T = double;
+  __device__ static T ld(const double* p, long long i) { return p[i]; }
+  __device__ static void st(double* p, long long i, T v) { p[i] = v; }
+  __device__ static T zero() { return 0.0; }
+  __device__ static T from_d(double x) { return x; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static T fma3(T a, T b, T c) { return fma(a, b, c); }
+  __device__ static T mulf(T a, float b) { return a * (double)b; }
+  __device__ static double to_d(T a) { return a; }
+  __device__ static T shfl_down(T a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+};
+template <>
+struct Ar<float2> {
+  using T = dfl;
+  __device__ static T ld(const float2* p, long long i) {
+    const float2 v = p[i];
+    return {v.x, v.y};
+  }
+  __device__ static void st(float2* p, long long i, T v) { p[i] = make_float2(v.h, v.l); }
+  __device__ static T zero() { return {0.f, 0.f}; }
+  __device__ static T from_d(double x) { return split_d(x); }
+  __device__ static T add(T a, T b) { return df_add(a, b); }
+  __device__ static T fma3(T a, T b, T c) { return df_fma(a, b, c); }
+  // a * b for a float b (b exact): TwoProduct on hi plus the lo term
+  __device__ static T mulf(T a, float b) {
+    const float p = a.h * b;
+    float e = fmaf(a.h, b, -p);
+    e = fmaf(a.l, b, e);
+    const float h = p + e;
+    return {h, e - (h - p)};
+  }
+  __device__ static double to_d(T a) { return df_to_d(a); }
+  __device__ static T shfl_down(T a, int o) {
+    return {__shfl_down_sync(0xffffffffu, a.h, o), __shfl_down_sync(0xffffffffu, a.l, o)};
+  }
+};
+
+// store a register value into a (possibly different) storage type
+__device__ __forceinline__ void st_any(double* p, long long i, double v) { p[i] = v; }
+__device__ __forceinline__ void st_any(double* p, long long i, dfl v) { p[i] = df_to_d(v); }
+__device__ __forceinline__ void st_any(float2* p, long long i, dfl v) { p[i] = make_float2(v.h, v.l); }
+
+// Block sum of NV per-thread values: warps reduce in the storage's
+// arithmetic, lane 0 widens once, warp 0 adds the warp results in float64
+// in warp order.  Valid in thread 0.
+template <typename S, int NV>
+__device__ __forceinline__ void block_sum_v(typename Ar<S>::T (&v)[NV], double (&out)[NV],
+                                            double* sh /* >= NV*32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    typename Ar<S>::T x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = Ar<S>::add(x, Ar<S>::shfl_down(x, o));
+    if (lane == 0) sh[q * 32 + warp] = Ar<S>::to_d(x);
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = lane < nw ? sh[q * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      out[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// single-value reduction finished by the last block: *out = sum
+template <typename S>
+__device__ __forceinline__ void reduce_to(typename Ar<S>::T v, double* out, double* partials,
+                                          unsigned* counter, double* sh) {
+  typename Ar<S>::T vv[1] = {v};
+  double o1[1];
+  block_sum_v<S, 1>(vv, o1, sh);
+  if (publish_partials<1>(o1, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) *out = o[0];
+  }
+}
+
+#define GRID_LOOP(k, n)                                                 \
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
+       k < (n); k += (long long)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------------------
+// Basic vector operations
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_vdot(long long n, const S* __restrict__ a, const S* __restrict__ b, double* partials,
+           unsigned* counter, double* out) {
+  using A = Ar<S>;
+  __shared__ double sh[32];
+  typename A::T v = A::zero();
+  GRID_LOOP(k, n) v = A::fma3(A::ld(a, k), A::ld(b, k), v);
+  reduce_to<S>(v, out, partials, counter, sh);
+}
+
+__global__ void __launch_bounds__(256) k_split(long long n, const double* __restrict__ in,
+                                               float2* __restrict__ out) {
+  GRID_LOOP(k, n) {
+    const dfl v = split_d(in[k]);
+    out[k] = make_float2(v.h, v.l);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_join(long long n, const float2* __restrict__ in,
+                                              double* __restrict__ out) {
+  GRID_LOOP(k, n) {
+    const float2 v = in[k];
+    out[k] = df_to_d({v.x, v.y});
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_vcopy(long long n, const S* __restrict__ a,
+                                               S* __restrict__ b) {
+  GRID_LOOP(k, n) b[k] = a[k];
+}
+
+// a *= 1/sqrt(*s2) (0 when *s2 <= 0); the scale is formed once per block
+template <typename S>
+__global__ void __launch_bounds__(256) k_vscale_inv_sqrt(long long n, S* __restrict__ a,
+                                                         const double* __restrict__ s2) {
+  using A = Ar<S>;
+  __shared__ double s_sc;
+  if (threadIdx.x == 0) s_sc = (*s2 > 0.0) ? 1.0 / sqrt(*s2) : 0.0;
+  __syncthreads();
+  const typename A::T sc = A::from_d(s_sc);
+  GRID_LOOP(k, n) A::st(a, k, A::fma3(A::ld(a, k), sc, A::zero()));
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrix G[i + ldg*j] = sum_k A[k + i*n] B[k + j*n] (i < na, j < nb,
+// both <= MAXB) in one pass over the data: a block stages a chunk of MD_CH
+// indices of every column in shared memory, then its threads accumulate
+// 2 x 2 tiles of G over interleaved index subsets.  Per-block partials are
+// summed by the last block in block order.
+// ---------------------------------------------------------------------------
+constexpr int MD_CH = 128;   // indices per chunk = threads per block
+
+template <typename S>
+__global__ void __launch_bounds__(MD_CH)
+    k_gram(long long n, const S* __restrict__ A, int na, const int* na_dev,
+           const S* __restrict__ B, int nb, const int* nb_dev, double* G, int ldg,
+           double* partials, unsigned* counter) {
+  using Rg = Ar<S>;
+  using V = typename Rg::T;
+  __shared__ V sv[2 * MAXB * MD_CH];
+  __shared__ bool s_last;
+  const int ma = na_dev ? min(max(*na_dev, 0), na) : na;
+  const int mb = nb_dev ? min(max(*nb_dev, 0), nb) : nb;
+  const int nv = ma + mb;
+  const int tr = (ma + 1) / 2, tc = (mb + 1) / 2;
+  const int ntile = tr * tc > 0 ? tr * tc : 1;
+  const int S_ = MD_CH / ntile;   // index subsets per tile (>= 2)
+  const int t = threadIdx.x;
+  const int tile = t % ntile, sub = t / ntile;
+  const bool active = tr * tc > 0 && sub < S_;
+  const int i0 = active ? 2 * (tile % tr) : 0, j0 = active ? 2 * (tile / tr) : 0;
+  V acc[2][2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) acc[p][q] = Rg::zero();
+  for (long long k0 = (long long)blockIdx.x * MD_CH; k0 < n; k0 += (long long)gridDim.x * MD_CH) {
+    const long long k = k0 + t;
+    for (int v = 0; v < nv; ++v) {
+      const S* col = v < ma ? A + (size_t)v * n : B + (size_t)(v - ma) * n;
+      sv[v * MD_CH + t] = k < n ? Rg::ld(col, k) : Rg::zero();
+    }
+    __syncthreads();
+    if (active) {
+      const V* a0 = sv + i0 * MD_CH;
+      const V* a1 = sv + (i0 + 1 < ma ? i0 + 1 : i0) * MD_CH;
+      const V* b0 = sv + (ma + j0) * MD_CH;
+      const V* b1 = sv + (ma + (j0 + 1 < mb ? j0 + 1 : j0)) * MD_CH;
+      for (int idx = sub; idx < MD_CH; idx += S_) {
+        const V x0 = a0[idx], x1 = a1[idx], y0 = b0[idx], y1 = b1[idx];
+        acc[0][0] = Rg::fma3(x0, y0, acc[0][0]);
+        acc[1][0] = Rg::fma3(x1, y0, acc[1][0]);
+        acc[0][1] = Rg::fma3(x0, y1, acc[0][1]);
+        acc[1][1] = Rg::fma3(x1, y1, acc[1][1]);
+      }
+    }
+    __syncthreads();
+  }
+  double* red = reinterpret_cast<double*>(sv);   // ntile * 4 * S_ <= 4 * MD_CH doubles
+  if (active) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) red[(tile * 4 + p + 2 * q) * S_ + sub] = Rg::to_d(acc[p][q]);
+  }
+  __syncthreads();
+  const int np = ma * mb;
+  double* part = partials + (size_t)blockIdx.x * (MAXB * MAXB);
+  for (int e = t; e < np; e += MD_CH) {
+    const int i = e % ma, j = e / ma;
+    const int tl = (i / 2) + tr * (j / 2), qq = (i & 1) + 2 * (j & 1);
+    double sum = 0.0;
+    for (int u = 0; u < S_; ++u) sum += red[(tl * 4 + qq) * S_ + u];
+    part[e] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int e = t; e < np; e += MD_CH) {
+    double sum = 0.0;
+    for (int bl = 0; bl < (int)gridDim.x; ++bl) sum += partials[(size_t)bl * (MAXB * MAXB) + e];
+    G[(e % ma) + (size_t)ldg * (e / ma)] = sum;
+  }
+  if (t == 0) *counter = 0u;
+}
+
+// Column case: g[i] = sum_k A[k + i*n] b[k].  Warp i of a block accumulates
+// column i (one accumulator per lane, two indices in flight), so registers
+// stay few and many loads are outstanding; lanes, warps' results and blocks
+// are summed in a fixed order.
+template <typename S>
+__global__ void __launch_bounds__(32 * MAXB)
+    k_gram_col(long long n, const S* __restrict__ A, int na, const int* na_dev,
+               const S* __restrict__ b, double* g, double* partials, unsigned* counter) {
+  using Rg = Ar<S>;
+  using V = typename Rg::T;
+  __shared__ double sh[MAXB];
+  __shared__ bool s_last;
+  const int ma = na_dev ? min(max(*na_dev, 0), na) : na;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  V acc = Rg::zero(), acc2 = Rg::zero();
+  if (wi < ma) {
+    const S* col = A + (size_t)wi * n;
+    const long long stride = (long long)gridDim.x * 32;
+    long long k = (long long)blockIdx.x * 32 + lane;
+    for (; k + stride < n; k += 2 * stride) {
+      const V a0 = Rg::ld(col, k), b0 = Rg::ld(b, k);
+      const V a1 = Rg::ld(col, k + stride), b1 = Rg::ld(b, k + stride);
+      acc = Rg::fma3(a0, b0, acc);
+      acc2 = Rg::fma3(a1, b1, acc2);
+    }
+    if (k < n) acc = Rg::fma3(Rg::ld(col, k), Rg::ld(b, k), acc);
+    acc = Rg::add(acc, acc2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = Rg::add(acc, Rg::shfl_down(acc, o));
+  }
+  if (lane == 0) sh[wi] = wi < ma ? Rg::to_d(acc) : 0.0;
+  __syncthreads();
+  if ((int)threadIdx.x < MAXB) {
+    const double v = (int)threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    partials[(size_t)blockIdx.x * MAXB + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if ((int)threadIdx.x < ma) {
+    double sum = 0.0;
+    for (int bl = 0; bl < (int)gridDim.x; ++bl) sum += partials[(size_t)bl * MAXB + threadIdx.x];
+    g[threadIdx.x] = sum;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// y = beta*y + sign*sum_i c[i] A[:, i] (i < m <= MMAX); optional
+// |y - w|^2 -> *rr.  A, w (and y when SY = S) in storage S; y may be
+// float64 when S is the pair format (one float64 add per stored value).
+template <typename S, typename SY, int MMAX>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_combine(long long n, const S* __restrict__ A, int m, const int* m_dev,
+              const double* __restrict__ c, double sign, double beta, SY* __restrict__ y,
+              const S* __restrict__ w, double* rr, double* partials, unsigned* counter) {
+  using Rg = Ar<S>;
+  using V = typename Rg::T;
+  __shared__ double sh[32];
+  const int mm = m_dev ? min(max(*m_dev, 0), m) : m;
+  V cc[MMAX];
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i) {
+    const double ci = i < mm ? c[i] : 0.0;
+    cc[i] = Rg::from_d(sign == 1.0 ? ci : sign == -1.0 ? -ci : sign * ci);
+  }
+  const V bb = Rg::from_d(beta);
+  V v = Rg::zero();
+  GRID_LOOP(k, n) {
+    V s = Rg::zero();
+    if (beta != 0.0) {
+      V yk;
+      if constexpr (std::is_same<SY, S>::value) yk = Rg::ld(y, k);
+      else yk = Rg::from_d((double)y[k]);
+      s = (beta == 1.0) ? yk : Rg::fma3(bb, yk, Rg::zero());
+    }
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i)
+      if (i < mm) s = Rg::fma3(cc[i], Rg::ld(A + (size_t)i * n, k), s);
+    st_any(y, k, s);
+    if (rr) {
+      V d = s;
+      if (w) d = Rg::add(s, Rg::fma3(Rg::ld(w, k), Rg::from_d(-1.0), Rg::zero()));
+      v = Rg::fma3(d, d, v);
+    }
+  }
+  if (!rr) return;
+  reduce_to<S>(v, rr, partials, counter, sh);
+}
+
+// Gram-Schmidt acceptance: if |r_src|^2 after orthogonalisation exceeds
+// tol^2 times its value before, R[:, k] = r_src / |r_src| with k the
+// current count (the count itself is advanced by k_gs_count afterwards)
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_gs_accept(long long n, S* R, int src, const double* scal, int n0, int n1, double tol,
+                const int* ints) {
+  using Rg = Ar<S>;
+  __shared__ double s_scale;
+  const double before = scal[n0], after = scal[n1];
+  const bool keep = after > tol * tol * before && after > 0.0;
+  if (!keep) return;
+  const int k = ints[I_KCOUNT];
+  if (threadIdx.x == 0) s_scale = 1.0 / sqrt(after);   // once per block
+  __syncthreads();
+  const typename Rg::T sc = Rg::from_d(s_scale);
+  const S* a = R + (size_t)src * n;
+  S* b = R + (size_t)k * n;
+  GRID_LOOP(i, n) Rg::st(b, i, Rg::fma3(Rg::ld(a, i), sc, Rg::zero()));
+}
+
+__global__ void k_gs_count(const double* scal, int n0, int n1, double tol, int* ints) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double before = scal[n0], after = scal[n1];
+  if (after > tol * tol * before && after > 0.0) ints[I_KCOUNT] += 1;
+}
+
+// ---------------------------------------------------------------------------
+// CG recursion of the mixed path: x, r, p in the pair format; the operator
+// works on the float32 shadow p32 -> q32 and the V-cycle returns z32.
+// alpha and beta are formed once per block from the float64 scalars.
+// ---------------------------------------------------------------------------
+// out = sum_k a[k] b[k], a pairs, b float32
+__global__ void __launch_bounds__(RED_THREADS)
+    k_dot_d2f(long long n, const float2* __restrict__ a, const float* __restrict__ b,
+              double* partials, unsigned* counter, double* out) {
+  using Rg = Ar<float2>;
+  __shared__ double sh[32];
+  dfl v = Rg::zero(), v2 = Rg::zero();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + stride < n; k += 2 * stride) {
+    const dfl a0 = Rg::ld(a, k), a1 = Rg::ld(a, k + stride);
+    const float b0 = b[k], b1 = b[k + stride];
+    v = df_add(Rg::mulf(a0, b0), v);
+    v2 = df_add(Rg::mulf(a1, b1), v2);
+  }
+  if (k < n) v = df_add(Rg::mulf(Rg::ld(a, k), b[k]), v);
+  reduce_to<float2>(df_add(v, v2), out, partials, counter, sh);
+}
+
+// alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q; scal[rr] = |r|^2
+__global__ void __launch_bounds__(RED_THREADS)
+    k_cg_xr_d2(long long n, float2* __restrict__ x, float2* __restrict__ r,
+               const float2* __restrict__ p, const float* __restrict__ q, double* scal, int num,
+               int den, int rr, double* partials, unsigned* counter) {
+  using Rg = Ar<float2>;
+  __shared__ double sh[32];
+  __shared__ double s_alpha;
+  if (threadIdx.x == 0) s_alpha = scal[num] / scal[den];
+  __syncthreads();
+  const dfl al = split_d(s_alpha), mal = {-al.h, -al.l};
+  dfl v = Rg::zero();
+  GRID_LOOP(k, n) {
+    Rg::st(x, k, df_fma(al, Rg::ld(p, k), Rg::ld(x, k)));
+    const dfl rk = df_add(Rg::mulf(mal, q[k]), Rg::ld(r, k));
+    Rg::st(r, k, rk);
+    v = df_fma(rk, rk, v);
+  }
+  reduce_to<float2>(v, scal + rr, partials, counter, sh);
+}
+
+// p = z + beta p (beta = scal[num]/scal[den], or p = z when num < 0);
+// p32 = p rounded to float32
+__global__ void __launch_bounds__(256)
+    k_cg_p_d2(long long n, float2* __restrict__ p, float* __restrict__ p32,
+              const float* __restrict__ z, const double* __restrict__ scal, int num, int den) {
+  using Rg = Ar<float2>;
+  __shared__ double s_beta;
+  if (threadIdx.x == 0) s_beta = num >= 0 ? scal[num] / scal[den] : 0.0;
+  __syncthreads();
+  const dfl be = split_d(s_beta);
+  GRID_LOOP(k, n) {
+    const dfl zk = {z[k], 0.f};
+    const dfl pk = num >= 0 ? df_add(df_mul(be, Rg::ld(p, k)), zk) : zk;
+    Rg::st(p, k, pk);
+    p32[k] = __fadd_rn(pk.h, pk.l);
+  }
+}
+
+#undef GRID_LOOP
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static inline int vgrid(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > RED_BLOCKS) b = RED_BLOCKS;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_vdot(long long n, int vt, const void* a, const void* b, double* partials,
+                        unsigned* counter, double* out, cudaStream_t s) {
+  if (vt == V_DF2)
+    k_vdot<float2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (const float2*)a, (const float2*)b,
+                                                      partials, counter, out);
+  else
+    k_vdot<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (const double*)a, (const double*)b,
+                                                      partials, counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vconvert(long long n, int tin, const void* in, int tout, void* out,
+                            cudaStream_t s) {
+  if (tin == tout) {
+    if (in == out) return cudaSuccess;
+    if (tin == V_DF2)
+      k_vcopy<float2><<<vgrid(n), 256, 0, s>>>(n, (const float2*)in, (float2*)out);
+    else
+      k_vcopy<double><<<vgrid(n), 256, 0, s>>>(n, (const double*)in, (double*)out);
+  } else if (tin == V_F64) {
+    k_split<<<vgrid(n), 256, 0, s>>>(n, (const double*)in, (float2*)out);
+  } else {
+    k_join<<<vgrid(n), 256, 0, s>>>(n, (const float2*)in, (double*)out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vscale_inv_sqrt(long long n, int vt, void* a, const double* s2,
+                                   cudaStream_t s) {
+  if (vt == V_DF2)
+    k_vscale_inv_sqrt<float2><<<vgrid(n), 256, 0, s>>>(n, (float2*)a, s2);
+  else
+    k_vscale_inv_sqrt<double><<<vgrid(n), 256, 0, s>>>(n, (double*)a, s2);
+  return cudaGetLastError();
+}
+
+template <typename S>
+static void gram_t(long long n, const void* A, int na, const int* na_dev, const void* B, int nb,
+                   const int* nb_dev, double* G, int ldg, double* partials, unsigned* counter,
+                   cudaStream_t s) {
+  if (nb == 1 && nb_dev == nullptr)
+    k_gram_col<S><<<RED_BLOCKS, 32 * na, 0, s>>>(n, (const S*)A, na, na_dev, (const S*)B, G,
+                                                 partials, counter);
+  else
+    k_gram<S><<<RED_BLOCKS, MD_CH, 0, s>>>(n, (const S*)A, na, na_dev, (const S*)B, nb, nb_dev,
+                                           G, ldg, partials, counter);
+}
+
+cudaError_t launch_gram(long long n, int vt, const void* A, int na, const int* na_dev,
+                        const void* B, int nb, const int* nb_dev, double* G, int ldg,
+                        double* partials, unsigned* counter, cudaStream_t s) {
+  if (na > MAXB || nb > MAXB || na < 1 || nb < 1) return cudaErrorInvalidValue;
+  if (vt == V_DF2)
+    gram_t<float2>(n, A, na, na_dev, B, nb, nb_dev, G, ldg, partials, counter, s);
+  else
+    gram_t<double>(n, A, na, na_dev, B, nb, nb_dev, G, ldg, partials, counter, s);
+  return cudaGetLastError();
+}
+
+template <typename S, typename SY>
+static void combine_t(long long n, const void* A, int m, const int* m_dev, const double* c,
+                      double sign, double beta, void* y, const void* w, double* rr,
+                      double* partials, unsigned* counter, cudaStream_t s) {
+  const S* a = (const S*)A;
+  const S* ww = (const S*)w;
+  SY* yy = (SY*)y;
+  if (m <= 4)
+    k_combine<S, SY, 4><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, m, m_dev, c, sign, beta, yy, ww,
+                                                           rr, partials, counter);
+  else if (m <= 8)
+    k_combine<S, SY, 8><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, m, m_dev, c, sign, beta, yy, ww,
+                                                           rr, partials, counter);
+  else if (m <= 12)
+    k_combine<S, SY, 12><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, m, m_dev, c, sign, beta, yy,
+                                                            ww, rr, partials, counter);
+  else
+    k_combine<S, SY, MAXB><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, m, m_dev, c, sign, beta, yy,
+                                                              ww, rr, partials, counter);
+}
+
+cudaError_t launch_combine(long long n, int vt, const void* A, int m, const int* m_dev,
+                           const double* c, double sign, double beta, void* y, int yt,
+                           const void* w, double* rr, double* partials, unsigned* counter,
+                           cudaStream_t s) {
+  if (m > MAXB || m < 0) return cudaErrorInvalidValue;
+  if (vt == V_DF2 && yt == V_DF2)
+    combine_t<float2, float2>(n, A, m, m_dev, c, sign, beta, y, w, rr, partials, counter, s);
+  else if (vt == V_DF2 && yt == V_F64)
+    combine_t<float2, double>(n, A, m, m_dev, c, sign, beta, y, w, rr, partials, counter, s);
+  else if (vt == V_F64 && yt == V_F64)
+    combine_t<double, double>(n, A, m, m_dev, c, sign, beta, y, w, rr, partials, counter, s);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double* scal, int n0,
+                             int n1, double tol, int* ints, cudaStream_t s) {
+  if (vt == V_DF2)
+    k_gs_accept<float2><<<vgrid(n), 256, 0, s>>>(n, (float2*)R, src, scal, n0, n1, tol, ints);
+  else
+    k_gs_accept<double><<<vgrid(n), 256, 0, s>>>(n, (double*)R, src, scal, n0, n1, tol, ints);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gs_count<<<1, 32, 0, s>>>(scal, n0, n1, tol, ints);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* partials,
+                           unsigned* counter, double* out, cudaStream_t s) {
+  k_dot_d2f<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (const float2*)a, b, partials, counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const float* q,
+                            double* scal, int num, int den, int rr, double* partials,
+                            unsigned* counter, cudaStream_t s) {
+  k_cg_xr_d2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (float2*)x, (float2*)r, (const float2*)p, q,
+                                                scal, num, den, rr, partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p_d2(long long n, void* p, float* p32, const float* z, const double* scal,
+                           int num, int den, cudaStream_t s) {
+  k_cg_p_d2<<<vgrid(n), 256, 0, s>>>(n, (float2*)p, p32, z, scal, num, den);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

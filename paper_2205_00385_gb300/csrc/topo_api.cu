@@ -302,6 +302,8 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   double *oclo = cv.take<double>(nel), *ochi = cv.take<double>(nel);
   float *E32 = cv.take<float>(nel), *Ep32 = cv.take<float>(nel), *dE32 = cv.take<float>(nel);
   double* f = cv.take<double>(n);
+  double* fd = cv.take<double>(n);
+  double* w64 = (mixed && dim != 3) ? cv.take<double>(n) : nullptr;
   double *r = cv.take<double>(n), *z = cv.take<double>(n), *p = cv.take<double>(n),
          *q = cv.take<double>(n);
   float *p32 = cv.take<float>(n), *q32 = cv.take<float>(n);
@@ -343,7 +345,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   if (c) {
     c->E64 = E64; c->Eprev64 = Ep64; c->dE64 = dE64; c->rho_phys = rho; c->invHs = invHs; c->oc_a = oca;
     c->oc_lo = oclo; c->oc_hi = ochi;
-    c->E32 = E32; c->Eprev32 = Ep32; c->dE32 = dE32; c->f = f;
+    c->E32 = E32; c->Eprev32 = Ep32; c->dE32 = dE32; c->f = f; c->fd = fd; c->w64 = w64;
     c->r = r; c->z = z; c->p = p; c->q = q; c->p32 = p32; c->q32 = q32;
     c->Phi = Phi; c->KPhi = KPhi; c->R = R; c->Q = Q; c->t = t;
     c->Qc64 = Qc64; c->Qc32 = Qc32;
@@ -500,6 +502,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
           c->qdiag[(ch * 8 + a) * 3 + cc] = Qc[(size_t)ch * 576 + (3 * a + cc) * 24 + 3 * a + cc];
   }
   INIT_TRY(cudaMemcpyAsync(c->f, f, c->n * 8, cudaMemcpyDeviceToDevice, s), "copy f");
+  if (c->mixed) INIT_TRY(launch_vconvert(c->n, V_F64, c->f, V_DF2, c->fd, s), "split f");
   INIT_TRY(cudaMemsetAsync(c->counters, 0, C_NCOUNTERS * sizeof(unsigned), s), "memset");
   INIT_TRY(cudaMemsetAsync(c->scal, 0, S_NSLOTS * 8, s), "memset");
   INIT_TRY(cudaMemsetAsync(c->ints, 0, I_NINTS * sizeof(int), s), "memset");
@@ -707,15 +710,15 @@ static to_status build_hierarchy(to_ctx* c) {
 }
 
 // zout (type zt: float64, or float32 in the mixed path) = V-cycle applied to
-// r (float64, n)
-static to_status vcycle(to_ctx* c, const double* rin, void* zout, int zt) {
+// r (storage rin_t: float64, or double-float pairs in the mixed path)
+static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int zt) {
   cudaStream_t s = c->stream;
   const int t = mg_t(c);
   const int L = c->L;
   ProfScope ps(c, PK_VCYCLE);
   LevelBuf* lv = c->lv;
   // finest level: smoothing from zero, residual, restriction
-  LAUNCH(c, launch_presmooth(t, T_F64, lv[0].n, rin, lv[0].b, lv[0].dinv, 0.6, lv[0].z, s),
+  LAUNCH(c, launch_presmooth(t, rin_t, lv[0].n, rin, lv[0].b, lv[0].dinv, 0.6, lv[0].z, s),
          "presmooth 0");
   to_status st;
   if ((st = run_op(c, fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
@@ -752,7 +755,7 @@ static to_status vcycle(to_ctx* c, const double* rin, void* zout, int zt) {
 // in float64), so it is captured once per (input, output, precision,
 // coefficients) as a CUDA graph and replayed: one launch per preconditioner
 // application instead of one per kernel, with no host gaps between kernels.
-static to_status vcycle_graphed(to_ctx* c, const double* rin, void* zout, int zt) {
+static to_status vcycle_graphed(to_ctx* c, const void* rin, int rin_t, void* zout, int zt) {
   const void* coef = mg_t(c) == T_F64 ? (const void*)c->E64 : (const void*)c->E32;
   to_ctx::VGraph* vg = nullptr;
   for (int q = 0; q < c->n_vgraph; ++q) {
@@ -772,7 +775,7 @@ static to_status vcycle_graphed(to_ctx* c, const double* rin, void* zout, int zt
     to_status st = TO_OK;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      st = vcycle(c, rin, zout, zt);
+      st = vcycle(c, rin, rin_t, zout, zt);
       const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
       if (e == cudaSuccess) e = e2;
     }
@@ -844,14 +847,55 @@ static to_status apply_op(to_ctx* c, int op, int prec, const double* x, double* 
                 "apply");
 }
 
+// Storage of the long float64-accurate vectors (CG iterate, r, p; Phi,
+// KPhi, R, Q, t): float64 on the FP64 path, double-float pairs on the mixed
+// path (arithmetic on the FP32 pipe; GB300's FP64 pipe is 1/128 of FP32).
+static int vt(const to_ctx* c) { return c->mixed ? V_DF2 : V_F64; }
+static int vt_code(const to_ctx* c) { return c->mixed ? T_D2 : T_F64; }
+
+// y = op(x) in the context's apply precision, x and y in vector storage:
+// float64 on the FP64 path; float32 through the shadows p32 -> q32 (the
+// solver's float32 operator) on the mixed path
+static to_status apply_vec(to_ctx* c, int op, const double* x, double* y) {
+  if (!c->mixed)
+    return run_op(c, fine_args(c, op, T_F64, T_F64, T_F64, x, y, nullptr, nullptr, EPI_APPLY),
+                  "apply");
+  LAUNCH(c, launch_convert(T_D2, T_F32, c->n, x, c->p32, c->stream), "round x");
+  to_status st = run_op(c, fine_args(c, op, T_F32, T_F32, T_F32, c->p32, c->q32, nullptr,
+                                     nullptr, EPI_APPLY), "apply");
+  if (st != TO_OK) return st;
+  LAUNCH(c, launch_convert(T_F32, T_D2, c->n, c->q32, y, c->stream), "widen y");
+  return TO_OK;
+}
+
+// float64-accurate y = op(x) (EPI_APPLY) or y = f - op(x) (EPI_RESID), x
+// and y in vector storage: float64 operator, double-float operator on pairs,
+// or (mixed 2D) the float64 operator through float64 scratch
+static to_status apply_accurate_vec(to_ctx* c, int op, const double* x, double* y, int epi) {
+  const bool resid = epi == EPI_RESID;
+  if (!c->mixed)
+    return run_op(c, fine_args(c, op, T_F64, T_F64, T_F64, x, y, resid ? c->f : nullptr, nullptr,
+                               epi), "accurate apply");
+  if (c->df_ok)
+    return run_op(c, fine_args(c, op, T_DF, T_D2, T_D2, x, y, resid ? c->fd : nullptr, nullptr,
+                               epi), "accurate apply");
+  LAUNCH(c, launch_vconvert(c->n, V_DF2, x, V_F64, c->q, c->stream), "widen x");
+  to_status st = run_op(c, fine_args(c, op, T_F64, T_F64, T_F64, c->q, c->w64,
+                                     resid ? c->f : nullptr, nullptr, epi), "accurate apply");
+  if (st != TO_OK) return st;
+  LAUNCH(c, launch_vconvert(c->n, V_F64, c->w64, V_DF2, y, c->stream), "split y");
+  return TO_OK;
+}
+
 static to_status parm_push(to_ctx* c, const double* u) {
   cudaStream_t s = c->stream;
   const int Ns = c->desc.n_parm;
   const int slot = c->parm_head;
   double* col = c->Phi + (size_t)slot * c->n;
-  LAUNCH(c, launch_dot(c->n, u, u, c->partials, c->counters + C_DOT, c->scal + S_NRM, s), "norm");
-  LAUNCH(c, launch_copy(c->n, u, col, s), "copy");
-  LAUNCH(c, launch_scale_by_inv_sqrt(c->n, col, c->scal + S_NRM, s), "scale");
+  LAUNCH(c, launch_vconvert(c->n, V_F64, u, vt(c), col, s), "copy");
+  LAUNCH(c, launch_vdot(c->n, vt(c), col, col, c->partials, c->counters + C_DOT, c->scal + S_NRM,
+                        s), "norm");
+  LAUNCH(c, launch_vscale_inv_sqrt(c->n, vt(c), col, c->scal + S_NRM, s), "scale");
   c->parm_head = (c->parm_head + 1) % Ns;
   c->parm_count = std::min(c->parm_count + 1, Ns);
   return TO_OK;
@@ -872,8 +916,8 @@ to_status to_vcycle(to_ctx* c, const double* r, double* z) {
     to_status st = build_hierarchy(c);
     if (st != TO_OK) return st;
   }
-  if (!c->mixed) return vcycle(c, r, z, T_F64);
-  to_status st = vcycle(c, r, c->lv[0].z2, T_F32);
+  if (!c->mixed) return vcycle(c, r, T_F64, z, T_F64);
+  to_status st = vcycle(c, r, T_F64, c->lv[0].z2, T_F32);
   if (st != TO_OK) return st;
   LAUNCH(c, launch_convert(T_F32, T_F64, c->n, c->lv[0].z2, z, c->stream), "convert");
   return TO_OK;
@@ -912,17 +956,23 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   to_status st;
   if (c->hier_stale && (st = build_hierarchy(c)) != TO_OK) return st;
   const long long n = c->n;
-  const int tc = apply_tc(c, TO_PREC_NATIVE);
-  double* x = u;
-  if (!(flags & TO_SOLVE_WARM_START)) CUDA_TRY(c, cudaMemsetAsync(x, 0, n * 8, s), "zero u");
-  // r = f - K x, always with the float64 operator (the true residual)
+  // Mixed path: the iterate x, r and p are double-float pairs (x in the
+  // otherwise unused float64 z buffer); the operator and the V-cycle work on
+  // float32 shadows (p32 -> q32, z32); dot products are double-float.
+  // FP64 path: everything float64, x = u.
+  const bool mixed = c->mixed;
+  double* x = mixed ? c->z : u;
+  const bool warm = (flags & TO_SOLVE_WARM_START) != 0;
+  if (mixed && warm)
+    LAUNCH(c, launch_vconvert(n, V_F64, u, V_DF2, x, s), "split u");
+  else if (!warm)
+    CUDA_TRY(c, cudaMemsetAsync(x, 0, n * 8, s), "zero x");
+  // r = f - K x with the float64-accurate operator (the true residual)
   auto true_residual = [&](double* rr_out) -> to_status {
     to_status e;
-    if ((e = run_op(c, fine_args(c, TO_OP_K, accurate_tc(c), T_F64, T_F64, x, c->r, c->f, nullptr,
-                                 EPI_RESID), "true residual")) != TO_OK)
-      return e;
-    LAUNCH(c, launch_dot(n, c->r, c->r, c->partials, c->counters + C_DOT, c->scal + S_RR, s),
-           "rr");
+    if ((e = apply_accurate_vec(c, TO_OP_K, x, c->r, EPI_RESID)) != TO_OK) return e;
+    LAUNCH(c, launch_vdot(n, vt(c), c->r, c->r, c->partials, c->counters + C_DOT,
+                          c->scal + S_RR, s), "rr");
     return read_scalar(c, c->scal + S_RR, rr_out);
   };
   double rr = 0.0;
@@ -931,18 +981,15 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   double rr_max = rr;          // largest residual since the last true-residual update
   int it = 0;
   bool conv = rel < rtol;
-  // In the mixed path the operator and the V-cycle work on float32 shadows
-  // (p32 -> q32, z32); x, r, p and all dot products stay float64.
-  const bool f32 = tc != T_F64;
   float* z32 = static_cast<float*>(c->lv[0].z2);
   auto precondition = [&](int slot) -> to_status {
     to_status e;
-    if (f32) {
-      if ((e = vcycle_graphed(c, c->r, z32, T_F32)) != TO_OK) return e;
-      LAUNCH(c, launch_dot_df(n, c->r, z32, c->partials, c->counters + C_DOT, c->scal + slot, s),
+    if (mixed) {
+      if ((e = vcycle_graphed(c, c->r, T_D2, z32, T_F32)) != TO_OK) return e;
+      LAUNCH(c, launch_dot_d2f(n, c->r, z32, c->partials, c->counters + C_DOT, c->scal + slot, s),
              "rz");
     } else {
-      if ((e = vcycle_graphed(c, c->r, c->z, T_F64)) != TO_OK) return e;
+      if ((e = vcycle_graphed(c, c->r, T_F64, c->z, T_F64)) != TO_OK) return e;
       LAUNCH(c, launch_dot(n, c->r, c->z, c->partials, c->counters + C_DOT, c->scal + slot, s),
              "rz");
     }
@@ -950,23 +997,23 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   };
   if (!conv) {
     if ((st = precondition(S_RZ0)) != TO_OK) return st;
-    if (f32)
-      LAUNCH(c, launch_cg_p_f(n, c->p, c->p32, z32, c->scal, -1, 0, s), "p = z");
+    if (mixed)
+      LAUNCH(c, launch_cg_p_d2(n, c->p, c->p32, z32, c->scal, -1, 0, s), "p = z");
     else
       LAUNCH(c, launch_copy(n, c->z, c->p, s), "p = z");
     int cur = S_RZ0, nxt = S_RZ1;
     for (it = 1; it <= maxit; ++it) {
-      if (f32) {
+      if (mixed) {
         if ((st = run_op(c, fine_args(c, TO_OP_K, T_F32, T_F32, T_F32, c->p32, c->q32, nullptr,
                                       nullptr, EPI_APPLY), "q = K p")) != TO_OK)
           return st;
-        LAUNCH(c, launch_dot_df(n, c->p, c->q32, c->partials, c->counters + C_DOT,
-                                c->scal + S_PQ, s), "pq");
-        LAUNCH(c, launch_cg_xr_f(n, x, c->r, c->p, c->q32, c->scal, cur, S_PQ, S_RR, c->partials,
-                                 c->counters + C_UPD, s), "x, r update");
+        LAUNCH(c, launch_dot_d2f(n, c->p, c->q32, c->partials, c->counters + C_DOT,
+                                 c->scal + S_PQ, s), "pq");
+        LAUNCH(c, launch_cg_xr_d2(n, x, c->r, c->p, c->q32, c->scal, cur, S_PQ, S_RR,
+                                  c->partials, c->counters + C_UPD, s), "x, r update");
       } else {
-        if ((st = run_op(c, fine_args(c, TO_OP_K, tc, T_F64, T_F64, c->p, c->q, nullptr, nullptr,
-                                      EPI_APPLY), "q = K p")) != TO_OK)
+        if ((st = run_op(c, fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, c->p, c->q, nullptr,
+                                      nullptr, EPI_APPLY), "q = K p")) != TO_OK)
           return st;
         LAUNCH(c, launch_dot(n, c->p, c->q, c->partials, c->counters + C_DOT, c->scal + S_PQ, s),
                "pq");
@@ -977,10 +1024,10 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
       rel = sqrt(rr) / c->fnorm;
       if (!isfinite(rel)) return fail(c, TO_E_SINGULAR, "CG breakdown (non-finite residual)");
       // Reliable updates: with a float32 operator the recursive residual
-      // drifts from f - K x, so it is replaced by the float64 true residual
-      // whenever it has dropped 100x since the last replacement and before
-      // convergence is declared.  The search direction is kept.
-      if (tc != T_F64 && (rel < rtol || rr < 1e-4 * rr_max)) {
+      // drifts from f - K x, so it is replaced by the float64-accurate true
+      // residual whenever it has dropped 100x since the last replacement and
+      // before convergence is declared.  The search direction is kept.
+      if (mixed && (rel < rtol || rr < 1e-4 * rr_max)) {
         if ((st = true_residual(&rr)) != TO_OK) return st;
         rel = sqrt(rr) / c->fnorm;
         rr_max = rr;
@@ -992,19 +1039,21 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
       }
       if (it == maxit) break;
       if ((st = precondition(nxt)) != TO_OK) return st;
-      if (f32)
-        LAUNCH(c, launch_cg_p_f(n, c->p, c->p32, z32, c->scal, nxt, cur, s), "p update");
+      if (mixed)
+        LAUNCH(c, launch_cg_p_d2(n, c->p, c->p32, z32, c->scal, nxt, cur, s), "p update");
       else
         LAUNCH(c, launch_cg_p(n, c->p, c->z, c->scal, nxt, cur, s), "p update");
       std::swap(cur, nxt);
     }
     if (it > maxit) it = maxit;
+    // the iterate back to float64 (untouched when no step was taken)
+    if (mixed) LAUNCH(c, launch_vconvert(n, V_DF2, x, V_F64, u, s), "widen x");
   }
   if (iters) *iters = it;
   if (relres) *relres = rel;
   if ((st = check_status(c)) != TO_OK) return st;
   if (flags & TO_SOLVE_PUSH_PARM) {
-    if ((st = parm_push(c, x)) != TO_OK) return st;
+    if ((st = parm_push(c, u)) != TO_OK) return st;
   }
   if (!conv) return fail(c, TO_E_NOT_CONVERGED, "MGCG reached maxit");
   return TO_OK;
@@ -1036,41 +1085,44 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
   const int Ns = c->desc.n_parm, m = c->desc.n_carm;
   to_status st;
   double* small = c->small;
+  const int v = vt(c);
   // K_Phi = Phi^T K_ref Phi  (Eq. 15)
   for (int i = 0; i < Ns; ++i)
-    if ((st = apply_op(c, TO_OP_KREF, TO_PREC_NATIVE, c->Phi + (size_t)i * n,
-                       c->KPhi + (size_t)i * n)) != TO_OK)
+    if ((st = apply_vec(c, TO_OP_KREF, c->Phi + (size_t)i * n, c->KPhi + (size_t)i * n)) != TO_OK)
       return st;
-  LAUNCH(c, launch_multidot(n, c->Phi, Ns, nullptr, c->KPhi, Ns, nullptr, small + SM_KPHI, Ns,
-                            c->partials, c->counters + C_MULTI, c->mixed, s), "K_Phi");
+  LAUNCH(c, launch_gram(n, v, c->Phi, Ns, nullptr, c->KPhi, Ns, nullptr, small + SM_KPHI, Ns,
+                        c->partials, c->counters + C_MULTI, s), "K_Phi");
   LAUNCH(c, launch_small_spd_inverse(Ns, nullptr, small + SM_KPHI, small + SM_KPHI_INV,
                                      c->ints + I_STATUS, s), "K_Phi inverse");
   // r_1 = u_last; r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}  (Eq. 18-20, 26)
-  LAUNCH(c, launch_copy(n, u_last, c->R, s), "r1");
+  LAUNCH(c, launch_vconvert(n, V_F64, u_last, v, c->R, s), "r1");
   for (int i = 1; i < m; ++i) {
-    if ((st = apply_op(c, TO_OP_DK, TO_PREC_NATIVE, c->R + (size_t)(i - 1) * n, c->t)) != TO_OK)
-      return st;
-    LAUNCH(c, launch_multidot(n, c->Phi, Ns, nullptr, c->t, 1, nullptr, small + SM_Z, Ns,
-                              c->partials, c->counters + C_MULTI, c->mixed, s), "Phi^T t");
+    if ((st = apply_vec(c, TO_OP_DK, c->R + (size_t)(i - 1) * n, c->t)) != TO_OK) return st;
+    LAUNCH(c, launch_gram(n, v, c->Phi, Ns, nullptr, c->t, 1, nullptr, small + SM_Z, Ns,
+                          c->partials, c->counters + C_MULTI, s), "Phi^T t");
     LAUNCH(c, launch_small_matvec(Ns, nullptr, small + SM_KPHI_INV, small + SM_Z, small + SM_W,
                                   -1.0, s), "K_Phi^-1 z");
-    LAUNCH(c, launch_combine(n, c->Phi, Ns, nullptr, small + SM_W, 1.0, 0.0,
-                             c->R + (size_t)i * n, nullptr, nullptr, c->partials,
-                             c->counters + C_UPD, c->mixed, s), "r_i");
+    LAUNCH(c, launch_combine(n, v, c->Phi, Ns, nullptr, small + SM_W, 1.0, 0.0,
+                             c->R + (size_t)i * n, v, nullptr, nullptr, c->partials,
+                             c->counters + C_UPD, s), "r_i");
   }
   // modified Gram-Schmidt with re-orthogonalisation, in place
   CUDA_TRY(c, cudaMemsetAsync(c->ints + I_KCOUNT, 0, sizeof(int), s), "reset k");
   for (int i = 0; i < m; ++i) {
     double* ri = c->R + (size_t)i * n;
-    LAUNCH(c, launch_dot(n, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM0, s), "|r|");
+    const int bound = std::max(i, 1);   // accepted columns so far <= i
+    LAUNCH(c, launch_vdot(n, v, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM0, s),
+           "|r|");
     for (int pass = 0; pass < 2; ++pass) {
-      LAUNCH(c, launch_multidot(n, c->R, std::max(i, 1), c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
-                                MAXB, c->partials, c->counters + C_MULTI, c->mixed, s), "GS dots");
-      LAUNCH(c, launch_combine(n, c->R, std::max(i, 1), c->ints + I_KCOUNT, small + SM_H, -1.0, 1.0, ri,
-                               nullptr, nullptr, c->partials, c->counters + C_UPD, c->mixed, s), "GS axpy");
+      LAUNCH(c, launch_gram(n, v, c->R, bound, c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
+                            MAXB, c->partials, c->counters + C_MULTI, s), "GS dots");
+      LAUNCH(c, launch_combine(n, v, c->R, bound, c->ints + I_KCOUNT, small + SM_H, -1.0, 1.0,
+                               ri, v, nullptr, nullptr, c->partials, c->counters + C_UPD, s),
+             "GS axpy");
     }
-    LAUNCH(c, launch_dot(n, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM1, s), "|r|");
-    LAUNCH(c, launch_gs_accept(n, c->R, i, c->scal, S_NRM0, S_NRM1, 1e-10, c->ints, s),
+    LAUNCH(c, launch_vdot(n, v, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM1, s),
+           "|r|");
+    LAUNCH(c, launch_gs_accept(n, v, c->R, i, c->scal, S_NRM0, S_NRM1, 1e-10, c->ints, s),
            "GS accept");
   }
   int k = 0;
@@ -1089,23 +1141,24 @@ to_status to_carm_solve(to_ctx* c, double* u, double* eps, double* eps_dev) {
   const int k = c->carm_built;
   to_status st;
   double* small = c->small;
+  const int v = vt(c);
+  const double* fv = c->mixed ? c->fd : c->f;
   // K R~ enters the reduced matrix and the residual check, so it always uses
-  // the float64 operator; the basis itself may be built in float32.
+  // the float64-accurate operator; the basis itself may be built in float32.
   for (int j = 0; j < k; ++j)
-    if ((st = run_op(c, fine_args(c, TO_OP_K, accurate_tc(c), T_F64, T_F64, c->R + (size_t)j * n,
-                                  c->Q + (size_t)j * n, nullptr, nullptr, EPI_APPLY),
-                     "K R")) != TO_OK)
+    if ((st = apply_accurate_vec(c, TO_OP_K, c->R + (size_t)j * n, c->Q + (size_t)j * n,
+                                 EPI_APPLY)) != TO_OK)
       return st;
-  LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->Q, k, nullptr, small + SM_KR, k, c->partials,
-                            c->counters + C_MULTI, c->mixed, s), "K_R");
-  LAUNCH(c, launch_multidot(n, c->R, k, nullptr, c->f, 1, nullptr, small + SM_FR, k, c->partials,
-                            c->counters + C_MULTI, c->mixed, s), "f_R");
+  LAUNCH(c, launch_gram(n, v, c->R, k, nullptr, c->Q, k, nullptr, small + SM_KR, k, c->partials,
+                        c->counters + C_MULTI, s), "K_R");
+  LAUNCH(c, launch_gram(n, v, c->R, k, nullptr, fv, 1, nullptr, small + SM_FR, k, c->partials,
+                        c->counters + C_MULTI, s), "f_R");
   LAUNCH(c, launch_small_chol_solve(k, nullptr, small + SM_KR, small + SM_FR, small + SM_Y,
                                     c->ints + I_STATUS, s), "K_R y = f_R");
-  LAUNCH(c, launch_combine(n, c->R, k, nullptr, small + SM_Y, 1.0, 0.0, u, nullptr, nullptr,
-                           c->partials, c->counters + C_UPD, c->mixed, s), "u = R y");
-  LAUNCH(c, launch_combine(n, c->Q, k, nullptr, small + SM_Y, 1.0, 0.0, c->t, c->f,
-                           c->scal + S_RR, c->partials, c->counters + C_UPD, c->mixed, s), "K R y - f");
+  LAUNCH(c, launch_combine(n, v, c->R, k, nullptr, small + SM_Y, 1.0, 0.0, u, V_F64, nullptr,
+                           nullptr, c->partials, c->counters + C_UPD, s), "u = R y");
+  LAUNCH(c, launch_combine(n, v, c->Q, k, nullptr, small + SM_Y, 1.0, 0.0, c->t, v, fv,
+                           c->scal + S_RR, c->partials, c->counters + C_UPD, s), "K R y - f");
   LAUNCH(c, launch_eps(c->scal, S_RR, S_FNORM2, c->scal + S_EPS, s), "eps");
   if (eps_dev)
     CUDA_TRY(c, cudaMemcpyAsync(eps_dev, c->scal + S_EPS, 8, cudaMemcpyDeviceToDevice, s), "eps");

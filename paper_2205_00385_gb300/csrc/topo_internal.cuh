@@ -235,6 +235,10 @@ struct to_ctx {
   double *E64, *Eprev64, *dE64, *rho_phys;
   float *E32, *Eprev32, *dE32;
   double *f, *invHs, *oc_a;   // invHs: 1 / row sums of the filter weights
+  // f as double-float pairs (mixed path; the long float64-accurate vectors
+  // r, p, Phi, KPhi, R, Q, t and the CG iterate are held as pairs there)
+  double* fd;
+  double* w64;   // float64 scratch of the mixed path without a double-float operator (2D)
   double *oc_lo, *oc_hi;      // OC move-limit bounds of the current update
   // CG
   double *r, *z, *p, *q;
