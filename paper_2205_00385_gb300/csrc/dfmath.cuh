@@ -71,6 +71,27 @@ __device__ __forceinline__ double f2d(float f) {
 // a * b + c
 __device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }
 
+// Dot-product accumulation acc += a * b in the manner of Ogita, Rump and
+// Oishi's Dot2: the leading product is formed exactly (FMA TwoProduct) and
+// added to acc.h with TwoSum; all error terms collect in acc.l without
+// renormalisation (as accurate as a dot product in twice the working
+// precision).  Normalise with df_norm before using acc as a pair.
+__device__ __forceinline__ void df_dot_acc(dfl& acc, dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = acc.h + p;
+  const float bb = s - acc.h;
+  const float t = (acc.h - (s - bb)) + (p - bb);
+  acc.h = s;
+  acc.l += t + e;
+}
+__device__ __forceinline__ dfl df_norm(dfl a) {
+  const float h = a.h + a.l;
+  return {h, a.l - (h - a.h)};
+}
+
 // (hi + lo) rounded to float64: the halves widen exactly, one float64 add
 __device__ __forceinline__ double df_to_d(dfl a) { return f2d(a.h) + f2d(a.l); }
 

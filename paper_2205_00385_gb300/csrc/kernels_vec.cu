@@ -31,6 +31,9 @@ struct Ar<double> {
   __device__ static T mulf(T a, float b) { return a * (double)b; }
   __device__ static double to_d(T a) { return a; }
   __device__ static T shfl_down(T a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+  // dot-product accumulation (acc += a b) and its final normalisation
+  __device__ static void dacc(T& acc, T a, T b) { acc = fma(a, b, acc); }
+  __device__ static T dfin(T a) { return a; }
 };
 template <>
 struct Ar<float2> {
@@ -56,6 +59,8 @@ struct Ar<float2> {
   __device__ static T shfl_down(T a, int o) {
     return {__shfl_down_sync(0xffffffffu, a.h, o), __shfl_down_sync(0xffffffffu, a.l, o)};
   }
+  __device__ static void dacc(T& acc, T a, T b) { df_dot_acc(acc, a, b); }
+  __device__ static T dfin(T a) { return df_norm(a); }
 };
 
 // store a register value into a (possibly different) storage type
@@ -118,8 +123,8 @@ __global__ void __launch_bounds__(RED_THREADS)
   using A = Ar<S>;
   __shared__ double sh[32];
   typename A::T v = A::zero();
-  GRID_LOOP(k, n) v = A::fma3(A::ld(a, k), A::ld(b, k), v);
-  reduce_to<S>(v, out, partials, counter, sh);
+  GRID_LOOP(k, n) A::dacc(v, A::ld(a, k), A::ld(b, k));
+  reduce_to<S>(A::dfin(v), out, partials, counter, sh);
 }
 
 __global__ void __launch_bounds__(256) k_split(long long n, const double* __restrict__ in,
@@ -165,6 +170,13 @@ __global__ void __launch_bounds__(256) k_vscale_inv_sqrt(long long n, S* __restr
 // ---------------------------------------------------------------------------
 constexpr int MD_CH = 128;   // indices per chunk = threads per block
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+
 template <typename S>
 __global__ void __launch_bounds__(MD_CH)
     k_gram(long long n, const S* __restrict__ A, int na, const int* na_dev,
@@ -172,7 +184,9 @@ __global__ void __launch_bounds__(MD_CH)
            double* partials, unsigned* counter) {
   using Rg = Ar<S>;
   using V = typename Rg::T;
-  __shared__ V sv[2 * MAXB * MD_CH];
+  static_assert(sizeof(V) == sizeof(S), "staged values keep the storage layout");
+  extern __shared__ unsigned char md_smem[];
+  V* sv = reinterpret_cast<V*>(md_smem);   // [2][nv][MD_CH]
   __shared__ bool s_last;
   const int ma = na_dev ? min(max(*na_dev, 0), na) : na;
   const int mb = nb_dev ? min(max(*nb_dev, 0), nb) : nb;
@@ -189,34 +203,52 @@ __global__ void __launch_bounds__(MD_CH)
   for (int p = 0; p < 2; ++p)
 #pragma unroll
     for (int q = 0; q < 2; ++q) acc[p][q] = Rg::zero();
-  for (long long k0 = (long long)blockIdx.x * MD_CH; k0 < n; k0 += (long long)gridDim.x * MD_CH) {
+  const long long cstride = (long long)gridDim.x * MD_CH;
+  // chunk k0 -> stage buffer st: thread t copies index k0 + t of every column
+  auto issue = [&](long long k0, int st) {
     const long long k = k0 + t;
+    const bool ok = k < n;
     for (int v = 0; v < nv; ++v) {
       const S* col = v < ma ? A + (size_t)v * n : B + (size_t)(v - ma) * n;
-      sv[v * MD_CH + t] = k < n ? Rg::ld(col, k) : Rg::zero();
+      cp_async8(sv + ((size_t)st * nv + v) * MD_CH + t, ok ? col + k : col, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  long long k0 = (long long)blockIdx.x * MD_CH;
+  int st = 0;
+  if (k0 < n) issue(k0, 0);
+  for (; k0 < n; k0 += cstride) {
+    if (k0 + cstride < n) {
+      issue(k0 + cstride, st ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     __syncthreads();
     if (active) {
-      const V* a0 = sv + i0 * MD_CH;
-      const V* a1 = sv + (i0 + 1 < ma ? i0 + 1 : i0) * MD_CH;
-      const V* b0 = sv + (ma + j0) * MD_CH;
-      const V* b1 = sv + (ma + (j0 + 1 < mb ? j0 + 1 : j0)) * MD_CH;
+      const V* base = sv + (size_t)st * nv * MD_CH;
+      const V* a0 = base + i0 * MD_CH;
+      const V* a1 = base + (i0 + 1 < ma ? i0 + 1 : i0) * MD_CH;
+      const V* b0 = base + (ma + j0) * MD_CH;
+      const V* b1 = base + (ma + (j0 + 1 < mb ? j0 + 1 : j0)) * MD_CH;
       for (int idx = sub; idx < MD_CH; idx += S_) {
         const V x0 = a0[idx], x1 = a1[idx], y0 = b0[idx], y1 = b1[idx];
-        acc[0][0] = Rg::fma3(x0, y0, acc[0][0]);
-        acc[1][0] = Rg::fma3(x1, y0, acc[1][0]);
-        acc[0][1] = Rg::fma3(x0, y1, acc[0][1]);
-        acc[1][1] = Rg::fma3(x1, y1, acc[1][1]);
+        Rg::dacc(acc[0][0], x0, y0);
+        Rg::dacc(acc[1][0], x1, y0);
+        Rg::dacc(acc[0][1], x0, y1);
+        Rg::dacc(acc[1][1], x1, y1);
       }
     }
     __syncthreads();
+    st ^= 1;
   }
-  double* red = reinterpret_cast<double*>(sv);   // ntile * 4 * S_ <= 4 * MD_CH doubles
+  double* red = reinterpret_cast<double*>(md_smem);   // ntile * 4 * S_ <= 4 * MD_CH doubles
   if (active) {
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int q = 0; q < 2; ++q) red[(tile * 4 + p + 2 * q) * S_ + sub] = Rg::to_d(acc[p][q]);
+      for (int q = 0; q < 2; ++q)
+        red[(tile * 4 + p + 2 * q) * S_ + sub] = Rg::to_d(Rg::dfin(acc[p][q]));
   }
   __syncthreads();
   const int np = ma * mb;
@@ -261,14 +293,19 @@ __global__ void __launch_bounds__(32 * MAXB)
     const S* col = A + (size_t)wi * n;
     const long long stride = (long long)gridDim.x * 32;
     long long k = (long long)blockIdx.x * 32 + lane;
-    for (; k + stride < n; k += 2 * stride) {
+    V acc3 = Rg::zero(), acc4 = Rg::zero();
+    for (; k + 3 * stride < n; k += 4 * stride) {
       const V a0 = Rg::ld(col, k), b0 = Rg::ld(b, k);
       const V a1 = Rg::ld(col, k + stride), b1 = Rg::ld(b, k + stride);
-      acc = Rg::fma3(a0, b0, acc);
-      acc2 = Rg::fma3(a1, b1, acc2);
+      const V a2 = Rg::ld(col, k + 2 * stride), b2 = Rg::ld(b, k + 2 * stride);
+      const V a3 = Rg::ld(col, k + 3 * stride), b3 = Rg::ld(b, k + 3 * stride);
+      Rg::dacc(acc, a0, b0);
+      Rg::dacc(acc2, a1, b1);
+      Rg::dacc(acc3, a2, b2);
+      Rg::dacc(acc4, a3, b3);
     }
-    if (k < n) acc = Rg::fma3(Rg::ld(col, k), Rg::ld(b, k), acc);
-    acc = Rg::add(acc, acc2);
+    for (; k < n; k += stride) Rg::dacc(acc, Rg::ld(col, k), Rg::ld(b, k));
+    acc = Rg::add(Rg::add(Rg::dfin(acc), Rg::dfin(acc2)), Rg::add(Rg::dfin(acc3), Rg::dfin(acc4)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc = Rg::add(acc, Rg::shfl_down(acc, o));
   }
@@ -295,40 +332,64 @@ __global__ void __launch_bounds__(32 * MAXB)
 // y = beta*y + sign*sum_i c[i] A[:, i] (i < m <= MMAX); optional
 // |y - w|^2 -> *rr.  A, w (and y when SY = S) in storage S; y may be
 // float64 when S is the pair format (one float64 add per stored value).
+// The coefficients sit in shared memory; each thread keeps two indices in
+// flight so that enough loads are outstanding to cover DRAM latency.
 template <typename S, typename SY, int MMAX>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, 4)
     k_combine(long long n, const S* __restrict__ A, int m, const int* m_dev,
               const double* __restrict__ c, double sign, double beta, SY* __restrict__ y,
               const S* __restrict__ w, double* rr, double* partials, unsigned* counter) {
   using Rg = Ar<S>;
   using V = typename Rg::T;
   __shared__ double sh[32];
+  __shared__ V scc[MMAX];
   const int mm = m_dev ? min(max(*m_dev, 0), m) : m;
-  V cc[MMAX];
-#pragma unroll
-  for (int i = 0; i < MMAX; ++i) {
-    const double ci = i < mm ? c[i] : 0.0;
-    cc[i] = Rg::from_d(sign == 1.0 ? ci : sign == -1.0 ? -ci : sign * ci);
+  if (threadIdx.x < MMAX) {
+    const double ci = (int)threadIdx.x < mm ? c[threadIdx.x] : 0.0;
+    scc[threadIdx.x] = Rg::from_d(sign == 1.0 ? ci : sign == -1.0 ? -ci : sign * ci);
   }
+  __syncthreads();
   const V bb = Rg::from_d(beta);
+  auto start = [&](long long k) -> V {
+    if (beta == 0.0) return Rg::zero();
+    V yk;
+    if constexpr (std::is_same<SY, S>::value) yk = Rg::ld(y, k);
+    else yk = Rg::from_d((double)y[k]);
+    return (beta == 1.0) ? yk : Rg::fma3(bb, yk, Rg::zero());
+  };
+  auto resid = [&](V s, long long k, V& acc) {
+    V d = s;
+    if (w) d = Rg::add(s, Rg::fma3(Rg::ld(w, k), Rg::from_d(-1.0), Rg::zero()));
+    acc = Rg::fma3(d, d, acc);
+  };
   V v = Rg::zero();
-  GRID_LOOP(k, n) {
-    V s = Rg::zero();
-    if (beta != 0.0) {
-      V yk;
-      if constexpr (std::is_same<SY, S>::value) yk = Rg::ld(y, k);
-      else yk = Rg::from_d((double)y[k]);
-      s = (beta == 1.0) ? yk : Rg::fma3(bb, yk, Rg::zero());
-    }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + stride < n; k += 2 * stride) {
+    const long long k1 = k + stride;
+    V s0 = start(k), s1 = start(k1);
 #pragma unroll
     for (int i = 0; i < MMAX; ++i)
-      if (i < mm) s = Rg::fma3(cc[i], Rg::ld(A + (size_t)i * n, k), s);
-    st_any(y, k, s);
+      if (i < mm) {
+        const V ci = scc[i];
+        const S* col = A + (size_t)i * n;
+        s0 = Rg::fma3(ci, Rg::ld(col, k), s0);
+        s1 = Rg::fma3(ci, Rg::ld(col, k1), s1);
+      }
+    st_any(y, k, s0);
+    st_any(y, k1, s1);
     if (rr) {
-      V d = s;
-      if (w) d = Rg::add(s, Rg::fma3(Rg::ld(w, k), Rg::from_d(-1.0), Rg::zero()));
-      v = Rg::fma3(d, d, v);
+      resid(s0, k, v);
+      resid(s1, k1, v);
     }
+  }
+  if (k < n) {
+    V s0 = start(k);
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i)
+      if (i < mm) s0 = Rg::fma3(scc[i], Rg::ld(A + (size_t)i * n, k), s0);
+    st_any(y, k, s0);
+    if (rr) resid(s0, k, v);
   }
   if (!rr) return;
   reduce_to<S>(v, rr, partials, counter, sh);
@@ -475,12 +536,18 @@ template <typename S>
 static void gram_t(long long n, const void* A, int na, const int* na_dev, const void* B, int nb,
                    const int* nb_dev, double* G, int ldg, double* partials, unsigned* counter,
                    cudaStream_t s) {
+  static bool smem_set = false;   // up to 2 stages x 2*MAXB columns x MD_CH values
+  if (!smem_set) {
+    cudaFuncSetAttribute(k_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * 2 * MAXB * MD_CH * sizeof(S)));
+    smem_set = true;
+  }
   if (nb == 1 && nb_dev == nullptr)
     k_gram_col<S><<<RED_BLOCKS, 32 * na, 0, s>>>(n, (const S*)A, na, na_dev, (const S*)B, G,
                                                  partials, counter);
   else
-    k_gram<S><<<RED_BLOCKS, MD_CH, 0, s>>>(n, (const S*)A, na, na_dev, (const S*)B, nb, nb_dev,
-                                           G, ldg, partials, counter);
+    k_gram<S><<<RED_BLOCKS, MD_CH, (size_t)2 * (na + nb) * MD_CH * sizeof(S), s>>>(
+        n, (const S*)A, na, na_dev, (const S*)B, nb, nb_dev, G, ldg, partials, counter);
 }
 
 cudaError_t launch_gram(long long n, int vt, const void* A, int na, const int* na_dev,
