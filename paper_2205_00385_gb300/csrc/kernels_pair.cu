@@ -35,16 +35,10 @@ struct WhtPair {
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b = fma(b, -1, a), rounded once: the packed FMA keeps the operands in
+// register pairs chosen by the compiler (no packed subtract intrinsic)
 __device__ __forceinline__ float2 psub(float2 a, float2 b) {
-  float2 r;
-  asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
-      "mov.b64 pa, {%2, %3};\n\t"
-      "mov.b64 pb, {%4, %5};\n\t"
-      "sub.rn.f32x2 pr, pa, pb;\n\t"
-      "mov.b64 {%0, %1}, pr;\n\t}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return r;
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
 // 4-point Walsh-Hadamard transform over the corners q = bx + 2 by of a face
@@ -123,7 +117,8 @@ struct PairArgs {
 // rows of FROW floats (odd, so the two half-warps' rows hit disjoint banks)
 constexpr int FNX = 2 * PX + 1, FNY = PY + 1, FROW = 3 * FNX, FTILE = FROW * FNY;
 constexpr int NSTAGE = 4;                                   // faces in flight
-constexpr int FCOPY = (FTILE + PX * PY - 1) / (PX * PY);    // 4-byte copies per thread
+static_assert((NSTAGE & (NSTAGE - 1)) == 0, "stage index uses a mask");
+static_assert(PX * PY == 128 && FNY <= 12 && FROW <= 128, "face copy: 4 warps x 3 rows x 4 lanes");
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -152,39 +147,47 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
   const bool eA = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
   const bool eB = i + 1 >= 0 && i + 1 < g.nx && j >= 0 && j < g.ny;
 
-  // copies of this thread: tile floats f = tid + k * blockDim, f = row * FROW + col
-  int coff[FCOPY];
-  unsigned cvalid = 0u;
+  // Face copies: warp w copies tile rows w, w + 4, w + 8; lane l copies the
+  // row's floats l + 32 j (j < 4).  Out-of-range nodes are zero-filled (copy
+  // size 0) from a clamped, in-range address.
+  const int lane = tid & 31, warp = tid >> 5;
+  int xoff[4];             // float offset of (lane, j) within a row of node x = 0
+  unsigned xok = 0u;       // bit j: column l + 32 j holds an in-range node
+  {
+    const int xc = min(max(X0 - 1, 0), g.nnx - 1);
 #pragma unroll
-  for (int k = 0; k < FCOPY; ++k) {
-    const int f = tid + k * PX * PY;
-    const int row = f / FROW, col = f % FROW;
-    const int ni = X0 - 1 + col / 3, nj = Y0 - 1 + row;
-    const bool ok = f < FTILE && ni >= 0 && ni < g.nnx && nj >= 0 && nj < g.nny;
-    cvalid |= (ok ? 1u : 0u) << k;
-    coff[k] = ok ? 3 * (ni + g.nnx * nj) + col % 3 : 0;
+    for (int j = 0; j < 4; ++j) {
+      const int col = lane + 32 * j;
+      const int ni = X0 - 1 + col / 3;
+      const bool ok = col < FROW && ni >= 0 && ni < g.nnx;
+      xok |= (ok ? 1u : 0u) << j;
+      xoff[j] = ok ? 3 * (X0 - 1) + col : 3 * xc;
+    }
   }
   const int fbase = z0 - 1;   // face index of stage 0
   auto issue_face = [&](int kz) {
+    const int slot = (kz - fbase) & (NSTAGE - 1);
     if (kz >= 0 && kz < g.nnz && kz <= z1) {
-      float* dst = sm.face[(kz - fbase) % NSTAGE];
+      float* dst = sm.face[slot];
       const float* src = a.x + 3 * plane * kz;
 #pragma unroll
-      for (int k = 0; k < FCOPY; ++k) {
-        const int f = tid + k * PX * PY;
-        if (f < FTILE) {
-          const bool ok = (cvalid >> k) & 1u;
-          cp_async4(dst + f, ok ? src + coff[k] : a.x, ok);
+      for (int rr = 0; rr < 3; ++rr) {
+        const int row = warp + 4 * rr;
+        if (row < FNY) {
+          const int nj = Y0 - 1 + row;
+          const bool rok = nj >= 0 && nj < g.nny;
+          const float* rsrc = src + 3LL * g.nnx * min(max(nj, 0), g.nny - 1);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (lane + 32 * j < FROW)
+              cp_async4(dst + row * FROW + lane + 32 * j, rsrc + xoff[j],
+                        rok && ((xok >> j) & 1u));
         }
       }
     } else if (kz >= z0 - 1 && kz <= z1) {
       // face outside the grid: zeros
-      float* dst = sm.face[(kz - fbase) % NSTAGE];
-#pragma unroll
-      for (int k = 0; k < FCOPY; ++k) {
-        const int f = tid + k * PX * PY;
-        if (f < FTILE) dst[f] = 0.f;
-      }
+      float* dst = sm.face[slot];
+      for (int f = tid; f < FTILE; f += PX * PY) dst[f] = 0.f;
     }
     cp_commit();
   };
@@ -204,7 +207,7 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
   };
   // face -> xy-Walsh coefficients of the pair, per component
   auto face_wht = [&](int kz, unsigned fm, float2 (&W)[3][4]) {
-    const float* fs = sm.face[(kz - fbase) % NSTAGE] + ty * FROW + 6 * tx;
+    const float* fs = sm.face[(kz - fbase) & (NSTAGE - 1)] + ty * FROW + 6 * tx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float v[2][3];
