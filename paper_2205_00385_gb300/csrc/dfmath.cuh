@@ -95,6 +95,38 @@ __device__ __forceinline__ dfl df_norm(dfl a) {
 // (hi + lo) rounded to float64: the halves widen exactly, one float64 add
 __device__ __forceinline__ double df_to_d(dfl a) { return f2d(a.h) + f2d(a.l); }
 
+// Block sum of NV double-float values: warps reduce in double-float, lane 0
+// widens once, warp 0 adds the warp results in float64 in warp order.  The
+// result is valid in thread 0.  sh holds at least NV*32 doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum_df(dfl (&v)[NV], double (&out)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    dfl x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const dfl y = {__shfl_down_sync(0xffffffffu, x.h, o), __shfl_down_sync(0xffffffffu, x.l, o)};
+      x = df_add(x, y);
+    }
+    if (lane == 0) sh[q * 32 + warp] = df_to_d(x);
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = lane < nw ? sh[q * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      out[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// a > b for normalised pairs
+__device__ __forceinline__ bool df_gt(dfl a, dfl b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+
 // storage access for float64-accurate values held as float64 or as pairs
 __device__ __forceinline__ dfl ld_df(const double* p, long long i) { return split_d(p[i]); }
 __device__ __forceinline__ dfl ld_df(const float2* p, long long i) {

@@ -185,6 +185,15 @@ cudaError_t launch_oc_prep_b(long long nel, const double* rho, const double* dc,
 cudaError_t launch_oc_step_b(long long nel, const double* a, const double* lo, const double* hi,
                              const double* dv, double target, double* scal, double* partials,
                              unsigned* counter, cudaStream_t s);
+// lambda search of the OC update: the candidate factors a = rho sqrt(-dc/dv)
+// (float64 copy a64 for the final update) and the move limits and dv as
+// double-float pairs; one launch narrows [l1, l2] eight-fold in double-float
+cudaError_t launch_oc_prep_d(long long nel, const double* rho, const double* dc,
+                             const double* dv, double move, double* a64, void* a2, void* lo2,
+                             void* hi2, void* dv2, double* scal, cudaStream_t s);
+cudaError_t launch_oc_section(long long nel, const void* a2, const void* lo2, const void* hi2,
+                              const void* dv2, double target, double* scal, double* partials,
+                              unsigned* counter, cudaStream_t s);
 cudaError_t launch_oc_final(long long nel, double* rho, const double* a, double move,
                             double* scal, double* change_dev, double* partials,
                             unsigned* counter, cudaStream_t s);

@@ -4,6 +4,7 @@
 // multiplier.  All float64.
 #include <math.h>
 
+#include "dfmath.cuh"
 #include "kernels.h"
 
 namespace topo {
@@ -267,6 +268,90 @@ __global__ void __launch_bounds__(RED_THREADS)
   }
 }
 
+// Context path of the mixed and float64 solvers alike: the lambda search
+// runs as an OC_SPLIT-way section per pass in double-float on the FP32 pipe
+// (the volume at OC_SPLIT - 1 interior points of [l1, l2] is summed for
+// every element in one sweep, and the sub-interval holding the root is
+// kept), 3 bits of bracket per sweep against 1 for a float64 bisection
+// step.  It stops at the same relative bracket of 1e-13.
+constexpr int OC_SPLIT = 8;
+
+__global__ void __launch_bounds__(256)
+    k_oc_prep_d(long long nel, const double* __restrict__ rho, const double* __restrict__ dc,
+                const double* __restrict__ dv, double move, double* __restrict__ a64,
+                float2* __restrict__ a, float2* __restrict__ lo, float2* __restrict__ hi,
+                float2* __restrict__ dvd, double* scal) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) {
+    scal[S_OC_L1] = 0.0;
+    scal[S_OC_L2] = 1e9;
+  }
+  if (e >= nel) return;
+  const double r = rho[e];
+  const double ae = r * sqrt(fmax(0.0, -dc[e] / dv[e]));
+  a64[e] = ae;
+  const dfl av = split_d(ae);
+  const dfl lv = split_d(fmax(0.0, r - move)), hv = split_d(fmin(1.0, r + move));
+  const dfl dd = split_d(dv[e]);
+  a[e] = make_float2(av.h, av.l);
+  lo[e] = make_float2(lv.h, lv.l);
+  hi[e] = make_float2(hv.h, hv.l);
+  dvd[e] = make_float2(dd.h, dd.l);
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_oc_section(long long nel, const float2* __restrict__ a, const float2* __restrict__ lo,
+                 const float2* __restrict__ hi, const float2* __restrict__ dvd, double target,
+                 double* scal, double* partials, unsigned* counter) {
+  constexpr int NP = OC_SPLIT - 1;
+  __shared__ double sh[NP * 32];
+  __shared__ dfl s_s[NP];
+  const double l1 = scal[S_OC_L1], l2 = scal[S_OC_L2];
+  if (!((l2 - l1) > 1e-13 * (l1 + l2))) return;
+  if (threadIdx.x < NP) {
+    const double lam = l1 + (double)(threadIdx.x + 1) * ((l2 - l1) / OC_SPLIT);
+    s_s[threadIdx.x] = split_d(1.0 / sqrt(lam));
+  }
+  __syncthreads();
+  dfl sv[NP], v[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    sv[j] = s_s[j];
+    v[j] = {0.f, 0.f};
+  }
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nel;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float2 a2 = a[e], l2v = lo[e], h2 = hi[e], d2 = dvd[e];
+    const dfl av = {a2.x, a2.y}, lv = {l2v.x, l2v.y}, hv = {h2.x, h2.y}, dd = {d2.x, d2.y};
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      dfl x = df_mul(av, sv[j]);
+      x = df_gt(x, hv) ? hv : (df_gt(lv, x) ? lv : x);
+      df_dot_acc(v[j], dd, x);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j) v[j] = df_norm(v[j]);
+  double o1[NP];
+  block_sum_df<NP>(v, o1, sh);
+  if (publish_partials<NP>(o1, partials, counter)) {
+    double o[NP];
+    finish_sum<NP>(partials, counter, o, sh);
+    if (threadIdx.x == 0) {
+      // the volume decreases with lambda: keep the last point above target
+      // and the first at or below it
+      int k = 0;
+      while (k < NP && o[k] > target) ++k;
+      const double w = (l2 - l1) / OC_SPLIT;
+      const double nl1 = k > 0 ? l1 + k * w : l1;
+      const double nl2 = k < NP ? l1 + (k + 1) * w : l2;
+      scal[S_OC_L1] = nl1;
+      scal[S_OC_L2] = nl2;
+      scal[S_OC_VOL] = k > 0 ? o[k - 1] : o[0];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
     k_oc_final(long long nel, double* __restrict__ rho, const double* __restrict__ a,
                double move, double* scal, double* change_dev, double* partials,
@@ -378,6 +463,23 @@ cudaError_t launch_oc_step_b(long long nel, const double* a, const double* lo, c
                              unsigned* counter, cudaStream_t s) {
   k_oc_step_b<<<RED_BLOCKS, RED_THREADS, 0, s>>>(nel, a, lo, hi, dv, target, scal, partials,
                                                  counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oc_prep_d(long long nel, const double* rho, const double* dc,
+                             const double* dv, double move, double* a64, void* a2, void* lo2,
+                             void* hi2, void* dv2, double* scal, cudaStream_t s) {
+  k_oc_prep_d<<<nblocks(nel, 256), 256, 0, s>>>(nel, rho, dc, dv, move, a64, (float2*)a2,
+                                                (float2*)lo2, (float2*)hi2, (float2*)dv2, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oc_section(long long nel, const void* a2, const void* lo2, const void* hi2,
+                              const void* dv2, double target, double* scal, double* partials,
+                              unsigned* counter, cudaStream_t s) {
+  k_oc_section<<<RED_BLOCKS, RED_THREADS, 0, s>>>(nel, (const float2*)a2, (const float2*)lo2,
+                                                  (const float2*)hi2, (const float2*)dv2, target,
+                                                  scal, partials, counter);
   return cudaGetLastError();
 }
 

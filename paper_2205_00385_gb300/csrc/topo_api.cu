@@ -300,6 +300,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   double *E64 = cv.take<double>(nel), *Ep64 = cv.take<double>(nel), *dE64 = cv.take<double>(nel);
   double *rho = cv.take<double>(nel), *invHs = cv.take<double>(nel), *oca = cv.take<double>(nel);
   double *oclo = cv.take<double>(nel), *ochi = cv.take<double>(nel);
+  double *oca2 = cv.take<double>(nel), *ocdv2 = cv.take<double>(nel);
   float *E32 = cv.take<float>(nel), *Ep32 = cv.take<float>(nel), *dE32 = cv.take<float>(nel);
   double* f = cv.take<double>(n);
   double* fd = cv.take<double>(n);
@@ -344,7 +345,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   void* Ai = cv.take<char>((size_t)nc * nc * ts);
   if (c) {
     c->E64 = E64; c->Eprev64 = Ep64; c->dE64 = dE64; c->rho_phys = rho; c->invHs = invHs; c->oc_a = oca;
-    c->oc_lo = oclo; c->oc_hi = ochi;
+    c->oc_lo = oclo; c->oc_hi = ochi; c->oc_a2 = oca2; c->oc_dv2 = ocdv2;
     c->E32 = E32; c->Eprev32 = Ep32; c->dE32 = dE32; c->f = f; c->fd = fd; c->w64 = w64;
     c->r = r; c->z = z; c->p = p; c->q = q; c->p32 = p32; c->q32 = q32;
     c->Phi = Phi; c->KPhi = KPhi; c->R = R; c->Q = Q; c->t = t;
@@ -1195,13 +1196,14 @@ to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_
   cudaStream_t s = c->stream;
   const long long nel = c->nel;
   const double target = volfrac * (double)nel;
-  LAUNCH(c, launch_oc_prep_b(nel, rho, dc_f, dv_f, move, c->oc_a, c->oc_lo, c->oc_hi, c->scal, s),
-         "oc prep");
-  // bisection steps run on the device; a step is a no-op once converged
-  for (int chunk = 0; chunk < 8; ++chunk) {
-    for (int q = 0; q < 32; ++q)
-      LAUNCH(c, launch_oc_step_b(nel, c->oc_a, c->oc_lo, c->oc_hi, dv_f, target, c->scal,
-                                 c->partials, c->counters + C_OC, s), "oc step");
+  LAUNCH(c, launch_oc_prep_d(nel, rho, dc_f, dv_f, move, c->oc_a, c->oc_a2, c->oc_lo, c->oc_hi,
+                             c->oc_dv2, c->scal, s), "oc prep");
+  // eight-way sections run on the device (3 bits of bracket each); a launch
+  // is a no-op once the bracket is within a relative 1e-13
+  for (int chunk = 0; chunk < 16; ++chunk) {
+    for (int q = 0; q < 8; ++q)
+      LAUNCH(c, launch_oc_section(nel, c->oc_a2, c->oc_lo, c->oc_hi, c->oc_dv2, target, c->scal,
+                                  c->partials, c->counters + C_OC, s), "oc section");
     double lr[2];
     CUDA_TRY(c, cudaMemcpyAsync(lr, c->scal + S_OC_L1, 16, cudaMemcpyDeviceToHost, s), "read");
     CUDA_TRY(c, cudaStreamSynchronize(s), "sync");

@@ -239,7 +239,8 @@ struct to_ctx {
   // r, p, Phi, KPhi, R, Q, t and the CG iterate are held as pairs there)
   double* fd;
   double* w64;   // float64 scratch of the mixed path without a double-float operator (2D)
-  double *oc_lo, *oc_hi;      // OC move-limit bounds of the current update
+  double *oc_lo, *oc_hi;      // OC move-limit bounds of the current update (pairs)
+  double *oc_a2, *oc_dv2;     // OC factors and dv as double-float pairs
   // CG
   double *r, *z, *p, *q;
   float *p32, *q32;     // float32 shadows of p and K p (mixed path)
