@@ -32,8 +32,15 @@ if ROOT not in sys.path:
 METRIC = "design iters/s at 5.4M DOFs"
 UNIT = "design_iters/s"
 WORKLOAD = ("3D cantilever 192x96x96 hex8 (5,447,811 DOFs), E0=1 Emin=1e-9 nu=0.3 p=3, "
-            "volfrac 0.12, rmin 2.0, 6-level MGCG (FP32 V-cycle/apply, FP64 CG, rtol 1e-8), "
+            "volfrac 0.12, rmin 2.0, 6-level MGCG ({prec}, rtol 1e-8), "
             "CARM s=10 (N_s=N_m=10, N_on=15, eps_tol 1e-3)")
+PREC_TEXT = {"mixed": "FP32 V-cycle/apply; CG vectors, dots, CARM and OC FP64-accurate in "
+                      "double-float on the FP32 pipe",
+             "fp64": "all float64"}
+
+
+def _workload(precision: str) -> str:
+    return WORKLOAD.format(prec=PREC_TEXT[precision])
 
 
 def _args():
@@ -318,9 +325,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": W, "ms_per_step": round(elapsed / K * 1e3, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if p.precision == "mixed"
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64" if p.precision == "mixed"
         else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if not args.small else "cantilever 48x24x24 (quick)",
+        "config": {"workload": _workload(p.precision) if not args.small else "cantilever 48x24x24 (quick)",
                    "precision": p.precision, "iterations_timed": f"{W + 1}..{W + K}",
                    "branches": {b: branches.count(b) for b in set(branches)},
                    "cg_iterations": cg, "final_compliance": C_final,
@@ -372,7 +379,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT,
             "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": round(tot / K * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
+            "dtype": "f64", "data": "synthetic", "config": {"workload": _workload(args.precision)},
             "cpu_baseline": cpu,
             "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
