@@ -337,12 +337,11 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
   cp_wait<0>();
 }
 
-#ifndef PAIR_MIN_BLOCKS
-#define PAIR_MIN_BLOCKS 3
-#endif
-
+// resident blocks per SM the register allocation targets: K p fits four
+// without spilling; the residual and smoother epilogues keep three
 template <int EPI>
-__global__ void __launch_bounds__(PX * PY, PAIR_MIN_BLOCKS) k_apply3_pair(PairArgs a, WhtPair kb) {
+__global__ void __launch_bounds__(PX * PY, EPI == EPI_APPLY ? 4 : 3)
+    k_apply3_pair(PairArgs a, WhtPair kb) {
   __shared__ PairSmem sm;
   const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
   const int i = blockIdx.x * POX - 1 + 2 * tx, j = blockIdx.y * POY - 1 + ty;
