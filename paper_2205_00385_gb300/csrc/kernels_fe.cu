@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int cj = 0; cj < DIM; ++cj) {
               const int col = DIM * bc + cj;
-              const TC kv = EXPL ? Kc[(size_t)e * ND * ND + row * ND + col] : ke.v[row * ND + col];
+              const TC kv = EXPL ? Kc[(size_t)e * tri_len(ND) + sym_idx(row, col, ND)]
+                                 : ke.v[row * ND + col];
               s = fma(kv, xn[sidx][cj], s);
             }
           }
@@ -234,60 +235,54 @@ __device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&
 // so all of an element's matrix is in flight at once); a node-centric gather
 // then sums the element rows belonging to each node in a fixed order.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__device__ __forceinline__ void load_row16(const T* __restrict__ p, T (&v)[N]) {
-  static_assert((N * sizeof(T)) % 16 == 0, "row must be a multiple of 16 bytes");
-  if constexpr (sizeof(T) == 4) {
-    const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-    for (int k = 0; k < N / 4; ++k) {
-      const float4 w = __ldg(q + k);
-      v[4 * k] = w.x;
-      v[4 * k + 1] = w.y;
-      v[4 * k + 2] = w.z;
-      v[4 * k + 3] = w.w;
-    }
-  } else {
-    const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-    for (int k = 0; k < N / 2; ++k) {
-      const double2 w = __ldg(q + k);
-      v[2 * k] = w.x;
-      v[2 * k + 1] = w.y;
-    }
-  }
-}
-
+// One warp per element: the element's packed upper triangle is staged in the
+// warp's slice of shared memory with 16-byte loads, then lane r forms row r
+// of K_e x_e reading K(r, c) symmetrically.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
     k_elem_gemv(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ Kc,
                 const T* __restrict__ x, T* __restrict__ eo) {
-  constexpr int ND = Geo<DIM>::ND;
-  const int lane = threadIdx.x & 31;
+  constexpr int ND = Geo<DIM>::ND, NT = tri_len(ND);
+  constexpr int VW = 16 / sizeof(T);                 // values per 16-byte load
+  static_assert((NT * sizeof(T)) % 16 == 0, "packed triangle must be a multiple of 16 bytes");
+  __shared__ __align__(16) T sk[8][NT];              // 8 warps per block
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  T* tk = sk[wib];
   for (long long e = warp; e < g.nel; e += nwarps) {
     const int ex = (int)(e % g.nx);
     const long long rest = e / g.nx;
     const int ey = (int)(rest % g.ny);
     const int ez = DIM == 3 ? (int)(rest / g.ny) : 0;
     T xv = T(0);
-    T row[ND];
     if (lane < ND) {
       const int a = lane / DIM, c = lane % DIM;
       const long long nd = (ex + (a & 1)) +
                            (long long)g.nnx * ((ey + ((a >> 1) & 1)) +
                                                (long long)g.nny * (DIM == 3 ? ez + ((a >> 2) & 1) : 0));
       xv = ((mask[nd] >> c) & 1u) ? T(0) : x[DIM * nd + c];
-      load_row16<T, ND>(Kc + (size_t)e * ND * ND + lane * ND, row);
     }
+    const T* src = Kc + (size_t)e * NT;
+    for (int q = lane; q < NT / VW; q += 32) {
+      if constexpr (sizeof(T) == 4)
+        reinterpret_cast<float4*>(tk)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
+      else
+        reinterpret_cast<double2*>(tk)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
+    }
+    __syncwarp();
+    // K(lane, c): tri_idx(c, lane) below the diagonal, whose step from c to
+    // c + 1 is ND - 1 - c, then consecutive entries of row lane
     T acc = T(0);
+    int idx = lane;
 #pragma unroll
     for (int c = 0; c < ND; ++c) {
       const T xc = __shfl_sync(0xffffffffu, xv, c);
-      if (lane < ND) acc = fma(row[c], xc, acc);
+      if (lane < ND) acc = fma(tk[idx], xc, acc);
+      idx += (c < lane) ? (ND - 1 - c) : 1;
     }
     if (lane < ND) eo[(size_t)e * ND + lane] = acc;
+    __syncwarp();
   }
 }
 
@@ -513,7 +508,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
           const int row = DIM * a + c;
-          d[c] += EXPL ? Kc[(size_t)e * ND * ND + row * ND + row] : coef[e] * ke.v[row * ND + row];
+          d[c] += EXPL ? Kc[(size_t)e * tri_len(ND) + tri_idx(row, row, ND)]
+                       : coef[e] * ke.v[row * ND + row];
         }
       }
   const unsigned m = mask[node];

@@ -42,7 +42,8 @@ constexpr int TBX = 32, TBY = 4;
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TBX * TBY, 8)
     k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
-               const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc) {
+               const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc,
+               const T* __restrict__ dinvc, T omega, T* __restrict__ zc) {
   const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
   const int K = DIM == 3 ? (int)blockIdx.z : 0;
   if (I >= gc.nnx || J >= gc.nny) return;
@@ -68,7 +69,13 @@ __global__ void __launch_bounds__(TBX * TBY, 8)
   const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
   const unsigned mc = maskc[node];
 #pragma unroll
-  for (int c = 0; c < DIM; ++c) bc[DIM * node + c] = ((mc >> c) & 1u) ? T(0) : acc[c];
+  for (int c = 0; c < DIM; ++c) {
+    const long long d = DIM * node + c;
+    const T bv = ((mc >> c) & 1u) ? T(0) : acc[c];
+    bc[d] = bv;
+    // the coarse level's pre-smoothing from a zero guess, z = omega D^-1 b
+    if (zc) zc[d] = omega * dinvc[d] * bv;
+  }
 }
 
 // z_f += Pm z_c: fine node (i,j,k) interpolates from coarse nodes
@@ -132,11 +139,14 @@ template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
     k_galerkin_fine(GridP gc, GridP gf, const T* __restrict__ coef, const T* __restrict__ Qc,
                     T* __restrict__ Kc) {
-  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
+  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE, NT = tri_len(ND);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= gc.nel * ND * ND) return;
-  const long long E = t / (ND * ND);
-  const int entry = (int)(t % (ND * ND));
+  if (t >= gc.nel * NT) return;
+  const long long E = t / NT;
+  const int pk = (int)(t % NT);
+  int r, cc;
+  tri_rc(pk, ND, r, cc);
+  const int entry = r * ND + cc;
   const int EX = (int)(E % gc.nx);
   const long long rest = E / gc.nx;
   const int EY = (int)(rest % gc.ny);
@@ -148,7 +158,7 @@ __global__ void __launch_bounds__(256)
     const long long fe = fx + (long long)gf.nx * (fy + (long long)gf.ny * (DIM == 3 ? fz : 0));
     acc += coef[fe] * Qc[c * ND * ND + entry];
   }
-  Kc[(size_t)E * ND * ND + entry] = acc;
+  Kc[(size_t)E * NT + pk] = acc;
 }
 
 // Level-1 diagonal without stored matrices (3D): node I of level 1 sums, over
@@ -200,10 +210,14 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_galerkin_l2(GridP g2, GridP gf, const T* __restrict__ coef, const T* __restrict__ R,
                   T* __restrict__ Kc) {
+  constexpr int NT = tri_len(24);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g2.nel * 576) return;
-  const long long E = t / 576;
-  const int entry = (int)(t % 576);
+  if (t >= g2.nel * NT) return;
+  const long long E = t / NT;
+  const int pk = (int)(t % NT);
+  int r, cc;
+  tri_rc(pk, 24, r, cc);
+  const int entry = r * 24 + cc;
   const int EX = (int)(E % g2.nx);
   const long long rest = E / g2.nx;
   const int EY = (int)(rest % g2.ny);
@@ -217,7 +231,7 @@ __global__ void __launch_bounds__(256)
     const int fz = 4 * EZ + 2 * ((c1 >> 2) & 1) + ((c0 >> 2) & 1);
     acc += coef[fx + (long long)gf.nx * (fy + (long long)gf.ny * fz)] * R[f * 576 + entry];
   }
-  Kc[(size_t)E * 576 + entry] = acc;
+  Kc[(size_t)E * NT + pk] = acc;
 }
 
 // Galerkin level l+1 from stored level-l element matrices.  One block of
@@ -226,7 +240,7 @@ __global__ void __launch_bounds__(256)
 template <int DIM, typename T>
 __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
     k_galerkin_coarse(GridP gc, GridP gf, const T* __restrict__ Kf, T* __restrict__ Kc) {
-  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
+  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE, NT = tri_len(ND);
   __shared__ T sK[ND * ND];
   __shared__ T sT[ND * ND];
   const long long E = blockIdx.x;
@@ -241,7 +255,7 @@ __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
   for (int c = 0; c < NPE; ++c) {
     const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + ((c >> 2) & 1);
     const long long fe = fx + (long long)gf.nx * (fy + (long long)gf.ny * (DIM == 3 ? fz : 0));
-    sK[tid] = Kf[(size_t)fe * ND * ND + tid];
+    sK[tid] = Kf[(size_t)fe * NT + sym_idx(I, J, ND)];
     __syncthreads();
     // T[i][J] = sum_b K[i][(b, cj)] W_c[b][AJ]   (i = I here)
     T tv = T(0);
@@ -254,7 +268,7 @@ __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
     for (int acn = 0; acn < NPE; ++acn) acc += T(wchild<DIM>(c, acn, AI)) * sT[(DIM * acn + ci) * ND + J];
     __syncthreads();
   }
-  Kc[(size_t)E * ND * ND + tid] = acc;
+  if (J >= I) Kc[(size_t)E * NT + tri_idx(I, J, ND)] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -292,7 +306,7 @@ __global__ void __launch_bounds__(256)
           const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
           const int ar = (ir - ex) + 2 * (jr - ey) + (DIM == 3 ? 4 * (kr - ez) : 0);
           const int ac = (ic - ex) + 2 * (jc - ey) + (DIM == 3 ? 4 * (kc - ez) : 0);
-          s += Kc[(size_t)e * ND * ND + (DIM * ar + cr) * ND + DIM * ac + cc];
+          s += Kc[(size_t)e * tri_len(ND) + sym_idx(DIM * ar + cr, DIM * ac + cc, ND)];
         }
   }
   A[t] = s;
@@ -467,19 +481,23 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 static cudaError_t restrict_t(const GridP& gf, const uint8_t* mf, const GridP& gc,
-                              const uint8_t* mc, const void* rf, void* bc, cudaStream_t s) {
+                              const uint8_t* mc, const void* rf, void* bc, const void* dinvc,
+                              double omega, void* zc, cudaStream_t s) {
   if (gc.nn <= 0) return cudaSuccess;
   dim3 grid((gc.nnx + TBX - 1) / TBX, (gc.nny + TBY - 1) / TBY, DIM == 3 ? gc.nnz : 1);
-  k_restrict<DIM, T><<<grid, dim3(TBX, TBY), 0, s>>>(gf, mf, gc, mc, (const T*)rf, (T*)bc);
+  k_restrict<DIM, T><<<grid, dim3(TBX, TBY), 0, s>>>(gf, mf, gc, mc, (const T*)rf, (T*)bc,
+                                                       (const T*)dinvc, T(omega), (T*)zc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(int dim, int t, const GridP& gf, const uint8_t* mf, const GridP& gc,
-                            const uint8_t* mc, const void* rf, void* bc, cudaStream_t s) {
-  if (dim == 2) return t == T_F64 ? restrict_t<2, double>(gf, mf, gc, mc, rf, bc, s)
-                                  : restrict_t<2, float>(gf, mf, gc, mc, rf, bc, s);
-  return t == T_F64 ? restrict_t<3, double>(gf, mf, gc, mc, rf, bc, s)
-                    : restrict_t<3, float>(gf, mf, gc, mc, rf, bc, s);
+                            const uint8_t* mc, const void* rf, void* bc, const void* dinvc,
+                            double omega, void* zc, cudaStream_t s) {
+  if (dim == 2)
+    return t == T_F64 ? restrict_t<2, double>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s)
+                      : restrict_t<2, float>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s);
+  return t == T_F64 ? restrict_t<3, double>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s)
+                    : restrict_t<3, float>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s);
 }
 
 template <int DIM, typename T>
@@ -541,7 +559,7 @@ template <int DIM, typename T>
 static cudaError_t gal_fine_t(const GridP& gc, const GridP& gf, const void* coef, const void* Qc,
                               void* Kc, cudaStream_t s) {
   constexpr int ND = Geo<DIM>::ND;
-  const long long tot = gc.nel * ND * ND;
+  const long long tot = gc.nel * tri_len(ND);
   k_galerkin_fine<DIM, T><<<nblocks(tot, 256), 256, 0, s>>>(gc, gf, (const T*)coef,
                                                             (const T*)Qc, (T*)Kc);
   return cudaGetLastError();
@@ -572,7 +590,7 @@ cudaError_t launch_diag_l1(int t, const GridP& g1, const GridP& gf, const uint8_
 
 cudaError_t launch_galerkin_l2(int t, const GridP& g2, const GridP& gf, const void* coef,
                                const void* R, void* Kc, cudaStream_t s) {
-  const long long tot = g2.nel * 576;
+  const long long tot = g2.nel * tri_len(24);
   if (t == T_F64)
     k_galerkin_l2<double><<<nblocks(tot, 256), 256, 0, s>>>(g2, gf, (const double*)coef,
                                                              (const double*)R, (double*)Kc);

@@ -337,7 +337,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
     lv[l].z2 = cv.take<char>(nl * ts);
     lv[l].r = cv.take<char>(nl * ts);
     const bool stored = l >= 2 || (l == 1 && !l1_implicit);
-    lv[l].Kc = stored ? (void*)cv.take<char>((size_t)nd * nd * g.nel * ts) : nullptr;
+    lv[l].Kc = stored ? (void*)cv.take<char>((size_t)tri_len(nd) * g.nel * ts) : nullptr;
     lv[l].eo = stored ? (void*)cv.take<char>((size_t)nd * g.nel * ts) : nullptr;
   }
   const long long nc = lv[L - 1].n;
@@ -725,15 +725,19 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
   if ((st = run_op(c, fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
                                 EPI_RESID), "resid 0")) != TO_OK)
     return st;
-  LAUNCH(c, launch_restrict(c->dim, t, lv[0].g, lv[0].mask, lv[1].g, lv[1].mask, lv[0].r,
-                            lv[1].b, s), "restrict 0");
+  // restriction into level l also pre-smooths level l from a zero guess
+  // (except on the coarsest level, which is solved exactly)
+  auto restrict_into = [&](int l) {
+    const bool smooth = l < L - 1;
+    return launch_restrict(c->dim, t, lv[l - 1].g, lv[l - 1].mask, lv[l].g, lv[l].mask,
+                           lv[l - 1].r, lv[l].b, smooth ? lv[l].dinv : nullptr, 0.6,
+                           smooth ? lv[l].z : nullptr, s);
+  };
+  LAUNCH(c, restrict_into(1), "restrict 0");
   for (int l = 1; l < L - 1; ++l) {
-    LAUNCH(c, launch_presmooth(t, t, lv[l].n, lv[l].b, nullptr, lv[l].dinv, 0.6, lv[l].z, s),
-           "presmooth l");
     if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID), "resid l")) != TO_OK)
       return st;
-    LAUNCH(c, launch_restrict(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].mask,
-                              lv[l].r, lv[l + 1].b, s), "restrict l");
+    LAUNCH(c, restrict_into(l + 1), "restrict l");
   }
   // coarsest grid: exact solve with the stored inverse
   LAUNCH(c, launch_dense_gemv(t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s), "coarse solve");

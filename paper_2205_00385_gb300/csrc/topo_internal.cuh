@@ -27,6 +27,26 @@ struct GridP {
   long long nn, nel;   // node and element counts
 };
 
+// Symmetric element matrices of the stored coarse levels keep their upper
+// triangle, row-major packed: entry (r, c), r <= c, at tri_idx(r, c, nd);
+// tri_len(nd) = nd (nd + 1) / 2 entries per element.
+__host__ __device__ constexpr int tri_len(int nd) { return nd * (nd + 1) / 2; }
+__host__ __device__ constexpr int tri_idx(int r, int c, int nd) {
+  return r * nd - (r * (r - 1)) / 2 + (c - r);
+}
+__host__ __device__ constexpr int sym_idx(int r, int c, int nd) {
+  return r <= c ? tri_idx(r, c, nd) : tri_idx(c, r, nd);
+}
+// packed index p -> (r, c)
+__host__ __device__ inline void tri_rc(int p, int nd, int& r, int& c) {
+  r = 0;
+  while (p >= nd - r) {
+    p -= nd - r;
+    ++r;
+  }
+  c = r + p;
+}
+
 template <int DIM>
 struct Geo {
   static constexpr int NPE = 1 << DIM;            // nodes per element
@@ -219,7 +239,7 @@ struct LevelBuf {
   void* z;               // T[n]
   void* z2;              // T[n]
   void* r;               // T[n]
-  void* Kc;              // T[nel*ND*ND], element-major (stored coarse levels)
+  void* Kc;              // T[nel*tri_len(ND)], packed upper triangles (stored levels)
   void* eo;              // T[nel*ND]: per-element operator rows (stored levels)
 };
 
