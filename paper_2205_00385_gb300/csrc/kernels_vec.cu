@@ -122,9 +122,21 @@ __global__ void __launch_bounds__(RED_THREADS)
            unsigned* counter, double* out) {
   using A = Ar<S>;
   __shared__ double sh[32];
-  typename A::T v = A::zero();
-  GRID_LOOP(k, n) A::dacc(v, A::ld(a, k), A::ld(b, k));
-  reduce_to<S>(A::dfin(v), out, partials, counter, sh);
+  typename A::T v[2] = {A::zero(), A::zero()};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + 3 * stride < n; k += 4 * stride) {
+    typename A::T av[4], bv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      av[u] = A::ld(a, k + u * stride);
+      bv[u] = A::ld(b, k + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) A::dacc(v[u & 1], av[u], bv[u]);
+  }
+  for (; k < n; k += stride) A::dacc(v[0], A::ld(a, k), A::ld(b, k));
+  reduce_to<S>(A::add(A::dfin(v[0]), A::dfin(v[1])), out, partials, counter, sh);
 }
 
 __global__ void __launch_bounds__(256) k_split(long long n, const double* __restrict__ in,
@@ -427,23 +439,33 @@ __global__ void k_gs_count(const double* scal, int n0, int n1, double tol, int* 
 // works on the float32 shadow p32 -> q32 and the V-cycle returns z32.
 // alpha and beta are formed once per block from the float64 scalars.
 // ---------------------------------------------------------------------------
+// The three passes below keep four indices per thread in flight (their
+// loads are issued before any of them is used), enough outstanding bytes to
+// stream at the copy bandwidth with one resident grid.
+constexpr int CG_U = 4;
+
 // out = sum_k a[k] b[k], a pairs, b float32
 __global__ void __launch_bounds__(RED_THREADS)
     k_dot_d2f(long long n, const float2* __restrict__ a, const float* __restrict__ b,
               double* partials, unsigned* counter, double* out) {
   using Rg = Ar<float2>;
   __shared__ double sh[32];
-  dfl v = Rg::zero(), v2 = Rg::zero();
+  dfl v[2] = {Rg::zero(), Rg::zero()};
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; k + stride < n; k += 2 * stride) {
-    const dfl a0 = Rg::ld(a, k), a1 = Rg::ld(a, k + stride);
-    const float b0 = b[k], b1 = b[k + stride];
-    v = df_add(Rg::mulf(a0, b0), v);
-    v2 = df_add(Rg::mulf(a1, b1), v2);
+  for (; k + (CG_U - 1) * stride < n; k += CG_U * stride) {
+    dfl av[CG_U];
+    float bv[CG_U];
+#pragma unroll
+    for (int u = 0; u < CG_U; ++u) {
+      av[u] = Rg::ld(a, k + u * stride);
+      bv[u] = b[k + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < CG_U; ++u) df_dot_acc(v[u & 1], av[u], dfl{bv[u], 0.f});
   }
-  if (k < n) v = df_add(Rg::mulf(Rg::ld(a, k), b[k]), v);
-  reduce_to<float2>(df_add(v, v2), out, partials, counter, sh);
+  for (; k < n; k += stride) df_dot_acc(v[0], Rg::ld(a, k), dfl{b[k], 0.f});
+  reduce_to<float2>(df_add(df_norm(v[0]), df_norm(v[1])), out, partials, counter, sh);
 }
 
 // alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q; scal[rr] = |r|^2
@@ -457,14 +479,31 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (threadIdx.x == 0) s_alpha = scal[num] / scal[den];
   __syncthreads();
   const dfl al = split_d(s_alpha), mal = {-al.h, -al.l};
-  dfl v = Rg::zero();
-  GRID_LOOP(k, n) {
-    Rg::st(x, k, df_fma(al, Rg::ld(p, k), Rg::ld(x, k)));
-    const dfl rk = df_add(Rg::mulf(mal, q[k]), Rg::ld(r, k));
-    Rg::st(r, k, rk);
-    v = df_fma(rk, rk, v);
+  dfl v[2] = {Rg::zero(), Rg::zero()};
+  auto step = [&](long long kk, dfl xk, dfl pk, dfl rk0, float qk, dfl& acc) {
+    Rg::st(x, kk, df_fma(al, pk, xk));
+    const dfl rk = df_add(Rg::mulf(mal, qk), rk0);
+    Rg::st(r, kk, rk);
+    df_dot_acc(acc, rk, rk);
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + (CG_U - 1) * stride < n; k += CG_U * stride) {
+    dfl xv[CG_U], pv[CG_U], rv[CG_U];
+    float qv[CG_U];
+#pragma unroll
+    for (int u = 0; u < CG_U; ++u) {
+      const long long kk = k + u * stride;
+      xv[u] = Rg::ld(x, kk);
+      pv[u] = Rg::ld(p, kk);
+      rv[u] = Rg::ld(r, kk);
+      qv[u] = q[kk];
+    }
+#pragma unroll
+    for (int u = 0; u < CG_U; ++u) step(k + u * stride, xv[u], pv[u], rv[u], qv[u], v[u & 1]);
   }
-  reduce_to<float2>(v, scal + rr, partials, counter, sh);
+  for (; k < n; k += stride) step(k, Rg::ld(x, k), Rg::ld(p, k), Rg::ld(r, k), q[k], v[0]);
+  reduce_to<float2>(df_add(df_norm(v[0]), df_norm(v[1])), scal + rr, partials, counter, sh);
 }
 
 // p = z + beta p (beta = scal[num]/scal[den], or p = z when num < 0);
@@ -477,12 +516,26 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) s_beta = num >= 0 ? scal[num] / scal[den] : 0.0;
   __syncthreads();
   const dfl be = split_d(s_beta);
-  GRID_LOOP(k, n) {
-    const dfl zk = {z[k], 0.f};
-    const dfl pk = num >= 0 ? df_add(df_mul(be, Rg::ld(p, k)), zk) : zk;
-    Rg::st(p, k, pk);
-    p32[k] = __fadd_rn(pk.h, pk.l);
+  auto step = [&](long long kk, float zv, dfl pold) {
+    const dfl zk = {zv, 0.f};
+    const dfl pk = num >= 0 ? df_add(df_mul(be, pold), zk) : zk;
+    Rg::st(p, kk, pk);
+    p32[kk] = __fadd_rn(pk.h, pk.l);
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + (CG_U - 1) * stride < n; k += CG_U * stride) {
+    float zv[CG_U];
+    dfl pv[CG_U];
+#pragma unroll
+    for (int u = 0; u < CG_U; ++u) {
+      zv[u] = z[k + u * stride];
+      pv[u] = num >= 0 ? Rg::ld(p, k + u * stride) : Rg::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < CG_U; ++u) step(k + u * stride, zv[u], pv[u]);
   }
+  for (; k < n; k += stride) step(k, z[k], num >= 0 ? Rg::ld(p, k) : Rg::zero());
 }
 
 #undef GRID_LOOP
