@@ -198,14 +198,6 @@ to_status to_apply(to_ctx* ctx, int32_t op, int32_t prec, const double* x, doubl
  * r, z dev float64 n (builds the hierarchy if stale). */
 to_status to_vcycle(to_ctx* ctx, const double* r, double* z);
 
-/* How the V-cycle runs the levels below level 1 (with 3 or more levels).
- * mode 0 (the default): one launch per step.  mode 1: one persistent
- * cooperative kernel with bounded grid barriers; a barrier wait that expires
- * ends it and the next solve returns TO_E_TIMEOUT.  Both give bit-identical
- * results.  TO_E_STATE when mode 1 is not available (fewer than 3 levels, or
- * no cooperative launch on the device); TO_E_INVALID for another mode. */
-to_status to_set_coarse_cycle(to_ctx* ctx, int32_t mode);
-
 /* Galerkin operator of level l >= 1 (coarse grid l of the hierarchy):
  * y = A_l x with x, y dev float64 of that level's DOF count (see
  * to_level_info).  For tests of the coarse operators. */

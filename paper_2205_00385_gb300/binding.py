@@ -61,7 +61,6 @@ _SIGS = {
     "to_vcycle": [_VP, _VP, _VP],
     "to_level_apply": [_VP, C.c_int32, _VP, _VP],
     "to_level_info": [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64)],
-    "to_set_coarse_cycle": [_VP, C.c_int32],
     "to_profile_enable": [_VP, C.c_int32],
     "to_profile_read": [_VP, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                         C.POINTER(C.c_double)],
@@ -210,11 +209,6 @@ def to_level_info(ctx, level):
     n = C.c_int64()
     _check(load().to_level_info(ctx, level, nel, C.byref(n)), ctx)
     return tuple(nel), n.value
-
-
-def to_set_coarse_cycle(ctx, mode: int):
-    """1: levels below level 1 in one persistent cooperative kernel; 0: one launch per step."""
-    _check(load().to_set_coarse_cycle(ctx, int(mode)), ctx)
 
 
 # profiling kinds (to_profile_read) and their bits in to_profile_enable

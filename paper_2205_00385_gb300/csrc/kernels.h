@@ -96,32 +96,6 @@ cudaError_t launch_cholesky_inverse(int t, int n, void* A, void* Ainv, int* stat
                                     cudaStream_t s);
 cudaError_t launch_dense_gemv(int t, int n, const void* A, const void* x, void* y,
                               cudaStream_t s);
-// Persistent coarse-grid cycle: every V-cycle step below level 1 (restriction
-// into level 2 through interpolation back into level 1) in one cooperative
-// grid with bounded grid barriers.  Level l's arrays are of type t; lv[1].r
-// holds the level-1 residual on entry, lv[1].z gains Pm z2_2 on exit.
-struct CoarseLevelP {
-  GridP g;
-  const uint8_t* mask;
-  const void* Kc;
-  void* eo;
-  void* b;
-  void* z;
-  void* z2;
-  void* r;
-  const void* dinv;
-};
-struct CoarseCycleP {
-  int L, nc;                  // levels, coarsest-grid DOFs
-  double omega;
-  CoarseLevelP lv[MAXL];
-  const void* Ainv;           // nc x nc inverse of the coarsest operator
-  unsigned* bar;              // barrier word (zero at first use)
-  unsigned* abort_w;          // set when a barrier wait expired
-  int* status;                // receives TO_E_TIMEOUT then
-};
-bool coarse_cycle_ok(int dim, const CoarseCycleP& P);
-cudaError_t launch_coarse_cycle(int dim, int t, const CoarseCycleP& P, cudaStream_t s);
 cudaError_t launch_convert(int tin, int tout, long long n, const void* in, void* out,
                            cudaStream_t s);
 

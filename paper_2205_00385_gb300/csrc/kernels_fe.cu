@@ -11,7 +11,6 @@
 #include <type_traits>
 
 #include "kernels.h"
-#include "mgdev.cuh"
 
 namespace topo {
 
@@ -236,18 +235,55 @@ __device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&
 // so all of an element's matrix is in flight at once); a node-centric gather
 // then sums the element rows belonging to each node in a fixed order.
 // ---------------------------------------------------------------------------
-// One warp per element (mgdev.cuh: gemv_elem); shared memory holds each
-// warp's staged packed triangle.
+// One warp per element: the element's packed upper triangle is staged in the
+// warp's slice of shared memory with 16-byte loads, then lane r forms row r
+// of K_e x_e reading K(r, c) symmetrically.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
     k_elem_gemv(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ Kc,
                 const T* __restrict__ x, T* __restrict__ eo) {
-  constexpr int NT = tri_len(Geo<DIM>::ND);
-  __shared__ __align__(16) T sk[8][NT];   // 8 warps per block
+  constexpr int ND = Geo<DIM>::ND, NT = tri_len(ND);
+  constexpr int VW = 16 / sizeof(T);                 // values per 16-byte load
+  static_assert((NT * sizeof(T)) % 16 == 0, "packed triangle must be a multiple of 16 bytes");
+  __shared__ __align__(16) T sk[8][NT];              // 8 warps per block
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long e = warp; e < g.nel; e += nwarps) gemv_elem<DIM, T>(g, mask, Kc, x, eo, e, lane, sk[wib]);
+  T* tk = sk[wib];
+  for (long long e = warp; e < g.nel; e += nwarps) {
+    const int ex = (int)(e % g.nx);
+    const long long rest = e / g.nx;
+    const int ey = (int)(rest % g.ny);
+    const int ez = DIM == 3 ? (int)(rest / g.ny) : 0;
+    T xv = T(0);
+    if (lane < ND) {
+      const int a = lane / DIM, c = lane % DIM;
+      const long long nd = (ex + (a & 1)) +
+                           (long long)g.nnx * ((ey + ((a >> 1) & 1)) +
+                                               (long long)g.nny * (DIM == 3 ? ez + ((a >> 2) & 1) : 0));
+      xv = ((mask[nd] >> c) & 1u) ? T(0) : x[DIM * nd + c];
+    }
+    const T* src = Kc + (size_t)e * NT;
+    for (int q = lane; q < NT / VW; q += 32) {
+      if constexpr (sizeof(T) == 4)
+        reinterpret_cast<float4*>(tk)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
+      else
+        reinterpret_cast<double2*>(tk)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
+    }
+    __syncwarp();
+    // K(lane, c): tri_idx(c, lane) below the diagonal, whose step from c to
+    // c + 1 is ND - 1 - c, then consecutive entries of row lane
+    T acc = T(0);
+    int idx = lane;
+#pragma unroll
+    for (int c = 0; c < ND; ++c) {
+      const T xc = __shfl_sync(0xffffffffu, xv, c);
+      if (lane < ND) acc = fma(tk[idx], xc, acc);
+      idx += (c < lane) ? (ND - 1 - c) : 1;
+    }
+    if (lane < ND) eo[(size_t)e * ND + lane] = acc;
+    __syncwarp();
+  }
 }
 
 template <int DIM, typename T, int EPI>
@@ -255,11 +291,43 @@ __global__ void __launch_bounds__(256)
     k_elem_gather(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ eo,
                   const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ b,
                   const T* __restrict__ dinv, T omega, T dfix) {
+  constexpr int ND = Geo<DIM>::ND;
+  constexpr int NZ = DIM == 3 ? 2 : 1;
   // threads on the node grid: x lanes along i, block rows along j, z = k
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y;
   const int k = DIM == 3 ? (int)blockIdx.z : 0;
   if (i >= g.nnx || j >= g.nny) return;
-  gather_at<DIM, T, EPI>(g, mask, eo, x, y, b, dinv, omega, dfix, i, j, k);
+  const long long node = i + (long long)g.nnx * (j + (long long)g.nny * k);
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int ez = 0; ez < NZ; ++ez)
+#pragma unroll
+    for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+      for (int ex = 0; ex < 2; ++ex) {
+        const int ei = i - 1 + ex, ej = j - 1 + ey, ek = k - 1 + ez;
+        bool in = ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
+        if (DIM == 3) in = in && ek >= 0 && ek < g.nz;
+        if (!in) continue;
+        const long long e = ei + (long long)g.nx * (ej + (long long)g.ny * (DIM == 3 ? ek : 0));
+        const int a = (1 - ex) + 2 * (1 - ey) + (DIM == 3 ? 4 * (1 - ez) : 0);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += eo[(size_t)e * ND + DIM * a + c];
+      }
+  const unsigned m = mask[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long d = DIM * node + c;
+    const T Ax = ((m >> c) & 1u) ? dfix * x[d] : acc[c];
+    if (EPI == EPI_APPLY)
+      y[d] = Ax;
+    else if (EPI == EPI_RESID)
+      y[d] = b[d] - Ax;
+    else
+      y[d] = x[d] + omega * dinv[d] * (b[d] - Ax);
+  }
 }
 
 template <int DIM, typename T, int EPI>

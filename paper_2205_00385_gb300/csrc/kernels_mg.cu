@@ -12,7 +12,6 @@
 
 #include "dfmath.cuh"
 #include "kernels.h"
-#include "mgdev.cuh"
 
 namespace topo {
 
@@ -48,7 +47,35 @@ __global__ void __launch_bounds__(TBX * TBY, 8)
   const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
   const int K = DIM == 3 ? (int)blockIdx.z : 0;
   if (I >= gc.nnx || J >= gc.nny) return;
-  restrict_at<DIM, T>(gf, maskf, gc, maskc, rf, bc, dinvc, omega, zc, I, J, K);
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+        bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
+        if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
+        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+        const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * (DIM == 3 ? k : 0));
+        const unsigned m = in ? (unsigned)maskf[fn] : 7u;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+          if (!((m >> c) & 1u)) acc[c] += w * rf[DIM * fn + c];
+      }
+  const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
+  const unsigned mc = maskc[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long d = DIM * node + c;
+    const T bv = ((mc >> c) & 1u) ? T(0) : acc[c];
+    bc[d] = bv;
+    // the coarse level's pre-smoothing from a zero guess, z = omega D^-1 b
+    if (zc) zc[d] = omega * dinvc[d] * bv;
+  }
 }
 
 // z_f += Pm z_c: fine node (i,j,k) interpolates from coarse nodes
@@ -60,7 +87,30 @@ __global__ void __launch_bounds__(TBX * TBY)
   const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
   const int k = DIM == 3 ? (int)blockIdx.z : 0;
   if (i >= gf.nnx || j >= gf.nny) return;
-  prolong_at<DIM, T>(gf, maskf, gc, zc, zf, i, j, k);
+  const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (DIM == 3 && (k & 1)) ? 2 : 1;
+  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1),
+          wz = (DIM == 3 && (k & 1)) ? T(0.5) : T(1);
+  const T w = wx * wy * wz;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        if (a >= nk || bb >= nj || cc >= ni) continue;
+        const long long cn = (i0 + cc) + (long long)gc.nnx * ((j0 + bb) + (long long)gc.nny * (k0 + a));
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += w * zc[DIM * cn + c];
+      }
+  const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+  const unsigned m = maskf[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+    if (!((m >> c) & 1u)) zf[DIM * node + c] += acc[c];
 }
 
 template <typename T, typename TIN>
@@ -419,7 +469,11 @@ __global__ void __launch_bounds__(256)
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
-  dense_row<T>(n, A, x, y, warp, lane);
+  T s = T(0);
+  for (int m = lane; m < n; m += 32) s += A[(size_t)warp * n + m] * x[m];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[warp] = s;
 }
 
 // ---------------------------------------------------------------------------

@@ -427,8 +427,6 @@ const char* to_last_error(const to_ctx* ctx) {
   return ctx ? ctx->last_error.c_str() : g_last_error.c_str();
 }
 
-static CoarseCycleP coarse_cycle_args(const to_ctx* c);
-
 to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, const double* f,
                        void* workspace, int64_t ws_bytes, void* stream, to_ctx** out) {
   std::string why;
@@ -459,7 +457,6 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->prof_mask = 0u;
   c->n_vgraph = 0;
   c->cap_stream = nullptr;
-  c->coarse_coop = false;
   if (!make_stencil(c->dim, desc->rmin, &c->stencil)) {
     delete c;
     return fail(nullptr, TO_E_INVALID, "filter stencil too large");
@@ -713,23 +710,6 @@ static to_status build_hierarchy(to_ctx* c) {
   return TO_OK;
 }
 
-// arguments of the persistent coarse-grid cycle (levels 2 .. L-1)
-static CoarseCycleP coarse_cycle_args(const to_ctx* c) {
-  CoarseCycleP P = {};
-  P.L = c->L;
-  P.nc = c->nc;
-  P.omega = 0.6;
-  for (int l = 0; l < c->L; ++l) {
-    const LevelBuf& v = c->lv[l];
-    P.lv[l] = CoarseLevelP{v.g, v.mask, v.Kc, v.eo, v.b, v.z, v.z2, v.r, v.dinv};
-  }
-  P.Ainv = c->Ainv;
-  P.bar = c->counters + C_BAR;
-  P.abort_w = c->counters + C_ABORT;
-  P.status = c->ints + I_STATUS;
-  return P;
-}
-
 // zout (type zt: float64, or float32 in the mixed path) = V-cycle applied to
 // r (storage rin_t: float64, or double-float pairs in the mixed path)
 static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int zt) {
@@ -754,38 +734,19 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
                            smooth ? lv[l].z : nullptr, s);
   };
   LAUNCH(c, restrict_into(1), "restrict 0");
-  if (L == 2) {
-    // level 1 is the coarsest grid
-    LAUNCH(c, launch_dense_gemv(t, c->nc, c->Ainv, lv[1].b, lv[1].z2, s), "coarse solve");
-  } else {
-    if ((st = run_op(c, coarse_args(c, 1, lv[1].z, lv[1].r, lv[1].b, EPI_RESID), "resid 1")) != TO_OK)
+  for (int l = 1; l < L - 1; ++l) {
+    if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID), "resid l")) != TO_OK)
       return st;
-    if (c->coarse_coop) {
-      // levels 2 .. L-1 in one persistent cooperative grid
-      CoarseCycleP P = coarse_cycle_args(c);
-      LAUNCH(c, launch_coarse_cycle(c->dim, t, P, s), "coarse cycle");
-    } else {
-      LAUNCH(c, restrict_into(2), "restrict 1");
-      for (int l = 2; l < L - 1; ++l) {
-        if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID), "resid l")) != TO_OK)
-          return st;
-        LAUNCH(c, restrict_into(l + 1), "restrict l");
-      }
-      // coarsest grid: exact solve with the stored inverse
-      LAUNCH(c, launch_dense_gemv(t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s), "coarse solve");
-      // upward: interpolate, post-smooth (result of level l lands in z2)
-      for (int l = L - 2; l >= 2; --l) {
-        LAUNCH(c, launch_prolong_add(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].z2,
-                                     lv[l].z, s), "prolong l");
-        if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH),
-                         "postsmooth l")) != TO_OK)
-          return st;
-      }
-      LAUNCH(c, launch_prolong_add(c->dim, t, lv[1].g, lv[1].mask, lv[2].g, lv[2].z2, lv[1].z, s),
-             "prolong 1");
-    }
-    if ((st = run_op(c, coarse_args(c, 1, lv[1].z, lv[1].z2, lv[1].b, EPI_SMOOTH),
-                     "postsmooth 1")) != TO_OK)
+    LAUNCH(c, restrict_into(l + 1), "restrict l");
+  }
+  // coarsest grid: exact solve with the stored inverse
+  LAUNCH(c, launch_dense_gemv(t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s), "coarse solve");
+  // upward: interpolate, post-smooth (result of level l lands in z2)
+  for (int l = L - 2; l >= 1; --l) {
+    LAUNCH(c, launch_prolong_add(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].z2,
+                                 lv[l].z, s), "prolong l");
+    if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH),
+                     "postsmooth l")) != TO_OK)
       return st;
   }
   LAUNCH(c, launch_prolong_add(c->dim, t, lv[0].g, lv[0].mask, lv[1].g, lv[1].z2, lv[0].z, s),
@@ -859,11 +820,6 @@ static to_status check_status(to_ctx* c) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
   if (st) {
     cudaMemsetAsync(c->ints + I_STATUS, 0, 4, c->stream);
-    if (st == TO_E_TIMEOUT) {
-      // the coarse cycle's barrier state is inconsistent after an abort
-      cudaMemsetAsync(c->counters + C_BAR, 0, 2 * sizeof(unsigned), c->stream);
-      return fail(c, TO_E_TIMEOUT, "a grid barrier wait of the coarse cycle expired");
-    }
     return fail(c, TO_E_SINGULAR, "a factorisation met a non-positive pivot");
   }
   return TO_OK;
@@ -1259,21 +1215,6 @@ to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_
   }
   LAUNCH(c, launch_oc_final(nel, rho, c->oc_a, move, c->scal, change_dev, c->partials,
                             c->counters + C_MAX, s), "oc final");
-  return TO_OK;
-}
-
-to_status to_set_coarse_cycle(to_ctx* c, int32_t mode) {
-  if (!c) return fail(c, TO_E_INVALID, "NULL ctx");
-  if (mode != 0 && mode != 1) return fail(c, TO_E_INVALID, "mode must be 0 or 1");
-  if (mode == 1 && !coarse_cycle_ok(c->dim, coarse_cycle_args(c)))
-    return fail(c, TO_E_STATE, "the persistent coarse cycle is not available here");
-  if (c->coarse_coop != (mode == 1)) {
-    // captured V-cycles hold the other launch sequence
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
-    for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
-    c->n_vgraph = 0;
-    c->coarse_coop = mode == 1;
-  }
   return TO_OK;
 }
 

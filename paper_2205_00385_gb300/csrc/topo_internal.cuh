@@ -308,7 +308,6 @@ struct to_ctx {
   };
   VGraph vgraph[4];
   int n_vgraph;
-  bool coarse_coop;   // levels 2 .. L-1 by the persistent cooperative kernel
   cudaStream_t cap_stream;   // private stream used only for graph capture
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
@@ -319,7 +318,7 @@ namespace topo {
 
 // Counter slots (ctx->counters, one per reduction site in flight)
 enum Counter { C_DOT = 0, C_MULTI = 1 /* .. +16 */, C_UPD = 20, C_OC = 21, C_SENS = 22,
-               C_MAX = 23, C_BAR = 24, C_ABORT = 25, C_NCOUNTERS = 32 };
+               C_MAX = 23, C_NCOUNTERS = 32 };
 
 // --- launch helpers (host) ---
 void note_launch(to_ctx* c);

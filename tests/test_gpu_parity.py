@@ -132,8 +132,8 @@ def test_vcycle_parity(kind, kw):
     assert np.linalg.norm(z - z_ref) <= 2e-3 * np.linalg.norm(z_ref)
 
 
-# hierarchies deep enough that the persistent coarse cycle runs restriction,
-# smoothing and interpolation on several levels below level 1
+# hierarchies deep enough that restriction, smoothing and interpolation run
+# on several stored levels below level 1
 DEEP = [
     ("mbb2d", dict(nelx=64, nely=32), 5),
     ("cantilever3d", dict(nelx=32, nely=16, nelz=16), 4),
@@ -142,10 +142,9 @@ DEEP = [
 
 @pytest.mark.parametrize("kind,kw,levels", DEEP)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_vcycle_coarse_cycle_modes(kind, kw, levels, precision):
-    """The persistent coarse cycle (one cooperative kernel below level 1)
-    against one launch per step: the same bits, and both against the oracle's
-    V-cycle."""
+def test_vcycle_deep_hierarchy(kind, kw, levels, precision):
+    """V-cycles of deep hierarchies against the oracle; repeated calls give
+    the same bits."""
     B = _B()
     p = small_problem(kind, mg_levels=levels, **kw)
     g, KE = _model(p)
@@ -156,27 +155,22 @@ def test_vcycle_coarse_cycle_modes(kind, kw, levels, precision):
     out = []
     with Ctx(p, precision=precision) as c:
         c.set_density(rho)
-        for mode in (1, 0, 1):
-            B.to_set_coarse_cycle(c.ctx, mode)
+        for _ in range(2):
             z = dev(np.zeros(g.ndof))
             B.to_vcycle(c.ctx, dev(r), z)
             out.append(host(z))
-        with pytest.raises(B.TopoError) as e:
-            B.to_set_coarse_cycle(c.ctx, 2)
-        assert e.value.status == B.TO_E_INVALID
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    assert np.array_equal(out[0], out[1])
     tol = 1e-10 if precision == "fp64" else 2e-3
     assert np.linalg.norm(out[0] - z_ref) <= tol * np.linalg.norm(z_ref)
 
 
 @pytest.mark.parametrize("kind,kw,levels", DEEP)
-def test_mgcg_coarse_cycle_modes(kind, kw, levels):
-    """MGCG on a mid-optimisation density with a deep hierarchy.  Mixed
-    precision (V-cycle replayed from a captured graph, the cooperative kernel
-    one of its nodes) in both coarse-cycle modes gives the same iterates; the
-    float64 path takes the oracle's iteration count (within 1) and the mixed
-    one at most half as many again (float32 rounding in the V-cycle and the
-    operator perturbs the preconditioned iteration); both reach the exact compliance."""
+def test_mgcg_deep_hierarchy(kind, kw, levels):
+    """MGCG on a mid-optimisation density with a deep hierarchy: the float64
+    path takes the oracle's iteration count (within 1) and the mixed one
+    (V-cycle replayed from a captured graph) at most half as many again
+    (float32 rounding in the V-cycle and the operator perturbs the
+    preconditioned iteration); both reach the exact compliance."""
     B = _B()
     p = small_problem(kind, mg_levels=levels, n_iter=8, **kw)
     g, KE = _model(p)
@@ -186,36 +180,19 @@ def test_mgcg_coarse_cycle_modes(kind, kw, levels):
     C_ref = p.f @ solvers.direct_solve(K, p.f, p.fixed)
     it_ref = solvers.mgcg(K, p.f, solvers.Multigrid(g, K, p.fixed, levels), rtol=1e-8,
                           maxit=500)[1]
-    res = []
-    with Ctx(p, precision="mixed") as c:
-        c.set_density(rho)
-        for mode in (1, 0):
-            B.to_set_coarse_cycle(c.ctx, mode)
+    sol = {}
+    for precision in ("mixed", "fp64"):
+        with Ctx(p, precision=precision) as c:
+            c.set_density(rho)
             u = dev(np.zeros(g.ndof))
             it, rel, ok = B.to_mgcg_solve(c.ctx, 1e-8, 500, 0, u)
-            assert ok and rel < 1e-8, (mode, it, rel)
-            res.append((it, host(u)))
-    assert res[0][0] == res[1][0] and np.array_equal(res[0][1], res[1][1])
-    assert res[0][0] <= 1.5 * it_ref + 2, (res[0][0], it_ref)
-    with Ctx(p, precision="fp64") as c:
-        c.set_density(rho)
-        u = dev(np.zeros(g.ndof))
-        it64, rel, ok = B.to_mgcg_solve(c.ctx, 1e-8, 500, 0, u)
-        u64 = host(u)
-    assert ok and abs(it64 - it_ref) <= 1, (it64, it_ref)
-    for uu, tol in ((res[0][1], 1e-6), (u64, 1e-10)):
-        C = sensitivity.compliance(E, sensitivity.element_energy(g, KE, uu, p.fixed))
+            assert ok and rel < 1e-8, (precision, it, rel)
+            sol[precision] = (it, host(u))
+    assert abs(sol["fp64"][0] - it_ref) <= 1, (sol["fp64"][0], it_ref)
+    assert sol["mixed"][0] <= 1.5 * it_ref + 2, (sol["mixed"][0], it_ref)
+    for precision, tol in (("mixed", 1e-6), ("fp64", 1e-10)):
+        C = sensitivity.compliance(E, sensitivity.element_energy(g, KE, sol[precision][1], p.fixed))
         assert abs(C - C_ref) <= tol * C_ref
-
-
-def test_coarse_cycle_needs_three_levels():
-    B = _B()
-    p = small_problem("cantilever3d", nelx=4, nely=2, nelz=2, mg_levels=2)
-    with Ctx(p, precision="fp64") as c:
-        B.to_set_coarse_cycle(c.ctx, 0)
-        with pytest.raises(B.TopoError) as e:
-            B.to_set_coarse_cycle(c.ctx, 1)
-        assert e.value.status == B.TO_E_STATE
 
 
 def _snapshot_density(p, k):
