@@ -144,10 +144,13 @@ cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double
 // mixed-path CG (pairs x, r, p; float32 shadows p32 -> q32 and z32)
 cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* partials,
                            unsigned* counter, double* out, cudaStream_t s);
-// x += alpha p, r -= alpha q, scal[rr] = |r|^2 with alpha = scal[num]/scal[den]
+// x += alpha p, r -= alpha q, scal[rr] = |r|^2 with alpha = scal[num]/scal[den];
+// with b non-null also b = float(r), zpre = omega dinv b (the next V-cycle's
+// right-hand side and pre-smoothing from zero)
 cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const float* q,
                             double* scal, int num, int den, int rr, double* partials,
-                            unsigned* counter, cudaStream_t s);
+                            unsigned* counter, float* b, float* zpre, const float* dinv,
+                            double omega, cudaStream_t s);
 // p = z + beta p (num < 0: p = z), beta = scal[num]/scal[den]; p32 = float(p)
 cudaError_t launch_cg_p_d2(long long n, void* p, float* p32, const float* z, const double* scal,
                            int num, int den, cudaStream_t s);

@@ -34,37 +34,62 @@ __host__ __device__ __forceinline__ double wchild(int c, int a, int A) {
 // Restriction b_c = Pm^T r_f (Pm = M_f P M_c): coarse node (I,J,K) gathers
 // the fine nodes around (2I,2J,2K) with weights prod(1 - |d|/2).  Threads
 // are laid out on the node grid (x lanes along I, block rows along J,
-// blockIdx.z = K), so no index division is needed; the 3^DIM gathers are
-// independent loads summed in a fixed order.
+// blockIdx.z = K), so no index division is needed.  Every fine load is
+// issued before any is used: indices are clamped into the grid and the
+// out-of-range and fixed terms are dropped by selects after the loads, so
+// the 3^DIM masks and values take one memory round trip; the terms are then
+// summed in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int TBX = 32, TBY = 4;
 
+template <typename T>
+__host__ __device__ constexpr int transfer_min_blocks() {
+  return sizeof(T) == 4 ? 4 : 2;   // registers for all loads in flight
+}
+
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TBX * TBY, 8)
+__global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
                const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc,
                const T* __restrict__ dinvc, T omega, T* __restrict__ zc) {
+  constexpr int NZ = DIM == 3 ? 3 : 1;
   const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
   const int K = DIM == 3 ? (int)blockIdx.z : 0;
   if (I >= gc.nnx || J >= gc.nny) return;
+  unsigned m[NZ][3][3];
+  T v[NZ][3][3][DIM];
+#pragma unroll
+  for (int a = 0; a < NZ; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int i = min(max(2 * I + q - 1, 0), gf.nnx - 1);
+        const int j = min(max(2 * J + b - 1, 0), gf.nny - 1);
+        const int k = DIM == 3 ? min(max(2 * K + a - 1, 0), gf.nnz - 1) : 0;
+        const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+        m[a][b][q] = maskf[fn];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) v[a][b][q][c] = rf[DIM * fn + c];
+      }
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
 #pragma unroll
-  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+  for (int a = 0; a < NZ; ++a)
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
+    for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
+      for (int q = 0; q < 3; ++q) {
+        const int dx = q - 1, dy = b - 1, dz = DIM == 3 ? a - 1 : 0;
         const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
         bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
         if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
         const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
-        const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * (DIM == 3 ? k : 0));
-        const unsigned m = in ? (unsigned)maskf[fn] : 7u;
+        const unsigned mm = in ? m[a][b][q] : 7u;
 #pragma unroll
         for (int c = 0; c < DIM; ++c)
-          if (!((m >> c) & 1u)) acc[c] += w * rf[DIM * fn + c];
+          acc[c] += ((mm >> c) & 1u) ? T(0) : w * v[a][b][q][c];
       }
   const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
   const unsigned mc = maskc[node];
@@ -79,38 +104,72 @@ __global__ void __launch_bounds__(TBX * TBY, 8)
 }
 
 // z_f += Pm z_c: fine node (i,j,k) interpolates from coarse nodes
-// floor(i/2) .. ceil(i/2) per axis (threads on the fine node grid).
+// floor(i/2) .. ceil(i/2) per axis.  Threads on the fine (i, j) grid, each
+// taking the fine nodes k = 2q and 2q+1 (3D), which share the coarse plane
+// q: the coarse values of planes q and q+1 and the fine values are all
+// loaded (clamped into the grid) before any sum, and each fine node then
+// sums its own terms in a fixed order.
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TBX * TBY)
+__global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     k_prolong_add(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
                   const T* __restrict__ zc, T* __restrict__ zf) {
+  constexpr int NK = DIM == 3 ? 2 : 1;   // fine nodes per thread along z
   const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
-  const int k = DIM == 3 ? (int)blockIdx.z : 0;
+  const int q = DIM == 3 ? (int)blockIdx.z : 0;
   if (i >= gf.nnx || j >= gf.nny) return;
-  const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (DIM == 3 && (k & 1)) ? 2 : 1;
-  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1),
-          wz = (DIM == 3 && (k & 1)) ? T(0.5) : T(1);
-  const T w = wx * wy * wz;
-  T acc[DIM];
+  const int i0 = i >> 1, j0 = j >> 1;
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
+  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
+  // coarse values: plane q (+ q+1 for the odd fine node), 2 x 2 around (i0, j0)
+  T cv[NK][2][2][DIM];
 #pragma unroll
-  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < NK; ++a)
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
-        if (a >= nk || bb >= nj || cc >= ni) continue;
-        const long long cn = (i0 + cc) + (long long)gc.nnx * ((j0 + bb) + (long long)gc.nny * (k0 + a));
+        const int ic = min(i0 + cc, gc.nnx - 1), jc = min(j0 + bb, gc.nny - 1);
+        const int kc = DIM == 3 ? min(q + a, gc.nnz - 1) : 0;
+        const long long cn = ic + (long long)gc.nnx * (jc + (long long)gc.nny * kc);
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) acc[c] += w * zc[DIM * cn + c];
+        for (int c = 0; c < DIM; ++c) cv[a][bb][cc][c] = zc[DIM * cn + c];
       }
-  const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
-  const unsigned m = maskf[node];
+  unsigned m[NK];
+  T zv[NK][DIM];
 #pragma unroll
-  for (int c = 0; c < DIM; ++c)
-    if (!((m >> c) & 1u)) zf[DIM * node + c] += acc[c];
+  for (int s = 0; s < NK; ++s) {
+    const int k = DIM == 3 ? min(2 * q + s, gf.nnz - 1) : 0;
+    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+    m[s] = maskf[node];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) zv[s][c] = zf[DIM * node + c];
+  }
+#pragma unroll
+  for (int s = 0; s < NK; ++s) {
+    const int k = DIM == 3 ? 2 * q + s : 0;
+    if (DIM == 3 && k >= gf.nnz) break;
+    const int nk = (DIM == 3 && (k & 1)) ? 2 : 1;
+    const T w = wx * wy * ((DIM == 3 && (k & 1)) ? T(0.5) : T(1));
+    T acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          if (a >= NK) continue;
+          // fine node k = 2q + s reads coarse plane (k >> 1) + a = q + a
+          const bool use = a < nk && bb < nj && cc < ni;
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) acc[c] += use ? w * cv[a][bb][cc][c] : T(0);
+        }
+    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      if (!((m[s] >> c) & 1u)) zf[DIM * node + c] = zv[s][c] + acc[c];
+  }
 }
 
 template <typename T, typename TIN>
@@ -504,7 +563,7 @@ template <int DIM, typename T>
 static cudaError_t prolong_t(const GridP& gf, const uint8_t* mf, const GridP& gc, const void* zc,
                              void* zf, cudaStream_t s) {
   if (gf.nn <= 0) return cudaSuccess;
-  dim3 grid((gf.nnx + TBX - 1) / TBX, (gf.nny + TBY - 1) / TBY, DIM == 3 ? gf.nnz : 1);
+  dim3 grid((gf.nnx + TBX - 1) / TBX, (gf.nny + TBY - 1) / TBY, DIM == 3 ? (gf.nnz + 1) / 2 : 1);
   k_prolong_add<DIM, T><<<grid, dim3(TBX, TBY), 0, s>>>(gf, mf, gc, (const T*)zc, (T*)zf);
   return cudaGetLastError();
 }

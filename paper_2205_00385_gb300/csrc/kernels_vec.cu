@@ -444,7 +444,9 @@ __global__ void k_gs_count(const double* scal, int n0, int n1, double tol, int* 
 // stream at the copy bandwidth with one resident grid.
 constexpr int CG_U = 4;
 
-// out = sum_k a[k] b[k], a pairs, b float32
+// out = sum_k a[k] b[k], a pairs, b float32.  Twelve bytes per index, so
+// eight indices per thread are kept in flight.
+constexpr int DOT_U = 8;
 __global__ void __launch_bounds__(RED_THREADS)
     k_dot_d2f(long long n, const float2* __restrict__ a, const float* __restrict__ b,
               double* partials, unsigned* counter, double* out) {
@@ -453,26 +455,31 @@ __global__ void __launch_bounds__(RED_THREADS)
   dfl v[2] = {Rg::zero(), Rg::zero()};
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; k + (CG_U - 1) * stride < n; k += CG_U * stride) {
-    dfl av[CG_U];
-    float bv[CG_U];
+  for (; k + (DOT_U - 1) * stride < n; k += DOT_U * stride) {
+    dfl av[DOT_U];
+    float bv[DOT_U];
 #pragma unroll
-    for (int u = 0; u < CG_U; ++u) {
+    for (int u = 0; u < DOT_U; ++u) {
       av[u] = Rg::ld(a, k + u * stride);
       bv[u] = b[k + u * stride];
     }
 #pragma unroll
-    for (int u = 0; u < CG_U; ++u) df_dot_acc(v[u & 1], av[u], dfl{bv[u], 0.f});
+    for (int u = 0; u < DOT_U; ++u) df_dot_acc(v[u & 1], av[u], dfl{bv[u], 0.f});
   }
   for (; k < n; k += stride) df_dot_acc(v[0], Rg::ld(a, k), dfl{b[k], 0.f});
   reduce_to<float2>(df_add(df_norm(v[0]), df_norm(v[1])), out, partials, counter, sh);
 }
 
-// alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q; scal[rr] = |r|^2
+// alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q; scal[rr] = |r|^2.
+// With b non-null it also starts the next V-cycle: b = r rounded to float32
+// and zpre = omega dinv b (its pre-smoothing from a zero guess), the values
+// the V-cycle's first kernel would compute.
+template <bool PRE>
 __global__ void __launch_bounds__(RED_THREADS)
     k_cg_xr_d2(long long n, float2* __restrict__ x, float2* __restrict__ r,
                const float2* __restrict__ p, const float* __restrict__ q, double* scal, int num,
-               int den, int rr, double* partials, unsigned* counter) {
+               int den, int rr, double* partials, unsigned* counter, float* __restrict__ b,
+               float* __restrict__ zpre, const float* __restrict__ dinv, float omega) {
   using Rg = Ar<float2>;
   __shared__ double sh[32];
   __shared__ double s_alpha;
@@ -480,17 +487,22 @@ __global__ void __launch_bounds__(RED_THREADS)
   __syncthreads();
   const dfl al = split_d(s_alpha), mal = {-al.h, -al.l};
   dfl v[2] = {Rg::zero(), Rg::zero()};
-  auto step = [&](long long kk, dfl xk, dfl pk, dfl rk0, float qk, dfl& acc) {
+  auto step = [&](long long kk, dfl xk, dfl pk, dfl rk0, float qk, float dk, dfl& acc) {
     Rg::st(x, kk, df_fma(al, pk, xk));
     const dfl rk = df_add(Rg::mulf(mal, qk), rk0);
     Rg::st(r, kk, rk);
     df_dot_acc(acc, rk, rk);
+    if (PRE) {
+      const float bv = __fadd_rn(rk.h, rk.l);
+      b[kk] = bv;
+      zpre[kk] = omega * dk * bv;
+    }
   };
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (; k + (CG_U - 1) * stride < n; k += CG_U * stride) {
     dfl xv[CG_U], pv[CG_U], rv[CG_U];
-    float qv[CG_U];
+    float qv[CG_U], dv[CG_U];
 #pragma unroll
     for (int u = 0; u < CG_U; ++u) {
       const long long kk = k + u * stride;
@@ -498,11 +510,14 @@ __global__ void __launch_bounds__(RED_THREADS)
       pv[u] = Rg::ld(p, kk);
       rv[u] = Rg::ld(r, kk);
       qv[u] = q[kk];
+      dv[u] = PRE ? dinv[kk] : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < CG_U; ++u) step(k + u * stride, xv[u], pv[u], rv[u], qv[u], v[u & 1]);
+    for (int u = 0; u < CG_U; ++u)
+      step(k + u * stride, xv[u], pv[u], rv[u], qv[u], dv[u], v[u & 1]);
   }
-  for (; k < n; k += stride) step(k, Rg::ld(x, k), Rg::ld(p, k), Rg::ld(r, k), q[k], v[0]);
+  for (; k < n; k += stride)
+    step(k, Rg::ld(x, k), Rg::ld(p, k), Rg::ld(r, k), q[k], PRE ? dinv[k] : 0.f, v[0]);
   reduce_to<float2>(df_add(df_norm(v[0]), df_norm(v[1])), scal + rr, partials, counter, sh);
 }
 
@@ -671,9 +686,18 @@ cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* p
 
 cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const float* q,
                             double* scal, int num, int den, int rr, double* partials,
-                            unsigned* counter, cudaStream_t s) {
-  k_cg_xr_d2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (float2*)x, (float2*)r, (const float2*)p, q,
-                                                scal, num, den, rr, partials, counter);
+                            unsigned* counter, float* b, float* zpre, const float* dinv,
+                            double omega, cudaStream_t s) {
+  if (b)
+    k_cg_xr_d2<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (float2*)x, (float2*)r,
+                                                        (const float2*)p, q, scal, num, den, rr,
+                                                        partials, counter, b, zpre, dinv,
+                                                        (float)omega);
+  else
+    k_cg_xr_d2<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (float2*)x, (float2*)r,
+                                                         (const float2*)p, q, scal, num, den, rr,
+                                                         partials, counter, nullptr, nullptr,
+                                                         nullptr, 0.f);
   return cudaGetLastError();
 }
 

@@ -711,16 +711,20 @@ static to_status build_hierarchy(to_ctx* c) {
 }
 
 // zout (type zt: float64, or float32 in the mixed path) = V-cycle applied to
-// r (storage rin_t: float64, or double-float pairs in the mixed path)
-static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int zt) {
+// r (storage rin_t: float64, or double-float pairs in the mixed path).  With
+// pre set, the finest level's right-hand side b = r and pre-smoothing
+// z = omega D^-1 b are already in place (written by the CG update).
+static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int zt,
+                        bool pre = false) {
   cudaStream_t s = c->stream;
   const int t = mg_t(c);
   const int L = c->L;
   ProfScope ps(c, PK_VCYCLE);
   LevelBuf* lv = c->lv;
   // finest level: smoothing from zero, residual, restriction
-  LAUNCH(c, launch_presmooth(t, rin_t, lv[0].n, rin, lv[0].b, lv[0].dinv, 0.6, lv[0].z, s),
-         "presmooth 0");
+  if (!pre)
+    LAUNCH(c, launch_presmooth(t, rin_t, lv[0].n, rin, lv[0].b, lv[0].dinv, 0.6, lv[0].z, s),
+           "presmooth 0");
   to_status st;
   if ((st = run_op(c, fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
                                 EPI_RESID), "resid 0")) != TO_OK)
@@ -760,12 +764,13 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
 // in float64), so it is captured once per (input, output, precision,
 // coefficients) as a CUDA graph and replayed: one launch per preconditioner
 // application instead of one per kernel, with no host gaps between kernels.
-static to_status vcycle_graphed(to_ctx* c, const void* rin, int rin_t, void* zout, int zt) {
+static to_status vcycle_graphed(to_ctx* c, const void* rin, int rin_t, void* zout, int zt,
+                                bool pre = false) {
   const void* coef = mg_t(c) == T_F64 ? (const void*)c->E64 : (const void*)c->E32;
   to_ctx::VGraph* vg = nullptr;
   for (int q = 0; q < c->n_vgraph; ++q) {
     to_ctx::VGraph& v = c->vgraph[q];
-    if (v.rin == rin && v.zout == zout && v.zt == zt && v.coef == coef) vg = &v;
+    if (v.rin == rin && v.zout == zout && v.zt == zt && v.coef == coef && v.pre == pre) vg = &v;
   }
   if (!vg) {
     if (!c->cap_stream)
@@ -780,7 +785,7 @@ static to_status vcycle_graphed(to_ctx* c, const void* rin, int rin_t, void* zou
     to_status st = TO_OK;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      st = vcycle(c, rin, rin_t, zout, zt);
+      st = vcycle(c, rin, rin_t, zout, zt, pre);
       const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
       if (e == cudaSuccess) e = e2;
     }
@@ -799,7 +804,7 @@ static to_status vcycle_graphed(to_ctx* c, const void* rin, int rin_t, void* zou
       c->n_vgraph = 3;
     }
     vg = &c->vgraph[c->n_vgraph++];
-    *vg = to_ctx::VGraph{rin, zout, coef, zt, exec, captured};
+    *vg = to_ctx::VGraph{rin, zout, coef, zt, pre, exec, captured};
   }
   ProfScope ps(c, PK_VCYCLE);
   CUDA_TRY(c, cudaGraphLaunch(vg->exec, c->stream), "V-cycle graph launch");
@@ -987,10 +992,13 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   int it = 0;
   bool conv = rel < rtol;
   float* z32 = static_cast<float*>(c->lv[0].z2);
+  // mixed path: the CG update also writes the next V-cycle's right-hand side
+  // and pre-smoothing (lv[0].b, lv[0].z); a true residual invalidates them
+  bool pre = false;
   auto precondition = [&](int slot) -> to_status {
     to_status e;
     if (mixed) {
-      if ((e = vcycle_graphed(c, c->r, T_D2, z32, T_F32)) != TO_OK) return e;
+      if ((e = vcycle_graphed(c, c->r, T_D2, z32, T_F32, pre)) != TO_OK) return e;
       LAUNCH(c, launch_dot_d2f(n, c->r, z32, c->partials, c->counters + C_DOT, c->scal + slot, s),
              "rz");
     } else {
@@ -1015,7 +1023,11 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
         LAUNCH(c, launch_dot_d2f(n, c->p, c->q32, c->partials, c->counters + C_DOT,
                                  c->scal + S_PQ, s), "pq");
         LAUNCH(c, launch_cg_xr_d2(n, x, c->r, c->p, c->q32, c->scal, cur, S_PQ, S_RR,
-                                  c->partials, c->counters + C_UPD, s), "x, r update");
+                                  c->partials, c->counters + C_UPD,
+                                  static_cast<float*>(c->lv[0].b), static_cast<float*>(c->lv[0].z),
+                                  static_cast<const float*>(c->lv[0].dinv), 0.6, s),
+               "x, r update");
+        pre = true;
       } else {
         if ((st = run_op(c, fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, c->p, c->q, nullptr,
                                       nullptr, EPI_APPLY), "q = K p")) != TO_OK)
@@ -1034,6 +1046,7 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
       // before convergence is declared.  The search direction is kept.
       if (mixed && (rel < rtol || rr < 1e-4 * rr_max)) {
         if ((st = true_residual(&rr)) != TO_OK) return st;
+        pre = false;
         rel = sqrt(rr) / c->fnorm;
         rr_max = rr;
       }

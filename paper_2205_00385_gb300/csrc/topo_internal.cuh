@@ -303,6 +303,7 @@ struct to_ctx {
     const void* zout;
     const void* coef;
     int zt;
+    bool pre;   // right-hand side and pre-smoothing already in place
     cudaGraphExec_t exec;
     long long launches;
   };
