@@ -39,7 +39,7 @@ struct ApplyArgs {
   const void* dinv;    // [n] of type tc
   double omega, dfix;
   int epi;
-  void* eo;            // explicit levels: per-element output rows [nel * ND] of type tc
+  const void* S;       // explicit levels: assembled stencil coefficients (type tc)
   const uint8_t* colfix = nullptr;   // per node column (i, j): 1 if any DOF of the
                                      // column is fixed (null: mask every node)
 };
@@ -90,6 +90,12 @@ cudaError_t launch_diag_l1(int t, const GridP& g1, const GridP& gf, const uint8_
                            const double* qdiag, const void* coef, void* dinv, cudaStream_t s);
 cudaError_t launch_galerkin_l2(int t, const GridP& g2, const GridP& gf, const void* coef,
                                const void* R, void* Kc, cudaStream_t s);
+// Assembled stencil of a stored level (16-byte coefficient groups, fixed
+// rows as identity rows, fixed columns zero) from its packed element
+// matrices; stencil_values gives its length in values of type t.
+cudaError_t launch_stencil_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
+                                    const void* Kc, void* S, cudaStream_t s);
+long long stencil_values(int dim, int t, const GridP& g);
 cudaError_t launch_dense_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
                                   const void* Kc, void* A, cudaStream_t s);
 cudaError_t launch_cholesky_inverse(int t, int n, void* A, void* Ainv, int* status,

@@ -229,135 +229,190 @@ __device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&
 }
 
 // ---------------------------------------------------------------------------
-// Coarse levels with stored Galerkin element matrices (element-major,
-// row-major 24x24 or 8x8 per element): one warp per element computes
-// eo_e = Kc_e x_e (lane r owns row r and loads it with 16-byte vector loads,
-// so all of an element's matrix is in flight at once); a node-centric gather
-// then sums the element rows belonging to each node in a fixed order.
+// Coarse levels with stored Galerkin element matrices are applied from their
+// assembled form: per DOF row, the coefficients of the 3^DIM neighbouring
+// nodes' DIM components (81 in 3D).  Boundary conditions are folded in at
+// assembly (fixed columns are zero, a fixed row is the identity row), so the
+// apply is a plain stencil product:  y_r = sum_q S_r[q] x[col(r, q)].
+// Coefficient qq of neighbour plane pz couples row r = DIM n + c with
+// component qq % DIM of the neighbour n + (dx, dy, dz), qq / DIM =
+// (dx+1) + 3 (dy+1), pz = dz + 1.  Layout: each plane's 9 DIM coefficients
+// are padded to a multiple of W = 16 / sizeof(T) and stored in W-wide groups
+// group-major, S[((pz GP + qq / W) rows + r) W + qq % W], so that a row's
+// coefficients are GP 16-byte loads per plane and a warp's load of one group
+// is 512 contiguous bytes.
 // ---------------------------------------------------------------------------
-// One warp per element: the element's packed upper triangle is staged in the
-// warp's slice of shared memory with 16-byte loads, then lane r forms row r
-// of K_e x_e reading K(r, c) symmetrically.
+template <int DIM, typename T>
+struct StencilLayout {
+  static constexpr int NP = DIM == 3 ? 3 : 1;          // neighbour planes
+  static constexpr int NQP = 9 * DIM;                  // coefficients per plane
+  static constexpr int W = 16 / (int)sizeof(T);        // values per group
+  static constexpr int GP = (NQP + W - 1) / W;         // groups per plane
+  __host__ __device__ static long long index(long long rows, long long r, int pz, int qq) {
+    return ((long long)(pz * GP + qq / W) * rows + r) * W + qq % W;
+  }
+  __host__ __device__ static long long values(long long rows) { return rows * NP * GP * W; }
+};
+
+// one thread per (row, padded slot): the sum over the elements containing
+// node n and its neighbour of the packed element matrix entry
+// (DIM a_n + c, DIM a_m + c'), elements in a fixed order; padding slots are 0
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
-    k_elem_gemv(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ Kc,
-                const T* __restrict__ x, T* __restrict__ eo) {
-  constexpr int ND = Geo<DIM>::ND, NT = tri_len(ND);
-  constexpr int VW = 16 / sizeof(T);                 // values per 16-byte load
-  static_assert((NT * sizeof(T)) % 16 == 0, "packed triangle must be a multiple of 16 bytes");
-  __shared__ __align__(16) T sk[8][NT];              // 8 warps per block
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  T* tk = sk[wib];
-  for (long long e = warp; e < g.nel; e += nwarps) {
-    const int ex = (int)(e % g.nx);
-    const long long rest = e / g.nx;
-    const int ey = (int)(rest % g.ny);
-    const int ez = DIM == 3 ? (int)(rest / g.ny) : 0;
-    T xv = T(0);
-    if (lane < ND) {
-      const int a = lane / DIM, c = lane % DIM;
-      const long long nd = (ex + (a & 1)) +
-                           (long long)g.nnx * ((ey + ((a >> 1) & 1)) +
-                                               (long long)g.nny * (DIM == 3 ? ez + ((a >> 2) & 1) : 0));
-      xv = ((mask[nd] >> c) & 1u) ? T(0) : x[DIM * nd + c];
-    }
-    const T* src = Kc + (size_t)e * NT;
-    for (int q = lane; q < NT / VW; q += 32) {
-      if constexpr (sizeof(T) == 4)
-        reinterpret_cast<float4*>(tk)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
-      else
-        reinterpret_cast<double2*>(tk)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
-    }
-    __syncwarp();
-    // K(lane, c): tri_idx(c, lane) below the diagonal, whose step from c to
-    // c + 1 is ND - 1 - c, then consecutive entries of row lane
-    T acc = T(0);
-    int idx = lane;
-#pragma unroll
-    for (int c = 0; c < ND; ++c) {
-      const T xc = __shfl_sync(0xffffffffu, xv, c);
-      if (lane < ND) acc = fma(tk[idx], xc, acc);
-      idx += (c < lane) ? (ND - 1 - c) : 1;
-    }
-    if (lane < ND) eo[(size_t)e * ND + lane] = acc;
-    __syncwarp();
-  }
-}
-
-template <int DIM, typename T, int EPI>
-__global__ void __launch_bounds__(256)
-    k_elem_gather(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ eo,
-                  const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ b,
-                  const T* __restrict__ dinv, T omega, T dfix) {
-  constexpr int ND = Geo<DIM>::ND;
-  constexpr int NZ = DIM == 3 ? 2 : 1;
-  // threads on the node grid: x lanes along i, block rows along j, z = k
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y;
-  const int k = DIM == 3 ? (int)blockIdx.z : 0;
-  if (i >= g.nnx || j >= g.nny) return;
-  const long long node = i + (long long)g.nnx * (j + (long long)g.nny * k);
-  T acc[DIM];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-#pragma unroll
-  for (int ez = 0; ez < NZ; ++ez)
-#pragma unroll
-    for (int ey = 0; ey < 2; ++ey)
-#pragma unroll
-      for (int ex = 0; ex < 2; ++ex) {
-        const int ei = i - 1 + ex, ej = j - 1 + ey, ek = k - 1 + ez;
-        bool in = ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
-        if (DIM == 3) in = in && ek >= 0 && ek < g.nz;
-        if (!in) continue;
-        const long long e = ei + (long long)g.nx * (ej + (long long)g.ny * (DIM == 3 ? ek : 0));
-        const int a = (1 - ex) + 2 * (1 - ey) + (DIM == 3 ? 4 * (1 - ez) : 0);
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) acc[c] += eo[(size_t)e * ND + DIM * a + c];
+    k_stencil_assemble(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ Kc,
+                       T* __restrict__ S) {
+  using SL = StencilLayout<DIM, T>;
+  constexpr int ND = Geo<DIM>::ND, NSLOT = SL::NP * SL::GP * SL::W;
+  const long long rows = DIM * g.nn;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * NSLOT) return;
+  const int slot = (int)(t / rows);
+  const long long r = t % rows;
+  const int pz = slot / (SL::GP * SL::W), qq = slot % (SL::GP * SL::W);
+  T s = T(0);
+  if (qq < SL::NQP) {
+    const long long n = r / DIM;
+    const int c = (int)(r % DIM), cp = qq % DIM, o = qq / DIM;
+    const int dx = o % 3 - 1, dy = o / 3 - 1, dz = DIM == 3 ? pz - 1 : 0;
+    const int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny);
+    const int k = DIM == 3 ? (int)(n / ((long long)g.nnx * g.nny)) : 0;
+    const int im = i + dx, jm = j + dy, km = k + dz;
+    bool in = im >= 0 && im < g.nnx && jm >= 0 && jm < g.nny;
+    if (DIM == 3) in = in && km >= 0 && km < g.nnz;
+    if (in) {
+      const long long m = im + (long long)g.nnx * (jm + (long long)g.nny * km);
+      if ((mask[n] >> c) & 1u) {
+        s = (m == n && cp == c) ? T(1) : T(0);     // fixed row: identity
+      } else if (!((mask[m] >> cp) & 1u)) {        // fixed column: zero
+        const int exlo = max(max(i, im) - 1, 0), exhi = min(min(i, im), g.nx - 1);
+        const int eylo = max(max(j, jm) - 1, 0), eyhi = min(min(j, jm), g.ny - 1);
+        const int ezlo = DIM == 3 ? max(max(k, km) - 1, 0) : 0;
+        const int ezhi = DIM == 3 ? min(min(k, km), g.nz - 1) : 0;
+        for (int ez = ezlo; ez <= ezhi; ++ez)
+          for (int ey = eylo; ey <= eyhi; ++ey)
+            for (int ex = exlo; ex <= exhi; ++ex) {
+              const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
+              const int ar = (i - ex) + 2 * (j - ey) + (DIM == 3 ? 4 * (k - ez) : 0);
+              const int ac = (im - ex) + 2 * (jm - ey) + (DIM == 3 ? 4 * (km - ez) : 0);
+              s += Kc[(size_t)e * tri_len(ND) + sym_idx(DIM * ar + c, DIM * ac + cp, ND)];
+            }
       }
-  const unsigned m = mask[node];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    const long long d = DIM * node + c;
-    const T Ax = ((m >> c) & 1u) ? dfix * x[d] : acc[c];
-    if (EPI == EPI_APPLY)
-      y[d] = Ax;
-    else if (EPI == EPI_RESID)
-      y[d] = b[d] - Ax;
-    else
-      y[d] = x[d] + omega * dinv[d] * (b[d] - Ax);
+    }
   }
+  S[SL::index(rows, r, pz, qq)] = s;
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  __device__ static float get(const float4& v, int l) {
+    return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w;
+  }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  __device__ static double get(const double2& v, int l) { return l == 0 ? v.x : v.y; }
+};
+
+// y = S x with the epilogue (K x, b - K x, or the damped Jacobi sweep); one
+// thread per row; each plane's coefficient groups and neighbour values are
+// all loaded before its sums, which run in a fixed order.
+template <int DIM, typename T, int EPI>
+__global__ void __launch_bounds__(256, 2)
+    k_stencil_apply(GridP g, const T* __restrict__ S, const T* __restrict__ x, T* __restrict__ y,
+                    const T* __restrict__ b, const T* __restrict__ dinv, T omega) {
+  using SL = StencilLayout<DIM, T>;
+  using VV = typename Vec16<T>::V;
+  const long long rows = DIM * g.nn;
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const long long n = r / DIM;
+  const int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny);
+  const int k = DIM == 3 ? (int)(n / ((long long)g.nnx * g.nny)) : 0;
+  // clamped neighbour indices (their coefficients are zero outside the grid)
+  int ix[3], jy[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ix[d] = min(max(i + d - 1, 0), g.nnx - 1);
+    jy[d] = min(max(j + d - 1, 0), g.nny - 1);
+  }
+  const VV* Sv = reinterpret_cast<const VV*>(S);
+  T acc = T(0);
+#pragma unroll
+  for (int pz = 0; pz < SL::NP; ++pz) {
+    const int kz = DIM == 3 ? min(max(k + pz - 1, 0), g.nnz - 1) : 0;
+    VV sv[SL::GP];
+    T xv[SL::NQP];
+#pragma unroll
+    for (int q = 0; q < SL::GP; ++q) sv[q] = __ldg(Sv + (long long)(pz * SL::GP + q) * rows + r);
+#pragma unroll
+    for (int qq = 0; qq < SL::NQP; ++qq) {
+      const int o = qq / DIM, cp = qq % DIM;
+      const long long m = ix[o % 3] + (long long)g.nnx * (jy[o / 3] + (long long)g.nny * kz);
+      xv[qq] = x[DIM * m + cp];
+    }
+#pragma unroll
+    for (int qq = 0; qq < SL::NQP; ++qq)
+      acc = fma(Vec16<T>::get(sv[qq / SL::W], qq % SL::W), xv[qq], acc);
+  }
+  if (EPI == EPI_APPLY)
+    y[r] = acc;
+  else if (EPI == EPI_RESID)
+    y[r] = b[r] - acc;
+  else
+    y[r] = x[r] + omega * dinv[r] * (b[r] - acc);
 }
 
 template <int DIM, typename T, int EPI>
-static cudaError_t run_expl(const ApplyArgs& a, cudaStream_t s) {
-  const long long warps = a.g.nel < 152LL * 64 ? a.g.nel : 152LL * 64;
-  k_elem_gemv<DIM, T><<<nblocks(warps * 32, 256), 256, 0, s>>>(
-      a.g, a.mask, static_cast<const T*>(a.Kc), static_cast<const T*>(a.x), static_cast<T*>(a.eo));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const dim3 ggrid((a.g.nnx + 31) / 32, (a.g.nny + 3) / 4, DIM == 3 ? a.g.nnz : 1);
-  k_elem_gather<DIM, T, EPI><<<ggrid, dim3(32, 4), 0, s>>>(
-      a.g, a.mask, static_cast<const T*>(a.eo), static_cast<const T*>(a.x), static_cast<T*>(a.y),
-      static_cast<const T*>(a.b), static_cast<const T*>(a.dinv), T(a.omega), T(a.dfix));
+static cudaError_t run_stencil(const ApplyArgs& a, cudaStream_t s) {
+  const long long rows = DIM * a.g.nn;
+  k_stencil_apply<DIM, T, EPI><<<nblocks(rows, 256), 256, 0, s>>>(
+      a.g, static_cast<const T*>(a.S), static_cast<const T*>(a.x), static_cast<T*>(a.y),
+      static_cast<const T*>(a.b), static_cast<const T*>(a.dinv), T(a.omega));
   return cudaGetLastError();
 }
 
 template <int DIM, typename T>
-static cudaError_t run_expl_epi(const ApplyArgs& a, cudaStream_t s) {
+static cudaError_t run_stencil_epi(const ApplyArgs& a, cudaStream_t s) {
   switch (a.epi) {
-    case EPI_APPLY: return run_expl<DIM, T, EPI_APPLY>(a, s);
-    case EPI_RESID: return run_expl<DIM, T, EPI_RESID>(a, s);
-    default: return run_expl<DIM, T, EPI_SMOOTH>(a, s);
+    case EPI_APPLY: return run_stencil<DIM, T, EPI_APPLY>(a, s);
+    case EPI_RESID: return run_stencil<DIM, T, EPI_RESID>(a, s);
+    default: return run_stencil<DIM, T, EPI_SMOOTH>(a, s);
   }
 }
 
+// the assembled form carries the identity rows of fixed DOFs, so only
+// dfix = 1 is representable
 static cudaError_t run_expl_any(const ApplyArgs& a, cudaStream_t s) {
-  if (a.tx != a.tc || a.ty != a.tc || a.eo == nullptr) return cudaErrorInvalidValue;
+  if (a.tx != a.tc || a.ty != a.tc || a.S == nullptr || a.dfix != 1.0) return cudaErrorInvalidValue;
   if (a.dim == 2)
-    return a.tc == T_F64 ? run_expl_epi<2, double>(a, s) : run_expl_epi<2, float>(a, s);
-  return a.tc == T_F64 ? run_expl_epi<3, double>(a, s) : run_expl_epi<3, float>(a, s);
+    return a.tc == T_F64 ? run_stencil_epi<2, double>(a, s) : run_stencil_epi<2, float>(a, s);
+  return a.tc == T_F64 ? run_stencil_epi<3, double>(a, s) : run_stencil_epi<3, float>(a, s);
+}
+
+template <int DIM, typename T>
+static cudaError_t stencil_t(const GridP& g, const uint8_t* mask, const void* Kc, void* S,
+                             cudaStream_t s) {
+  const long long tot = StencilLayout<DIM, T>::values((long long)DIM * g.nn);
+  k_stencil_assemble<DIM, T><<<nblocks(tot, 256), 256, 0, s>>>(g, mask, (const T*)Kc, (T*)S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
+                                    const void* Kc, void* S, cudaStream_t s) {
+  if (dim == 2) return t == T_F64 ? stencil_t<2, double>(g, mask, Kc, S, s)
+                                  : stencil_t<2, float>(g, mask, Kc, S, s);
+  return t == T_F64 ? stencil_t<3, double>(g, mask, Kc, S, s) : stencil_t<3, float>(g, mask, Kc, S, s);
+}
+
+long long stencil_values(int dim, int t, const GridP& g) {
+  const long long rows = (long long)dim * g.nn;
+  if (dim == 2)
+    return t == T_F64 ? StencilLayout<2, double>::values(rows) : StencilLayout<2, float>::values(rows);
+  return t == T_F64 ? StencilLayout<3, double>::values(rows) : StencilLayout<3, float>::values(rows);
 }
 
 // Element operator of the column-streaming kernel

@@ -338,7 +338,8 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
     lv[l].r = cv.take<char>(nl * ts);
     const bool stored = l >= 2 || (l == 1 && !l1_implicit);
     lv[l].Kc = stored ? (void*)cv.take<char>((size_t)tri_len(nd) * g.nel * ts) : nullptr;
-    lv[l].eo = stored ? (void*)cv.take<char>((size_t)nd * g.nel * ts) : nullptr;
+    lv[l].S = stored ? (void*)cv.take<char>((size_t)stencil_values(dim, mixed ? T_F32 : T_F64, g) * ts)
+                     : nullptr;
   }
   const long long nc = lv[L - 1].n;
   void* Ad = cv.take<char>((size_t)nc * nc * ts);
@@ -603,7 +604,7 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.wht = c->dim == 3 ? (wide ? (const void*)c->wht64 : (const void*)c->wht32) : nullptr;
   a.gal1 = false;
   a.gf = c->lv[0].g;
-  a.eo = nullptr;
+  a.S = nullptr;
   a.colfix = c->lv[0].colfix;
   a.x = x;
   a.y = y;
@@ -632,7 +633,7 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
   a.wht = nullptr;
   a.gal1 = false;
   a.gf = c->lv[0].g;
-  a.eo = c->lv[l].eo;
+  a.S = c->lv[l].S;
   a.colfix = c->lv[l].colfix;
   if (l == 1 && c->l1_implicit) {
     // level-1 Galerkin operator evaluated from the finest moduli
@@ -658,10 +659,9 @@ static double apply_bytes(const ApplyArgs& a) {
   const double sx = a.tx == T_F64 ? 8.0 : 4.0, sy = a.ty == T_F64 ? 8.0 : 4.0;
   const double sc = a.tc == T_F32 ? 4.0 : 8.0;
   const double n = (double)a.dim * (double)a.g.nn, nel = (double)a.g.nel;
-  const int nd = a.dim * (1 << a.dim);
-  double b = n * (sx + sy) + (double)a.g.nn;          // x, y, node masks
-  b += a.expl ? (double)nd * nd * nel * sc             // element matrices,
-              : (a.gal1 ? 8.0 : 1.0) * nel * sc;       // or (child) moduli
+  double b = n * (sx + sy);                             // x, y
+  b += a.expl ? n * (a.dim == 3 ? 27 : 9) * a.dim * sc   // assembled stencil,
+              : (double)a.g.nn + (a.gal1 ? 8.0 : 1.0) * nel * sc;   // or masks and (child) moduli
   if (a.epi != EPI_APPLY) b += n * sx;                 // right-hand side
   if (a.epi == EPI_SMOOTH) b += n * sc;                // inverse diagonal
   return b;
@@ -698,9 +698,12 @@ static to_status build_hierarchy(to_ctx* c) {
   for (int l = lfirst; l < c->L; ++l)
     LAUNCH(c, launch_galerkin_coarse(c->dim, t, c->lv[l].g, c->lv[l - 1].g, c->lv[l - 1].Kc,
                                      c->lv[l].Kc, s), "galerkin l");
-  for (int l = c->l1_implicit ? 2 : 1; l < c->L; ++l)
+  for (int l = c->l1_implicit ? 2 : 1; l < c->L; ++l) {
     LAUNCH(c, launch_diag(c->dim, c->lv[l].g, c->lv[l].mask, t, true, nullptr, c->lv[l].Kc,
                           nullptr, c->lv[l].dinv, s), "diag l");
+    LAUNCH(c, launch_stencil_assemble(c->dim, t, c->lv[l].g, c->lv[l].mask, c->lv[l].Kc,
+                                      c->lv[l].S, s), "stencil l");
+  }
   const int Lc = c->L - 1;
   LAUNCH(c, launch_dense_assemble(c->dim, t, c->lv[Lc].g, c->lv[Lc].mask, c->lv[Lc].Kc,
                                   c->Adense, s), "dense assemble");

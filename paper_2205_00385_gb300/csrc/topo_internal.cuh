@@ -240,7 +240,7 @@ struct LevelBuf {
   void* z2;              // T[n]
   void* r;               // T[n]
   void* Kc;              // T[nel*tri_len(ND)], packed upper triangles (stored levels)
-  void* eo;              // T[nel*ND]: per-element operator rows (stored levels)
+  void* S;               // T[DIM*nn * 3^DIM*DIM]: assembled stencil (stored levels)
 };
 
 struct to_ctx {
