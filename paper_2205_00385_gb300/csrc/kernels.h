@@ -50,6 +50,8 @@ bool pair_apply_ok(const ApplyArgs& a);
 cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s);
 // caches the pair kernel's resident-block counts for the current device
 void pair_prepare();
+// occupancy queries of the level-1 Galerkin column kernel (call at set-up)
+void col_prepare();
 // colfix[i + nnx j] = 1 if any node (i, j, k) of the grid has a fixed DOF
 cudaError_t launch_colfix(const GridP& g, const uint8_t* mask, uint8_t* colfix, cudaStream_t s);
 // Double-float finest-grid operator (kernels_df.cu): float64 x/b/y, float64

@@ -419,7 +419,7 @@ long long stencil_values(int dim, int t, const GridP& g) {
 enum { OPK_FINE = 0, OPK_GAL1 = 1 };
 
 template <typename TC, typename TX, typename TY, int EPI, int OP>
-__global__ void __launch_bounds__(WX * WY)
+__global__ void __launch_bounds__(WX * WY, (OP == OPK_GAL1 && sizeof(TC) == 4) ? 4 : 1)
     k_apply3_col(GridP g, GridP gf, const uint8_t* __restrict__ mask, WhtBlocks<TC> kb,
                  const TC* __restrict__ coef, int zc, const TX* __restrict__ x,
                  TY* __restrict__ y, const TX* __restrict__ b, const TC* __restrict__ dinv,
@@ -617,6 +617,30 @@ static cudaError_t run_apply_dim(const ApplyArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+// resident blocks of the float32 level-1 Galerkin column kernel (cached per
+// device; queried at set-up, outside any stream capture)
+template <int EPI>
+static long long gal1_slots() {
+  static long long cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cache[dev] > 0) return cache[dev];
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, k_apply3_col<float, float, float, EPI, OPK_GAL1>, WX * WY, 0) != cudaSuccess ||
+      sms <= 0 || per_sm <= 0)
+    return 0;
+  cache[dev] = (long long)sms * per_sm;
+  return cache[dev];
+}
+
+void col_prepare() {
+  gal1_slots<EPI_APPLY>();
+  gal1_slots<EPI_RESID>();
+  gal1_slots<EPI_SMOOTH>();
+}
+
 template <typename TC, typename TX, typename TY, int EPI, int OP>
 static cudaError_t run_col(const ApplyArgs& a, cudaStream_t s) {
   WhtBlocks<TC> kb;
@@ -627,6 +651,21 @@ static cudaError_t run_col(const ApplyArgs& a, cudaStream_t s) {
   // launch still covers the GPU (each chunk recomputes one element layer)
   int zc = WZC;
   while (zc > 2 && (long long)gx * gy * ((a.g.nnz + zc - 1) / zc) < 2 * 152) zc /= 2;
+  // level-1 Galerkin operator (latency-bound, one block per column chunk):
+  // the chunk length minimising waves x (layers + 1 recomputed)
+  const long long slots =
+      (OP == OPK_GAL1 && sizeof(TC) == 4 && sizeof(TX) == 4 && sizeof(TY) == 4) ? gal1_slots<EPI>() : 0;
+  if (slots > 0) {
+    long long best = -1;
+    for (int c = 2; c <= WZC; ++c) {
+      const long long blocks = (long long)gx * gy * ((a.g.nnz + c - 1) / c);
+      const long long cost = ((blocks + slots - 1) / slots) * (c + 1);
+      if (best < 0 || cost < best || (cost == best && c > zc)) {
+        best = cost;
+        zc = c;
+      }
+    }
+  }
   dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
   k_apply3_col<TC, TX, TY, EPI, OP><<<grid, WX * WY, 0, s>>>(
       a.g, a.gf, a.mask, kb, static_cast<const TC*>(a.coef), zc, static_cast<const TX*>(a.x),
