@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(256, 2)
   using VV = typename Vec16<T>::V;
   const long long rows = DIM * g.nn;
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
   if (r >= rows) return;
   const long long n = r / DIM;
   const int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny);
@@ -364,15 +365,15 @@ __global__ void __launch_bounds__(256, 2)
     y[r] = b[r] - acc;
   else
     y[r] = x[r] + omega * dinv[r] * (b[r] - acc);
+  pdl_launch_dependents();
 }
 
 template <int DIM, typename T, int EPI>
 static cudaError_t run_stencil(const ApplyArgs& a, cudaStream_t s) {
   const long long rows = DIM * a.g.nn;
-  k_stencil_apply<DIM, T, EPI><<<nblocks(rows, 256), 256, 0, s>>>(
-      a.g, static_cast<const T*>(a.S), static_cast<const T*>(a.x), static_cast<T*>(a.y),
-      static_cast<const T*>(a.b), static_cast<const T*>(a.dinv), T(a.omega));
-  return cudaGetLastError();
+  return launch_pdl(k_stencil_apply<DIM, T, EPI>, dim3(nblocks(rows, 256)), dim3(256), 0, s, a.g,
+                    static_cast<const T*>(a.S), static_cast<const T*>(a.x), static_cast<T*>(a.y),
+                    static_cast<const T*>(a.b), static_cast<const T*>(a.dinv), T(a.omega));
 }
 
 template <int DIM, typename T>
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(WX * WY, (OP == OPK_GAL1 && sizeof(TC) == 4) ?
   using TE = typename std::conditional<(sizeof(TY) > sizeof(TC)), double, TC>::type;
   constexpr bool GAL1 = OP == OPK_GAL1;
   __shared__ TC part[2][4][WY][WX][3];
+  pdl_wait();
   const int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
   const int x0 = blockIdx.x * WOX, y0 = blockIdx.y * WOY;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nnz);
@@ -531,6 +533,7 @@ __global__ void __launch_bounds__(WX * WY, (OP == OPK_GAL1 && sizeof(TC) == 4) ?
     }
     buf ^= 1;
   }
+  pdl_launch_dependents();
 }
 
 template <int DIM, typename TC, bool EXPL>
@@ -667,11 +670,10 @@ static cudaError_t run_col(const ApplyArgs& a, cudaStream_t s) {
     }
   }
   dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
-  k_apply3_col<TC, TX, TY, EPI, OP><<<grid, WX * WY, 0, s>>>(
-      a.g, a.gf, a.mask, kb, static_cast<const TC*>(a.coef), zc, static_cast<const TX*>(a.x),
-      static_cast<TY*>(a.y), static_cast<const TX*>(a.b), static_cast<const TC*>(a.dinv),
-      TC(a.omega), TC(a.dfix));
-  return cudaGetLastError();
+  return launch_pdl(k_apply3_col<TC, TX, TY, EPI, OP>, grid, dim3(WX * WY), 0, s, a.g, a.gf, a.mask,
+                    kb, static_cast<const TC*>(a.coef), zc, static_cast<const TX*>(a.x),
+                    static_cast<TY*>(a.y), static_cast<const TX*>(a.b),
+                    static_cast<const TC*>(a.dinv), TC(a.omega), TC(a.dfix));
 }
 
 template <typename TC, typename TX, typename TY, int OP>

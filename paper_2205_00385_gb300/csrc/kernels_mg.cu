@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
   constexpr int NZ = DIM == 3 ? 3 : 1;
   const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
   const int K = DIM == 3 ? (int)blockIdx.z : 0;
+  pdl_wait();
   if (I >= gc.nnx || J >= gc.nny) return;
   unsigned m[NZ][3][3];
   T v[NZ][3][3][DIM];
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     // the coarse level's pre-smoothing from a zero guess, z = omega D^-1 b
     if (zc) zc[d] = omega * dinvc[d] * bv;
   }
+  pdl_launch_dependents();
 }
 
 // z_f += Pm z_c: fine node (i,j,k) interpolates from coarse nodes
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
   constexpr int NK = DIM == 3 ? 2 : 1;   // fine nodes per thread along z
   const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
   const int q = DIM == 3 ? (int)blockIdx.z : 0;
+  pdl_wait();
   if (i >= gf.nnx || j >= gf.nny) return;
   const int i0 = i >> 1, j0 = j >> 1;
   const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
@@ -170,6 +173,7 @@ __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     for (int c = 0; c < DIM; ++c)
       if (!((m[s] >> c) & 1u)) zf[DIM * node + c] = zv[s][c] + acc[c];
   }
+  pdl_launch_dependents();
 }
 
 template <typename T, typename TIN>
@@ -177,10 +181,12 @@ __global__ void __launch_bounds__(256)
     k_presmooth(long long n, const TIN* __restrict__ bin, T* __restrict__ bout,
                 const T* __restrict__ dinv, T omega, T* __restrict__ z) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
   if (q >= n) return;
   const T bv = cvt<T>(bin[q]);
   if (bout) bout[q] = bv;
   z[q] = omega * dinv[q] * bv;
+  pdl_launch_dependents();
 }
 
 template <typename TIN, typename TOUT>
@@ -527,12 +533,14 @@ __global__ void __launch_bounds__(256)
     k_gemv(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  pdl_wait();
   if (warp >= n) return;
   T s = T(0);
   for (int m = lane; m < n; m += 32) s += A[(size_t)warp * n + m] * x[m];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) y[warp] = s;
+  pdl_launch_dependents();
 }
 
 // ---------------------------------------------------------------------------
@@ -544,9 +552,8 @@ static cudaError_t restrict_t(const GridP& gf, const uint8_t* mf, const GridP& g
                               double omega, void* zc, cudaStream_t s) {
   if (gc.nn <= 0) return cudaSuccess;
   dim3 grid((gc.nnx + TBX - 1) / TBX, (gc.nny + TBY - 1) / TBY, DIM == 3 ? gc.nnz : 1);
-  k_restrict<DIM, T><<<grid, dim3(TBX, TBY), 0, s>>>(gf, mf, gc, mc, (const T*)rf, (T*)bc,
-                                                       (const T*)dinvc, T(omega), (T*)zc);
-  return cudaGetLastError();
+  return launch_pdl(k_restrict<DIM, T>, grid, dim3(TBX, TBY), 0, s, gf, mf, gc, mc, (const T*)rf,
+                    (T*)bc, (const T*)dinvc, T(omega), (T*)zc);
 }
 
 cudaError_t launch_restrict(int dim, int t, const GridP& gf, const uint8_t* mf, const GridP& gc,
@@ -564,8 +571,8 @@ static cudaError_t prolong_t(const GridP& gf, const uint8_t* mf, const GridP& gc
                              void* zf, cudaStream_t s) {
   if (gf.nn <= 0) return cudaSuccess;
   dim3 grid((gf.nnx + TBX - 1) / TBX, (gf.nny + TBY - 1) / TBY, DIM == 3 ? (gf.nnz + 1) / 2 : 1);
-  k_prolong_add<DIM, T><<<grid, dim3(TBX, TBY), 0, s>>>(gf, mf, gc, (const T*)zc, (T*)zf);
-  return cudaGetLastError();
+  return launch_pdl(k_prolong_add<DIM, T>, grid, dim3(TBX, TBY), 0, s, gf, mf, gc, (const T*)zc,
+                    (T*)zf);
 }
 
 cudaError_t launch_prolong_add(int dim, int t, const GridP& gf, const uint8_t* mf,
@@ -581,17 +588,17 @@ cudaError_t launch_presmooth(int t, int tin, long long n, const void* bin, void*
   const int nb = nblocks(n, 256);
   if (t == T_F64) {
     if (tin != T_F64) return cudaErrorInvalidValue;
-    k_presmooth<double, double><<<nb, 256, 0, s>>>(n, (const double*)bin, (double*)bout,
-                                                   (const double*)dinv, omega, (double*)z);
+    return launch_pdl(k_presmooth<double, double>, dim3(nb), dim3(256), 0, s, n,
+                      (const double*)bin, (double*)bout, (const double*)dinv, omega, (double*)z);
   } else if (tin == T_F64) {
-    k_presmooth<float, double><<<nb, 256, 0, s>>>(n, (const double*)bin, (float*)bout,
-                                                  (const float*)dinv, (float)omega, (float*)z);
+    return launch_pdl(k_presmooth<float, double>, dim3(nb), dim3(256), 0, s, n,
+                      (const double*)bin, (float*)bout, (const float*)dinv, (float)omega, (float*)z);
   } else if (tin == T_D2) {
-    k_presmooth<float, float2><<<nb, 256, 0, s>>>(n, (const float2*)bin, (float*)bout,
-                                                  (const float*)dinv, (float)omega, (float*)z);
+    return launch_pdl(k_presmooth<float, float2>, dim3(nb), dim3(256), 0, s, n,
+                      (const float2*)bin, (float*)bout, (const float*)dinv, (float)omega, (float*)z);
   } else {
-    k_presmooth<float, float><<<nb, 256, 0, s>>>(n, (const float*)bin, (float*)bout,
-                                                 (const float*)dinv, (float)omega, (float*)z);
+    return launch_pdl(k_presmooth<float, float>, dim3(nb), dim3(256), 0, s, n,
+                      (const float*)bin, (float*)bout, (const float*)dinv, (float)omega, (float*)z);
   }
   return cudaGetLastError();
 }
@@ -726,9 +733,11 @@ cudaError_t launch_dense_gemv(int t, int n, const void* A, const void* x, void* 
                               cudaStream_t s) {
   const int nb = nblocks((long long)n * 32, 256);
   if (t == T_F64)
-    k_gemv<double><<<nb, 256, 0, s>>>(n, (const double*)A, (const double*)x, (double*)y);
+    return launch_pdl(k_gemv<double>, dim3(nb), dim3(256), 0, s, n, (const double*)A,
+                      (const double*)x, (double*)y);
   else
-    k_gemv<float><<<nb, 256, 0, s>>>(n, (const float*)A, (const float*)x, (float*)y);
+    return launch_pdl(k_gemv<float>, dim3(nb), dim3(256), 0, s, n, (const float*)A,
+                      (const float*)x, (float*)y);
   return cudaGetLastError();
 }
 

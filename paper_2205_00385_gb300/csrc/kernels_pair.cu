@@ -352,12 +352,16 @@ __global__ void __launch_bounds__(PX * PY, EPI == EPI_APPLY ? 4 : 3)
     for (int n = 0; n < 3; ++n)
       if (a.colfix && i + n >= 0 && i + n < a.g.nnx && j + r >= 0 && j + r < a.g.nny)
         flag |= a.colfix[(i + n) + (long long)a.g.nnx * (j + r)] != 0;
+  // (the column flags are set up once; everything below reads the vectors
+  // of preceding kernels)
+  pdl_wait();
   // all threads of a block must take the same branch (both contain
   // __syncthreads), so the decision is block-wide
   if (__syncthreads_or(flag))
     pair_loop<EPI, true>(a, kb, sm);
   else
     pair_loop<EPI, false>(a, kb, sm);
+  pdl_launch_dependents();
 }
 
 __global__ void k_colfix(GridP g, const uint8_t* __restrict__ mask, uint8_t* __restrict__ colfix) {
@@ -452,9 +456,9 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   p.zc = (a.g.nnz + best - 1) / best;
   dim3 grid(gx, gy, best);
   switch (a.epi) {
-    case EPI_APPLY: k_apply3_pair<EPI_APPLY><<<grid, PX * PY, 0, s>>>(p, kb); break;
-    case EPI_RESID: k_apply3_pair<EPI_RESID><<<grid, PX * PY, 0, s>>>(p, kb); break;
-    default: k_apply3_pair<EPI_SMOOTH><<<grid, PX * PY, 0, s>>>(p, kb); break;
+    case EPI_APPLY: return launch_pdl(k_apply3_pair<EPI_APPLY>, grid, dim3(PX * PY), 0, s, p, kb);
+    case EPI_RESID: return launch_pdl(k_apply3_pair<EPI_RESID>, grid, dim3(PX * PY), 0, s, p, kb);
+    default: return launch_pdl(k_apply3_pair<EPI_SMOOTH>, grid, dim3(PX * PY), 0, s, p, kb);
   }
   return cudaGetLastError();
 }

@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(RED_THREADS)
               double* partials, unsigned* counter, double* out) {
   using Rg = Ar<float2>;
   __shared__ double sh[32];
+  pdl_wait();
   dfl v[2] = {Rg::zero(), Rg::zero()};
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   }
   for (; k < n; k += stride) df_dot_acc(v[0], Rg::ld(a, k), dfl{b[k], 0.f});
   reduce_to<float2>(df_add(df_norm(v[0]), df_norm(v[1])), out, partials, counter, sh);
+  pdl_launch_dependents();
 }
 
 // alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q; scal[rr] = |r|^2.
@@ -483,6 +485,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   using Rg = Ar<float2>;
   __shared__ double sh[32];
   __shared__ double s_alpha;
+  pdl_wait();
   if (threadIdx.x == 0) s_alpha = scal[num] / scal[den];
   __syncthreads();
   const dfl al = split_d(s_alpha), mal = {-al.h, -al.l};
@@ -519,6 +522,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   for (; k < n; k += stride)
     step(k, Rg::ld(x, k), Rg::ld(p, k), Rg::ld(r, k), q[k], PRE ? dinv[k] : 0.f, v[0]);
   reduce_to<float2>(df_add(df_norm(v[0]), df_norm(v[1])), scal + rr, partials, counter, sh);
+  pdl_launch_dependents();
 }
 
 // p = z + beta p (beta = scal[num]/scal[den], or p = z when num < 0);
@@ -528,6 +532,7 @@ __global__ void __launch_bounds__(256)
               const float* __restrict__ z, const double* __restrict__ scal, int num, int den) {
   using Rg = Ar<float2>;
   __shared__ double s_beta;
+  pdl_wait();
   if (threadIdx.x == 0) s_beta = num >= 0 ? scal[num] / scal[den] : 0.0;
   __syncthreads();
   const dfl be = split_d(s_beta);
@@ -551,6 +556,7 @@ __global__ void __launch_bounds__(256)
     for (int u = 0; u < CG_U; ++u) step(k + u * stride, zv[u], pv[u]);
   }
   for (; k < n; k += stride) step(k, z[k], num >= 0 ? Rg::ld(p, k) : Rg::zero());
+  pdl_launch_dependents();
 }
 
 #undef GRID_LOOP
@@ -680,8 +686,8 @@ cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double
 
 cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* partials,
                            unsigned* counter, double* out, cudaStream_t s) {
-  k_dot_d2f<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (const float2*)a, b, partials, counter, out);
-  return cudaGetLastError();
+  return launch_pdl(k_dot_d2f, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n, (const float2*)a, b,
+                    partials, counter, out);
 }
 
 cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const float* q,
@@ -689,22 +695,18 @@ cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const 
                             unsigned* counter, float* b, float* zpre, const float* dinv,
                             double omega, cudaStream_t s) {
   if (b)
-    k_cg_xr_d2<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (float2*)x, (float2*)r,
-                                                        (const float2*)p, q, scal, num, den, rr,
-                                                        partials, counter, b, zpre, dinv,
-                                                        (float)omega);
-  else
-    k_cg_xr_d2<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (float2*)x, (float2*)r,
-                                                         (const float2*)p, q, scal, num, den, rr,
-                                                         partials, counter, nullptr, nullptr,
-                                                         nullptr, 0.f);
-  return cudaGetLastError();
+    return launch_pdl(k_cg_xr_d2<true>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n, (float2*)x,
+                      (float2*)r, (const float2*)p, q, scal, num, den, rr, partials, counter, b,
+                      zpre, dinv, (float)omega);
+  return launch_pdl(k_cg_xr_d2<false>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n, (float2*)x,
+                    (float2*)r, (const float2*)p, q, scal, num, den, rr, partials, counter,
+                    (float*)nullptr, (float*)nullptr, (const float*)nullptr, 0.f);
 }
 
 cudaError_t launch_cg_p_d2(long long n, void* p, float* p32, const float* z, const double* scal,
                            int num, int den, cudaStream_t s) {
-  k_cg_p_d2<<<vgrid(n), 256, 0, s>>>(n, (float2*)p, p32, z, scal, num, den);
-  return cudaGetLastError();
+  return launch_pdl(k_cg_p_d2, dim3(vgrid(n)), dim3(256), 0, s, n, (float2*)p, p32, z, scal, num,
+                    den);
 }
 
 }  // namespace topo

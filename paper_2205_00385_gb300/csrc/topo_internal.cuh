@@ -172,6 +172,33 @@ __device__ __forceinline__ void block_max(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl() may be
+// scheduled while its predecessor in the stream is still running.  It calls
+// pdl_wait() before touching memory a preceding kernel writes (it returns
+// once every preceding grid has completed and its writes are visible; a
+// no-op for an ordinary launch), and pdl_launch_dependents() when its own
+// work is issued, which lets the next such kernel start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Writes this block's partials; returns true in all threads of the last block
 // to arrive (which may then read all partials).  counter is reset by it.
 template <int NV>
