@@ -52,6 +52,8 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s);
 void pair_prepare();
 // occupancy queries of the level-1 Galerkin column kernel (call at set-up)
 void col_prepare();
+// occupancy queries of the pair-storage double-float operator (call at set-up)
+void df_prepare();
 // colfix[i + nnx j] = 1 if any node (i, j, k) of the grid has a fixed DOF
 cudaError_t launch_colfix(const GridP& g, const uint8_t* mask, uint8_t* colfix, cudaStream_t s);
 // Double-float finest-grid operator (kernels_df.cu): float64 x/b/y, float64

@@ -172,6 +172,29 @@ bool df_blocks_ok(const double* wht64) {
   return true;
 }
 
+// resident blocks of the pair-storage double-float kernel (cached per device;
+// queried at set-up, outside any stream capture)
+template <int EPI>
+static long long df_slots() {
+  static long long cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cache[dev] > 0) return cache[dev];
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply3_df<EPI, float2>, DX * DY, 0) !=
+          cudaSuccess ||
+      sms <= 0 || per_sm <= 0)
+    return 0;
+  cache[dev] = (long long)sms * per_sm;
+  return cache[dev];
+}
+
+void df_prepare() {
+  df_slots<EPI_APPLY>();
+  df_slots<EPI_RESID>();
+}
+
 template <typename S>
 static void run_df(const ApplyArgs& a, const DfBlocks& kb, dim3 grid, int zc, cudaStream_t s) {
   if (a.epi == EPI_RESID)
@@ -199,6 +222,21 @@ cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s) {
   const int gx = (a.g.nnx + DOX - 1) / DOX, gy = (a.g.nny + DOY - 1) / DOY;
   int zc = 16;
   while (zc > 2 && (long long)gx * gy * ((a.g.nnz + zc - 1) / zc) < 2 * 152) zc /= 2;
+  // pair storage (the mixed path's accurate products): the chunk length
+  // minimising waves x (layers + 1 recomputed) for the queried occupancy
+  const long long slots =
+      a.tx == T_D2 ? (a.epi == EPI_RESID ? df_slots<EPI_RESID>() : df_slots<EPI_APPLY>()) : 0;
+  if (slots > 0) {
+    long long best = -1;
+    for (int c = 2; c <= a.g.nnz; ++c) {
+      const long long blocks = (long long)gx * gy * ((a.g.nnz + c - 1) / c);
+      const long long cost = ((blocks + slots - 1) / slots) * (c + 1);
+      if (best < 0 || cost < best) {
+        best = cost;
+        zc = c;
+      }
+    }
+  }
   dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
   if (a.tx == T_D2)
     run_df<float2>(a, kb, grid, zc, s);

@@ -519,6 +519,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   if (c->dim == 3) {
     pair_prepare();
     col_prepare();
+    df_prepare();
   }
   for (int l = 0; l < c->L; ++l)
     INIT_TRY(launch_colfix(c->lv[l].g, c->lv[l].mask, c->lv[l].colfix, s), "column flags");
