@@ -516,6 +516,56 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// X = L^{-1} by column blocks: CTA jb owns the 32 columns jb*32 .. jb*32+31
+// of X (zero above row block jb) and walks the row blocks ib = jb, jb+1, ...
+// downwards: R = I(ib, jb) - sum_{kb < ib} L(ib, kb) X(kb, jb) (32 x 32
+// products, the L block staged in shared memory, the X column block kept
+// there), then one warp solves L(ib, ib) X(ib, jb) = R by forward
+// substitution, a column per lane.  1024 threads: (ty, tx) = (row, column)
+// within a block.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_lower_inverse_blocked(int n, const T* __restrict__ L,
+                                                                T* __restrict__ X) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nbk = (n + 31) / 32;
+  T* Xs = reinterpret_cast<T*>(smem_raw);   // [nbk * 32][32]
+  T* Ls = Xs + (size_t)nbk * 32 * 32;       // [32][33]
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int jb = blockIdx.x;
+  for (int ib = jb; ib < nbk; ++ib) {
+    T r = (ib == jb && ty == tx) ? T(1) : T(0);
+    const int lr = ib * 32 + ty;
+    for (int kb = jb; kb < ib; ++kb) {
+      const int lc = kb * 32 + tx;
+      Ls[ty * 33 + tx] = (lr < n && lc < n) ? L[(size_t)lr * n + lc] : T(0);
+      __syncthreads();
+#pragma unroll 8
+      for (int m = 0; m < 32; ++m) r -= Ls[ty * 33 + m] * Xs[(kb * 32 + m) * 32 + tx];
+      __syncthreads();
+    }
+    // diagonal block (identity beyond n, so padded rows solve to zero)
+    {
+      const int dc = ib * 32 + tx;
+      Ls[ty * 33 + tx] = (lr < n && dc < n) ? L[(size_t)lr * n + dc] : (ty == tx ? T(1) : T(0));
+    }
+    Xs[(ib * 32 + ty) * 32 + tx] = r;
+    __syncthreads();
+    if (ty == 0) {
+      T* xb = Xs + (size_t)ib * 32 * 32;
+      for (int k = 0; k < 32; ++k) {
+        T v = xb[k * 32 + tx];
+        for (int m = 0; m < k; ++m) v -= Ls[k * 33 + m] * xb[m * 32 + tx];
+        xb[k * 32 + tx] = v / Ls[k * 33 + k];
+      }
+    }
+    __syncthreads();
+  }
+  const int col = jb * 32 + tx;
+  if (col < n)
+    for (int row = ty; row < n; row += 32)
+      X[(size_t)row * n + col] = row >= jb * 32 ? Xs[row * 32 + tx] : T(0);
+}
+
 // Ainv = X^T X (X = L^{-1} lower triangular): Ainv[i][j] = sum_{m>=max(i,j)} X[m][i] X[m][j]
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -714,7 +764,16 @@ static cudaError_t cholinv_t(int n, void* A, void* Ainv, int* status, cudaStream
   if (e != cudaSuccess) return e;
   // Ainv is used as scratch for L^{-1} first, then A receives X^T X and
   // the buffers are swapped by copying back.
-  k_lower_inverse<T><<<nblocks((long long)n * 32, 256), 256, 0, s>>>(n, (const T*)A, (T*)Ainv);
+  const int nbk = (n + 31) / 32;
+  const size_t ismem = ((size_t)nbk * 32 * 32 + 32 * 33) * sizeof(T);
+  if (ismem <= 227 * 1024) {
+    e = cudaFuncSetAttribute(k_lower_inverse_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ismem);
+    if (e != cudaSuccess) return e;
+    k_lower_inverse_blocked<T><<<nbk, 1024, ismem, s>>>(n, (const T*)A, (T*)Ainv);
+  } else {
+    k_lower_inverse<T><<<nblocks((long long)n * 32, 256), 256, 0, s>>>(n, (const T*)A, (T*)Ainv);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_gram_lower<T><<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, (const T*)Ainv, (T*)A);
