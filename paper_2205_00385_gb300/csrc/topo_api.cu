@@ -1138,15 +1138,15 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
     const int bound = std::max(i, 1);   // accepted columns so far <= i
     LAUNCH(c, launch_vdot(n, v, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM0, s),
            "|r|");
+    // two classical passes; the second also returns |r_i|^2 after them
     for (int pass = 0; pass < 2; ++pass) {
       LAUNCH(c, launch_gram(n, v, c->R, bound, c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
                             MAXB, c->partials, c->counters + C_MULTI, s), "GS dots");
       LAUNCH(c, launch_combine(n, v, c->R, bound, c->ints + I_KCOUNT, small + SM_H, -1.0, 1.0,
-                               ri, v, nullptr, nullptr, c->partials, c->counters + C_UPD, s),
+                               ri, v, nullptr, pass == 1 ? c->scal + S_NRM1 : nullptr,
+                               c->partials, c->counters + C_UPD, s),
              "GS axpy");
     }
-    LAUNCH(c, launch_vdot(n, v, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM1, s),
-           "|r|");
     LAUNCH(c, launch_gs_accept(n, v, c->R, i, c->scal, S_NRM0, S_NRM1, 1e-10, c->ints, s),
            "GS accept");
   }
