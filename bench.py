@@ -187,8 +187,8 @@ def _traffic_from_profiles(kernel_tag: str):
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     rec = {}
     for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
+        if ": " in line and line.startswith("- "):
+            k, v = line[2:].split(": ", 1)   # keys may hold a colon ("sha256[:16]")
             rec[k.strip()] = v.strip().strip("`")
     if rec.get("kernels_pair.cu sha256[:16]") != sha:
         return None
