@@ -182,6 +182,14 @@ cudaError_t launch_filter(int dim, const GridP& g, const StencilP& st, int mode,
                           const double* invHs, const double* in, double* out, cudaStream_t s);
 cudaError_t launch_filter_norm(int dim, const GridP& g, const StencilP& st, double* invHs,
                                cudaStream_t s);
+// 3D compliance and sensitivity in double-float arithmetic (mixed path);
+// needs the Walsh blocks and an integer penal in [1, 9]
+bool sensitivity_df_ok(int dim, double penal);
+cudaError_t launch_sensitivity_df(const GridP& g, const uint8_t* mask, const double* wht,
+                                  const double* u, const double* E, const double* rho,
+                                  double penal, double E0, double Emin, double* dc,
+                                  double* compliance, double* partials, unsigned* counter,
+                                  cudaStream_t s);
 // wht: host pointer to the float64 Walsh blocks of KE (3D), else null
 cudaError_t launch_sensitivity(int dim, const GridP& g, const uint8_t* mask, const double* ke,
                                const double* wht, const double* u, const double* E,

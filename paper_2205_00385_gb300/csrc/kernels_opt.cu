@@ -74,6 +74,79 @@ __global__ void __launch_bounds__(256)
     out[e] = 1.0 / acc;
 }
 
+// Double-float Walsh blocks of KE (hi and lo parts of each float64 entry)
+struct WhtDf {
+  float h[8][3][3], l[8][3][3];
+};
+
+// 3D compliance and sensitivity of k_sensitivity3_wht in double-float
+// arithmetic (mixed path), for an integer penalisation exponent:
+// dc_e = pfac rho_e^ipen ce_e with pfac = -penal (E0 - Emin), ipen = penal - 1.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_sensitivity3_df(GridP g, const uint8_t* __restrict__ mask, WhtDf kb,
+                      const double* __restrict__ u, const double* __restrict__ E,
+                      const double* __restrict__ rho, double pfac, int ipen,
+                      double* __restrict__ dc, double* compliance, double* partials,
+                      unsigned* counter) {
+  __shared__ double sh[32];
+  const dfl pf = split_d(pfac);
+  dfl v[1] = {{0.f, 0.f}};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.nel;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int ex = (int)(e % g.nx);
+    const long long rest = e / g.nx;
+    const int ey = (int)(rest % g.ny);
+    const int ez = (int)(rest / g.ny);
+    dfl X[3][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int i = ex + (a & 1), j = ey + ((a >> 1) & 1), k = ez + ((a >> 2) & 1);
+      const long long nd = i + (long long)g.nnx * (j + (long long)g.nny * k);
+      const unsigned m = mask[nd];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        X[c][a] = ((m >> c) & 1u) ? dfl{0.f, 0.f} : split_d(u[3 * nd + c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (!(a & h)) {
+            const dfl p = X[c][a], q = X[c][a + h];
+            X[c][a] = df_add(p, q);
+            X[c][a + h] = df_add(p, df_neg(q));
+          }
+    dfl ce = {0.f, 0.f};
+#pragma unroll
+    for (int tau = 0; tau < 8; ++tau) {
+      dfl z[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) z[c] = X[c][tau ^ (1 << c)];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dfl s = df_mul(dfl{kb.h[tau][c][0], kb.l[tau][c][0]}, z[0]);
+        s = df_add(df_mul(dfl{kb.h[tau][c][1], kb.l[tau][c][1]}, z[1]), s);
+        s = df_add(df_mul(dfl{kb.h[tau][c][2], kb.l[tau][c][2]}, z[2]), s);
+        ce = df_add(df_mul(z[c], s), ce);
+      }
+    }
+    const dfl re = split_d(rho[e]);
+    dfl f = pf;
+    for (int q = 0; q < ipen; ++q) f = df_mul(f, re);
+    dc[e] = df_to_d(df_mul(f, ce));
+    v[0] = df_add(df_mul(split_d(E[e]), ce), v[0]);
+  }
+  double o1[1];
+  block_sum_df<1>(v, o1, sh);
+  if (publish_partials<1>(o1, partials, counter)) {
+    double o[1];
+    finish_sum<1>(partials, counter, o, sh);
+    if (threadIdx.x == 0) *compliance = o[0];
+  }
+}
+
 // ce_e = u_e^T KE u_e; dc_e = -penal (E0-Emin) rho_e^(penal-1) ce_e;
 // compliance = sum_e E_e ce_e (deterministic reduction).
 // 3D: u_e^T KE u_e = X^T B X with X the Walsh transform of u_e (KE = T B T),
@@ -399,6 +472,28 @@ cudaError_t launch_filter(int dim, const GridP& g, const StencilP& st, int mode,
     k_filter<2><<<nblocks(g.nel, 256), 256, 0, s>>>(g, st, mode, Hs, in, out);
   else
     k_filter<3><<<nblocks(g.nel, 256), 256, 0, s>>>(g, st, mode, Hs, in, out);
+  return cudaGetLastError();
+}
+
+bool sensitivity_df_ok(int dim, double penal) {
+  return dim == 3 && penal >= 1.0 && penal <= 9.0 && penal == (double)(int)penal;
+}
+
+cudaError_t launch_sensitivity_df(const GridP& g, const uint8_t* mask, const double* wht,
+                                  const double* u, const double* E, const double* rho,
+                                  double penal, double E0, double Emin, double* dc,
+                                  double* compliance, double* partials, unsigned* counter,
+                                  cudaStream_t s) {
+  if (!wht || !sensitivity_df_ok(3, penal)) return cudaErrorInvalidValue;
+  WhtDf kb;
+  for (int q = 0; q < 72; ++q) {
+    const float h = (float)wht[q];
+    (&kb.h[0][0][0])[q] = h;
+    (&kb.l[0][0][0])[q] = (float)(wht[q] - (double)h);
+  }
+  k_sensitivity3_df<<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, mask, kb, u, E, rho,
+                                                       -penal * (E0 - Emin), (int)penal - 1, dc,
+                                                       compliance, partials, counter);
   return cudaGetLastError();
 }
 

@@ -1197,10 +1197,16 @@ to_status to_sensitivity(to_ctx* c, const double* u, double* compliance_dev, dou
   if (!c || !u || !compliance_dev || !dc) return fail(c, TO_E_INVALID, "NULL argument");
   if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
   const to_mesh_desc& d = c->desc;
-  LAUNCH(c, launch_sensitivity(c->dim, c->lv[0].g, c->lv[0].mask, c->KE64,
-                               c->dim == 3 ? c->wht64 : nullptr, u, c->E64,
-                               c->rho_phys, d.penal, d.E0, d.Emin, dc, compliance_dev,
-                               c->partials, c->counters + C_SENS, c->stream), "sensitivity");
+  // mixed path: double-float arithmetic on the FP32 pipe (float64 otherwise)
+  if (c->mixed && sensitivity_df_ok(c->dim, d.penal))
+    LAUNCH(c, launch_sensitivity_df(c->lv[0].g, c->lv[0].mask, c->wht64, u, c->E64, c->rho_phys,
+                                    d.penal, d.E0, d.Emin, dc, compliance_dev, c->partials,
+                                    c->counters + C_SENS, c->stream), "sensitivity");
+  else
+    LAUNCH(c, launch_sensitivity(c->dim, c->lv[0].g, c->lv[0].mask, c->KE64,
+                                 c->dim == 3 ? c->wht64 : nullptr, u, c->E64,
+                                 c->rho_phys, d.penal, d.E0, d.Emin, dc, compliance_dev,
+                                 c->partials, c->counters + C_SENS, c->stream), "sensitivity");
   return TO_OK;
 }
 

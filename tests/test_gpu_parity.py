@@ -228,8 +228,13 @@ def test_mgcg_solve_parity(kind, kw, precision):
 
 
 @pytest.mark.parametrize("kind,kw", PROBLEMS)
-def test_filter_sensitivity_oc_parity(kind, kw):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_filter_sensitivity_oc_parity(kind, kw, precision):
+    """fp64: float64 arithmetic throughout.  mixed: the 3D compliance and
+    sensitivity in double-float arithmetic (~2^-48 relative per operation,
+    inputs split to 48 significant bits), within the same bounds."""
     B = _B()
+    fabs_tol = 1e-14
     p = small_problem(kind, mg_levels=3, **kw)
     g, KE = _model(p)
     H, Hs = filters.filter_matrix(g, p.rmin)
@@ -243,11 +248,11 @@ def test_filter_sensitivity_oc_parity(kind, kw):
     dcf_ref = filters.sensitivity_filter(H, Hs, dc_ref)
     dvf_ref = filters.sensitivity_filter(H, Hs, np.ones(g.nel))
     rho_new_ref, lam, change_ref = oc.oc_update(rho, dcf_ref, dvf_ref, H, Hs, p.volfrac, 0.2)
-    with Ctx(p, precision="fp64") as c:
+    with Ctx(p, precision=precision) as c:
         rp = dev(np.zeros(g.nel))
         B.to_filter(c.ctx, B.TO_FILTER_DENSITY, dev(rho), rp)
         rho_phys = host(rp)
-        assert np.max(np.abs(rho_phys - rho_phys_ref)) <= 1e-14
+        assert np.max(np.abs(rho_phys - rho_phys_ref)) <= fabs_tol
         c.set_density(rho_phys_ref)
         Cd = dev(np.zeros(1))
         dcd = dev(np.zeros(g.nel))
@@ -259,7 +264,7 @@ def test_filter_sensitivity_oc_parity(kind, kw):
         assert np.max(np.abs(host(dcf) - dcf_ref)) <= 1e-12 * np.max(np.abs(dcf_ref))
         dvf = dev(np.zeros(g.nel))
         B.to_filter(c.ctx, B.TO_FILTER_SENS, dev(np.ones(g.nel)), dvf)
-        assert np.max(np.abs(host(dvf) - dvf_ref)) <= 1e-14
+        assert np.max(np.abs(host(dvf) - dvf_ref)) <= fabs_tol
         rd = dev(rho)
         ch = dev(np.zeros(1))
         B.to_oc_update(c.ctx, p.volfrac, 0.2, dev(dcf_ref), dev(dvf_ref), rd, ch)
