@@ -372,6 +372,16 @@ __global__ void __launch_bounds__(256)
   dvd[e] = make_float2(dd.h, dd.l);
 }
 
+// Section point j (1 .. OC_SPLIT-1) of the bracket [l1, l2]: evenly spaced,
+// or, while the lower end is still 0, geometric (l2 / 8^(OC_SPLIT - j)), which
+// brings an upper end far above lambda down by up to 8^7 per sweep; point
+// OC_SPLIT is l2 itself.
+__device__ __forceinline__ double oc_point(double l1, double l2, int j) {
+  if (j >= OC_SPLIT) return l2;
+  if (l1 == 0.0) return ldexp(l2, -3 * (OC_SPLIT - j));
+  return l1 + (double)j * ((l2 - l1) / OC_SPLIT);
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
     k_oc_section(long long nel, const float2* __restrict__ a, const float2* __restrict__ lo,
                  const float2* __restrict__ hi, const float2* __restrict__ dvd, double target,
@@ -382,7 +392,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   const double l1 = scal[S_OC_L1], l2 = scal[S_OC_L2];
   if (!((l2 - l1) > 1e-13 * (l1 + l2))) return;
   if (threadIdx.x < NP) {
-    const double lam = l1 + (double)(threadIdx.x + 1) * ((l2 - l1) / OC_SPLIT);
+    const double lam = oc_point(l1, l2, threadIdx.x + 1);
     s_s[threadIdx.x] = split_d(1.0 / sqrt(lam));
   }
   __syncthreads();
@@ -415,9 +425,8 @@ __global__ void __launch_bounds__(RED_THREADS)
       // and the first at or below it
       int k = 0;
       while (k < NP && o[k] > target) ++k;
-      const double w = (l2 - l1) / OC_SPLIT;
-      const double nl1 = k > 0 ? l1 + k * w : l1;
-      const double nl2 = k < NP ? l1 + (k + 1) * w : l2;
+      const double nl1 = k > 0 ? oc_point(l1, l2, k) : l1;
+      const double nl2 = oc_point(l1, l2, k + 1);
       scal[S_OC_L1] = nl1;
       scal[S_OC_L2] = nl2;
       scal[S_OC_VOL] = k > 0 ? o[k - 1] : o[0];

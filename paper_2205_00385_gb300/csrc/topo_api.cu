@@ -1228,10 +1228,13 @@ to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_
   const double target = volfrac * (double)nel;
   LAUNCH(c, launch_oc_prep_d(nel, rho, dc_f, dv_f, move, c->oc_a, c->oc_a2, c->oc_lo, c->oc_hi,
                              c->oc_dv2, c->scal, s), "oc prep");
-  // eight-way sections run on the device (3 bits of bracket each); a launch
-  // is a no-op once the bracket is within a relative 1e-13
-  for (int chunk = 0; chunk < 16; ++chunk) {
-    for (int q = 0; q < 8; ++q)
+  // eight-way sections run on the device; a launch is a no-op once the
+  // bracket is within a relative 1e-13.  From [0, 1e9] geometric cuts reach
+  // lambda's magnitude in a few sweeps (at most 7 for lambda >= 1e-40) and
+  // 15 more evenly spaced cuts reach 1e-13, so 24 are queued before the
+  // host first looks, then 8 at a time.
+  for (int chunk = 0, nsec = 24; chunk < 16; ++chunk, nsec = 8) {
+    for (int q = 0; q < nsec; ++q)
       LAUNCH(c, launch_oc_section(nel, c->oc_a2, c->oc_lo, c->oc_hi, c->oc_dv2, target, c->scal,
                                   c->partials, c->counters + C_OC, s), "oc section");
     double lr[2];
