@@ -139,6 +139,10 @@ cudaError_t launch_vscale_inv_sqrt(long long n, int vt, void* a, const double* s
 cudaError_t launch_gram(long long n, int vt, const void* A, int na, const int* na_dev,
                         const void* B, int nb, const int* nb_dev, double* G, int ldg,
                         double* partials, unsigned* counter, cudaStream_t s);
+// G = A^T B for a product known to be symmetric (A^T K A with B = K A): the
+// upper triangle is summed (about half the tiles) and mirrored
+cudaError_t launch_gram_sym(long long n, int vt, const void* A, const void* B, int m, double* G,
+                            int ldg, double* partials, unsigned* counter, cudaStream_t s);
 // y = beta*y + sign * sum_i c[i] A[:, i] (i < m, or *m_dev); if rr != 0 also
 // writes |y - w|^2 (w may be null) to *rr.  A and w have storage vt, y has
 // storage yt (yt = vt, or V_F64 with vt = V_DF2).

@@ -193,7 +193,7 @@ template <typename S>
 __global__ void __launch_bounds__(MD_CH)
     k_gram(long long n, const S* __restrict__ A, int na, const int* na_dev,
            const S* __restrict__ B, int nb, const int* nb_dev, double* G, int ldg,
-           double* partials, unsigned* counter) {
+           double* partials, unsigned* counter, bool sym) {
   using Rg = Ar<S>;
   using V = typename Rg::T;
   static_assert(sizeof(V) == sizeof(S), "staged values keep the storage layout");
@@ -204,12 +204,21 @@ __global__ void __launch_bounds__(MD_CH)
   const int mb = nb_dev ? min(max(*nb_dev, 0), nb) : nb;
   const int nv = ma + mb;
   const int tr = (ma + 1) / 2, tc = (mb + 1) / 2;
-  const int ntile = tr * tc > 0 ? tr * tc : 1;
+  // sym (a symmetric product, ma == mb): only the 2 x 2 tiles on or above
+  // the diagonal, numbered column by column (tile = tj (tj+1)/2 + ti)
+  const int ntt = sym ? tr * (tr + 1) / 2 : tr * tc;
+  const int ntile = ntt > 0 ? ntt : 1;
   const int S_ = MD_CH / ntile;   // index subsets per tile (>= 2)
   const int t = threadIdx.x;
   const int tile = t % ntile, sub = t / ntile;
-  const bool active = tr * tc > 0 && sub < S_;
-  const int i0 = active ? 2 * (tile % tr) : 0, j0 = active ? 2 * (tile / tr) : 0;
+  const bool active = ntt > 0 && sub < S_;
+  int ti = tile % (tr > 0 ? tr : 1), tj = tile / (tr > 0 ? tr : 1);
+  if (sym) {
+    tj = 0;
+    while ((tj + 1) * (tj + 2) / 2 <= tile) ++tj;
+    ti = tile - tj * (tj + 1) / 2;
+  }
+  const int i0 = active ? 2 * ti : 0, j0 = active ? 2 * tj : 0;
   V acc[2][2];
 #pragma unroll
   for (int p = 0; p < 2; ++p)
@@ -267,7 +276,9 @@ __global__ void __launch_bounds__(MD_CH)
   double* part = partials + (size_t)blockIdx.x * (MAXB * MAXB);
   for (int e = t; e < np; e += MD_CH) {
     const int i = e % ma, j = e / ma;
-    const int tl = (i / 2) + tr * (j / 2), qq = (i & 1) + 2 * (j & 1);
+    if (sym && i > j) continue;
+    const int tl = sym ? (j / 2) * (j / 2 + 1) / 2 + i / 2 : (i / 2) + tr * (j / 2);
+    const int qq = (i & 1) + 2 * (j & 1);
     double sum = 0.0;
     for (int u = 0; u < S_; ++u) sum += red[(tl * 4 + qq) * S_ + u];
     part[e] = sum;
@@ -279,9 +290,12 @@ __global__ void __launch_bounds__(MD_CH)
   if (!s_last) return;
   __threadfence();
   for (int e = t; e < np; e += MD_CH) {
+    const int i = e % ma, j = e / ma;
+    if (sym && i > j) continue;
     double sum = 0.0;
     for (int bl = 0; bl < (int)gridDim.x; ++bl) sum += partials[(size_t)bl * (MAXB * MAXB) + e];
-    G[(e % ma) + (size_t)ldg * (e / ma)] = sum;
+    G[i + (size_t)ldg * j] = sum;
+    if (sym) G[j + (size_t)ldg * i] = sum;
   }
   if (t == 0) *counter = 0u;
 }
@@ -609,19 +623,29 @@ cudaError_t launch_vscale_inv_sqrt(long long n, int vt, void* a, const double* s
 template <typename S>
 static void gram_t(long long n, const void* A, int na, const int* na_dev, const void* B, int nb,
                    const int* nb_dev, double* G, int ldg, double* partials, unsigned* counter,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool sym = false) {
   static bool smem_set = false;   // up to 2 stages x 2*MAXB columns x MD_CH values
   if (!smem_set) {
     cudaFuncSetAttribute(k_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * 2 * MAXB * MD_CH * sizeof(S)));
     smem_set = true;
   }
-  if (nb == 1 && nb_dev == nullptr)
+  if (nb == 1 && nb_dev == nullptr && !sym)
     k_gram_col<S><<<RED_BLOCKS, 32 * na, 0, s>>>(n, (const S*)A, na, na_dev, (const S*)B, G,
                                                  partials, counter);
   else
     k_gram<S><<<RED_BLOCKS, MD_CH, (size_t)2 * (na + nb) * MD_CH * sizeof(S), s>>>(
-        n, (const S*)A, na, na_dev, (const S*)B, nb, nb_dev, G, ldg, partials, counter);
+        n, (const S*)A, na, na_dev, (const S*)B, nb, nb_dev, G, ldg, partials, counter, sym);
+}
+
+cudaError_t launch_gram_sym(long long n, int vt, const void* A, const void* B, int m, double* G,
+                            int ldg, double* partials, unsigned* counter, cudaStream_t s) {
+  if (m > MAXB || m < 1) return cudaErrorInvalidValue;
+  if (vt == V_DF2)
+    gram_t<float2>(n, A, m, nullptr, B, m, nullptr, G, ldg, partials, counter, s, true);
+  else
+    gram_t<double>(n, A, m, nullptr, B, m, nullptr, G, ldg, partials, counter, s, true);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram(long long n, int vt, const void* A, int na, const int* na_dev,

@@ -1115,8 +1115,8 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
   for (int i = 0; i < Ns; ++i)
     if ((st = apply_vec(c, TO_OP_KREF, c->Phi + (size_t)i * n, c->KPhi + (size_t)i * n)) != TO_OK)
       return st;
-  LAUNCH(c, launch_gram(n, v, c->Phi, Ns, nullptr, c->KPhi, Ns, nullptr, small + SM_KPHI, Ns,
-                        c->partials, c->counters + C_MULTI, s), "K_Phi");
+  LAUNCH(c, launch_gram_sym(n, v, c->Phi, c->KPhi, Ns, small + SM_KPHI, Ns, c->partials,
+                            c->counters + C_MULTI, s), "K_Phi");
   LAUNCH(c, launch_small_spd_inverse(Ns, nullptr, small + SM_KPHI, small + SM_KPHI_INV,
                                      c->ints + I_STATUS, s), "K_Phi inverse");
   // r_1 = u_last; r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}  (Eq. 18-20, 26)
@@ -1174,8 +1174,8 @@ to_status to_carm_solve(to_ctx* c, double* u, double* eps, double* eps_dev) {
     if ((st = apply_accurate_vec(c, TO_OP_K, c->R + (size_t)j * n, c->Q + (size_t)j * n,
                                  EPI_APPLY)) != TO_OK)
       return st;
-  LAUNCH(c, launch_gram(n, v, c->R, k, nullptr, c->Q, k, nullptr, small + SM_KR, k, c->partials,
-                        c->counters + C_MULTI, s), "K_R");
+  LAUNCH(c, launch_gram_sym(n, v, c->R, c->Q, k, small + SM_KR, k, c->partials,
+                            c->counters + C_MULTI, s), "K_R");
   LAUNCH(c, launch_gram(n, v, c->R, k, nullptr, fv, 1, nullptr, small + SM_FR, k, c->partials,
                         c->counters + C_MULTI, s), "f_R");
   LAUNCH(c, launch_small_chol_solve(k, nullptr, small + SM_KR, small + SM_FR, small + SM_Y,
