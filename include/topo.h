@@ -135,6 +135,11 @@ to_status to_parm_reset(to_ctx* ctx);
  * dropped.  Needs a full PARM (else TO_E_STATE). */
 to_status to_carm_build(to_ctx* ctx, const double* u_last);
 
+/* Test hook: *err (host) = max_ij |(R~^T R~)_ij - delta_ij| over the last
+ * CARM basis (synchronises).  Overwrites the reduced matrix, so call
+ * to_carm_solve afterwards, not before. */
+to_status to_carm_basis_error(to_ctx* ctx, double* err);
+
 /* Reduced solve on the last CARM basis (K R~ is always formed with the
  * float64 operator, also in TO_MIXED): K_R = R~^T K R~, f_R = R~^T f,
  * y = K_R^{-1} f_R (Eq. 23-24), u = R~ y (Eq. 25, dev float64 n, out) and

@@ -45,6 +45,7 @@ _VP = C.c_void_p
 _SIGS = {
     "to_workspace_bytes": [C.POINTER(to_mesh_desc), C.POINTER(C.c_int64)],
     "to_mesh_init": [C.POINTER(to_mesh_desc), _VP, _VP, _VP, C.c_int64, _VP, C.POINTER(_VP)],
+    "to_carm_basis_error": [_VP, C.POINTER(C.c_double)],
     "to_set_density": [_VP, _VP],
     "to_mgcg_solve": [_VP, C.c_double, C.c_int32, C.c_int32, _VP, C.POINTER(C.c_int32),
                       C.POINTER(C.c_double)],
@@ -170,6 +171,13 @@ def to_carm_solve(ctx, u, eps_dev=None, read_eps=True):
     _check(load().to_carm_solve(ctx, _ptr(u), C.byref(e) if read_eps else None, _ptr(eps_dev)),
            ctx)
     return e.value if read_eps else None
+
+
+def to_carm_basis_error(ctx) -> float:
+    """max |R~^T R~ - I| of the last CARM basis (test hook)."""
+    e = C.c_double()
+    _check(load().to_carm_basis_error(ctx, C.byref(e)), ctx)
+    return e.value
 
 
 def to_sensitivity(ctx, u, compliance_dev, dc):

@@ -146,6 +146,12 @@ cudaError_t launch_gram_sym(long long n, int vt, const void* A, const void* B, i
 // y = beta*y + sign * sum_i c[i] A[:, i] (i < m, or *m_dev); if rr != 0 also
 // writes |y - w|^2 (w may be null) to *rr.  A and w have storage vt, y has
 // storage yt (yt = vt, or V_F64 with vt = V_DF2).
+// y <- y - A c (m = *m_dev columns when given) and then h = A^T y for the
+// updated y, in one pass over A (a Gram-Schmidt pass fused with the next
+// pass's projections); m <= 12
+cudaError_t launch_combine_dots(long long n, int vt, const void* A, int m, const int* m_dev,
+                                const double* c, void* y, double* h, double* partials,
+                                unsigned* counter, cudaStream_t s);
 cudaError_t launch_combine(long long n, int vt, const void* A, int m, const int* m_dev,
                            const double* c, double sign, double beta, void* y, int yt,
                            const void* w, double* rr, double* partials, unsigned* counter,

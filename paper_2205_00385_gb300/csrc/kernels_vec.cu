@@ -421,6 +421,55 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
   reduce_to<S>(v, rr, partials, counter, sh);
 }
 
+// One classical Gram-Schmidt pass fused with the next pass's projections:
+// y <- y - sum_{i<m} c[i] A[:, i], then h[i] = A[:, i] . y for the new y
+// (m = *m_dev when given).  The columns are read once for both; the dots
+// are double-float, summed per block and then over blocks in order.
+template <typename S, int MMAX>
+__global__ void __launch_bounds__(RED_THREADS, 2)
+    k_combine_dots(long long n, const S* __restrict__ A, int m, const int* m_dev,
+                   const double* __restrict__ c, S* __restrict__ y, double* h,
+                   double* partials, unsigned* counter) {
+  using Rg = Ar<S>;
+  using V = typename Rg::T;
+  __shared__ double sh[MMAX * 32];
+  __shared__ V scc[MMAX];
+  pdl_wait();
+  const int mm = m_dev ? min(max(*m_dev, 0), m) : m;
+  if (threadIdx.x < MMAX)
+    scc[threadIdx.x] = Rg::from_d((int)threadIdx.x < mm ? -c[threadIdx.x] : 0.0);
+  __syncthreads();
+  V hacc[MMAX];
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i) hacc[i] = Rg::zero();
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    V a[MMAX];
+    V sv = Rg::ld(y, k);
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i) a[i] = i < mm ? Rg::ld(A + (size_t)i * n, k) : Rg::zero();
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i)
+      if (i < mm) sv = Rg::fma3(scc[i], a[i], sv);
+    Rg::st(y, k, sv);
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i)
+      if (i < mm) Rg::dacc(hacc[i], a[i], sv);
+  }
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i) hacc[i] = Rg::dfin(hacc[i]);
+  double o1[MMAX];
+  block_sum_v<S, MMAX>(hacc, o1, sh);
+  if (publish_partials<MMAX>(o1, partials, counter)) {
+    double o[MMAX];
+    finish_sum<MMAX>(partials, counter, o, sh);
+    // the block sums are complete in thread 0 only
+    if (threadIdx.x == 0)
+      for (int q = 0; q < mm; ++q) h[q] = o[q];
+  }
+  pdl_launch_dependents();
+}
+
 // Gram-Schmidt acceptance: if |r_src|^2 after orthogonalisation exceeds
 // tol^2 times its value before, R[:, k] = r_src / |r_src| with k the
 // current count (the count itself is advanced by k_gs_count afterwards)
@@ -678,6 +727,24 @@ static void combine_t(long long n, const void* A, int m, const int* m_dev, const
   else
     k_combine<S, SY, MAXB><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, m, m_dev, c, sign, beta, yy,
                                                               ww, rr, partials, counter);
+}
+
+cudaError_t launch_combine_dots(long long n, int vt, const void* A, int m, const int* m_dev,
+                                const double* c, void* y, double* h, double* partials,
+                                unsigned* counter, cudaStream_t s) {
+  if (m > 12 || m < 0) return cudaErrorInvalidValue;
+  if (vt == V_DF2) {
+    if (m <= 4)
+      return launch_pdl(k_combine_dots<float2, 4>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n,
+                        (const float2*)A, m, m_dev, c, (float2*)y, h, partials, counter);
+    return launch_pdl(k_combine_dots<float2, 12>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n,
+                      (const float2*)A, m, m_dev, c, (float2*)y, h, partials, counter);
+  }
+  if (m <= 4)
+    return launch_pdl(k_combine_dots<double, 4>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n,
+                      (const double*)A, m, m_dev, c, (double*)y, h, partials, counter);
+  return launch_pdl(k_combine_dots<double, 12>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n,
+                    (const double*)A, m, m_dev, c, (double*)y, h, partials, counter);
 }
 
 cudaError_t launch_combine(long long n, int vt, const void* A, int m, const int* m_dev,

@@ -1138,15 +1138,17 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
     const int bound = std::max(i, 1);   // accepted columns so far <= i
     LAUNCH(c, launch_vdot(n, v, ri, ri, c->partials, c->counters + C_DOT, c->scal + S_NRM0, s),
            "|r|");
-    // two classical passes; the second also returns |r_i|^2 after them
-    for (int pass = 0; pass < 2; ++pass) {
-      LAUNCH(c, launch_gram(n, v, c->R, bound, c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
-                            MAXB, c->partials, c->counters + C_MULTI, s), "GS dots");
-      LAUNCH(c, launch_combine(n, v, c->R, bound, c->ints + I_KCOUNT, small + SM_H, -1.0, 1.0,
-                               ri, v, nullptr, pass == 1 ? c->scal + S_NRM1 : nullptr,
-                               c->partials, c->counters + C_UPD, s),
-             "GS axpy");
-    }
+    // two classical passes: projections, then the first update fused with
+    // the second pass's projections, then the second update, which also
+    // returns |r_i|^2 after them
+    LAUNCH(c, launch_gram(n, v, c->R, bound, c->ints + I_KCOUNT, ri, 1, nullptr, small + SM_H,
+                          MAXB, c->partials, c->counters + C_MULTI, s), "GS dots");
+    LAUNCH(c, launch_combine_dots(n, v, c->R, bound, c->ints + I_KCOUNT, small + SM_H, ri,
+                                  small + SM_H2, c->partials, c->counters + C_MULTI, s),
+           "GS axpy + dots");
+    LAUNCH(c, launch_combine(n, v, c->R, bound, c->ints + I_KCOUNT, small + SM_H2, -1.0, 1.0, ri,
+                             v, nullptr, c->scal + S_NRM1, c->partials, c->counters + C_UPD, s),
+           "GS axpy");
     LAUNCH(c, launch_gs_accept(n, v, c->R, i, c->scal, S_NRM0, S_NRM1, 1e-10, c->ints, s),
            "GS accept");
   }
@@ -1155,6 +1157,23 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
   CUDA_TRY(c, cudaStreamSynchronize(s), "sync");
   c->carm_built = k;
   if (k < 1) return fail(c, TO_E_SINGULAR, "CARM basis is empty");
+  return TO_OK;
+}
+
+to_status to_carm_basis_error(to_ctx* c, double* err) {
+  if (!c || !err) return fail(c, TO_E_INVALID, "NULL argument");
+  if (c->carm_built < 1) return fail(c, TO_E_STATE, "to_carm_build has not been called");
+  const int k = c->carm_built;
+  LAUNCH(c, launch_gram_sym(c->n, vt(c), c->R, c->R, k, c->small + SM_KR, k, c->partials,
+                            c->counters + C_MULTI, c->stream), "basis Gram");
+  std::vector<double> G((size_t)k * k);
+  CUDA_TRY(c, cudaMemcpyAsync(G.data(), c->small + SM_KR, sizeof(double) * k * k,
+                              cudaMemcpyDeviceToHost, c->stream), "read");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  double e = 0.0;
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < k; ++i) e = std::max(e, fabs(G[i + (size_t)k * j] - (i == j ? 1.0 : 0.0)));
+  *err = e;
   return TO_OK;
 }
 

@@ -117,7 +117,8 @@ enum SmallOff {
   SM_KR = SM_H + 16,                // m x m
   SM_FR = SM_KR + 256,              // m
   SM_Y = SM_FR + 16,                // m
-  SM_TOTAL = SM_Y + 16 + 64
+  SM_H2 = SM_Y + 16,                // GS coefficients of the second pass
+  SM_TOTAL = SM_H2 + 16 + 48
 };
 
 enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_NINTS = 16 };

@@ -312,6 +312,25 @@ def test_carm_parity(kind, kw, precision):
         assert abs(C - C_ref) <= 1e-6 * C_ref
 
 
+@pytest.mark.parametrize("kind,kw", PROBLEMS[:2])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("ns", [4, 10])
+def test_carm_basis_orthonormal(kind, kw, precision, ns):
+    """The orthonormalised CARM basis (Eq. 21) of a real trajectory:
+    R~^T R~ = I to rounding, for the few- and many-column paths of the
+    re-orthogonalising Gram-Schmidt."""
+    B = _B()
+    p, s = _carm_case(kind, kw, ns, ns + 5)
+    with Ctx(p, precision=precision) as c:
+        c.set_density(s["rho_phys_prev"])
+        c.set_density(s["rho_phys"])
+        for i in range(s["Phi"].shape[1]):
+            B.to_parm_push(c.ctx, dev(s["Phi"][:, i]))
+        B.to_carm_build(c.ctx, dev(s["u_last"]))
+        err = B.to_carm_basis_error(c.ctx)
+    assert err <= 1e-12, err
+
+
 def test_carm_zero_change_gives_scaled_last_solution():
     """dK = 0 (same density twice): every r_i, i >= 2, vanishes and the
     reduced solution is the Rayleigh-Ritz multiple of u_last."""
