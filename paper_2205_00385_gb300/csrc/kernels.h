@@ -18,7 +18,9 @@ enum { EPI_APPLY = 0, EPI_RESID = 1, EPI_SMOOTH = 2 };
 //   y = x + omega * dinv * (b - that)                      (EPI_SMOOTH)
 // with Ke_e = coef_e * KE on the finest level (explicit = false) or the
 // stored Galerkin element matrix Kc_e on coarse levels (explicit = true).
-// Stored element matrices are element-major, row-major: Kc[e*ND*ND + r*ND + c].
+// Explicit levels are applied from their assembled stencil S (fixed rows
+// stored as identity rows, so dfix must be 1); the element matrices Kc are
+// packed upper triangles, Kc[e*tri_len(ND) + tri_idx(r, c, ND)], r <= c.
 struct ApplyArgs {
   int dim;
   GridP g;
@@ -27,7 +29,7 @@ struct ApplyArgs {
   int tx, ty;          // storage types of x (and b) and of y
   bool expl;
   const void* coef;    // [nel] of type tc (fine level)
-  const void* Kc;      // [ND*ND*nel] of type tc (coarse levels)
+  const void* Kc;      // [tri_len(ND)*nel] of type tc (coarse levels)
   const void* ke;      // host pointer to the ND*ND element matrix of type tc
   const void* wht;     // host pointer to the 8x3x3 Walsh-Hadamard blocks of KE
                        // (type tc; 3D finest grid only, else null)
