@@ -129,7 +129,7 @@ to_status to_parm_reset(to_ctx* ctx);
 
 /* Build the CARM basis R~ from u_last (dev, float64, n): K_Phi = Phi^T K_ref
  * Phi (Eq. 15), r_1 = u_last, r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}
- * (Eq. 18-20, 26), orthonormalised by modified Gram-Schmidt with
+ * (Eq. 18-20, 26), orthonormalised by classical Gram-Schmidt with
  * re-orthogonalisation (the basis-orthogonalisation step of Eq. 21); a
  * column whose norm after two passes is <= 1e-10 of its norm before is
  * dropped.  Needs a full PARM (else TO_E_STATE). */

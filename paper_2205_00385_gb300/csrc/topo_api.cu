@@ -1131,7 +1131,7 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
                              c->R + (size_t)i * n, v, nullptr, nullptr, c->partials,
                              c->counters + C_UPD, s), "r_i");
   }
-  // modified Gram-Schmidt with re-orthogonalisation, in place
+  // classical Gram-Schmidt with one re-orthogonalisation pass, in place
   CUDA_TRY(c, cudaMemsetAsync(c->ints + I_KCOUNT, 0, sizeof(int), s), "reset k");
   for (int i = 0; i < m; ++i) {
     double* ri = c->R + (size_t)i * n;
