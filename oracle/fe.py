@@ -189,6 +189,22 @@ class Grid:
                 out[:, d * a + c] = d * en[:, a] + c
         return out
 
+    def dofs_of(self, elems) -> np.ndarray:
+        """Rows of ``element_dofs()`` for the given elements only (for grids
+        whose full table would be large)."""
+        e = np.asarray(elems, dtype=np.int64)
+        ex = e % self.nelx
+        ey = (e // self.nelx) % self.nely
+        ez = e // (self.nelx * self.nely) if self.dim == 3 else np.zeros_like(e)
+        d = self.dim
+        out = np.empty((e.size, d * self.npe), dtype=np.int64)
+        for a in range(self.npe):
+            bx, by, bz = a & 1, (a >> 1) & 1, (a >> 2) & 1
+            n = self.node(ex + bx, ey + by, ez + bz)
+            for c in range(d):
+                out[:, d * a + c] = d * n + c
+        return out
+
     def element_centers(self) -> np.ndarray:
         ex, ey, ez = self.element_ijk()
         if self.dim == 2:
@@ -253,3 +269,31 @@ def apply_ebe(grid: Grid, coef: np.ndarray, KE: np.ndarray, x: np.ndarray,
     ye = coef[:, None] * (xe @ KE.T)                # KE symmetric
     y = np.bincount(edofs.ravel(), weights=ye.ravel(), minlength=grid.ndof)
     return y * m + diag_fixed * fixed.astype(float) * x
+
+
+def apply_ebe_rows(grid: Grid, coef: np.ndarray, KE: np.ndarray, x: np.ndarray,
+                   fixed: np.ndarray, rows, diag_fixed: float = 1.0) -> np.ndarray:
+    """Selected entries of ``apply_ebe``: for DOF i = dim*node + c,
+    y_i = m_i sum_e coef_e (KE A_e M x)_(local index of i in e) + diag_fixed (1 - m_i) x_i,
+    the sum running over the (up to 2**dim) elements that share the node.
+    Used where only sampled outputs of a large grid are compared."""
+    rows = np.asarray(rows, dtype=np.int64)
+    d = grid.dim
+    m = 1.0 - fixed.astype(float)
+    xm = x * m
+    node, comp = rows // d, rows % d
+    nx1, ny1 = grid.nelx + 1, grid.nely + 1
+    ix, iy, iz = node % nx1, (node // nx1) % ny1, node // (nx1 * ny1)
+    nz = grid.nelz if d == 3 else 1
+    y = np.zeros(rows.size)
+    for a in range(grid.npe):
+        bx, by, bz = a & 1, (a >> 1) & 1, (a >> 2) & 1
+        ex, ey, ez = ix - bx, iy - by, iz - bz
+        ok = (ex >= 0) & (ex < grid.nelx) & (ey >= 0) & (ey < grid.nely) & (ez >= 0) & (ez < nz)
+        if not np.any(ok):
+            continue
+        e = ex[ok] + grid.nelx * (ey[ok] + grid.nely * ez[ok])
+        dofs = grid.dofs_of(e)                                 # (s, nd)
+        ke_rows = KE[d * a + comp[ok]]                         # (s, nd)
+        y[ok] += coef[e] * np.sum(ke_rows * xm[dofs], axis=1)
+    return y * m[rows] + diag_fixed * fixed[rows].astype(float) * x[rows]

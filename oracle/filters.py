@@ -56,3 +56,65 @@ def sensitivity_filter(H, Hs, d: np.ndarray) -> np.ndarray:
     """Eq. 33 (transpose reading): chain rule through the density filter,
     returns H^T (d / Hs)."""
     return H.T @ (d / Hs)
+
+
+# ----------------------------------------------------------------------------
+# The same filter without forming H, for grids where the sparse matrix would
+# not fit in host memory (8.19M elements x 81 neighbours for r = 2.5).  Each
+# cone offset (dx, dy, dz) with weight w = r - |offset| > 0 adds w times the
+# shifted field to every element whose neighbour lies inside the domain
+# (Eq. 31-32, truncated at the boundary).  H is symmetric (the weight depends
+# on |offset| only, and "both inside" is symmetric), so Eq. 33's transpose is
+# the same stencil applied to d / Hs.
+# ----------------------------------------------------------------------------
+
+def _cone_offsets(dim: int, rmin: float):
+    R = int(np.ceil(rmin))
+    offs = range(-R, R + 1)
+    cand = itertools.product(offs, offs, offs if dim == 3 else (0,))
+    out = []
+    for dx, dy, dz in cand:
+        w = rmin - np.sqrt(dx * dx + dy * dy + dz * dz)
+        if w > 0.0:
+            out.append((dx, dy, dz, w))
+    return out
+
+
+def _block(grid: Grid, v: np.ndarray) -> np.ndarray:
+    """Element field as an array indexed [ez, ey, ex] (x fastest)."""
+    return v.reshape(max(grid.nelz, 1), grid.nely, grid.nelx)
+
+
+def _stencil_sum(grid: Grid, rmin: float, v: np.ndarray) -> np.ndarray:
+    """(H v)_i = sum over in-domain neighbours j of w_ij v_j."""
+    nz, ny, nx = max(grid.nelz, 1), grid.nely, grid.nelx
+    src = _block(grid, v)
+    acc = np.zeros((nz, ny, nx))
+    for dx, dy, dz, w in _cone_offsets(grid.dim, rmin):
+        # element i = (x, y, z) receives v at j = (x+dx, y+dy, z+dz)
+        xi, xj = slice(max(0, -dx), min(nx, nx - dx)), slice(max(0, dx), min(nx, nx + dx))
+        yi, yj = slice(max(0, -dy), min(ny, ny - dy)), slice(max(0, dy), min(ny, ny + dy))
+        zi, zj = slice(max(0, -dz), min(nz, nz - dz)), slice(max(0, dz), min(nz, nz + dz))
+        acc[zi, yi, xi] += w * src[zj, yj, xj]
+    return acc.ravel()
+
+
+def filter_weight_sums(grid: Grid, rmin: float) -> np.ndarray:
+    """Hs_i = sum_j w_ij over the truncated cone (Eq. 31's denominator)."""
+    return _stencil_sum(grid, rmin, np.ones(grid.nel))
+
+
+def density_filter_stencil(grid: Grid, rmin: float, rho: np.ndarray,
+                           Hs: np.ndarray | None = None) -> np.ndarray:
+    """Eq. 31 without the matrix: (H rho) / Hs."""
+    if Hs is None:
+        Hs = filter_weight_sums(grid, rmin)
+    return _stencil_sum(grid, rmin, rho) / Hs
+
+
+def sensitivity_filter_stencil(grid: Grid, rmin: float, d: np.ndarray,
+                               Hs: np.ndarray | None = None) -> np.ndarray:
+    """Eq. 33 (transpose reading) without the matrix: H^T (d / Hs) = H (d / Hs)."""
+    if Hs is None:
+        Hs = filter_weight_sums(grid, rmin)
+    return _stencil_sum(grid, rmin, d / Hs)

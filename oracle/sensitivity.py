@@ -29,6 +29,14 @@ def element_energy(grid: Grid, KE: np.ndarray, u: np.ndarray, fixed: np.ndarray)
     return np.einsum("ei,ij,ej->e", ue, KE, ue)
 
 
+def element_energy_at(grid: Grid, KE: np.ndarray, u: np.ndarray, fixed: np.ndarray,
+                      elems) -> np.ndarray:
+    """``element_energy`` for the given elements only."""
+    um = u * (1.0 - fixed.astype(float))
+    ue = um[grid.dofs_of(elems)]
+    return np.einsum("ei,ij,ej->e", ue, KE, ue)
+
+
 def compliance(E: np.ndarray, ce: np.ndarray) -> float:
     """Eq. 3 as the element sum of E_e u_e^T KE u_e."""
     return float(np.sum(E * ce))

@@ -194,6 +194,32 @@ def test_ebe_apply_equals_csr_and_bruteforce(dim):
     assert np.all(y0[fixed == 1] == 0.0)
 
 
+@pytest.mark.parametrize("shape", [(3, 5, 3, 4), (3, 1, 2, 1), (2, 6, 5, 0), (2, 1, 1, 0)])
+def test_sampled_outputs_equal_full_products(shape):
+    """The per-row apply, per-element DOF table and per-element energy used
+    for sampled checks on large grids give the full products' entries, for
+    every row in a shuffled order (corner, edge, face and interior nodes,
+    fixed and free DOFs, identity and zero diagonals)."""
+    from oracle import sensitivity
+    g = fe.Grid(*shape)
+    dim = g.dim
+    KE = fe.element_stiffness(dim, 0.3)
+    rng = np.random.default_rng(9)
+    E = rng.uniform(0.01, 1.0, g.nel)
+    x = rng.standard_normal(g.ndof)
+    fixed = (rng.uniform(size=g.ndof) < 0.25).astype(np.uint8)
+    rows = rng.permutation(g.ndof)
+    for d in (1.0, 0.0):
+        full = fe.apply_ebe(g, E, KE, x, fixed, diag_fixed=d)
+        part = fe.apply_ebe_rows(g, E, KE, x, fixed, rows, diag_fixed=d)
+        assert np.allclose(part, full[rows], rtol=0, atol=1e-13)
+    elems = rng.permutation(g.nel)
+    assert np.array_equal(g.dofs_of(elems), g.element_dofs()[elems])
+    ce = sensitivity.element_energy(g, KE, x, fixed)
+    assert np.allclose(sensitivity.element_energy_at(g, KE, x, fixed, elems), ce[elems],
+                       rtol=1e-14, atol=0)
+
+
 def test_grid_numbering_conventions():
     g = fe.Grid(3, 4, 3, 2)
     en = g.element_nodes()

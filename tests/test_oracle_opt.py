@@ -50,6 +50,24 @@ def test_filter_fixed_point_rows_and_adjoint():
     assert np.allclose((H.toarray() / Hs[:, None]).sum(axis=1), 1.0, atol=1e-15)
 
 
+@pytest.mark.parametrize("shape,rmin", [((3, 7, 5, 4), 1.5), ((3, 6, 5, 4), 2.0),
+                                        ((3, 9, 4, 6), 2.5), ((3, 3, 2, 2), 3.0),
+                                        ((2, 11, 6, 0), 1.5), ((2, 5, 8, 0), 2.5)])
+def test_stencil_filter_equals_matrix_filter(shape, rmin):
+    """The matrix-free filter (shifted-slice sums over the cone's offsets)
+    gives the matrix filter's weight sums, filtered densities and filtered
+    sensitivities, including grids thinner than the cone."""
+    g = fe.Grid(*shape)
+    H, Hs = filters.filter_matrix(g, rmin)
+    rng = np.random.default_rng(11)
+    rho, d = rng.uniform(size=g.nel), rng.standard_normal(g.nel)
+    assert np.allclose(filters.filter_weight_sums(g, rmin), Hs, rtol=1e-15, atol=0)
+    assert np.allclose(filters.density_filter_stencil(g, rmin, rho),
+                       filters.density_filter(H, Hs, rho), rtol=1e-14, atol=0)
+    assert np.allclose(filters.sensitivity_filter_stencil(g, rmin, d),
+                       filters.sensitivity_filter(H, Hs, d), rtol=1e-13, atol=1e-15)
+
+
 def test_simp_endpoints():
     E = sensitivity.simp_modulus(np.array([0.0, 1.0, 0.5]), 1.0, 1e-9, 3.0)
     assert E[0] == 1e-9 and E[1] == 1.0

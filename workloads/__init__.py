@@ -2,7 +2,7 @@
 
 This package holds problem definitions only: grid sizes, which degrees of
 freedom are supported, the nodal load vector, the initial density field and
-seeded random vectors.  It performs none of the method's arithmetic (no
+seeded random vectors and smooth synthetic fields.  It performs none of the method's arithmetic (no
 stiffness, no filtering, no solves), so both sides can import it without
 sharing any computation.
 """
@@ -22,5 +22,6 @@ from .problems import (  # noqa: F401
     small_problem,
     rand_vector,
     rand_density,
+    smooth_fields,
     grid_counts,
 )

@@ -279,3 +279,24 @@ def rand_vector(n: int, seed: int, fixed: np.ndarray | None = None) -> np.ndarra
 def rand_density(nel: int, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
     """Uniform float64 density field in [lo, hi]."""
     return np.random.default_rng(seed).uniform(lo, hi, nel)
+
+
+def smooth_fields(nelx: int, nely: int, nelz: int, fixed: np.ndarray, count: int) -> List[np.ndarray]:
+    """Smooth displacement-like 3D nodal fields (interleaved x, y, z
+    components), zero on the fixed DOFs: component c of field i is
+    x^(1 + (i + c) mod 3) cos((i + 1) y + c) cos(i z / 2) in coordinates
+    scaled to [0, 1].  Linearly independent for distinct i; a stand-in for
+    stored displacement solutions where none can be computed."""
+    nn = (nelx + 1) * (nely + 1) * (nelz + 1)
+    n = np.arange(nn)
+    x = (n % (nelx + 1)) / nelx
+    y = ((n // (nelx + 1)) % (nely + 1)) / nely
+    z = (n // ((nelx + 1) * (nely + 1))) / nelz
+    out = []
+    for i in range(count):
+        v = np.zeros(3 * nn)
+        for c in range(3):
+            v[c::3] = x ** (1 + (i + c) % 3) * np.cos((i + 1) * y + c) * np.cos(0.5 * i * z)
+        v[fixed.astype(bool)] = 0.0
+        out.append(v)
+    return out
