@@ -52,6 +52,10 @@ def test_workspace_bytes_and_validation():
     assert nbytes < 6 * 2 ** 30
     bad = [
         B.make_desc(4, (8, 8, 8)),
+        B.make_desc(3, (0, 8, 8)),       # empty meshes
+        B.make_desc(3, (8, 8, 0)),
+        B.make_desc(2, (0, 8, 0)),
+        B.make_desc(3, (-2, 8, 8)),
         B.make_desc(3, (9, 8, 8), mg_levels=2),
         B.make_desc(3, (8, 8, 8), mg_levels=1),
         B.make_desc(3, (8, 8, 8), precision=7),
