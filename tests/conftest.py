@@ -13,7 +13,14 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
+# Files that run after every other test, so that a run stopping at the first
+# failure has already run the rest: the full-size workloads (minutes of host
+# oracle work and the largest device footprints).
+RUN_LAST = ("test_gpu_fullsize.py",)
+
+
 def pytest_collection_modifyitems(config, items):
+    items.sort(key=lambda it: os.path.basename(str(it.fspath)) in RUN_LAST)
     # GPU tests are skipped (not failed) on machines without a GPU.
     try:
         import torch

@@ -28,6 +28,9 @@ where it does not, and otherwise the conditions that define the result.
 * 3D cantilever 48 x 24 x 24 (91,875 DOFs; float64, 4 levels): an MGCG
   solve against the oracle's MGCG (iteration count and compliance).
 
+The tests run from the paths the small-grid tests already exercise (the
+48 x 24 x 24 solve) to the largest grid (the bridge, last), and the file
+runs after every other test file.
 Tolerances are those of the small-grid parity tests, which depend on the
 arithmetic per entry, not on the grid size.
 """
@@ -70,6 +73,31 @@ def _upsample(rho, nelx, nely, nelz, k):
     """Each element of an (nelx, nely, nelz) field repeated over a k^3 block."""
     r = rho.reshape(nelz, nely, nelx)
     return np.repeat(np.repeat(np.repeat(r, k, 0), k, 1), k, 2).ravel()
+
+
+# ---------------------------------------------------------------------------
+# 3D cantilever 48 x 24 x 24, float64 (4 levels)
+# ---------------------------------------------------------------------------
+
+def test_cantilever48_fp64_mgcg_against_oracle(design48):
+    B = _B()
+    p = config2_cantilever3d()
+    g, KE = _model(p)
+    E = _E(p, design48)
+    K = fe.stiffness(g, E, KE, p.fixed)
+    mg = solvers.Multigrid(g, K, p.fixed, p.mg_levels)
+    it_ref = solvers.mgcg(K, p.f, mg, rtol=p.rtol, maxit=p.maxit)[1]
+    u_ref = solvers.mgcg(K, p.f, mg, rtol=1e-12, maxit=500)[0]
+    C_ref = sensitivity.compliance(E, sensitivity.element_energy(g, KE, u_ref, p.fixed))
+    with Ctx(p) as c:
+        c.set_density(design48)
+        u = dev(np.zeros(g.ndof))
+        it, rel, ok = B.to_mgcg_solve(c.ctx, p.rtol, p.maxit, 0, u)
+        u = host(u)
+    assert ok and rel < p.rtol
+    assert abs(it - it_ref) <= 1, (it, it_ref)
+    C = sensitivity.compliance(E, sensitivity.element_energy(g, KE, u, p.fixed))
+    assert abs(C - C_ref) <= 1e-10 * C_ref
 
 
 # ---------------------------------------------------------------------------
@@ -311,28 +339,3 @@ def test_bridge320_largest_workload():
     assert np.count_nonzero(at_hi) > 1000
     assert np.all(cand[at_lo] <= lo[at_lo] * (1 + 1e-9))
     assert np.all(cand[at_hi] >= hi[at_hi] * (1 - 1e-9))
-
-
-# ---------------------------------------------------------------------------
-# 3D cantilever 48 x 24 x 24, float64 (4 levels)
-# ---------------------------------------------------------------------------
-
-def test_cantilever48_fp64_mgcg_against_oracle(design48):
-    B = _B()
-    p = config2_cantilever3d()
-    g, KE = _model(p)
-    E = _E(p, design48)
-    K = fe.stiffness(g, E, KE, p.fixed)
-    mg = solvers.Multigrid(g, K, p.fixed, p.mg_levels)
-    it_ref = solvers.mgcg(K, p.f, mg, rtol=p.rtol, maxit=p.maxit)[1]
-    u_ref = solvers.mgcg(K, p.f, mg, rtol=1e-12, maxit=500)[0]
-    C_ref = sensitivity.compliance(E, sensitivity.element_energy(g, KE, u_ref, p.fixed))
-    with Ctx(p) as c:
-        c.set_density(design48)
-        u = dev(np.zeros(g.ndof))
-        it, rel, ok = B.to_mgcg_solve(c.ctx, p.rtol, p.maxit, 0, u)
-        u = host(u)
-    assert ok and rel < p.rtol
-    assert abs(it - it_ref) <= 1, (it, it_ref)
-    C = sensitivity.compliance(E, sensitivity.element_energy(g, KE, u, p.fixed))
-    assert abs(C - C_ref) <= 1e-10 * C_ref
