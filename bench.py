@@ -176,6 +176,24 @@ def _dist():
     return ws, rank, local
 
 
+def slowest_rank(seconds: float, ws: int, device: str = "cuda") -> float:
+    """Time of the slowest rank: an all-reduce MAX over the process group
+    (NCCL on GPUs, gloo on the host), or the local time when alone."""
+    if ws <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps: int, ws: int, slowest_s: float) -> float:
+    """Design iterations per second of all replicas together: every rank
+    runs `steps` iterations of its own job, and the job ends with the slowest."""
+    return ws * steps / slowest_s
+
+
 def _traffic_from_profiles(kernel_tag: str):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
@@ -260,13 +278,8 @@ def run_ours(args):
     del s
     torch.cuda.empty_cache()
 
-    elapsed = max(dev_s, 1e-9)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = ws * K / elapsed
+    elapsed = slowest_rank(max(dev_s, 1e-9), ws)
+    value = whole_job_rate(K, ws, elapsed)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -294,12 +307,8 @@ def run_ours(args):
         barrier()
         e2e_s = e0.elapsed_time(e1) / 1e3
         s.close()
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": ws * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": p.nel * 8,
+        e2e_s = slowest_rank(e2e_s, ws)
+        e2e = {"value": whole_job_rate(K, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": p.nel * 8,
                "d2h_bytes_per_step": p.nel * 8 + 16}
 
     if rank != 0:
