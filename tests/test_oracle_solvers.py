@@ -233,3 +233,27 @@ def test_aarmr_with_full_parm_reduces_to_classical_ca():
     u_c, _, eps_c = reanalysis.reduced_solve(lambda v: K @ v, reanalysis.orthonormalize(R), p.f)
     assert np.linalg.norm(u_a - u_c) < 1e-8 * np.linalg.norm(u_c)
     assert abs(eps_a - eps_c) < 1e-6 * eps_c
+
+
+def test_basis_sizes_the_paper_reports_as_overlapping():
+    """Sec. 4.1's basis-size study reports that the settings
+    (N_s, N_m) = (1, 1), (1, 10) and (10, 1) give exactly overlapping
+    results.  The method explains it: with N_m = 1 the reduced space is
+    span{u_last} whatever N_s; with N_s = 1 every CA vector beyond r_1 lies
+    in span{phi_1}, which holds u_last (the last MGCG solution, or a Galerkin
+    multiple of it).  The three design trajectories, with CARM accepted
+    repeatedly, must coincide: same branches, compliances equal to rounding."""
+    from workloads import config1_mbb2d
+    base = config1_mbb2d()
+    runs = {}
+    for ns, nm in ((1, 1), (1, 10), (10, 1)):
+        p = base.with_(n_parm=ns, n_carm=nm, n_on=12, eps_tol=0.3)
+        runs[(ns, nm)] = aarmr.run(p, n_iter=40, mode="aarmr").history
+    ref = runs[(1, 1)]
+    assert sum(h.branch == "carm" for h in ref) >= 5
+    assert sum(h.branch == "mgcg-fallback" for h in ref) >= 5
+    for key in ((1, 10), (10, 1)):
+        hist = runs[key]
+        assert [h.branch for h in hist] == [h.branch for h in ref], key
+        for a, b in zip(ref, hist):
+            assert abs(a.compliance - b.compliance) <= 1e-9 * a.compliance, (key, a, b)
