@@ -14,13 +14,17 @@ def pytest_configure(config):
 
 
 # Files that run after every other test, so that a run stopping at the first
-# failure has already run the rest: the full-size workloads (minutes of host
-# oracle work and the largest device footprints).
-RUN_LAST = ("test_gpu_fullsize.py",)
+# failure has already run the rest: the newest GPU checks, and the full-size
+# workloads (minutes of host oracle work and the largest device footprints).
+RUN_LAST = ("test_gpu_paper_properties.py", "test_gpu_fullsize.py")
 
 
 def pytest_collection_modifyitems(config, items):
-    items.sort(key=lambda it: os.path.basename(str(it.fspath)) in RUN_LAST)
+    def rank(it):
+        name = os.path.basename(str(it.fspath))
+        return RUN_LAST.index(name) + 1 if name in RUN_LAST else 0
+
+    items.sort(key=rank)
     # GPU tests are skipped (not failed) on machines without a GPU.
     try:
         import torch
