@@ -14,9 +14,9 @@ def pytest_configure(config):
 
 
 # Files that run after every other test, so that a run stopping at the first
-# failure has already run the rest: the newest GPU checks, and the full-size
-# workloads (minutes of host oracle work and the largest device footprints).
-RUN_LAST = ("test_gpu_paper_properties.py", "test_gpu_fullsize.py")
+# failure has already run the rest: the full-size workloads (minutes of host
+# oracle work and the largest device footprints), then the newest checks.
+RUN_LAST = ("test_gpu_fullsize.py", "test_gpu_paper_properties.py")
 
 
 def pytest_collection_modifyitems(config, items):
