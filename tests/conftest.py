@@ -21,7 +21,7 @@ RUN_LAST = ("test_gpu_fullsize.py", "test_gpu_paper_properties.py")
 
 def pytest_collection_modifyitems(config, items):
     def rank(it):
-        name = os.path.basename(str(it.fspath))
+        name = os.path.basename(str(getattr(it, "path", None) or it.fspath))
         return RUN_LAST.index(name) + 1 if name in RUN_LAST else 0
 
     items.sort(key=rank)
