@@ -21,6 +21,7 @@ the paper's printed results (parity unpinned beyond the per-step pins).
 
 from __future__ import annotations
 
+import time
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional
 
@@ -82,6 +83,7 @@ class IterRecord:
     cg_iters: int
     change: float
     w_percent: float
+    seconds: float = 0.0      # wall time of the iteration (timing only)
 
 
 @dataclass
@@ -108,6 +110,7 @@ def run(prob, n_iter: Optional[int] = None, mode: str = "aarmr", snapshot_at=(),
     rho_phys_prev = None
     traj = Trajectory(rho)
     for k in range(1, n_iter + 1):
+        t0 = time.perf_counter()
         rho_phys = filters.density_filter(m.H, m.Hs, rho)
         E = m.modulus(rho_phys)
         K = m.K(E)
@@ -142,7 +145,8 @@ def run(prob, n_iter: Optional[int] = None, mode: str = "aarmr", snapshot_at=(),
         dc_f = filters.sensitivity_filter(m.H, m.Hs, dc)
         rho_new, _, change = oc.oc_update(rho, dc_f, m.dv_f, m.H, m.Hs, p.volfrac, p.move)
         w = float(np.mean(np.abs(rho_new - rho)) * 100.0)      # Eq. 30
-        traj.history.append(IterRecord(k, branch, C, eps, iters, change, w))
+        traj.history.append(IterRecord(k, branch, C, eps, iters, change, w,
+                                       time.perf_counter() - t0))
         rho = rho_new
         u_last = u
         E_prev = E

@@ -13,10 +13,14 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
-# Files that run after every other test, so that a run stopping at the first
-# failure has already run the rest: the full-size workloads (minutes of host
-# oracle work and the largest device footprints), then the newest checks.
-RUN_LAST = ("test_gpu_fullsize.py", "test_gpu_paper_properties.py")
+# Files that run after every other test, in this order, so that a run
+# stopping at the first failure has already run the rest: the CARM and
+# trajectory checks at the workloads' basis sizes (a minute or more of host
+# oracle work each), the full-size workloads (the largest device
+# footprints), the paper's reported properties, and last the entry point
+# that works without device allocations.
+RUN_LAST = ("test_gpu_carm_s10.py", "test_gpu_trajectories.py", "test_gpu_fullsize.py",
+            "test_gpu_paper_properties.py", "test_zz_no_alloc.py")
 
 
 def pytest_collection_modifyitems(config, items):

@@ -1,44 +1,29 @@
-"""Host logic of bench.py that needs no GPU: reading the per-launch DRAM
-traffic of the dominant kernel from the committed ncu summary."""
-
-import hashlib
-import os
+"""Host logic of bench.py that needs no GPU: the oracle's timed window and
+the extrapolation of its time per iteration, and the aggregation of
+replicas under torchrun."""
 
 import bench
 
 
-def _fake_tree(tmp_path, source: bytes, record_sha: str, nbytes: str):
-    csrc = tmp_path / "paper_2205_00385_gb300" / "csrc"
-    csrc.mkdir(parents=True)
-    (csrc / "kernels_pair.cu").write_bytes(source)
-    prof = tmp_path / "profiles"
-    prof.mkdir()
-    (prof / "apply_pair_cantilever192.md").write_text(
-        "# summary\n\n"
-        "- note: a line whose value: has colons\n"
-        f"- kernels_pair.cu sha256[:16]: `{record_sha}`\n"
-        f"- k_apply3_pair dram bytes per launch: `{nbytes}`\n")
+def test_extrapolation_fits_the_growth_exponent():
+    small = {"per_iter_s": 1.0, "dofs": 1000}
+    large = {"per_iter_s": 8.0 * 2 ** 0.5, "dofs": 8000}      # ~ DOFs^(7/6)
+    alpha, t = bench.extrapolate_time(small, large, 64000)
+    assert abs(alpha - 7.0 / 6.0) < 1e-12
+    assert abs(t - large["per_iter_s"] * 8.0 ** alpha) < 1e-9
 
 
-def test_traffic_read_when_the_source_hash_matches(tmp_path, monkeypatch):
-    src = b"__global__ void k() {}\n"
-    sha = hashlib.sha256(src).hexdigest()[:16]
-    _fake_tree(tmp_path, src, sha, "30485760")
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic_from_profiles("k_apply3_pair") == 30485760.0
+def test_extrapolation_never_grows_slower_than_linear():
+    alpha, t = bench.extrapolate_time({"per_iter_s": 1.0, "dofs": 1000},
+                                      {"per_iter_s": 2.0, "dofs": 8000}, 16000)
+    assert alpha == 1.0 and t == 4.0
 
 
-def test_traffic_dropped_when_the_kernel_changed(tmp_path, monkeypatch):
-    _fake_tree(tmp_path, b"new source\n", "0123456789abcdef", "30485760")
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic_from_profiles("k_apply3_pair") is None
-
-
-def test_committed_summary_names_the_kernel_source_hash():
-    path = os.path.join(bench.ROOT, "profiles", "apply_pair_cantilever192.md")
-    text = open(path).read()
-    assert "- kernels_pair.cu sha256[:16]: `" in text
-    assert "- k_apply3_pair dram bytes per launch: `" in text
+def test_oracle_window_times_the_requested_iterations():
+    w = bench.oracle_window("24x12x12", 1, 2)
+    assert w["iterations"] == "2..3" and len(w["seconds"]) == 2
+    assert w["dofs"] == 3 * 25 * 13 * 13
+    assert sum(w["branches"].values()) == 2 and w["per_iter_s"] > 0.0
 
 
 # ---------------------------------------------------------------------------
@@ -94,7 +79,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     import argparse
     monkeypatch.setenv("WORLD_SIZE", "2")
     monkeypatch.setenv("RANK", "1")
-    monkeypatch.setattr(bench, "cpu_baseline",
+    monkeypatch.setattr(bench, "oracle_window",
                         lambda *a, **k: (_ for _ in ()).throw(AssertionError("ran on rank 1")))
     args = argparse.Namespace(warmup=3, steps=2, precision="mixed")
     assert bench.run_reference(args) is None

@@ -9,6 +9,9 @@ Tolerances (relative unless stated):
   coarse inverse is formed explicitly); float32 V-cycle: 2e-3 (the coarsest
   grid's explicit inverse is formed in float32 from a matrix of condition
   ~1e4, so its relative error is ~1e-3);
+* CARM build and solve: the same kept directions (Eq. 21), then u~, eps and
+  compliance within 1e-9 / 1e-8 / 1e-10 (float64) and 1e-6 (mixed), see
+  CARM_TOL;
 * MGCG solutions: compliance within 1e-10 (float64 path, rtol 1e-12) and
   1e-6 (mixed path) of the exact solve -- the stated per-solve targets;
 * filter, sensitivity filter: 1e-12; compliance and sensitivity: 1e-10
@@ -73,7 +76,16 @@ def test_apply_parity(kind, kw, op):
         y64, y32, ydf = host(y64), host(y32), host(ydf)
     scale = np.max(np.abs(y_ref))
     assert np.max(np.abs(y64 - y_ref)) <= 1e-13 * scale
-    assert np.linalg.norm(y32 - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+    # float32, entry by entry: x, E and KE are rounded to float32 and each
+    # element product passes through magnitudes up to max|KE| sum_j |x_j|
+    # (transforms and block products of ~20 rounding steps, 8 element sums
+    # per node), so the error of entry i is bounded by ~160 u32 ~ 1e-5 of
+    # S_i = sum_e |E_e| max|KE| sum_(j in e) |x_j|; a lost or doubled element
+    # contribution would be ~5e-3 of S_i
+    S = fe.apply_ebe(g, np.abs(coef), np.full_like(KE, np.max(np.abs(KE))), np.abs(x), p.fixed,
+                     diag_fixed=1.0)
+    print(f"[apply f32 {kind} op{op}] max |err|/S = {np.max(np.abs(y32 - y_ref) / S):.2e}")
+    assert np.all(np.abs(y32 - y_ref) <= 1e-5 * S + 1e-30), np.max(np.abs(y32 - y_ref) / S)
     # double-float: 48-bit significands, errors relative to |KE| |x_e| summed
     # over ~30 terms per entry -> 1e-12 of the largest entry
     assert np.max(np.abs(ydf - y_ref)) <= 1e-12 * scale
@@ -272,6 +284,18 @@ def test_filter_sensitivity_oc_parity(kind, kw, precision):
         assert abs(host(ch)[0] - change_ref) <= 1e-10
 
 
+# CARM parity on the oracle's inputs.  Both sides build the basis with
+# float64-accurate products and keep the same singular directions; what
+# differs is rounding of the basis (float64 or double-float, ~1e-16 or
+# ~4e-15 per operation, amplified by the cancellation of K on smooth
+# fields), which moves the kept directions by that much over their
+# singular value (>= 1e-6 of the largest).  The Galerkin compliance is
+# stationary in the subspace, so it moves at second order; u~ and eps at
+# first order.
+CARM_TOL = {"fp64": {"u": 1e-9, "eps": 1e-8, "C": 1e-10},
+            "mixed": {"u": 1e-6, "eps": 1e-6, "C": 1e-6}}
+
+
 def _carm_case(kind, kw, ns, k_snap):
     p = small_problem(kind, mg_levels=3, n_on=6, n_parm=ns, n_carm=ns, eps_tol=10.0,
                       rtol=1e-12, **kw)
@@ -299,17 +323,17 @@ def test_carm_parity(kind, kw, precision):
         for i in range(s["Phi"].shape[1]):
             B.to_parm_push(c.ctx, dev(s["Phi"][:, i]))
         B.to_carm_build(c.ctx, dev(s["u_last"]))
+        _, k, _ = B.to_carm_info(c.ctx)
         u = dev(np.zeros(g.ndof))
         eps = B.to_carm_solve(c.ctx, u)
         u = host(u)
+    # both sides keep the directions with sigma > 1e-6 sigma_1 (Eq. 21)
+    assert k == Rt.shape[1], (k, Rt.shape[1])
     C, C_ref = p.f @ u, p.f @ u_ref
-    if precision == "fp64":
-        assert abs(eps - eps_ref) <= 1e-6 * eps_ref
-        assert np.linalg.norm(u - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
-        assert abs(C - C_ref) <= 1e-9 * C_ref
-    else:
-        assert abs(eps - eps_ref) <= 1e-3 * eps_ref + 1e-6
-        assert abs(C - C_ref) <= 1e-6 * C_ref
+    tol = CARM_TOL[precision]
+    assert np.linalg.norm(u - u_ref) <= tol["u"] * np.linalg.norm(u_ref)
+    assert abs(eps - eps_ref) <= tol["eps"] * eps_ref
+    assert abs(C - C_ref) <= tol["C"] * C_ref
 
 
 @pytest.mark.parametrize("kind,kw", PROBLEMS[:2])

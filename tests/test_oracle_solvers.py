@@ -113,6 +113,49 @@ def test_approx_inverse_invariant_to_scaling_and_permutation():
     assert np.linalg.norm(a - b) < 1e-10 * np.linalg.norm(a)
 
 
+def test_singular_k_phi_takes_the_pseudo_inverse():
+    """The fallback of the K_Phi inverse (Cholesky fails: pseudo-inverse).
+    A = B B^T with B = [[1, 0], [0, 1], [1, 1]] is singular with integer
+    entries, so Cholesky meets an exactly zero third pivot (2 - 1 - 1) and
+    the eigen branch runs.  Its Moore-Penrose inverse has the closed form
+    B (B^T B)^-2 B^T = [[5, -4, 1], [-4, 5, 1], [1, 1, 2]] / 9, worked out
+    by hand from B^T B = [[2, 1], [1, 2]]; a kept null direction (wrong
+    cutoff) or a transposed eigenvector matrix would not give it."""
+    A = np.array([[1.0, 0.0, 1.0], [0.0, 1.0, 1.0], [1.0, 1.0, 2.0]])
+    with pytest.raises(np.linalg.LinAlgError):
+        sla.cho_factor(A)
+    P = reanalysis.small_spd_inverse(A)
+    closed = np.array([[5.0, -4.0, 1.0], [-4.0, 5.0, 1.0], [1.0, 1.0, 2.0]]) / 9.0
+    assert np.max(np.abs(P - closed)) < 1e-14
+    # Penrose conditions
+    assert np.max(np.abs(A @ P @ A - A)) < 1e-14
+    assert np.max(np.abs(P @ A @ P - P)) < 1e-14
+    assert np.max(np.abs((A @ P).T - A @ P)) < 1e-14
+
+
+def test_approx_inverse_with_a_repeated_parm_column():
+    """Eq. 18 depends on span(Phi) only (span invariance): a PARM holding
+    one column twice (K_Phi singular) gives the operator of the PARM without
+    the repeat, whichever branch the K_Phi inverse takes; and a PARM with a
+    zero column (exact zero pivot, so the pseudo-inverse branch) gives that
+    of the PARM without it."""
+    p, g, KE = _setup("cantilever3d", nelx=4, nely=2, nelz=2)
+    rng = np.random.default_rng(18)
+    Kr = fe.stiffness(g, rng.uniform(0.2, 1, g.nel), KE, p.fixed)
+    Phi = rng.standard_normal((g.ndof, 3))
+    v = rng.standard_normal(g.ndof)
+    kphi = lambda F: reanalysis.k_phi(F, lambda x: Kr @ x)
+    ref = reanalysis.approx_inverse(Phi, kphi(Phi))(v)
+    rep = Phi[:, [0, 1, 1, 2]]
+    assert np.linalg.norm(reanalysis.approx_inverse(rep, kphi(rep))(v) - ref) <= \
+        1e-10 * np.linalg.norm(ref)
+    zc = np.concatenate([Phi[:, :2], np.zeros((g.ndof, 1)), Phi[:, 2:]], axis=1)
+    with pytest.raises(np.linalg.LinAlgError):
+        sla.cho_factor(0.5 * (kphi(zc) + kphi(zc).T))
+    assert np.linalg.norm(reanalysis.approx_inverse(zc, kphi(zc))(v) - ref) <= \
+        1e-10 * np.linalg.norm(ref)
+
+
 def _carm_fixture(seed=9, ns=3):
     p, g, KE = _setup("cantilever3d", nelx=6, nely=2, nelz=2)
     rng = np.random.default_rng(seed)

@@ -5,8 +5,9 @@ takes no context and no workspace; its scratch is a static device array of
 the library).  Two calls in a row must give the same design update as
 to_oc_update, within the OC tolerance of the parity tests (1e-10 absolute on
 rho), so leftover scratch contents from the first call cannot leak into the
-second.  This file sorts last so that a run that stops at the first failure
-has already run every other test.
+second.  The test suite's ordering (tests/conftest.py) puts this file last,
+so that a run that stops at the first failure has already run every other
+test.
 """
 
 import numpy as np
