@@ -110,13 +110,19 @@ to_status to_set_density(to_ctx* ctx, const double* rho_phys);
  *   residual is tested; in TO_MIXED (float32 operator inside CG) the
  *   recursive residual is replaced by the float64 true residual f - K u
  *   whenever it has dropped 100x since the last replacement, and
- *   convergence is declared on the true residual.
+ *   convergence is declared on the true residual; where the true residual
+ *   exceeds the recursive one by more than 1.5x, CG restarts from it.
  * maxit: CG iteration cap (>= 1).  On the cap the last iterate is returned
  *   with TO_E_NOT_CONVERGED.
  * flags & TO_SOLVE_PUSH_PARM: append u/||u|| to the PARM (Eq. 28), dropping
  *   the oldest column when full (Sec. 3.1).
  * iters (host, may be NULL): CG iterations taken; relres (host, may be
- *   NULL): final relative residual.  This call synchronises the stream. */
+ *   NULL): final relative residual.  This call synchronises the stream.
+ * The host reads |r|^2 once per CG iteration; the read is enqueued before
+ * the next preconditioner application and waited on after it, so the
+ * V-cycle runs during the round trip (its result is discarded on the
+ * iteration that stops).  The first call on a context allocates 64 bytes of
+ * pinned host memory for that read (released by to_destroy). */
 to_status to_mgcg_solve(to_ctx* ctx, double rtol, int32_t maxit, int32_t flags, double* u,
                         int32_t* iters, double* relres);
 
@@ -127,13 +133,74 @@ to_status to_parm_count(to_ctx* ctx, int32_t* count);
 /* Remove all PARM columns. */
 to_status to_parm_reset(to_ctx* ctx);
 
+/* Truncation of the CARM basis (Eq. 21, which states no rule): with the
+ * basis columns scaled to unit length, singular directions with
+ * sigma_i <= TO_CARM_SVD_TOL * sigma_1 are dropped.  The value sits well
+ * above the rounding level of the basis in either precision (both build it
+ * with float64-accurate products) and below every direction that changes
+ * the reduced solution measurably. */
+#define TO_CARM_SVD_TOL 1e-6
+/* A basis column keeping <= TO_QR_DEPENDENT_TOL of its norm after being
+ * orthogonalised twice against the earlier ones is numerically dependent on
+ * them: it adds no column to the orthonormal factor (its projections stay
+ * in the triangular factor, so the SVD still sees it). */
+#define TO_QR_DEPENDENT_TOL 1e-10
+
 /* Build the CARM basis R~ from u_last (dev, float64, n): K_Phi = Phi^T K_ref
  * Phi (Eq. 15), r_1 = u_last, r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}
- * (Eq. 18-20, 26), orthonormalised by classical Gram-Schmidt with
- * re-orthogonalisation (the basis-orthogonalisation step of Eq. 21); a
- * column whose norm after two passes is <= 1e-10 of its norm before is
- * dropped.  Needs a full PARM (else TO_E_STATE). */
+ * (Eq. 18-20, 26), with float64-accurate products in both precisions; then
+ * Eq. 21: R (columns scaled to unit length) = R~ Sigma V^T truncated at
+ * TO_CARM_SVD_TOL, computed as a QR factorisation of R (classical
+ * Gram-Schmidt, two passes per column) followed by the SVD of the small
+ * triangular factor on the device.  R~ has the kept left singular vectors
+ * as columns, in descending order of sigma.  Needs a full PARM (else
+ * TO_E_STATE); TO_E_SINGULAR if nothing is kept (u_last = 0).
+ * Synchronises once (reads the kept count). */
 to_status to_carm_build(to_ctx* ctx, const double* u_last);
+
+/* Autotuner of the launch shapes of the column-streaming 3D operators.
+ * Their free parameter is the number of node layers a block streams along
+ * z (each chunk recomputes one element layer below it, so fewer, longer
+ * chunks do less redundant work but fill fewer SMs).  to_autotune times,
+ * with CUDA events on the context stream, every distinct chunk length of
+ * each kernel the context's solver runs on this grid:
+ *   TO_TUNE_OP_APPLY / _RESID / _SMOOTH: the finest-grid operator of the
+ *     solver (float32 in TO_MIXED, float64 in TO_FP64) as K p, as the
+ *     V-cycle's residual and as its post-smoother;
+ *   TO_TUNE_GAL1_RESID / _SMOOTH: the level-1 Galerkin operator applied
+ *     from the finest moduli (3D, >= 3 levels);
+ *   TO_TUNE_ACC_APPLY / _RESID: the double-float operator (TO_MIXED).
+ * It keeps the fastest (the occupancy heuristic's own shape when within 1 %
+ * of it), applies it to every later launch of that kernel on this context,
+ * drops the captured V-cycle graphs so that they are recaptured with it, and
+ * caches it for the process under (device, kernel, grid), so later
+ * contexts of the same grid take it without timing.  Results do not depend
+ * on the chunking (every node sums its element contributions in the same
+ * order).  reps: timed launches per candidate (>= 1); results (host, may be
+ * NULL): up to cap entries, one per kernel; *count (host): entries written.
+ * Needs to_set_density first (TO_E_STATE); synchronises; do not call during
+ * stream capture.  2D contexts have nothing to tune (*count = 0). */
+enum { TO_TUNE_OP_APPLY = 0, TO_TUNE_OP_RESID = 1, TO_TUNE_OP_SMOOTH = 2, TO_TUNE_GAL1_RESID = 3,
+       TO_TUNE_GAL1_SMOOTH = 4, TO_TUNE_ACC_APPLY = 5, TO_TUNE_ACC_RESID = 6, TO_TUNE_N = 7 };
+typedef struct {
+  int32_t kernel;        /* TO_TUNE_* */
+  int32_t candidates;    /* chunk lengths timed (0: taken from the process cache) */
+  int32_t chunk_layers;  /* chosen node layers per chunk (0: the heuristic's shape) */
+  double chosen_us;      /* average launch time of the chosen shape (0 when cached) */
+  double heuristic_us;   /* average launch time of the heuristic's shape (0 when cached) */
+} to_tune_result;
+to_status to_autotune(to_ctx* ctx, int32_t reps, to_tune_result* results, int32_t cap,
+                      int32_t* count);
+
+/* Test hook on the last CARM basis: *kq (host) = columns of the QR factor,
+ * *k (host) = directions kept by Eq. 21, sigma (host, may be NULL, n_carm
+ * doubles) = singular values of the unit-column basis, descending
+ * (synchronises when sigma is given).  TO_E_STATE before to_carm_build. */
+to_status to_carm_info(to_ctx* ctx, int32_t* kq, int32_t* k, double* sigma);
+
+/* Test hook: column j (0 <= j < k) of the last CARM basis R~, widened to
+ * float64 into out (dev, n).  TO_E_INVALID for j out of range. */
+to_status to_carm_basis_column(to_ctx* ctx, int32_t j, double* out);
 
 /* Test hook: *err (host) = max_ij |(R~^T R~)_ij - delta_ij| over the last
  * CARM basis (synchronises).  Overwrites the reduced matrix, so call
@@ -178,12 +245,15 @@ to_status to_oc_update(to_ctx* ctx, double volfrac, double move, const double* d
  *   cudaStream_t (as void*) on which the kernels are enqueued; the call does
  *   not synchronise.
  * Scratch: a ~16 MiB file-scope device array of the library, which every GPU
- * that loads libtopo.so holds until the process exits.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
- * share the array: calls that overlap on the GPU (different streams, devices
- * are separate) race and must be serialised by the caller.  Errors are
- * reported by the return code and to_last_error(NULL). */
+ * that loads libtopo.so holds until the process exits.  Its device address
+ * belongs to the CUDA context current when the call is made: the first call
+ * in each context (the primary context of a device, a context the caller
+ * created and made current, or the new primary context after a
+ * cudaDeviceReset) looks the address up (cudaGetSymbolAddress) and caches
+ * it under the context's unique ID; make that first call before any stream
+ * capture.  All calls in one context share the array: calls that overlap on
+ * the GPU (different streams) race and must be serialised by the caller.
+ * Errors are reported by the return code and to_last_error(NULL). */
 to_status to_oc_update_noalloc(int64_t nel, double volfrac, double move, const double* dc_f,
                                const double* dv_f, double* rho, double* change_dev,
                                void* stream);

@@ -46,6 +46,9 @@ _SIGS = {
     "to_workspace_bytes": [C.POINTER(to_mesh_desc), C.POINTER(C.c_int64)],
     "to_mesh_init": [C.POINTER(to_mesh_desc), _VP, _VP, _VP, C.c_int64, _VP, C.POINTER(_VP)],
     "to_carm_basis_error": [_VP, C.POINTER(C.c_double)],
+    "to_carm_info": [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _VP],
+    "to_autotune": [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)],
+    "to_carm_basis_column": [_VP, C.c_int32, _VP],
     "to_set_density": [_VP, _VP],
     "to_mgcg_solve": [_VP, C.c_double, C.c_int32, C.c_int32, _VP, C.POINTER(C.c_int32),
                       C.POINTER(C.c_double)],
@@ -178,6 +181,40 @@ def to_carm_basis_error(ctx) -> float:
     e = C.c_double()
     _check(load().to_carm_basis_error(ctx, C.byref(e)), ctx)
     return e.value
+
+
+def to_carm_info(ctx, n_carm=None):
+    """(kq, k, sigma) of the last CARM basis (test hook): QR columns, kept
+    directions and, when n_carm is given, the singular values (descending)."""
+    kq, k = C.c_int32(), C.c_int32()
+    sig = (C.c_double * n_carm)() if n_carm else None
+    _check(load().to_carm_info(ctx, C.byref(kq), C.byref(k),
+                               C.cast(sig, _VP) if sig is not None else None), ctx)
+    return kq.value, k.value, (list(sig) if sig is not None else None)
+
+
+TUNE_KERNELS = ("op_apply", "op_resid", "op_smooth", "gal1_resid", "gal1_smooth", "acc_apply",
+                "acc_resid")
+
+
+class to_tune_result(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("candidates", C.c_int32), ("chunk_layers", C.c_int32),
+                ("chosen_us", C.c_double), ("heuristic_us", C.c_double)]
+
+
+def to_autotune(ctx, reps=10):
+    """Times the launch shapes of the context's column-streaming operators and
+    keeps the fastest (see include/topo.h); returns one dict per kernel."""
+    res = (to_tune_result * len(TUNE_KERNELS))()
+    n = C.c_int32()
+    _check(load().to_autotune(ctx, reps, C.cast(res, _VP), len(TUNE_KERNELS), C.byref(n)), ctx)
+    return [dict(kernel=TUNE_KERNELS[r.kernel], candidates=r.candidates,
+                 chunk_layers=r.chunk_layers, chosen_us=r.chosen_us, heuristic_us=r.heuristic_us)
+            for r in res[:n.value]]
+
+
+def to_carm_basis_column(ctx, j, out):
+    _check(load().to_carm_basis_column(ctx, j, _ptr(out)), ctx)
 
 
 def to_sensitivity(ctx, u, compliance_dev, dc):

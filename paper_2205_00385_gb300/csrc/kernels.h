@@ -44,6 +44,8 @@ struct ApplyArgs {
   const void* S;       // explicit levels: assembled stencil coefficients (type tc)
   const uint8_t* colfix = nullptr;   // per node column (i, j): 1 if any DOF of the
                                      // column is fixed (null: mask every node)
+  int zsplit = 0;      // layers per z-chunk of the column-streaming 3D kernels, set
+                       // by the autotuner (0: the launcher's occupancy heuristic)
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 // Float32 3D finest-grid operator, two element columns per thread with packed
@@ -102,11 +104,14 @@ cudaError_t launch_galerkin_l2(int t, const GridP& g2, const GridP& gf, const vo
 cudaError_t launch_stencil_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
                                     const void* Kc, void* S, cudaStream_t s);
 long long stencil_values(int dim, int t, const GridP& g);
-cudaError_t launch_dense_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
-                                  const void* Kc, void* A, cudaStream_t s);
+// coarsest grid: the dense matrix A (float64, row-major) from the level's
+// packed element matrices of storage t; its Cholesky-based explicit inverse
+// (float64); y = A x with A float64 and x, y of storage t
+cudaError_t launch_dense_assemble(int dim, int t, int ta, const GridP& g, const uint8_t* mask,
+                                  const void* Kc, void* A, double shift, cudaStream_t s);
 cudaError_t launch_cholesky_inverse(int t, int n, void* A, void* Ainv, int* status,
                                     cudaStream_t s);
-cudaError_t launch_dense_gemv(int t, int n, const void* A, const void* x, void* y,
+cudaError_t launch_dense_gemv(int ta, int t, int n, const void* A, const void* x, void* y,
                               cudaStream_t s);
 cudaError_t launch_convert(int tin, int tout, long long n, const void* in, void* out,
                            cudaStream_t s);
@@ -158,11 +163,18 @@ cudaError_t launch_combine(long long n, int vt, const void* A, int m, const int*
                            const double* c, double sign, double beta, void* y, int yt,
                            const void* w, double* rr, double* partials, unsigned* counter,
                            cudaStream_t s);
-// Gram-Schmidt step: column src of R (norm^2 before in scal[n0], after in
-// scal[n1]) is appended to the basis at position ints[I_KCOUNT] if it kept
-// more than tol of its length, normalised.
+// Gram-Schmidt step of the QR factorisation of the CARM basis: column src
+// of R (norm^2 before in scal[n0], after in scal[n1]) is appended to the
+// orthonormal factor at position ints[I_KCOUNT] if it kept more than tol of
+// its length, normalised; column src of the triangular factor Rt (ld MAXB)
+// receives its projections h1 + h2 on the earlier columns (and its remaining
+// norm when accepted), rn[src] its norm before orthogonalisation.
 cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double* scal, int n0,
-                             int n1, double tol, int* ints, cudaStream_t s);
+                             int n1, double tol, const double* h1, const double* h2, double* Rt,
+                             double* rn, int* ints, cudaStream_t s);
+// Y[:, j] = sum_{i < kq} U[i + MAXB j] Q[:, i] for j < k <= kq (Y != Q)
+cudaError_t launch_combine_multi(long long n, int vt, const void* Q, int kq, const double* U,
+                                 int k, void* Y, cudaStream_t s);
 // mixed-path CG (pairs x, r, p; float32 shadows p32 -> q32 and z32)
 cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* partials,
                            unsigned* counter, double* out, cudaStream_t s);
@@ -183,6 +195,12 @@ cudaError_t launch_small_matvec(int m, const int* m_dev, const double* A, const 
                                 double* y, double sign, cudaStream_t s);
 cudaError_t launch_small_chol_solve(int m, const int* m_dev, const double* A, const double* b,
                                     double* x, int* status, cudaStream_t s);
+// truncated SVD of the unit-column basis from its QR factor (one warp):
+// U (ld MAXB) <- kept left singular vectors of Rt diag(rn)^-1 with
+// sigma > tau sigma_1, ints[I_KRED] <- their count, sig <- singular values
+cudaError_t launch_small_svd_trunc(int m, const int* kq_dev, const double* Rt, const double* rn,
+                                   double tau, double* U, double* sig, int* ints,
+                                   cudaStream_t s);
 cudaError_t launch_eps(const double* scal, int rr, int f2, double* eps_dev, cudaStream_t s);
 
 // ---- design-optimisation kernels (kernels_opt.cu) ----

@@ -218,9 +218,87 @@ __global__ void k_small_chol_solve(int mmax, const int* m_dev, const double* A, 
   chol_solve_small(m, L, b, x);
 }
 
-// Gram-Schmidt acceptance: column src (already orthogonalised twice) is
-// kept if |r|^2 after > tol^2 |r|^2 before; it is then normalised into
-// column k = ints[I_KCOUNT] and k is incremented.  Runs as a grid.
+// Truncated SVD of Eq. 21 from the QR factor of the CARM basis.  The
+// basis R (m columns) equals Q Rt with Q orthonormal (kq columns) and Rt
+// kq x m; with D the column norms of R, the unit-column basis R D^-1 has the
+// singular values of A = Rt D^-1, and its left singular vectors are Q U with
+// U those of A.  One warp runs one-sided (Hestenes) Jacobi on the columns of
+// A, lane r holding row r: each rotation makes a pair of columns
+// orthogonal, until every pair is orthogonal to 1e-15 of the product of
+// their norms; the column norms are then the singular values.  Directions
+// with sigma <= tau sigma_1 are dropped; the kept ones, in descending order,
+// are written to U (ld MAXB), their count to ints[I_KRED] and every
+// singular value, descending, to sig.  A column of R that is zero (norm 0)
+// contributes nothing.
+__global__ void k_small_svd_trunc(int m, const int* kq_dev, const double* Rt, const double* rn,
+                                  double tau, double* U, double* sig, int* ints) {
+  __shared__ double sA[MAXB * 32];   // column j, row r at sA[32 j + r]
+  __shared__ double snrm[MAXB];
+  __shared__ int sord[MAXB];
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int r = threadIdx.x;
+  const int kq = min(max(*kq_dev, 0), MAXB);
+  m = min(max(m, 0), MAXB);
+  for (int j = 0; j < MAXB; ++j) {
+    double v = 0.0;
+    if (j < m && r < kq && rn[j] > 0.0) v = Rt[r + (size_t)MAXB * j] / rn[j];
+    sA[32 * j + r] = v;
+  }
+  __syncwarp();
+  auto wsum = [](double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  };
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rotated = false;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double ap = sA[32 * p + r], aq = sA[32 * q + r];
+        const double alpha = wsum(ap * ap), beta = wsum(aq * aq), gamma = wsum(ap * aq);
+        if (!(fabs(gamma) > 1e-15 * sqrt(alpha * beta))) continue;
+        rotated = true;
+        const double zeta = (beta - alpha) / (2.0 * gamma);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        sA[32 * p + r] = c * ap - sn * aq;
+        sA[32 * q + r] = sn * ap + c * aq;
+        __syncwarp();
+      }
+    if (!rotated) break;
+  }
+  for (int j = 0; j < MAXB; ++j) {
+    const double a = sA[32 * j + r];
+    const double nj = sqrt(wsum(a * a));
+    if (r == 0) snrm[j] = j < m ? nj : -1.0;
+  }
+  __syncwarp();
+  if (r == 0) {
+    // descending order of the column norms (ties keep column order)
+    bool used[MAXB];
+    for (int j = 0; j < MAXB; ++j) used[j] = false;
+    for (int t = 0; t < m; ++t) {
+      int best = -1;
+      for (int j = 0; j < m; ++j)
+        if (!used[j] && (best < 0 || snrm[j] > snrm[best])) best = j;
+      used[best] = true;
+      sord[t] = best;
+    }
+  }
+  __syncwarp();
+  const double s1 = m > 0 ? snrm[sord[0]] : 0.0;
+  int k = 0;
+  for (int t = 0; t < m; ++t) {
+    const int j = sord[t];
+    const double sj = snrm[j];
+    if (r == 0) sig[t] = sj;
+    if (!(s1 > 0.0) || !(sj > tau * s1)) continue;
+    if (r < kq) U[r + (size_t)MAXB * k] = sA[32 * j + r] / sj;
+    ++k;
+  }
+  if (r == 0) ints[I_KRED] = k;
+}
+
 
 __global__ void k_eps(const double* scal, int rr, int f2, double* eps_dev) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *eps_dev = sqrt(scal[rr] / scal[f2]);
@@ -289,6 +367,14 @@ cudaError_t launch_small_chol_solve(int m, const int* m_dev, const double* A, co
   return cudaGetLastError();
 }
 
+
+cudaError_t launch_small_svd_trunc(int m, const int* kq_dev, const double* Rt, const double* rn,
+                                   double tau, double* U, double* sig, int* ints,
+                                   cudaStream_t s) {
+  if (m < 1 || m > MAXB) return cudaErrorInvalidValue;
+  k_small_svd_trunc<<<1, 32, 0, s>>>(m, kq_dev, Rt, rn, tau, U, sig, ints);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_eps(const double* scal, int rr, int f2, double* eps_dev, cudaStream_t s) {
   k_eps<<<1, 32, 0, s>>>(scal, rr, f2, eps_dev);

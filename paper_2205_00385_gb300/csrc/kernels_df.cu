@@ -237,6 +237,7 @@ cudaError_t launch_apply_df(const ApplyArgs& a, cudaStream_t s) {
       }
     }
   }
+  if (a.zsplit > 0) zc = min(a.zsplit, (int)a.g.nnz);   // chosen by the autotuner
   dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
   if (a.tx == T_D2)
     run_df<float2>(a, kb, grid, zc, s);

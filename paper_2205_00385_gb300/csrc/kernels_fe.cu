@@ -669,6 +669,7 @@ static cudaError_t run_col(const ApplyArgs& a, cudaStream_t s) {
       }
     }
   }
+  if (a.zsplit > 0) zc = min(a.zsplit, (int)a.g.nnz);   // chosen by the autotuner
   dim3 grid(gx, gy, (a.g.nnz + zc - 1) / zc);
   return launch_pdl(k_apply3_col<TC, TX, TY, EPI, OP>, grid, dim3(WX * WY), 0, s, a.g, a.gf, a.mask,
                     kb, static_cast<const TC*>(a.coef), zc, static_cast<const TX*>(a.x),

@@ -341,10 +341,10 @@ __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
 // One thread per matrix entry, summing over the elements shared by both
 // nodes (deterministic).  Row-major n x n.
 // ---------------------------------------------------------------------------
-template <int DIM, typename T>
+template <int DIM, typename T, typename TA>
 __global__ void __launch_bounds__(256)
     k_dense_assemble(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ Kc,
-                     T* __restrict__ A) {
+                     TA* __restrict__ A, double shift) {
   constexpr int ND = Geo<DIM>::ND;
   const long long n = DIM * g.nn;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -354,12 +354,12 @@ __global__ void __launch_bounds__(256)
   const int cr = (int)(row % DIM), cc = (int)(col % DIM);
   const bool fr = (mask[nr] >> cr) & 1u, fc = (mask[nc] >> cc) & 1u;
   if (fr || fc) {
-    A[t] = (row == col) ? T(1) : T(0);
+    A[t] = (row == col) ? TA(1) : TA(0);
     return;
   }
   const int ir = (int)(nr % g.nnx), jr = (int)((nr / g.nnx) % g.nny), kr = DIM == 3 ? (int)(nr / ((long long)g.nnx * g.nny)) : 0;
   const int ic = (int)(nc % g.nnx), jc = (int)((nc / g.nnx) % g.nny), kc = DIM == 3 ? (int)(nc / ((long long)g.nnx * g.nny)) : 0;
-  T s = T(0);
+  TA s = TA(0);
   if (abs(ir - ic) <= 1 && abs(jr - jc) <= 1 && abs(kr - kc) <= 1) {
     const int exlo = max(max(ir, ic) - 1, 0), exhi = min(min(ir, ic), g.nx - 1);
     const int eylo = max(max(jr, jc) - 1, 0), eyhi = min(min(jr, jc), g.ny - 1);
@@ -371,10 +371,10 @@ __global__ void __launch_bounds__(256)
           const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
           const int ar = (ir - ex) + 2 * (jr - ey) + (DIM == 3 ? 4 * (kr - ez) : 0);
           const int ac = (ic - ex) + 2 * (jc - ey) + (DIM == 3 ? 4 * (kc - ez) : 0);
-          s += Kc[(size_t)e * tri_len(ND) + sym_idx(DIM * ar + cr, DIM * ac + cc, ND)];
+          s += (TA)Kc[(size_t)e * tri_len(ND) + sym_idx(DIM * ar + cr, DIM * ac + cc, ND)];
         }
   }
-  A[t] = s;
+  A[t] = row == col ? (TA)((double)s * (1.0 + shift)) : s;
 }
 
 // In-place Cholesky (lower) of the n x n row-major matrix A by one block,
@@ -578,18 +578,19 @@ __global__ void __launch_bounds__(256)
   Ainv[t] = s;
 }
 
-template <typename T>
+// y = A x with the matrix (and the accumulation) in TA and the vectors in TV
+template <typename TA, typename TV>
 __global__ void __launch_bounds__(256)
-    k_gemv(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
+    k_gemv(int n, const TA* __restrict__ A, const TV* __restrict__ x, TV* __restrict__ y) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   pdl_wait();
   if (warp >= n) return;
-  T s = T(0);
-  for (int m = lane; m < n; m += 32) s += A[(size_t)warp * n + m] * x[m];
+  TA s = TA(0);
+  for (int m = lane; m < n; m += 32) s += A[(size_t)warp * n + m] * (TA)x[m];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[warp] = s;
+  if (lane == 0) y[warp] = (TV)s;
   pdl_launch_dependents();
 }
 
@@ -733,19 +734,27 @@ cudaError_t launch_galerkin_coarse(int dim, int t, const GridP& gc, const GridP&
                     : gal_coarse_t<3, float>(gc, gf, Kf, Kc, s);
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, typename TA>
 static cudaError_t dense_t(const GridP& g, const uint8_t* mask, const void* Kc, void* A,
-                           cudaStream_t s) {
+                           double shift, cudaStream_t s) {
   const long long n = DIM * g.nn;
-  k_dense_assemble<DIM, T><<<nblocks(n * n, 256), 256, 0, s>>>(g, mask, (const T*)Kc, (T*)A);
+  k_dense_assemble<DIM, T, TA><<<nblocks(n * n, 256), 256, 0, s>>>(g, mask, (const T*)Kc,
+                                                                   (TA*)A, shift);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense_assemble(int dim, int t, const GridP& g, const uint8_t* mask,
-                                  const void* Kc, void* A, cudaStream_t s) {
-  if (dim == 2) return t == T_F64 ? dense_t<2, double>(g, mask, Kc, A, s)
-                                  : dense_t<2, float>(g, mask, Kc, A, s);
-  return t == T_F64 ? dense_t<3, double>(g, mask, Kc, A, s) : dense_t<3, float>(g, mask, Kc, A, s);
+cudaError_t launch_dense_assemble(int dim, int t, int ta, const GridP& g, const uint8_t* mask,
+                                  const void* Kc, void* A, double shift, cudaStream_t s) {
+  if (t == T_F64 && ta == T_F64)
+    return dim == 2 ? dense_t<2, double, double>(g, mask, Kc, A, shift, s)
+                    : dense_t<3, double, double>(g, mask, Kc, A, shift, s);
+  if (t == T_F32 && ta == T_F64)
+    return dim == 2 ? dense_t<2, float, double>(g, mask, Kc, A, shift, s)
+                    : dense_t<3, float, double>(g, mask, Kc, A, shift, s);
+  if (t == T_F32 && ta == T_F32)
+    return dim == 2 ? dense_t<2, float, float>(g, mask, Kc, A, shift, s)
+                    : dense_t<3, float, float>(g, mask, Kc, A, shift, s);
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -788,16 +797,17 @@ cudaError_t launch_cholesky_inverse(int t, int n, void* A, void* Ainv, int* stat
                     : cholinv_t<float>(n, A, Ainv, status, s);
 }
 
-cudaError_t launch_dense_gemv(int t, int n, const void* A, const void* x, void* y,
+cudaError_t launch_dense_gemv(int ta, int t, int n, const void* A, const void* x, void* y,
                               cudaStream_t s) {
   const int nb = nblocks((long long)n * 32, 256);
-  if (t == T_F64)
-    return launch_pdl(k_gemv<double>, dim3(nb), dim3(256), 0, s, n, (const double*)A,
+  if (ta == T_F64 && t == T_F64)
+    return launch_pdl(k_gemv<double, double>, dim3(nb), dim3(256), 0, s, n, (const double*)A,
                       (const double*)x, (double*)y);
-  else
-    return launch_pdl(k_gemv<float>, dim3(nb), dim3(256), 0, s, n, (const float*)A,
+  if (ta == T_F64)
+    return launch_pdl(k_gemv<double, float>, dim3(nb), dim3(256), 0, s, n, (const double*)A,
                       (const float*)x, (float*)y);
-  return cudaGetLastError();
+  return launch_pdl(k_gemv<float, float>, dim3(nb), dim3(256), 0, s, n, (const float*)A,
+                    (const float*)x, (float*)y);
 }
 
 }  // namespace topo

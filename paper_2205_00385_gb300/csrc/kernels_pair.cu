@@ -443,7 +443,8 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   const long long nxy = (long long)gx * gy;
   int best = 1;
   long long best_cost = -1;
-  for (int nzc = 1; nzc <= a.g.nnz; ++nzc) {
+  // a chunk length chosen by the autotuner replaces the search
+  for (int nzc = 1; a.zsplit <= 0 && nzc <= a.g.nnz; ++nzc) {
     const int zc = (a.g.nnz + nzc - 1) / nzc;
     if ((a.g.nnz + zc - 1) / zc != nzc) continue;
     const long long waves = (nxy * nzc + slots - 1) / slots;
@@ -453,7 +454,8 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
       best = nzc;
     }
   }
-  p.zc = (a.g.nnz + best - 1) / best;
+  p.zc = a.zsplit > 0 ? min(a.zsplit, (int)a.g.nnz) : (a.g.nnz + best - 1) / best;
+  best = (a.g.nnz + p.zc - 1) / p.zc;
   dim3 grid(gx, gy, best);
   switch (a.epi) {
     case EPI_APPLY: return launch_pdl(k_apply3_pair<EPI_APPLY>, grid, dim3(PX * PY), 0, s, p, kb);

@@ -259,6 +259,12 @@ __global__ void __launch_bounds__(MD_CH)
         Rg::dacc(acc[0][1], x0, y1);
         Rg::dacc(acc[1][1], x1, y1);
       }
+      // renormalise the double-float accumulators once per chunk, so that
+      // their error terms never grow over more than one chunk's products
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[p][q] = Rg::dfin(acc[p][q]);
     }
     __syncthreads();
     st ^= 1;
@@ -491,10 +497,22 @@ __global__ void __launch_bounds__(256)
   GRID_LOOP(i, n) Rg::st(b, i, Rg::fma3(Rg::ld(a, i), sc, Rg::zero()));
 }
 
-__global__ void k_gs_count(const double* scal, int n0, int n1, double tol, int* ints) {
+// Records column src of the QR factor of the basis, Rt[:, src] (ld MAXB):
+// its projections h1 + h2 on the k columns accepted before it and, when it
+// is accepted, its remaining norm at row k; then advances the count.  Also
+// stores the column's norm before orthogonalisation in rn[src].
+__global__ void k_gs_record(const double* scal, int n0, int n1, double tol, int src,
+                            const double* h1, const double* h2, double* Rt, double* rn,
+                            int* ints) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double before = scal[n0], after = scal[n1];
-  if (after > tol * tol * before && after > 0.0) ints[I_KCOUNT] += 1;
+  const bool keep = after > tol * tol * before && after > 0.0;
+  const int k = ints[I_KCOUNT];
+  double* col = Rt + (size_t)MAXB * src;
+  for (int j = 0; j < MAXB; ++j) col[j] = j < k ? h1[j] + h2[j] : 0.0;
+  if (keep) col[k] = sqrt(after);
+  rn[src] = sqrt(fmax(before, 0.0));
+  if (keep) ints[I_KCOUNT] = k + 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -764,14 +782,72 @@ cudaError_t launch_combine(long long n, int vt, const void* A, int m, const int*
 }
 
 cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double* scal, int n0,
-                             int n1, double tol, int* ints, cudaStream_t s) {
+                             int n1, double tol, const double* h1, const double* h2, double* Rt,
+                             double* rn, int* ints, cudaStream_t s) {
+  if (src < 0 || src >= MAXB) return cudaErrorInvalidValue;
   if (vt == V_DF2)
     k_gs_accept<float2><<<vgrid(n), 256, 0, s>>>(n, (float2*)R, src, scal, n0, n1, tol, ints);
   else
     k_gs_accept<double><<<vgrid(n), 256, 0, s>>>(n, (double*)R, src, scal, n0, n1, tol, ints);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_gs_count<<<1, 32, 0, s>>>(scal, n0, n1, tol, ints);
+  k_gs_record<<<1, 32, 0, s>>>(scal, n0, n1, tol, src, h1, h2, Rt, rn, ints);
+  return cudaGetLastError();
+}
+
+// Y[:, j] = sum_{i < kq} U[i + MAXB j] Q[:, i] for j < k: the kept left
+// singular directions of the basis expressed in its orthonormal QR factor.
+// Each thread loads the kq entries of one index once and forms all k
+// outputs; U sits in shared memory.
+template <typename S, int KQ>
+__global__ void __launch_bounds__(256)
+    k_combine_multi(long long n, const S* __restrict__ Q, int kq, const double* __restrict__ U,
+                    int k, S* __restrict__ Y) {
+  using Rg = Ar<S>;
+  using V = typename Rg::T;
+  __shared__ V su[KQ * MAXB];
+  for (int e = threadIdx.x; e < KQ * MAXB; e += blockDim.x) {
+    const int i = e % KQ, j = e / KQ;
+    su[e] = Rg::from_d(i < kq && j < k ? U[i + (size_t)MAXB * j] : 0.0);
+  }
+  __syncthreads();
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    V q[KQ];
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) q[i] = i < kq ? Rg::ld(Q + (size_t)i * n, idx) : Rg::zero();
+    for (int j = 0; j < k; ++j) {
+      V acc = Rg::zero();
+#pragma unroll
+      for (int i = 0; i < KQ; ++i)
+        if (i < kq) acc = Rg::fma3(su[i + KQ * j], q[i], acc);
+      Rg::st(Y + (size_t)j * n, idx, acc);
+    }
+  }
+}
+
+template <typename S>
+static void combine_multi_t(long long n, const void* Q, int kq, const double* U, int k, void* Y,
+                            cudaStream_t s) {
+  const int g = vgrid(n);
+  if (kq <= 4)
+    k_combine_multi<S, 4><<<g, 256, 0, s>>>(n, (const S*)Q, kq, U, k, (S*)Y);
+  else if (kq <= 8)
+    k_combine_multi<S, 8><<<g, 256, 0, s>>>(n, (const S*)Q, kq, U, k, (S*)Y);
+  else if (kq <= 12)
+    k_combine_multi<S, 12><<<g, 256, 0, s>>>(n, (const S*)Q, kq, U, k, (S*)Y);
+  else
+    k_combine_multi<S, MAXB><<<g, 256, 0, s>>>(n, (const S*)Q, kq, U, k, (S*)Y);
+}
+
+cudaError_t launch_combine_multi(long long n, int vt, const void* Q, int kq, const double* U,
+                                 int k, void* Y, cudaStream_t s) {
+  if (kq < 1 || kq > MAXB || k < 0 || k > kq || Q == Y) return cudaErrorInvalidValue;
+  if (k == 0) return cudaSuccess;
+  if (vt == V_DF2)
+    combine_multi_t<float2>(n, Q, kq, U, k, Y, s);
+  else
+    combine_multi_t<double>(n, Q, kq, U, k, Y, s);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@
 // factors, the bisection bracket and the reduction partials) lives in the
 // file-scope device array below, which every GPU that loads libtopo.so holds
 // until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "kernels.h"
@@ -29,26 +31,71 @@ constexpr int NOALLOC_OC_STEPS = 192;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-unsigned char* g_dev_ptr[MAX_DEVICES] = {nullptr};
+// The array's device address belongs to a CUDA context: each context that
+// loads the library (the primary context of every device, a context the
+// host application created and made current, the new primary context after
+// a cudaDeviceReset) has its own copy.  In host code the array's name is
+// only a host-side stand-in, so the address is resolved with the context
+// current, once per context, and cached under the context's unique ID
+// (cuCtxGetId; a context's handle may be reused after it is destroyed, its
+// ID never is).  The two driver functions are fetched through the runtime,
+// so the library needs no link to the driver library.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the scratch array on the current device.  In host code
-// the array's name is only a host-side stand-in, so its device address is
-// resolved once per device (with that device current) and cached.
-cudaError_t scratch_for_current_device(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+constexpr int CACHE_SLOTS = 64;
+std::mutex g_mu;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+unsigned long long g_ctx_id[CACHE_SLOTS] = {0};
+unsigned char* g_ctx_ptr[CACHE_SLOTS] = {nullptr};
+int g_next_slot = 0;
+
+cudaError_t driver_functions() {
+  if (g_ctx_get_current && g_ctx_get_id) return cudaSuccess;
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                   cudaEnableDefault, &q1);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+  if (e != cudaSuccess) return e;
+  if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+    return cudaErrorSymbolNotFound;
+  g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+  g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  return cudaSuccess;
+}
+
+// Device address of the scratch array in the calling thread's current
+// context (the runtime binds the current device's primary context first if
+// none is current).
+cudaError_t scratch_for_current_context(unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_dev_ptr[dev] = static_cast<unsigned char*>(p);
+  cudaError_t e = driver_functions();
+  if (e != cudaSuccess) return e;
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  void* p = nullptr;
+  if (!ctx) {
+    // nothing current yet: resolving the symbol binds the primary context
+    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
   }
-  *out = g_dev_ptr[dev];
+  unsigned long long id = 0;
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  for (int i = 0; i < CACHE_SLOTS; ++i)
+    if (g_ctx_ptr[i] && g_ctx_id[i] == id) {
+      *out = g_ctx_ptr[i];
+      return cudaSuccess;
+    }
+  if (!p && (e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+  const int slot = g_next_slot;
+  g_next_slot = (g_next_slot + 1) % CACHE_SLOTS;
+  g_ctx_id[slot] = id;
+  g_ctx_ptr[slot] = static_cast<unsigned char*>(p);
+  *out = g_ctx_ptr[slot];
   return cudaSuccess;
 }
 
@@ -71,7 +118,7 @@ extern "C" to_status to_oc_update_noalloc(int64_t nel, double volfrac, double mo
     return set_global_error("bad volfrac/move"), TO_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* base = nullptr;
-  cudaError_t e = scratch_for_current_device(&base);
+  cudaError_t e = scratch_for_current_context(&base);
   if (e != cudaSuccess) return cuda_err("scratch address", e);
   double* a = reinterpret_cast<double*>(base + NA_A);
   double* partials = reinterpret_cast<double*>(base + NA_PARTIALS);

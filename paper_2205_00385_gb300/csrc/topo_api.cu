@@ -4,6 +4,9 @@
 // bookkeeping (level geometry, PARM ring position, iteration counts); every
 // arithmetic step of the solver path runs in the library's kernels.  Device
 // memory comes exclusively from the caller's workspace.
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -342,8 +345,10 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
                      : nullptr;
   }
   const long long nc = lv[L - 1].n;
-  void* Ad = cv.take<char>((size_t)nc * nc * ts);
-  void* Ai = cv.take<char>((size_t)nc * nc * ts);
+  // the coarsest matrix and its inverse, sized for float64 (the storage of
+  // the float64 path, and of the mixed path's coarse factorisation)
+  void* Ad = cv.take<char>((size_t)nc * nc * 8);
+  void* Ai = cv.take<char>((size_t)nc * nc * 8);
   if (c) {
     c->E64 = E64; c->Eprev64 = Ep64; c->dE64 = dE64; c->rho_phys = rho; c->invHs = invHs; c->oc_a = oca;
     c->oc_lo = oclo; c->oc_hi = ochi; c->oc_a2 = oca2; c->oc_dv2 = ocdv2;
@@ -451,12 +456,18 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->nel = c->lv[0].g.nel;
   c->nn = c->lv[0].g.nn;
   c->n = c->lv[0].n;
-  c->parm_count = c->parm_head = c->carm_built = 0;
+  c->parm_count = c->parm_head = c->carm_built = c->carm_qr = 0;
   c->have_density = false;
   c->hier_stale = true;
   c->launches = 0;
   c->prof_mask = 0u;
   c->n_vgraph = 0;
+  c->vcycle_bytes = 0.0;
+  c->coarse_t = c->mixed ? T_F32 : T_F64;
+  c->coarse_shift = 0.0;
+  for (int q = 0; q < 8; ++q) c->tuned_zc[q] = 0;
+  c->host_rr = nullptr;
+  c->rr_event = nullptr;
   c->cap_stream = nullptr;
   if (!make_stencil(c->dim, desc->rmin, &c->stencil)) {
     delete c;
@@ -557,6 +568,8 @@ void to_destroy(to_ctx* ctx) {
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (int q = 0; q < ctx->n_vgraph; ++q) cudaGraphExecDestroy(ctx->vgraph[q].exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->rr_event) cudaEventDestroy(ctx->rr_event);
+  if (ctx->host_rr) cudaFreeHost(ctx->host_rr);
   delete ctx;
 }
 
@@ -591,6 +604,16 @@ static const void* coef_for(const to_ctx* c, int op, int tc) {
          : op == TO_OP_KREF ? (const void*)c->Eprev32 : (const void*)c->dE32;
 }
 
+// autotuned kernel kind of a finest-grid launch (-1: not tuned)
+static int tune_kind_fine(const to_ctx* c, int tc, int epi) {
+  if (c->dim != 3) return -1;
+  if (c->mixed ? tc == T_F32 : tc == T_F64)
+    return epi == EPI_APPLY ? TO_TUNE_OP_APPLY : epi == EPI_RESID ? TO_TUNE_OP_RESID
+                                                                  : TO_TUNE_OP_SMOOTH;
+  if (tc == T_DF) return epi == EPI_RESID ? TO_TUNE_ACC_RESID : TO_TUNE_ACC_APPLY;
+  return -1;
+}
+
 static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, const void* x,
                            void* y, const void* b, const void* dinv, int epi) {
   ApplyArgs a;
@@ -617,6 +640,8 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.omega = 0.6;
   a.dfix = op == TO_OP_DK ? 0.0 : 1.0;
   a.epi = epi;
+  const int k = tune_kind_fine(c, tc, epi);
+  a.zsplit = k >= 0 ? c->tuned_zc[k] : 0;
   return a;
 }
 
@@ -646,6 +671,8 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
     a.coef = t == T_F64 ? (const void*)c->E64 : (const void*)c->E32;
     a.Kc = nullptr;
     a.wht = t == T_F64 ? (const void*)c->wht64 : (const void*)c->wht32;
+    a.zsplit = epi == EPI_RESID ? c->tuned_zc[TO_TUNE_GAL1_RESID]
+             : epi == EPI_SMOOTH ? c->tuned_zc[TO_TUNE_GAL1_SMOOTH] : 0;
   }
   a.x = x;
   a.y = y;
@@ -658,14 +685,17 @@ static ApplyArgs coarse_args(const to_ctx* c, int l, const void* x, void* y, con
 }
 
 // Algorithmic DRAM bytes of one operator launch: every input and output
-// array touched once (the 3^dim neighbourhood reuse is not counted).
+// array touched once (the 3^dim neighbourhood reuse is not counted): x and
+// y, the moduli (or the assembled stencil of a stored level), and the
+// right-hand side and inverse diagonal of the fused epilogues.  The
+// one-byte-per-node support masks are boundary data, not counted.
 static double apply_bytes(const ApplyArgs& a) {
-  const double sx = a.tx == T_F64 ? 8.0 : 4.0, sy = a.ty == T_F64 ? 8.0 : 4.0;
+  const double sx = a.tx == T_F32 ? 4.0 : 8.0, sy = a.ty == T_F32 ? 4.0 : 8.0;
   const double sc = a.tc == T_F32 ? 4.0 : 8.0;
   const double n = (double)a.dim * (double)a.g.nn, nel = (double)a.g.nel;
   double b = n * (sx + sy);                             // x, y
   b += a.expl ? n * (a.dim == 3 ? 27 : 9) * a.dim * sc   // assembled stencil,
-              : (double)a.g.nn + (a.gal1 ? 8.0 : 1.0) * nel * sc;   // or masks and (child) moduli
+              : (a.gal1 ? 8.0 : 1.0) * nel * sc;         // or (child) moduli
   if (a.epi != EPI_APPLY) b += n * sx;                 // right-hand side
   if (a.epi == EPI_SMOOTH) b += n * sc;                // inverse diagonal
   return b;
@@ -709,10 +739,10 @@ static to_status build_hierarchy(to_ctx* c) {
                                       c->lv[l].S, s), "stencil l");
   }
   const int Lc = c->L - 1;
-  LAUNCH(c, launch_dense_assemble(c->dim, t, c->lv[Lc].g, c->lv[Lc].mask, c->lv[Lc].Kc,
-                                  c->Adense, s), "dense assemble");
-  LAUNCH(c, launch_cholesky_inverse(t, c->nc, c->Adense, c->Ainv, c->ints + I_STATUS, s),
-         "coarse factor");
+  LAUNCH(c, launch_dense_assemble(c->dim, t, c->coarse_t, c->lv[Lc].g, c->lv[Lc].mask,
+                                  c->lv[Lc].Kc, c->Adense, c->coarse_shift, s), "dense assemble");
+  LAUNCH(c, launch_cholesky_inverse(c->coarse_t, c->nc, c->Adense, c->Ainv, c->ints + I_STATUS,
+                                    s), "coarse factor");
   c->hier_stale = false;
   return TO_OK;
 }
@@ -721,6 +751,27 @@ static to_status build_hierarchy(to_ctx* c) {
 // r (storage rin_t: float64, or double-float pairs in the mixed path).  With
 // pre set, the finest level's right-hand side b = r and pre-smoothing
 // z = omega D^-1 b are already in place (written by the CG update).
+// Algorithmic DRAM bytes of the V-cycle's kernels, each array a kernel
+// touches counted once: presmoothing from zero reads the right-hand side and
+// D^-1 and writes b and z; restriction reads the fine residual and writes
+// the coarse right-hand side (and, pre-smoothing, reads D^-1 and writes z);
+// interpolation reads the coarse correction and updates the fine iterate;
+// the coarsest solve reads the dense inverse and two vectors.
+static double vbytes_presmooth(long long n, int tin, int t) {
+  return (double)n * ((tin == T_F64 || tin == T_D2 ? 8.0 : 4.0) + 3.0 * (t == T_F64 ? 8.0 : 4.0));
+}
+static double vbytes_restrict(long long nf, long long nc, int t, bool smooth) {
+  const double ts = t == T_F64 ? 8.0 : 4.0;
+  return ts * ((double)nf + (double)nc * (smooth ? 3.0 : 1.0));
+}
+static double vbytes_prolong(long long nf, long long nc, int t) {
+  return (t == T_F64 ? 8.0 : 4.0) * (2.0 * (double)nf + (double)nc);
+}
+static double vbytes_coarse(long long nc, int ta, int t) {
+  return (ta == T_F64 ? 8.0 : 4.0) * (double)nc * (double)nc +
+         2.0 * (t == T_F64 ? 8.0 : 4.0) * (double)nc;
+}
+
 static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int zt,
                         bool pre = false) {
   cudaStream_t s = c->stream;
@@ -728,14 +779,20 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
   const int L = c->L;
   ProfScope ps(c, PK_VCYCLE);
   LevelBuf* lv = c->lv;
+  double vb = 0.0;
   // finest level: smoothing from zero, residual, restriction
-  if (!pre)
+  if (!pre) {
     LAUNCH(c, launch_presmooth(t, rin_t, lv[0].n, rin, lv[0].b, lv[0].dinv, 0.6, lv[0].z, s),
            "presmooth 0");
+    vb += vbytes_presmooth(lv[0].n, rin_t, t);
+  }
   to_status st;
-  if ((st = run_op(c, fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
-                                EPI_RESID), "resid 0")) != TO_OK)
-    return st;
+  {
+    const ApplyArgs a = fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
+                                  EPI_RESID);
+    vb += apply_bytes(a);
+    if ((st = run_op(c, a, "resid 0")) != TO_OK) return st;
+  }
   // restriction into level l also pre-smooths level l from a zero guess
   // (except on the coarsest level, which is solved exactly)
   auto restrict_into = [&](int l) {
@@ -745,25 +802,36 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
                            smooth ? lv[l].z : nullptr, s);
   };
   LAUNCH(c, restrict_into(1), "restrict 0");
+  vb += vbytes_restrict(lv[0].n, lv[1].n, t, 1 < L - 1);
   for (int l = 1; l < L - 1; ++l) {
-    if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID), "resid l")) != TO_OK)
-      return st;
+    const ApplyArgs a = coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID);
+    vb += apply_bytes(a);
+    if ((st = run_op(c, a, "resid l")) != TO_OK) return st;
     LAUNCH(c, restrict_into(l + 1), "restrict l");
+    vb += vbytes_restrict(lv[l].n, lv[l + 1].n, t, l + 1 < L - 1);
   }
   // coarsest grid: exact solve with the stored inverse
-  LAUNCH(c, launch_dense_gemv(t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s), "coarse solve");
+  LAUNCH(c, launch_dense_gemv(c->coarse_t, t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s),
+         "coarse solve");
+  vb += vbytes_coarse(c->nc, c->coarse_t, t);
   // upward: interpolate, post-smooth (result of level l lands in z2)
   for (int l = L - 2; l >= 1; --l) {
     LAUNCH(c, launch_prolong_add(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].z2,
                                  lv[l].z, s), "prolong l");
-    if ((st = run_op(c, coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH),
-                     "postsmooth l")) != TO_OK)
-      return st;
+    vb += vbytes_prolong(lv[l].n, lv[l + 1].n, t);
+    const ApplyArgs a = coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH);
+    vb += apply_bytes(a);
+    if ((st = run_op(c, a, "postsmooth l")) != TO_OK) return st;
   }
   LAUNCH(c, launch_prolong_add(c->dim, t, lv[0].g, lv[0].mask, lv[1].g, lv[1].z2, lv[0].z, s),
          "prolong 0");
-  return run_op(c, fine_args(c, TO_OP_K, t, t, zt, lv[0].z, zout, lv[0].b, lv[0].dinv,
-                             EPI_SMOOTH), "postsmooth 0");
+  vb += vbytes_prolong(lv[0].n, lv[1].n, t);
+  const ApplyArgs a = fine_args(c, TO_OP_K, t, t, zt, lv[0].z, zout, lv[0].b, lv[0].dinv,
+                                EPI_SMOOTH);
+  vb += apply_bytes(a);
+  ps.bytes = vb;
+  c->vcycle_bytes = vb;
+  return run_op(c, a, "postsmooth 0");
 }
 
 // The V-cycle's launch sequence depends only on buffer addresses fixed at
@@ -811,9 +879,9 @@ static to_status vcycle_graphed(to_ctx* c, const void* rin, int rin_t, void* zou
       c->n_vgraph = 3;
     }
     vg = &c->vgraph[c->n_vgraph++];
-    *vg = to_ctx::VGraph{rin, zout, coef, zt, pre, exec, captured};
+    *vg = to_ctx::VGraph{rin, zout, coef, zt, pre, exec, captured, c->vcycle_bytes};
   }
-  ProfScope ps(c, PK_VCYCLE);
+  ProfScope ps(c, PK_VCYCLE, vg->bytes);
   CUDA_TRY(c, cudaGraphLaunch(vg->exec, c->stream), "V-cycle graph launch");
   c->launches += vg->launches;
   return TO_OK;
@@ -972,6 +1040,15 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   cudaStream_t s = c->stream;
   to_status st;
   if (c->hier_stale && (st = build_hierarchy(c)) != TO_OK) return st;
+  if (!c->host_rr) {
+    // 64 bytes of pinned host memory per context, so that the residual read
+    // is an asynchronous copy the host can wait on with an event
+    void* h = nullptr;
+    CUDA_TRY(c, cudaMallocHost(&h, 64), "pinned residual slot");
+    c->host_rr = static_cast<double*>(h);
+  }
+  if (!c->rr_event)
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->rr_event, cudaEventDisableTiming), "rr event");
   const long long n = c->n;
   // Mixed path: the iterate x, r and p are double-float pairs (x in the
   // otherwise unused float64 z buffer); the operator and the V-cycle work on
@@ -1022,11 +1099,27 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
     else
       LAUNCH(c, launch_copy(n, c->z, c->p, s), "p = z");
     int cur = S_RZ0, nxt = S_RZ1;
+    // Precision escalation (mixed path): q = K p in float32 carries ~1e-4
+    // relative error on smooth search directions (K cancels by 1e3-1e4
+    // there), and on some designs CG stagnates on it, the recursive and
+    // true residuals stuck together.  Healthy convergence gains >= 10x in
+    // 16 iterations; when the residual fails to halve over 16 iterations,
+    // the rest of the solve forms q with the double-float operator (then
+    // rounded to float32, which loses nothing to cancellation) and CG
+    // restarts from the true residual.
+    bool accurate_q = false;
+    double rel_window = rel;
+    int it_window = 0;
     for (it = 1; it <= maxit; ++it) {
-      if (mixed) {
+      if (mixed && accurate_q) {
+        if ((st = apply_accurate_vec(c, TO_OP_K, c->p, c->t, EPI_APPLY)) != TO_OK) return st;
+        LAUNCH(c, launch_convert(T_D2, T_F32, n, c->t, c->q32, s), "q to float32");
+      } else if (mixed) {
         if ((st = run_op(c, fine_args(c, TO_OP_K, T_F32, T_F32, T_F32, c->p32, c->q32, nullptr,
                                       nullptr, EPI_APPLY), "q = K p")) != TO_OK)
           return st;
+      }
+      if (mixed) {
         LAUNCH(c, launch_dot_d2f(n, c->p, c->q32, c->partials, c->counters + C_DOT,
                                  c->scal + S_PQ, s), "pq");
         LAUNCH(c, launch_cg_xr_d2(n, x, c->r, c->p, c->q32, c->scal, cur, S_PQ, S_RR,
@@ -1044,18 +1137,45 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
         LAUNCH(c, launch_cg_xr(n, x, c->r, c->p, c->q, c->scal, cur, S_PQ, S_RR, c->partials,
                                c->counters + C_UPD, s), "x, r update");
       }
-      if ((st = read_scalar(c, c->scal + S_RR, &rr)) != TO_OK) return st;
+      // |r|^2 goes to the host, and the next preconditioner application is
+      // enqueued before the host waits for it: the V-cycle runs while the
+      // host reads the residual and decides.  The preconditioner writes only
+      // its own scratch and scal[nxt], so when the loop stops (or a true
+      // residual replaces r) its result is discarded (or recomputed) and
+      // the iterates are the same as with the read first.
+      CUDA_TRY(c, cudaMemcpyAsync(c->host_rr, c->scal + S_RR, 8, cudaMemcpyDeviceToHost, s),
+               "read rr");
+      CUDA_TRY(c, cudaEventRecord(c->rr_event, s), "rr event");
+      bool fresh = it < maxit;
+      if (fresh && (st = precondition(nxt)) != TO_OK) return st;
+      CUDA_TRY(c, cudaEventSynchronize(c->rr_event), "wait rr");
+      rr = *c->host_rr;
       rel = sqrt(rr) / c->fnorm;
       if (!isfinite(rel)) return fail(c, TO_E_SINGULAR, "CG breakdown (non-finite residual)");
       // Reliable updates: with a float32 operator the recursive residual
       // drifts from f - K x, so it is replaced by the float64-accurate true
       // residual whenever it has dropped 100x since the last replacement and
-      // before convergence is declared.  The search direction is kept.
-      if (mixed && (rel < rtol || rr < 1e-4 * rr_max)) {
+      // before convergence is declared.  The search direction is kept when
+      // the two agree; when the true residual is more than 1.5x the
+      // recursive one the recursion has drifted (its directions were built
+      // for a different residual), and CG restarts from the true residual
+      // (p = z).
+      bool restart = false;
+      bool escalate = false;
+      if (mixed && !accurate_q && it - it_window >= 16) {
+        escalate = rel > 0.5 * rel_window;
+        rel_window = rel;
+        it_window = it;
+      }
+      if (mixed && (rel < rtol || rr < 1e-4 * rr_max || escalate)) {
+        const double rr_rec = rr;
         if ((st = true_residual(&rr)) != TO_OK) return st;
         pre = false;
+        fresh = false;
+        restart = escalate || rr > 2.25 * rr_rec;
         rel = sqrt(rr) / c->fnorm;
         rr_max = rr;
+        if (escalate) accurate_q = true;
       }
       rr_max = std::max(rr_max, rr);
       if (rel < rtol) {
@@ -1063,9 +1183,10 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
         break;
       }
       if (it == maxit) break;
-      if ((st = precondition(nxt)) != TO_OK) return st;
+      if (!fresh && (st = precondition(nxt)) != TO_OK) return st;
       if (mixed)
-        LAUNCH(c, launch_cg_p_d2(n, c->p, c->p32, z32, c->scal, nxt, cur, s), "p update");
+        LAUNCH(c, launch_cg_p_d2(n, c->p, c->p32, z32, c->scal, restart ? -1 : nxt, cur, s),
+               "p update");
       else
         LAUNCH(c, launch_cg_p(n, c->p, c->z, c->scal, nxt, cur, s), "p update");
       std::swap(cur, nxt);
@@ -1111,9 +1232,14 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
   to_status st;
   double* small = c->small;
   const int v = vt(c);
+  c->carm_built = c->carm_qr = 0;
+  // Both products below use the float64-accurate operator in either
+  // precision: for smooth displacement fields K x cancels heavily, and a
+  // float32 product would leave the basis with errors of ~1e-3.
   // K_Phi = Phi^T K_ref Phi  (Eq. 15)
   for (int i = 0; i < Ns; ++i)
-    if ((st = apply_vec(c, TO_OP_KREF, c->Phi + (size_t)i * n, c->KPhi + (size_t)i * n)) != TO_OK)
+    if ((st = apply_accurate_vec(c, TO_OP_KREF, c->Phi + (size_t)i * n, c->KPhi + (size_t)i * n,
+                                 EPI_APPLY)) != TO_OK)
       return st;
   LAUNCH(c, launch_gram_sym(n, v, c->Phi, c->KPhi, Ns, small + SM_KPHI, Ns, c->partials,
                             c->counters + C_MULTI, s), "K_Phi");
@@ -1122,7 +1248,9 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
   // r_1 = u_last; r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}  (Eq. 18-20, 26)
   LAUNCH(c, launch_vconvert(n, V_F64, u_last, v, c->R, s), "r1");
   for (int i = 1; i < m; ++i) {
-    if ((st = apply_vec(c, TO_OP_DK, c->R + (size_t)(i - 1) * n, c->t)) != TO_OK) return st;
+    if ((st = apply_accurate_vec(c, TO_OP_DK, c->R + (size_t)(i - 1) * n, c->t, EPI_APPLY)) !=
+        TO_OK)
+      return st;
     LAUNCH(c, launch_gram(n, v, c->Phi, Ns, nullptr, c->t, 1, nullptr, small + SM_Z, Ns,
                           c->partials, c->counters + C_MULTI, s), "Phi^T t");
     LAUNCH(c, launch_small_matvec(Ns, nullptr, small + SM_KPHI_INV, small + SM_Z, small + SM_W,
@@ -1131,7 +1259,11 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
                              c->R + (size_t)i * n, v, nullptr, nullptr, c->partials,
                              c->counters + C_UPD, s), "r_i");
   }
-  // classical Gram-Schmidt with one re-orthogonalisation pass, in place
+  // Eq. 21 (R = R~ Sigma V^T, truncated).  QR of R in place by classical
+  // Gram-Schmidt run twice per column: Q lands in the first kq columns of R,
+  // the triangular factor in small[SM_RT].  A column left with <= 1e-10 of
+  // its norm after both passes is numerically dependent on the earlier ones
+  // and gets no column of Q (its projections stay in the factor).
   CUDA_TRY(c, cudaMemsetAsync(c->ints + I_KCOUNT, 0, sizeof(int), s), "reset k");
   for (int i = 0; i < m; ++i) {
     double* ri = c->R + (size_t)i * n;
@@ -1149,14 +1281,171 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
     LAUNCH(c, launch_combine(n, v, c->R, bound, c->ints + I_KCOUNT, small + SM_H2, -1.0, 1.0, ri,
                              v, nullptr, c->scal + S_NRM1, c->partials, c->counters + C_UPD, s),
            "GS axpy");
-    LAUNCH(c, launch_gs_accept(n, v, c->R, i, c->scal, S_NRM0, S_NRM1, 1e-10, c->ints, s),
-           "GS accept");
+    LAUNCH(c, launch_gs_accept(n, v, c->R, i, c->scal, S_NRM0, S_NRM1, TO_QR_DEPENDENT_TOL,
+                               small + SM_H, small + SM_H2, small + SM_RT, small + SM_RN, c->ints,
+                               s), "GS accept");
   }
-  int k = 0;
-  CUDA_TRY(c, cudaMemcpyAsync(&k, c->ints + I_KCOUNT, 4, cudaMemcpyDeviceToHost, s), "read k");
+  // singular values of the unit-column basis from the small factor; the
+  // directions with sigma > TO_CARM_SVD_TOL sigma_1 span R~
+  LAUNCH(c, launch_small_svd_trunc(m, c->ints + I_KCOUNT, small + SM_RT, small + SM_RN,
+                                   TO_CARM_SVD_TOL, small + SM_U, small + SM_SIG, c->ints, s),
+         "truncated SVD");
+  int kk[3] = {0, 0, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(kk, c->ints, sizeof(kk), cudaMemcpyDeviceToHost, s), "read counts");
   CUDA_TRY(c, cudaStreamSynchronize(s), "sync");
+  const int kq = kk[I_KCOUNT], k = kk[I_KRED];
+  if (kq < 1 || k < 1) return fail(c, TO_E_SINGULAR, "CARM basis is empty");
+  // R~ = Q U into the Q buffer, then the two buffers trade places (both hold
+  // n x N_m values of the same storage)
+  LAUNCH(c, launch_combine_multi(n, v, c->R, kq, small + SM_U, k, c->Q, s), "R~ = Q U");
+  std::swap(c->R, c->Q);
+  c->carm_qr = kq;
   c->carm_built = k;
-  if (k < 1) return fail(c, TO_E_SINGULAR, "CARM basis is empty");
+  return TO_OK;
+}
+
+// process-wide cache of tuned chunk lengths: (device, kernel, grid) -> layers
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, long long, long long, long long>, int> g_tune_cache;
+
+to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t cap,
+                      int32_t* count) {
+  if (!c || !count || reps < 1 || cap < 0 || (cap > 0 && !results))
+    return fail(c, TO_E_INVALID, "bad arguments");
+  if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
+  *count = 0;
+  if (c->dim != 3) return TO_OK;
+  cudaStream_t s = c->stream;
+  to_status st;
+  if (c->hier_stale && (st = build_hierarchy(c)) != TO_OK) return st;
+  int dev = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev), "device");
+  // the launches as the solver makes them, on scratch buffers
+  const int t = mg_t(c);
+  auto args_of = [&](int kind, ApplyArgs* a) -> bool {
+    LevelBuf* lv = c->lv;
+    switch (kind) {
+      case TO_TUNE_OP_APPLY:
+        *a = c->mixed ? fine_args(c, TO_OP_K, T_F32, T_F32, T_F32, c->p32, c->q32, nullptr, nullptr,
+                                  EPI_APPLY)
+                      : fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, c->p, c->q, nullptr, nullptr,
+                                  EPI_APPLY);
+        return true;
+      case TO_TUNE_OP_RESID:
+      case TO_TUNE_OP_SMOOTH:
+        *a = fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
+                       kind == TO_TUNE_OP_RESID ? EPI_RESID : EPI_SMOOTH);
+        return true;
+      case TO_TUNE_GAL1_RESID:
+      case TO_TUNE_GAL1_SMOOTH:
+        if (!c->l1_implicit) return false;
+        *a = coarse_args(c, 1, lv[1].z, kind == TO_TUNE_GAL1_RESID ? lv[1].r : lv[1].z2, lv[1].b,
+                         kind == TO_TUNE_GAL1_RESID ? EPI_RESID : EPI_SMOOTH);
+        return true;
+      case TO_TUNE_ACC_APPLY:
+      case TO_TUNE_ACC_RESID:
+        if (!(c->mixed && c->df_ok)) return false;
+        *a = fine_args(c, TO_OP_K, T_DF, T_D2, T_D2, c->p, c->t,
+                       kind == TO_TUNE_ACC_RESID ? c->fd : nullptr, nullptr,
+                       kind == TO_TUNE_ACC_RESID ? EPI_RESID : EPI_APPLY);
+        return true;
+    }
+    return false;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(c, cudaEventCreate(&e0), "event");
+  CUDA_TRY(c, cudaEventCreate(&e1), "event");
+  auto time_us = [&](const ApplyArgs& a, double* us) -> cudaError_t {
+    cudaError_t e;
+    for (int w = 0; w < 2; ++w)
+      if ((e = launch_apply(a, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
+    for (int r = 0; r < reps; ++r)
+      if ((e = launch_apply(a, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+    *us = 1e3 * ms / reps;
+    return cudaSuccess;
+  };
+  cudaError_t err = cudaSuccess;
+  for (int kind = 0; kind < TO_TUNE_N && err == cudaSuccess; ++kind) {
+    ApplyArgs a;
+    if (!args_of(kind, &a)) continue;
+    const auto key = std::make_tuple(dev * 64 + kind * 2 + (c->mixed ? 1 : 0), kind,
+                                     (long long)a.g.nnx, (long long)a.g.nny, (long long)a.g.nnz);
+    to_tune_result r{kind, 0, 0, 0.0, 0.0};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        c->tuned_zc[kind] = it->second;
+        r.chunk_layers = it->second;
+        if (*count < cap) results[*count] = r;
+        ++*count;
+        continue;
+      }
+    }
+    a.zsplit = 0;
+    double h_us = 0.0;
+    if ((err = time_us(a, &h_us)) != cudaSuccess) break;
+    double best_us = h_us;
+    int best = 0, tried = 0;
+    const int nnz = (int)a.g.nnz;
+    for (int nzc = 1; nzc <= nnz && nzc <= 64; ++nzc) {
+      const int zc = (nnz + nzc - 1) / nzc;
+      if (zc < 2 || (nnz + zc - 1) / zc != nzc) continue;
+      a.zsplit = zc;
+      double us = 0.0;
+      if ((err = time_us(a, &us)) != cudaSuccess) break;
+      ++tried;
+      if (us < 0.99 * best_us) {
+        best_us = us;
+        best = zc;
+      }
+    }
+    if (err != cudaSuccess) break;
+    c->tuned_zc[kind] = best;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune_cache[key] = best;
+    }
+    r.candidates = tried;
+    r.chunk_layers = best;
+    r.chosen_us = best_us;
+    r.heuristic_us = h_us;
+    if (*count < cap) results[*count] = r;
+    ++*count;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(c, "autotune", err);
+  // captured V-cycles carry the old launch shapes
+  for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
+  c->n_vgraph = 0;
+  return TO_OK;
+}
+
+to_status to_carm_info(to_ctx* c, int32_t* kq, int32_t* k, double* sigma) {
+  if (!c || !kq || !k) return fail(c, TO_E_INVALID, "NULL argument");
+  if (c->carm_built < 1) return fail(c, TO_E_STATE, "to_carm_build has not been called");
+  *kq = c->carm_qr;
+  *k = c->carm_built;
+  if (sigma) {
+    CUDA_TRY(c, cudaMemcpyAsync(sigma, c->small + SM_SIG, sizeof(double) * c->desc.n_carm,
+                                cudaMemcpyDeviceToHost, c->stream), "read sigma");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  }
+  return TO_OK;
+}
+
+to_status to_carm_basis_column(to_ctx* c, int32_t j, double* out) {
+  if (!c || !out) return fail(c, TO_E_INVALID, "NULL argument");
+  if (c->carm_built < 1) return fail(c, TO_E_STATE, "to_carm_build has not been called");
+  if (j < 0 || j >= c->carm_built) return fail(c, TO_E_INVALID, "column index out of range");
+  LAUNCH(c, launch_vconvert(c->n, vt(c), c->R + (size_t)j * c->n, V_F64, out, c->stream),
+         "basis column");
   return TO_OK;
 }
 

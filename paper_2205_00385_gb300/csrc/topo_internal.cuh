@@ -118,10 +118,16 @@ enum SmallOff {
   SM_FR = SM_KR + 256,              // m
   SM_Y = SM_FR + 16,                // m
   SM_H2 = SM_Y + 16,                // GS coefficients of the second pass
-  SM_TOTAL = SM_H2 + 16 + 48
+  SM_RT = SM_H2 + 16,               // QR factor of the CARM basis, MAXB x N_m (ld MAXB)
+  SM_RN = SM_RT + 256,              // norms of the CARM basis columns before orthogonalisation
+  SM_U = SM_RN + 16,                // left singular vectors kept by Eq. 21, kq x k (ld MAXB)
+  SM_SIG = SM_U + 256,              // singular values of the unit-column basis, descending
+  SM_TOTAL = SM_SIG + 16 + 48
 };
 
-enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_NINTS = 16 };
+// I_KCOUNT: columns accepted by the QR of the CARM basis; I_KRED: directions
+// kept by the truncated SVD of Eq. 21
+enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_KRED = 2, I_NINTS = 16 };
 
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of NV float64 values, finished by the last
@@ -294,7 +300,9 @@ struct to_ctx {
   float *p32, *q32;     // float32 shadows of p and K p (mixed path)
   // PARM / CARM
   double *Phi, *KPhi, *R, *Q, *t;
-  int parm_count, parm_head, carm_built;
+  int parm_count, parm_head;
+  int carm_built;   // directions of the last CARM basis R~ kept by Eq. 21 (0: none built)
+  int carm_qr;      // columns of its QR factor (directions before truncation)
   // Galerkin tables (level-1 child matrices Q_c), float64 and float32
   double* Qc64;
   float* Qc32;
@@ -334,10 +342,17 @@ struct to_ctx {
     bool pre;   // right-hand side and pre-smoothing already in place
     cudaGraphExec_t exec;
     long long launches;
+    double bytes;   // algorithmic DRAM bytes of one replay
   };
+  double vcycle_bytes;   // algorithmic bytes of the last V-cycle enqueued
+  int coarse_t;          // storage of the coarsest matrix and its inverse
+  double coarse_shift;   // relative diagonal shift of the coarsest matrix
+  int tuned_zc[8];       // autotuned layers per z-chunk per TO_TUNE_* kernel (0: heuristic)
   VGraph vgraph[4];
   int n_vgraph;
   cudaStream_t cap_stream;   // private stream used only for graph capture
+  double* host_rr;           // pinned host slot for the CG residual read
+  cudaEvent_t rr_event;      // marks that read on the context stream
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   std::vector<double> ev_bytes;

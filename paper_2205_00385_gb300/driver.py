@@ -36,12 +36,15 @@ class IterLog:
     cg_iters: int
     change: float
     seconds: float
+    relres: Optional[float] = None   # final recursive-residual ratio of the MGCG solve
+    converged: bool = True           # False when the MGCG solve stopped at maxit
 
 
 class TopoSolver:
     """One optimisation job resident on the GPU."""
 
-    def __init__(self, prob, device="cuda", stream=None, precision: Optional[str] = None):
+    def __init__(self, prob, device="cuda", stream=None, precision: Optional[str] = None,
+                 autotune: bool = False):
         torch = _torch()
         self.prob = prob
         self.device = torch.device(device)
@@ -73,6 +76,12 @@ class TopoSolver:
             self.scalars = torch.zeros(4, **f64)       # compliance, change, eps, spare
             ones = torch.ones(nel, **f64)
             B.to_filter(self.ctx, B.TO_FILTER_SENS, ones, self.dv_f)
+            self.tuning = None
+            if autotune:
+                # launch shapes timed on this grid (cached per process by grid)
+                B.to_filter(self.ctx, B.TO_FILTER_DENSITY, self.rho, self.rho_phys)
+                B.to_set_density(self.ctx, self.rho_phys)
+                self.tuning = B.to_autotune(self.ctx)
         self.k = 0
         self.history: List[IterLog] = []
 
@@ -97,12 +106,12 @@ class TopoSolver:
         B.to_filter(ctx, B.TO_FILTER_DENSITY, self.rho, self.rho_phys)
         B.to_set_density(ctx, self.rho_phys)
         eps = None
-        iters = 0
+        iters, rel, ok = 0, None, True
         if k <= p.n_on or B.to_parm_count(ctx) < p.n_parm:
             flags = (B.TO_SOLVE_WARM_START if k > 1 else 0)
             if k > p.n_on - p.n_parm:
                 flags |= B.TO_SOLVE_PUSH_PARM
-            iters, _, _ = B.to_mgcg_solve(ctx, p.rtol, p.maxit, flags, self.u)
+            iters, rel, ok = B.to_mgcg_solve(ctx, p.rtol, p.maxit, flags, self.u)
             branch = "mgcg"
         else:
             B.to_carm_build(ctx, self.u)
@@ -110,9 +119,9 @@ class TopoSolver:
             if eps < p.eps_tol:
                 branch = "carm"
             else:
-                iters, _, _ = B.to_mgcg_solve(ctx, p.rtol, p.maxit,
-                                              B.TO_SOLVE_WARM_START | B.TO_SOLVE_PUSH_PARM,
-                                              self.u)
+                iters, rel, ok = B.to_mgcg_solve(ctx, p.rtol, p.maxit,
+                                                 B.TO_SOLVE_WARM_START | B.TO_SOLVE_PUSH_PARM,
+                                                 self.u)
                 branch = "mgcg-fallback"
         B.to_sensitivity(ctx, self.u, self.scalars[0:1], self.dc)
         B.to_filter(ctx, B.TO_FILTER_SENS, self.dc, self.dc_f)
@@ -124,7 +133,7 @@ class TopoSolver:
             with torch.cuda.stream(self.stream):
                 vals = self.scalars[:2].cpu().numpy()
             C, change = float(vals[0]), float(vals[1])
-        log = IterLog(k, branch, C, eps, iters, change, time.perf_counter() - t0)
+        log = IterLog(k, branch, C, eps, iters, change, time.perf_counter() - t0, rel, ok)
         self.history.append(log)
         return log
 
