@@ -56,6 +56,10 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the plain float64 run of the same workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the occupancy heuristic's launch shapes")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="finest-grid float32 operator on the tensor cores (tcgen05)")
     ap.add_argument("--small", action="store_true", help="48x24x24 instead (quick checks)")
     ap.add_argument("--kernel", default=None, choices=[None, "apply"],
                     help="time one kernel alone (profiling) instead of the design loop")
@@ -234,14 +238,15 @@ def whole_job_rate(steps: int, ws: int, slowest_s: float) -> float:
     return ws * steps / slowest_s
 
 
-def _timed_run(p, W, K, ws, barrier, profile=True, clocks=None):
+def _timed_run(p, W, K, ws, barrier, profile=True, clocks=None, autotune=True,
+               tensor_cores=False):
     """W untimed and K timed design iterations of one job; the compliance of
     every timed iteration is copied on the device (no host read inside the
     timed region) and read afterwards."""
     import torch
     from paper_2205_00385_gb300 import binding as B
     from paper_2205_00385_gb300.driver import TopoSolver
-    s = TopoSolver(p)
+    s = TopoSolver(p, autotune=autotune, tensor_cores=tensor_cores)
     for _ in range(W):
         s.step(read_compliance=False)
     if profile:
@@ -271,6 +276,7 @@ def _timed_run(p, W, K, ws, barrier, profile=True, clocks=None):
     wall = time.perf_counter() - t0
     clk = clocks.stop() if clocks else None
     out = {"dev_s": ev0.elapsed_time(ev1) / 1e3, "wall_s": wall, "clocks": clk, "logs": logs,
+           "tuning": s.tuning,
            "launches": B.to_launch_count(s.ctx),
            "compliance": comp.cpu().numpy().tolist()}
     if profile:
@@ -302,7 +308,8 @@ def run_ours(args):
             torch.cuda.synchronize()
 
     # ---- device-resident run ----
-    r = _timed_run(p, W, K, ws, barrier, clocks=ClockSampler(local))
+    r = _timed_run(p, W, K, ws, barrier, clocks=ClockSampler(local), autotune=not args.no_autotune,
+                   tensor_cores=args.tensor_cores)
     logs = r["logs"]
     branches = [h.branch for h in logs]
     cg = sum(h.cg_iters for h in logs)
@@ -311,7 +318,9 @@ def run_ours(args):
     n_f, ms_f, by_f = r["prof"][B.PK_FINE32]
     n_v, ms_v, by_v = r["prof"][B.PK_VCYCLE]
     n_o, ms_o, by_o = r["prof"][B.PK_FINE_OTHER]
-    kname = "k_apply3_pair<EPI_APPLY> (finest-grid K p, float32, two element columns per thread)"
+    kname = ("k_apply3_tc<EPI_APPLY> (finest-grid K p, float32 storage, tcgen05 TF32x3 MMAs)"
+             if args.tensor_cores else
+             "k_apply3_pair<EPI_APPLY> (finest-grid K p, float32, two element columns per thread)")
     if n_f == 0:   # float64 path: the finest-grid operator runs in float64
         n_f, ms_f, by_f = n_o, ms_o, by_o
         kname = "k_apply3_col<double> (finest-grid K p, float64)"
@@ -319,7 +328,8 @@ def run_ours(args):
     # ---- the same workload in plain float64 (the comparison the target names) ----
     fp64 = None
     if p.precision == "mixed" and not args.no_fp64_arm:
-        r64 = _timed_run(p.with_(precision="fp64"), W, K, ws, barrier, profile=False)
+        r64 = _timed_run(p.with_(precision="fp64"), W, K, ws, barrier, profile=False,
+                         autotune=not args.no_autotune)
         e64 = slowest_rank(max(r64["dev_s"], 1e-9), ws)
         c32, c64 = np.array(r["compliance"]), np.array(r64["compliance"])
         b64 = [h.branch for h in r64["logs"]]
@@ -335,7 +345,7 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
-        s = TopoSolver(p)
+        s = TopoSolver(p, autotune=not args.no_autotune)
         rho_host = torch.empty(p.nel, dtype=torch.float64, pin_memory=True)
         rho_host.copy_(torch.from_numpy(p.rho0))
         out_host = torch.empty(p.nel + 2, dtype=torch.float64, pin_memory=True)
@@ -406,6 +416,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (43.6 MB per float64 vector; >2 GB state)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline, "fp64_arm": fp64, "e2e": e2e, "gpu_launches": int(r["launches"]),
+        "autotune": ([{k: (round(v, 2) if isinstance(v, float) else v) for k, v in q.items()}
+                      for q in r["tuning"]] if r["tuning"] else None),
         "clocks": r["clocks"], "wall_s": round(r["wall_s"], 3),
     }
     if args.serve_jobs > 0 and ws == 1:
@@ -491,7 +503,7 @@ def run_kernel_apply(args):
     from paper_2205_00385_gb300 import binding as B
     from paper_2205_00385_gb300.driver import TopoSolver
     p = _problem(args)
-    s = TopoSolver(p)
+    s = TopoSolver(p, tensor_cores=args.tensor_cores)
     rho = torch.full((p.nel,), p.volfrac, dtype=torch.float64, device="cuda")
     B.to_set_density(s.ctx, rho)
     x = torch.from_numpy(np.random.default_rng(1).standard_normal(p.ndof)).cuda()
@@ -505,7 +517,8 @@ def run_kernel_apply(args):
         B.to_apply(s.ctx, B.TO_OP_K, prec, x, y)
     n, ms, by = B.to_profile_read(s.ctx, 0)
     s.close()
-    return {"kernel": "k_apply", "precision": args.kernel_prec, "launches": n,
+    return {"kernel": "k_apply3_tc" if args.tensor_cores else "k_apply", "precision": args.kernel_prec,
+            "launches": n,
             "avg_us": ms / n * 1e3, "GB/s": by / (ms / 1e3) / 1e9,
             "bytes_per_launch": by / n, "workload": p.name + f" {p.nelx}x{p.nely}x{p.nelz}"}
 

@@ -192,6 +192,71 @@ typedef struct {
 to_status to_autotune(to_ctx* ctx, int32_t reps, to_tune_result* results, int32_t cap,
                       int32_t* count);
 
+/* Continuous batching of design iterations.  A serving loop advances every
+ * active job by one design iteration per round (Fig. 1): the density phase
+ * of all jobs, each job's solve (MGCG or CARM, on its own stream), then the
+ * update phase of all jobs; jobs join and leave between rounds.
+ * to_batch_step runs one phase of n jobs as ONE CUDA graph launch on
+ * `stream` (a cudaStream_t as void*):
+ *   TO_PHASE_DENSITY: rho_phys = H(rho)/Hs (Eq. 31-32), then
+ *     to_set_density(ctx, rho_phys) (Eq. 1);
+ *   TO_PHASE_UPDATE: C and dc of u (Eq. 3, 6/34) into compliance_dev and
+ *     dc, dc_f = H^T(dc/Hs) (Eq. 33), and the OC update of rho (ref. [31] of
+ *     the paper), its change into change_dev (may be NULL).
+ * Each job's kernels are one branch of the graph, captured from the job's
+ * context stream with its own buffers in the order the single-job calls
+ * use, so every job computes bitwise what the single-job calls compute; the
+ * branches run concurrently.  The graph is captured on the first call for a
+ * job table and cached (up to 64 tables, least recently used dropped; a
+ * table holding a destroyed context is dropped) and replayed while the
+ * table repeats (including which of each job's two modulus buffers is the
+ * current one, so a steady set of jobs alternates between two cached graphs
+ * per phase).  The call enqueues and returns; `stream`
+ * waits for nothing else, so order it after each job's previous work (for
+ * example by making `stream` one of the jobs' context streams, or with
+ * events).  No other thread may use the jobs' context streams during the
+ * call.  n in [1, TO_BATCH_MAX_JOBS]; a context appearing twice, NULL
+ * arrays, a context without a density (update phase) or bad volfrac/move
+ * give TO_E_INVALID with nothing launched; errors are read with
+ * to_last_error(NULL).  The paper runs one design loop; the batching is an
+ * extension for serving several. */
+#define TO_BATCH_MAX_JOBS 256
+enum { TO_PHASE_DENSITY = 0, TO_PHASE_UPDATE = 1 };
+typedef struct {
+  to_ctx* ctx;
+  double* rho;              /* design variables (dev, nel): read; written by the update */
+  double* rho_phys;         /* physical densities (dev, nel): written by the density phase */
+  const double* u;          /* displacement (dev, n): read by the update */
+  double* dc;               /* compliance sensitivity (dev, nel): written by the update */
+  double* dc_f;             /* filtered sensitivity (dev, nel): written by the update */
+  const double* dv_f;       /* filtered volume sensitivity (dev, nel): read by the update */
+  double* compliance_dev;   /* dev, 1 double: written by the update */
+  double* change_dev;       /* dev, 1 double, or NULL */
+  double volfrac, move;     /* OC parameters (update) */
+} to_batch_job;
+to_status to_batch_step(const to_batch_job* jobs, int32_t n, int32_t phase, void* stream);
+
+/* Options of the float32 finest-grid operator of a 3D TO_MIXED context
+ * (default 0).  TO_OPERATOR_TENSOR_CORES: its products (K p of CG, the
+ * V-cycle's finest residual and smoother) run on the tensor cores (tcgen05,
+ * TF32 split into two parts per operand, three products, float32
+ * accumulation: about 2^-21 relative per element product) instead of the
+ * CUDA cores.  Results then differ from the default at that rounding level.
+ * Drops the captured V-cycle graphs and the autotuned launch shapes (tune
+ * again).  A device wait that expires in these kernels makes the next
+ * to_mgcg_solve return TO_E_TIMEOUT.  TO_E_INVALID for unknown bits or a
+ * 2D context. */
+#define TO_OPERATOR_TENSOR_CORES 1
+to_status to_operator_options(to_ctx* ctx, int32_t flags);
+
+/* Options of to_carm_build (default 0).  TO_CARM_R1_PROJECTED_LOAD: the
+ * first basis vector is the load multiplied by the approximate inverse of
+ * Eq. 18, r_1 = Phi K_Phi^{-1} Phi^T f, instead of u_last (the alternative
+ * the paper compares in Fig. 2 and finds to change little); u_last is then
+ * still required but unused.  Unknown bits give TO_E_INVALID. */
+#define TO_CARM_R1_PROJECTED_LOAD 1
+to_status to_carm_options(to_ctx* ctx, int32_t flags);
+
 /* Test hook on the last CARM basis: *kq (host) = columns of the QR factor,
  * *k (host) = directions kept by Eq. 21, sigma (host, may be NULL, n_carm
  * doubles) = singular values of the unit-column basis, descending

@@ -11,6 +11,10 @@ Each design iteration k:
      the PARM (FIFO);
   C, dC/drho~ (Eq. 3, 6/34), filtered sensitivities (Eq. 33), OC update.
 
+Variants the paper studies: the first CA basis vector Phi K_Phi^-1 Phi^T f
+instead of u_last (Fig. 2; problem field carm_r1) and a volume fraction
+lowered in the middle of the run (Fig. 3; problem field volfrac_ramp).
+
 Readings: Algorithm 1's "loop < N_on" versus the text's "more than N_on"
 are reconciled as MGCG for k <= N_on and CARM from k = N_on + 1; K_ref is
 the stiffness of the previous design iteration (the text says the last
@@ -129,7 +133,7 @@ def run(prob, n_iter: Optional[int] = None, mode: str = "aarmr", snapshot_at=(),
             dK = m.dK(E, E_prev)
             u, eps, _ = reanalysis.aarmr_solve(lambda v: K @ v, lambda v: K_ref @ v,
                                                lambda v: dK @ v, m.f, u_last, parm.matrix(),
-                                               p.n_carm)
+                                               p.n_carm, r1=p.carm_r1)
             if eps < p.eps_tol:
                 branch = "carm"
             else:
@@ -143,7 +147,7 @@ def run(prob, n_iter: Optional[int] = None, mode: str = "aarmr", snapshot_at=(),
                 parm.push(u)
         C, dc = m.sensitivities(u, rho_phys, E)
         dc_f = filters.sensitivity_filter(m.H, m.Hs, dc)
-        rho_new, _, change = oc.oc_update(rho, dc_f, m.dv_f, m.H, m.Hs, p.volfrac, p.move)
+        rho_new, _, change = oc.oc_update(rho, dc_f, m.dv_f, m.H, m.Hs, p.volfrac_at(k), p.move)
         w = float(np.mean(np.abs(rho_new - rho)) * 100.0)      # Eq. 30
         traj.history.append(IterRecord(k, branch, C, eps, iters, change, w,
                                        time.perf_counter() - t0))

@@ -131,12 +131,18 @@ def reduced_solve(K_apply: Callable, Rt: np.ndarray, f: np.ndarray):
 
 
 def aarmr_solve(K_apply: Callable, K_ref_apply: Callable, dK_apply: Callable,
-                f: np.ndarray, u_last: np.ndarray, Phi: np.ndarray, m: int):
+                f: np.ndarray, u_last: np.ndarray, Phi: np.ndarray, m: int,
+                r1: str = "u_last"):
     """One CARM build and solve as in Algorithm 1's else-branch:
-    K_Phi (Eq. 15), basis from u_last (Eq. 26), SVD (Eq. 21), reduced solve
-    (Eq. 23-25) and force residual (Eq. 29).  Returns (u~, eps, R~)."""
+    K_Phi (Eq. 15), basis from r_1 (Eq. 26), SVD (Eq. 21), reduced solve
+    (Eq. 23-25) and force residual (Eq. 29).  Returns (u~, eps, R~).
+
+    r_1 is u_last (Sec. 3.1, the choice the paper uses), or with
+    r1="projected_load" the load multiplied by the approximate inverse of
+    Eq. 18, Phi K_Phi^-1 Phi^T f, the alternative Fig. 2 compares."""
     KP = k_phi(Phi, K_ref_apply)
-    R = carm_basis(u_last, Phi, KP, dK_apply, m)
+    r_first = u_last if r1 == "u_last" else approx_inverse(Phi, KP)(f)
+    R = carm_basis(r_first, Phi, KP, dK_apply, m)
     Rt = orthonormalize(R)
     u, _, eps = reduced_solve(K_apply, Rt, f)
     return u, eps, Rt

@@ -48,6 +48,9 @@ _SIGS = {
     "to_carm_basis_error": [_VP, C.POINTER(C.c_double)],
     "to_carm_info": [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _VP],
     "to_autotune": [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)],
+    "to_batch_step": [_VP, C.c_int32, C.c_int32, _VP],
+    "to_carm_options": [_VP, C.c_int32],
+    "to_operator_options": [_VP, C.c_int32],
     "to_carm_basis_column": [_VP, C.c_int32, _VP],
     "to_set_density": [_VP, _VP],
     "to_mgcg_solve": [_VP, C.c_double, C.c_int32, C.c_int32, _VP, C.POINTER(C.c_int32),
@@ -211,6 +214,39 @@ def to_autotune(ctx, reps=10):
     return [dict(kernel=TUNE_KERNELS[r.kernel], candidates=r.candidates,
                  chunk_layers=r.chunk_layers, chosen_us=r.chosen_us, heuristic_us=r.heuristic_us)
             for r in res[:n.value]]
+
+
+TO_PHASE_DENSITY, TO_PHASE_UPDATE = 0, 1
+TO_CARM_R1_PROJECTED_LOAD = 1
+
+
+TO_OPERATOR_TENSOR_CORES = 1
+
+
+def to_operator_options(ctx, flags):
+    _check(load().to_operator_options(ctx, flags), ctx)
+
+
+def to_carm_options(ctx, flags):
+    _check(load().to_carm_options(ctx, flags), ctx)
+
+
+class to_batch_job(C.Structure):
+    _fields_ = [("ctx", _VP), ("rho", _VP), ("rho_phys", _VP), ("u", _VP), ("dc", _VP),
+                ("dc_f", _VP), ("dv_f", _VP), ("compliance_dev", _VP), ("change_dev", _VP),
+                ("volfrac", C.c_double), ("move", C.c_double)]
+
+
+def to_batch_step(jobs, phase, stream_handle):
+    """One design-loop phase of several jobs as one graph launch; jobs are
+    dicts with the to_batch_job fields (device arrays as tensors)."""
+    arr = (to_batch_job * len(jobs))()
+    for q, j in enumerate(jobs):
+        arr[q] = to_batch_job(j["ctx"], _ptr(j["rho"]), _ptr(j.get("rho_phys")), _ptr(j.get("u")),
+                              _ptr(j.get("dc")), _ptr(j.get("dc_f")), _ptr(j.get("dv_f")),
+                              _ptr(j.get("compliance_dev")), _ptr(j.get("change_dev")),
+                              float(j.get("volfrac", 0.0)), float(j.get("move", 0.0)))
+    _check(load().to_batch_step(C.cast(arr, _VP), len(jobs), phase, stream_handle))
 
 
 def to_carm_basis_column(ctx, j, out):

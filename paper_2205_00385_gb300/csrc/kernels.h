@@ -46,6 +46,9 @@ struct ApplyArgs {
                                      // column is fixed (null: mask every node)
   int zsplit = 0;      // layers per z-chunk of the column-streaming 3D kernels, set
                        // by the autotuner (0: the launcher's occupancy heuristic)
+  bool use_tc = false;            // float32 finest grid: the tensor-core operator
+  const void* bmat = nullptr;     // its B operand (tc_pack_b), device
+  int* status = nullptr;          // device word receiving TO_E_TIMEOUT from bounded waits
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 // Float32 3D finest-grid operator, two element columns per thread with packed
@@ -54,6 +57,14 @@ bool pair_apply_ok(const ApplyArgs& a);
 cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s);
 // caches the pair kernel's resident-block counts for the current device
 void pair_prepare();
+// Float32 3D finest-grid operator on the tensor cores (kernels_tc.cu):
+// B operand packing (host, 2 x 1024 floats from the float64 KE), set-up of
+// the kernels' shared-memory limit (outside stream capture), applicability
+// and launch.
+void tc_pack_b(const double* KE, float* out);
+cudaError_t tc_prepare();
+bool tc_apply_ok(const ApplyArgs& a);
+cudaError_t launch_apply_tc(const ApplyArgs& a, cudaStream_t s);
 // occupancy queries of the level-1 Galerkin column kernel (call at set-up)
 void col_prepare();
 // occupancy queries of the pair-storage double-float operator (call at set-up)

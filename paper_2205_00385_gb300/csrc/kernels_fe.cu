@@ -706,6 +706,7 @@ cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   if (a.expl) return run_expl_any(a, s);
   if (a.dim == 3) {
     if (a.gal1) return run_col_types<OPK_GAL1>(a, s);
+    if (a.use_tc && tc_apply_ok(a)) return launch_apply_tc(a, s);
     if (pair_apply_ok(a)) return launch_apply_pair(a, s);
     if (a.wht != nullptr) return run_col_types<OPK_FINE>(a, s);
   }

@@ -757,13 +757,20 @@ cudaError_t launch_dense_assemble(int dim, int t, int ta, const GridP& g, const 
   return cudaErrorInvalidValue;
 }
 
+// The blocked kernels' dynamic shared memory limit is set to the largest
+// size any call uses (227 KB), not to each call's own size: contexts of
+// different sizes run their set-up from different host threads, and a limit
+// lowered by one thread between another thread's setting and launch would
+// reject that launch.
+constexpr int COARSE_SMEM_MAX = 227 * 1024;
+
 template <typename T>
 static cudaError_t cholinv_t(int n, void* A, void* Ainv, int* status, cudaStream_t s) {
   const size_t smem = (size_t)(CB * CBP + (size_t)n * CBP) * sizeof(T);
   cudaError_t e;
-  if (smem <= 227 * 1024) {
+  if (smem <= (size_t)COARSE_SMEM_MAX) {
     e = cudaFuncSetAttribute(k_cholesky_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+                             COARSE_SMEM_MAX);
     if (e != cudaSuccess) return e;
     k_cholesky_blocked<T><<<1, 1024, smem, s>>>(n, (T*)A, status);
   } else {
@@ -775,9 +782,9 @@ static cudaError_t cholinv_t(int n, void* A, void* Ainv, int* status, cudaStream
   // the buffers are swapped by copying back.
   const int nbk = (n + 31) / 32;
   const size_t ismem = ((size_t)nbk * 32 * 32 + 32 * 33) * sizeof(T);
-  if (ismem <= 227 * 1024) {
+  if (ismem <= (size_t)COARSE_SMEM_MAX) {
     e = cudaFuncSetAttribute(k_lower_inverse_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ismem);
+                             COARSE_SMEM_MAX);
     if (e != cudaSuccess) return e;
     k_lower_inverse_blocked<T><<<nbk, 1024, ismem, s>>>(n, (const T*)A, (T*)Ainv);
   } else {

@@ -9,6 +9,7 @@
 // need no conversion and the FP64 pipe is left idle.  Reductions use a
 // fixed grid and fixed summation orders, so results do not depend on
 // scheduling.
+#include <mutex>
 #include <type_traits>
 
 #include "dfmath.cuh"
@@ -691,12 +692,13 @@ template <typename S>
 static void gram_t(long long n, const void* A, int na, const int* na_dev, const void* B, int nb,
                    const int* nb_dev, double* G, int ldg, double* partials, unsigned* counter,
                    cudaStream_t s, bool sym = false) {
-  static bool smem_set = false;   // up to 2 stages x 2*MAXB columns x MD_CH values
-  if (!smem_set) {
+  // up to 2 stages x 2*MAXB columns x MD_CH values; set once, before any
+  // launch of any host thread
+  static std::once_flag smem_once;
+  std::call_once(smem_once, [] {
     cudaFuncSetAttribute(k_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * 2 * MAXB * MD_CH * sizeof(S)));
-    smem_set = true;
-  }
+  });
   if (nb == 1 && nb_dev == nullptr && !sym)
     k_gram_col<S><<<RED_BLOCKS, 32 * na, 0, s>>>(n, (const S*)A, na, na_dev, (const S*)B, G,
                                                  partials, counter);

@@ -314,6 +314,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
   double *Phi = cv.take<double>((size_t)n * Ns), *KPhi = cv.take<double>((size_t)n * Ns);
   double *R = cv.take<double>((size_t)n * Nm), *Q = cv.take<double>((size_t)n * Nm);
   double* t = cv.take<double>(n);
+  float* tc_bmat = dim == 3 ? cv.take<float>(2048) : nullptr;
   double* Qc64 = cv.take<double>((size_t)npe * nd * nd);
   float* Qc32 = cv.take<float>((size_t)npe * nd * nd);
   // 3D with >= 3 levels: level 1 is applied without stored matrices and
@@ -356,6 +357,7 @@ static size_t carve(const to_mesh_desc& d, to_ctx* c, char* base) {
     c->r = r; c->z = z; c->p = p; c->q = q; c->p32 = p32; c->q32 = q32;
     c->Phi = Phi; c->KPhi = KPhi; c->R = R; c->Q = Q; c->t = t;
     c->Qc64 = Qc64; c->Qc32 = Qc32;
+    c->tc_bmat = tc_bmat;
     c->l1_implicit = l1_implicit; c->R2_64 = R2_64; c->R2_32 = R2_32;
     c->partials = partials; c->counters = counters; c->scal = scal; c->small = small;
     c->ints = ints;
@@ -444,6 +446,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   if (((uintptr_t)workspace) & 255) return fail(nullptr, TO_E_INVALID, "workspace not 256-byte aligned");
   const size_t need = carve(*desc, nullptr, nullptr);
   if (ws_bytes < (int64_t)need) return fail(nullptr, TO_E_OOM, "workspace too small");
+  (void)cudaGetLastError();   // an error left by other code is not this call's
   to_ctx* c = new to_ctx();
   c->desc = *desc;
   c->dim = desc->dim;
@@ -466,6 +469,8 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->coarse_t = c->mixed ? T_F32 : T_F64;
   c->coarse_shift = 0.0;
   for (int q = 0; q < 8; ++q) c->tuned_zc[q] = 0;
+  c->carm_flags = 0;
+  c->use_tc = false;
   c->host_rr = nullptr;
   c->rr_event = nullptr;
   c->cap_stream = nullptr;
@@ -501,6 +506,14 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   } while (0)
   INIT_TRY(cudaMemcpyAsync(c->Qc64, Qc.data(), Qc.size() * 8, cudaMemcpyHostToDevice, s), "copy Qc");
   INIT_TRY(cudaMemcpyAsync(c->Qc32, Qc32.data(), Qc32.size() * 4, cudaMemcpyHostToDevice, s), "copy Qc32");
+  std::vector<float> bpack(2048);
+  if (c->dim == 3) {
+    tc_pack_b(c->KE64, bpack.data());
+    INIT_TRY(cudaMemcpyAsync(c->tc_bmat, bpack.data(), 2048 * 4, cudaMemcpyHostToDevice, s),
+             "copy tensor-core B");
+    INIT_TRY(cudaStreamSynchronize(s), "sync");
+    INIT_TRY(tc_prepare(), "tensor-core operator set-up");
+  }
   if (c->l1_implicit) {
     std::vector<double> R2((size_t)64 * 576);
     grandchild_galerkin(Qc.data(), R2.data());
@@ -567,6 +580,7 @@ void to_destroy(to_ctx* ctx) {
   }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (int q = 0; q < ctx->n_vgraph; ++q) cudaGraphExecDestroy(ctx->vgraph[q].exec);
+  batch_forget(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->rr_event) cudaEventDestroy(ctx->rr_event);
   if (ctx->host_rr) cudaFreeHost(ctx->host_rr);
@@ -642,6 +656,9 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.epi = epi;
   const int k = tune_kind_fine(c, tc, epi);
   a.zsplit = k >= 0 ? c->tuned_zc[k] : 0;
+  a.use_tc = c->use_tc;
+  a.bmat = c->tc_bmat;
+  a.status = c->ints + I_TIMEOUT;
   return a;
 }
 
@@ -710,6 +727,9 @@ static to_status run_op(to_ctx* c, const ApplyArgs& a, const char* what) {
 }
 
 static to_status build_hierarchy(to_ctx* c) {
+  // the launchers report cudaGetLastError(): clear what other code in this
+  // thread may have left, so that it is not reported as this launch's error
+  (void)cudaGetLastError();
   if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
   cudaStream_t s = c->stream;
   const int t = mg_t(c);
@@ -894,11 +914,15 @@ static to_status read_scalar(to_ctx* c, const double* dev, double* host) {
 }
 
 static to_status check_status(to_ctx* c) {
-  int st = 0;
-  CUDA_TRY(c, cudaMemcpyAsync(&st, c->ints + I_STATUS, 4, cudaMemcpyDeviceToHost, c->stream),
+  int st[4] = {0, 0, 0, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(st, c->ints, sizeof(st), cudaMemcpyDeviceToHost, c->stream),
            "read status");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
-  if (st) {
+  if (st[I_TIMEOUT]) {
+    cudaMemsetAsync(c->ints + I_TIMEOUT, 0, 4, c->stream);
+    return fail(c, TO_E_TIMEOUT, "a bounded device wait expired (tensor-core operator)");
+  }
+  if (st[I_STATUS]) {
     cudaMemsetAsync(c->ints + I_STATUS, 0, 4, c->stream);
     return fail(c, TO_E_SINGULAR, "a factorisation met a non-positive pivot");
   }
@@ -1245,8 +1269,19 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
                             c->counters + C_MULTI, s), "K_Phi");
   LAUNCH(c, launch_small_spd_inverse(Ns, nullptr, small + SM_KPHI, small + SM_KPHI_INV,
                                      c->ints + I_STATUS, s), "K_Phi inverse");
-  // r_1 = u_last; r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}  (Eq. 18-20, 26)
-  LAUNCH(c, launch_vconvert(n, V_F64, u_last, v, c->R, s), "r1");
+  // r_1 = u_last (or Phi K_Phi^{-1} Phi^T f, the alternative of Fig. 2);
+  // r_i = -Phi K_Phi^{-1} Phi^T dK r_{i-1}  (Eq. 18-20, 26)
+  if (c->carm_flags & TO_CARM_R1_PROJECTED_LOAD) {
+    const double* fv = c->mixed ? c->fd : c->f;
+    LAUNCH(c, launch_gram(n, v, c->Phi, Ns, nullptr, fv, 1, nullptr, small + SM_Z, Ns,
+                          c->partials, c->counters + C_MULTI, s), "Phi^T f");
+    LAUNCH(c, launch_small_matvec(Ns, nullptr, small + SM_KPHI_INV, small + SM_Z, small + SM_W,
+                                  1.0, s), "K_Phi^-1 Phi^T f");
+    LAUNCH(c, launch_combine(n, v, c->Phi, Ns, nullptr, small + SM_W, 1.0, 0.0, c->R, v, nullptr,
+                             nullptr, c->partials, c->counters + C_UPD, s), "r1");
+  } else {
+    LAUNCH(c, launch_vconvert(n, V_F64, u_last, v, c->R, s), "r1");
+  }
   for (int i = 1; i < m; ++i) {
     if ((st = apply_accurate_vec(c, TO_OP_DK, c->R + (size_t)(i - 1) * n, c->t, EPI_APPLY)) !=
         TO_OK)
@@ -1373,7 +1408,8 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
   for (int kind = 0; kind < TO_TUNE_N && err == cudaSuccess; ++kind) {
     ApplyArgs a;
     if (!args_of(kind, &a)) continue;
-    const auto key = std::make_tuple(dev * 64 + kind * 2 + (c->mixed ? 1 : 0), kind,
+    const auto key = std::make_tuple(dev * 64 + kind * 4 + (c->mixed ? 1 : 0) + (c->use_tc ? 2 : 0),
+                                     kind,
                                      (long long)a.g.nnx, (long long)a.g.nny, (long long)a.g.nnz);
     to_tune_result r{kind, 0, 0, 0.0, 0.0};
     {
@@ -1424,6 +1460,27 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
   // captured V-cycles carry the old launch shapes
   for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
   c->n_vgraph = 0;
+  return TO_OK;
+}
+
+to_status to_operator_options(to_ctx* c, int32_t flags) {
+  if (!c) return fail(c, TO_E_INVALID, "NULL argument");
+  if (flags & ~TO_OPERATOR_TENSOR_CORES) return fail(c, TO_E_INVALID, "unknown operator option");
+  const bool tc = (flags & TO_OPERATOR_TENSOR_CORES) != 0;
+  if (tc && !c->tc_bmat) return fail(c, TO_E_INVALID, "the tensor-core operator is 3D only");
+  if (tc != c->use_tc) {
+    c->use_tc = tc;
+    for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
+    c->n_vgraph = 0;   // recaptured with the selected kernel
+    for (int q = 0; q < 8; ++q) c->tuned_zc[q] = 0;
+  }
+  return TO_OK;
+}
+
+to_status to_carm_options(to_ctx* c, int32_t flags) {
+  if (!c) return fail(c, TO_E_INVALID, "NULL argument");
+  if (flags & ~TO_CARM_R1_PROJECTED_LOAD) return fail(c, TO_E_INVALID, "unknown CARM option");
+  c->carm_flags = flags;
   return TO_OK;
 }
 
@@ -1525,6 +1582,29 @@ to_status to_filter(to_ctx* c, int32_t mode, const double* in, double* out) {
          "filter");
   return TO_OK;
 }
+
+}  // extern "C"
+
+// The OC update with a fixed number of lambda sections and no host read, so
+// that it can be captured into a graph: a section is a no-op once the
+// bracket is within 1e-13, and 48 sections cover the 7 geometric and ~16
+// even cuts the search takes, so the result equals to_oc_update's.
+to_status oc_update_enqueue(to_ctx* c, double volfrac, double move, const double* dc_f,
+                            const double* dv_f, double* rho, double* change_dev) {
+  cudaStream_t s = c->stream;
+  const long long nel = c->nel;
+  const double target = volfrac * (double)nel;
+  LAUNCH(c, launch_oc_prep_d(nel, rho, dc_f, dv_f, move, c->oc_a, c->oc_a2, c->oc_lo, c->oc_hi,
+                             c->oc_dv2, c->scal, s), "oc prep");
+  for (int q = 0; q < 48; ++q)
+    LAUNCH(c, launch_oc_section(nel, c->oc_a2, c->oc_lo, c->oc_hi, c->oc_dv2, target, c->scal,
+                                c->partials, c->counters + C_OC, s), "oc section");
+  LAUNCH(c, launch_oc_final(nel, rho, c->oc_a, move, c->scal, change_dev, c->partials,
+                            c->counters + C_MAX, s), "oc final");
+  return TO_OK;
+}
+
+extern "C" {
 
 to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_f,
                        const double* dv_f, double* rho, double* change_dev) {

@@ -127,7 +127,8 @@ enum SmallOff {
 
 // I_KCOUNT: columns accepted by the QR of the CARM basis; I_KRED: directions
 // kept by the truncated SVD of Eq. 21
-enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_KRED = 2, I_NINTS = 16 };
+// I_TIMEOUT: a bounded device wait expired (TO_E_TIMEOUT)
+enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_KRED = 2, I_TIMEOUT = 3, I_NINTS = 16 };
 
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of NV float64 values, finished by the last
@@ -348,6 +349,9 @@ struct to_ctx {
   int coarse_t;          // storage of the coarsest matrix and its inverse
   double coarse_shift;   // relative diagonal shift of the coarsest matrix
   int tuned_zc[8];       // autotuned layers per z-chunk per TO_TUNE_* kernel (0: heuristic)
+  int carm_flags;        // TO_CARM_* options of to_carm_build
+  bool use_tc;           // float32 finest-grid operator on the tensor cores
+  float* tc_bmat;        // its B operand (device, 2 x 1024 floats)
   VGraph vgraph[4];
   int n_vgraph;
   cudaStream_t cap_stream;   // private stream used only for graph capture
@@ -357,6 +361,13 @@ struct to_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   std::vector<double> ev_bytes;
 };
+
+// (topo_api.cu) the OC update with a fixed number of lambda sections and no
+// host read, capturable into a graph; same result as to_oc_update
+to_status oc_update_enqueue(to_ctx* c, double volfrac, double move, const double* dc_f,
+                            const double* dv_f, double* rho, double* change_dev);
+// (batch.cu) drops the cached batch graphs that reference c
+void batch_forget(const to_ctx* c);
 
 namespace topo {
 

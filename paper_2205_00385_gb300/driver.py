@@ -44,7 +44,7 @@ class TopoSolver:
     """One optimisation job resident on the GPU."""
 
     def __init__(self, prob, device="cuda", stream=None, precision: Optional[str] = None,
-                 autotune: bool = False):
+                 autotune: bool = False, tensor_cores: bool = False):
         torch = _torch()
         self.prob = prob
         self.device = torch.device(device)
@@ -76,6 +76,10 @@ class TopoSolver:
             self.scalars = torch.zeros(4, **f64)       # compliance, change, eps, spare
             ones = torch.ones(nel, **f64)
             B.to_filter(self.ctx, B.TO_FILTER_SENS, ones, self.dv_f)
+            if tensor_cores and prob.dim == 3 and prec == "mixed":
+                B.to_operator_options(self.ctx, B.TO_OPERATOR_TENSOR_CORES)
+            if getattr(prob, "carm_r1", "u_last") == "projected_load":
+                B.to_carm_options(self.ctx, B.TO_CARM_R1_PROJECTED_LOAD)
             self.tuning = None
             if autotune:
                 # launch shapes timed on this grid (cached per process by grid)
@@ -97,14 +101,24 @@ class TopoSolver:
             pass
 
     # -- one design iteration -------------------------------------------------
-    def step(self, read_compliance: bool = True) -> IterLog:
+    # Fig. 1: the density phase (filter, SIMP), the solve (Algorithm 1) and
+    # the update phase (compliance, sensitivity, its filter, OC).  A serving
+    # loop runs the two phases of many jobs as batched launches
+    # (to_batch_step) and only the solves job by job; step() runs all three
+    # for one job with the single-job calls.
+    def density_phase(self):
+        B.to_filter(self.ctx, B.TO_FILTER_DENSITY, self.rho, self.rho_phys)
+        B.to_set_density(self.ctx, self.rho_phys)
+
+    def solve_phase(self):
+        """Algorithm 1 for the next design iteration k: MGCG while k <= N_on
+        (its last N_s solutions fill the PARM), else the CARM, accepted when
+        eps < eps_tol, otherwise MGCG warm-started from it and pushed into the
+        PARM.  Returns (branch, eps, cg_iters, relres, converged)."""
         p = self.prob
         ctx = self.ctx
         self.k += 1
         k = self.k
-        t0 = time.perf_counter()
-        B.to_filter(ctx, B.TO_FILTER_DENSITY, self.rho, self.rho_phys)
-        B.to_set_density(ctx, self.rho_phys)
         eps = None
         iters, rel, ok = 0, None, True
         if k <= p.n_on or B.to_parm_count(ctx) < p.n_parm:
@@ -123,17 +137,38 @@ class TopoSolver:
                                                  B.TO_SOLVE_WARM_START | B.TO_SOLVE_PUSH_PARM,
                                                  self.u)
                 branch = "mgcg-fallback"
-        B.to_sensitivity(ctx, self.u, self.scalars[0:1], self.dc)
-        B.to_filter(ctx, B.TO_FILTER_SENS, self.dc, self.dc_f)
-        B.to_oc_update(ctx, p.volfrac, p.move, self.dc_f, self.dv_f, self.rho,
+        return branch, eps, iters, rel, ok
+
+    def update_phase(self):
+        """Compliance, sensitivity, its filter and the OC update for the
+        current design iteration (the volume fraction may follow a ramp)."""
+        p = self.prob
+        B.to_sensitivity(self.ctx, self.u, self.scalars[0:1], self.dc)
+        B.to_filter(self.ctx, B.TO_FILTER_SENS, self.dc, self.dc_f)
+        B.to_oc_update(self.ctx, p.volfrac_at(self.k), p.move, self.dc_f, self.dv_f, self.rho,
                        self.scalars[1:2])
+
+    def batch_job(self):
+        """This job's entry of a to_batch_step table (for the update phase of
+        the current iteration k, after solve_phase)."""
+        p = self.prob
+        return dict(ctx=self.ctx, rho=self.rho, rho_phys=self.rho_phys, u=self.u, dc=self.dc,
+                    dc_f=self.dc_f, dv_f=self.dv_f, compliance_dev=self.scalars[0:1],
+                    change_dev=self.scalars[1:2], volfrac=p.volfrac_at(max(self.k, 1)),
+                    move=p.move)
+
+    def step(self, read_compliance: bool = True) -> IterLog:
+        t0 = time.perf_counter()
+        self.density_phase()
+        branch, eps, iters, rel, ok = self.solve_phase()
+        self.update_phase()
         C = change = float("nan")
         if read_compliance:
             torch = _torch()
             with torch.cuda.stream(self.stream):
                 vals = self.scalars[:2].cpu().numpy()
             C, change = float(vals[0]), float(vals[1])
-        log = IterLog(k, branch, C, eps, iters, change, time.perf_counter() - t0, rel, ok)
+        log = IterLog(self.k, branch, C, eps, iters, change, time.perf_counter() - t0, rel, ok)
         self.history.append(log)
         return log
 

@@ -300,3 +300,44 @@ def test_basis_sizes_the_paper_reports_as_overlapping():
         assert [h.branch for h in hist] == [h.branch for h in ref], key
         for a, b in zip(ref, hist):
             assert abs(a.compliance - b.compliance) <= 1e-9 * a.compliance, (key, a, b)
+
+
+def test_projected_load_start_with_full_parm_is_pcg():
+    """The alternative first basis vector of Fig. 2, r_1 = Phi K_Phi^-1
+    Phi^T f: with Phi spanning R^n, Eq. 18 is K_ref^-1 exactly, so r_1 =
+    K_ref^-1 f and the CARM with m vectors is Kirsch's CA, i.e. the m-th PCG
+    iterate preconditioned by K_ref (the result cited in the introduction).
+    The u_last start would not give the PCG iterate."""
+    p, g, KE = _setup("cantilever3d", nelx=4, nely=2, nelz=2)
+    rng = np.random.default_rng(15)
+    E_ref = rng.uniform(0.2, 1.0, g.nel)
+    E = E_ref * rng.uniform(0.7, 1.3, g.nel)
+    K = fe.stiffness(g, E, KE, p.fixed).toarray()
+    Kr = fe.stiffness(g, E_ref, KE, p.fixed).toarray()
+    dK = K - Kr
+    Phi = rng.standard_normal((g.ndof, g.ndof))
+    cf = sla.cho_factor(Kr)
+    u_last = rng.standard_normal(g.ndof)
+    for m in (1, 2, 3):
+        u, _, _ = reanalysis.aarmr_solve(lambda v: K @ v, lambda v: Kr @ v, lambda v: dK @ v,
+                                         p.f, u_last, Phi, m, r1="projected_load")
+        u_pcg, _, _ = solvers.pcg(K, p.f, precond=lambda v: sla.cho_solve(cf, v), rtol=0.0,
+                                  maxit=m)
+        assert np.linalg.norm(u - u_pcg) < 1e-7 * np.linalg.norm(u_pcg)
+        u_l, _, _ = reanalysis.aarmr_solve(lambda v: K @ v, lambda v: Kr @ v, lambda v: dK @ v,
+                                           p.f, u_last, Phi, m)
+        assert np.linalg.norm(u_l - u_pcg) > 1e-3 * np.linalg.norm(u_pcg)
+
+
+def test_volume_ramp_is_followed():
+    """Fig. 3's study lowers the volume fraction in the middle of the run; the
+    OC update (Eq. 3) then holds the filtered volume at the ramped fraction of
+    every iteration: sum rho~ = volfrac(k) N."""
+    p = small_problem("mbb2d", nelx=24, nely=8, n_iter=9, volfrac=0.5,
+                      volfrac_ramp=(4, 0.45, 0.02))
+    assert [p.volfrac_at(k) for k in (3, 4, 5, 6, 7, 9)] == [0.5, 0.5, 0.48, 0.46, 0.45, 0.45]
+    m = aarmr.OracleModel(p)
+    t = aarmr.run(p, mode="mgcg", model=m, snapshot_at=tuple(range(2, 10)))
+    for k in range(2, 10):
+        rho_phys = t.snapshots[k]["rho_phys"]      # the design made by iteration k - 1
+        assert abs(rho_phys.sum() - p.volfrac_at(k - 1) * p.nel) < 1e-9 * p.nel

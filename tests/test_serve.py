@@ -1,8 +1,12 @@
 """Serving: admission control (host logic, CPU) and the alone-versus-mix
 property on the GPU -- every job's result is the same when it runs alone
-and when it runs concurrently with others.  Each job has its own context,
-workspace and stream, and every reduction uses a fixed grid and order, so
-the results must agree bit for bit."""
+and when it runs concurrently with others, both in the continuous-batching
+server (the density and update phases of all active jobs as one graph
+launch each, the solves concurrently) and in the per-job-stream server.
+Each job has its own context, workspace and stream, its kernels run in the
+same order either way, and every reduction uses a fixed grid and order, so
+the results must agree bit for bit.  The jobs reach the CARM phase of
+Algorithm 1 (N_on = 3) within their six iterations."""
 
 import threading
 import time
@@ -60,18 +64,44 @@ def _jobs():
     return jobs
 
 
-@pytest.mark.gpu
-def test_each_job_same_alone_and_in_the_mix():
-    import torch
-    from paper_2205_00385_gb300.serve import JobRecord, Server, run_job_on_stream
-    torch.cuda.set_device(0)
-    jobs = _jobs()
+def _alone(jobs):
+    from paper_2205_00385_gb300.serve import JobRecord, run_job_on_stream
     alone = {}
     for j in jobs:
-        rec = run_job_on_stream(j.problem, j.problem.n_iter, keep_rho=True,
-                                record=JobRecord(j.job_id, 0.0, 0))
-        alone[j.job_id] = rec
-    server = Server(budget_bytes=64 * 2 ** 30, max_active=4, keep_rho=True)
+        alone[j.job_id] = run_job_on_stream(j.problem, j.problem.n_iter, keep_rho=True,
+                                            record=JobRecord(j.job_id, 0.0, 0))
+    return alone
+
+
+@pytest.mark.gpu
+def test_each_job_same_alone_and_in_the_batched_mix():
+    import torch
+    from paper_2205_00385_gb300.serve import BatchServer
+    torch.cuda.set_device(0)
+    jobs = _jobs()
+    alone = _alone(jobs)
+    assert any("carm" in r.branches or "mgcg-fallback" in r.branches for r in alone.values())
+    server = BatchServer(budget_bytes=64 * 2 ** 30, max_active=4, keep_rho=True)
+    rep = server.run(jobs, n_iter=6)
+    records = {r.job_id: r for r in rep["_records"]}
+    assert rep["jobs_done"] == len(jobs) and not rep["jobs_failed"]
+    assert rep["peak_active_jobs"] >= 2 and rep["mean_jobs_per_round"] > 1.0   # shared launches
+    assert rep["iter_latency_ms"]["p99"] >= rep["iter_latency_ms"]["p50"] > 0
+    for j in jobs:
+        a, m = alone[j.job_id], records[j.job_id]
+        assert a.branches == m.branches
+        assert a.compliance == m.compliance            # bitwise
+        assert np.array_equal(a.rho, m.rho)
+
+
+@pytest.mark.gpu
+def test_each_job_same_alone_and_in_the_stream_mix():
+    import torch
+    from paper_2205_00385_gb300.serve import StreamServer
+    torch.cuda.set_device(0)
+    jobs = _jobs()
+    alone = _alone(jobs)
+    server = StreamServer(budget_bytes=64 * 2 ** 30, max_active=4, keep_rho=True)
     records = {}
     orig_report = server.report
 
@@ -84,7 +114,6 @@ def test_each_job_same_alone_and_in_the_mix():
     rep = server.run(jobs, n_iter=6)
     assert rep["jobs_done"] == len(jobs) and not rep["jobs_failed"]
     assert rep["peak_active_jobs"] >= 2            # they did overlap
-    assert rep["iter_latency_ms"]["p99"] >= rep["iter_latency_ms"]["p50"] > 0
     for j in jobs:
         a, m = alone[j.job_id], records[j.job_id]
         assert a.branches == m.branches
@@ -95,11 +124,35 @@ def test_each_job_same_alone_and_in_the_mix():
 @pytest.mark.gpu
 def test_tight_budget_serialises_jobs():
     import torch
-    from paper_2205_00385_gb300.serve import Server, job_device_bytes
+    from paper_2205_00385_gb300.serve import BatchServer, job_device_bytes
     torch.cuda.set_device(0)
     jobs = _jobs()
     biggest = max(job_device_bytes(j.problem) for j in jobs)
-    server = Server(budget_bytes=biggest + 1024, max_active=4)
+    server = BatchServer(budget_bytes=biggest + 1024, max_active=4)
     rep = server.run(jobs, n_iter=2)
     assert rep["jobs_done"] == len(jobs)
     assert rep["peak_admitted_gb"] * 2 ** 30 <= biggest + 1024
+
+
+@pytest.mark.gpu
+def test_batch_step_rejects_bad_tables():
+    """to_batch_step checks its table before launching anything."""
+    import torch
+    from paper_2205_00385_gb300 import binding as B
+    from paper_2205_00385_gb300.driver import TopoSolver
+    torch.cuda.set_device(0)
+    s = TopoSolver(_jobs()[3].problem)
+    try:
+        j = s.batch_job()
+        sh = torch.cuda.current_stream().cuda_stream
+        for bad, phase in (([j, j], B.TO_PHASE_DENSITY),                      # same context twice
+                           ([dict(j, rho_phys=None)], B.TO_PHASE_DENSITY),    # missing output
+                           ([dict(j, volfrac=0.0)], B.TO_PHASE_UPDATE),       # bad OC parameter
+                           ([j], 7)):                                           # bad phase
+            with pytest.raises(B.TopoError) as e:
+                B.to_batch_step(bad, phase, sh)
+            assert e.value.status == B.TO_E_INVALID
+        with pytest.raises(B.TopoError):
+            B.to_batch_step([], B.TO_PHASE_DENSITY, sh)
+    finally:
+        s.close()

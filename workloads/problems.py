@@ -61,7 +61,17 @@ class Problem:
     eps_tol: float = 1e-3     # force-residual criterion of Eq. 29
     rtol: float = 1e-8        # MGCG convergence tolerance
     maxit: int = 200          # MGCG iteration cap
+    carm_r1: str = "u_last"   # first CA basis vector: "u_last" or "projected_load" (Phi K_Phi^-1 Phi^T f)
+    volfrac_ramp: tuple = ()  # (k0, v_end, step): from iteration k0 the volume fraction
+                              # falls by `step` per iteration down to v_end
     meta: dict = field(default_factory=dict)
+
+    def volfrac_at(self, k: int) -> float:
+        """Volume fraction of design iteration k (constant unless ramped)."""
+        if not self.volfrac_ramp:
+            return self.volfrac
+        k0, v_end, step = self.volfrac_ramp
+        return max(v_end, self.volfrac - step * max(0, k - k0))
 
     @property
     def nel(self) -> int:
