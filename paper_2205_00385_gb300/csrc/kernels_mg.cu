@@ -757,21 +757,33 @@ cudaError_t launch_dense_assemble(int dim, int t, int ta, const GridP& g, const 
   return cudaErrorInvalidValue;
 }
 
-// The blocked kernels' dynamic shared memory limit is set to the largest
-// size any call uses (227 KB), not to each call's own size: contexts of
-// different sizes run their set-up from different host threads, and a limit
-// lowered by one thread between another thread's setting and launch would
-// reject that launch.
-constexpr int COARSE_SMEM_MAX = 227 * 1024;
+// The blocked kernels' dynamic shared memory limit is set once, to the most
+// the device allows next to the kernel's static shared memory, not to each
+// call's own size: contexts of different sizes run their set-up from
+// different host threads, and a limit lowered by one thread between another
+// thread's setting and launch would reject that launch.
+template <typename K>
+static int raise_dyn_smem_limit(K kernel) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, kernel) != cudaSuccess)
+    return 48 * 1024;
+  const int lim = optin - (int)fa.sharedSizeBytes;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) ==
+                 cudaSuccess
+             ? lim
+             : 48 * 1024;
+}
 
 template <typename T>
 static cudaError_t cholinv_t(int n, void* A, void* Ainv, int* status, cudaStream_t s) {
   const size_t smem = (size_t)(CB * CBP + (size_t)n * CBP) * sizeof(T);
+  static const int chol_lim = raise_dyn_smem_limit(k_cholesky_blocked<T>);
+  static const int inv_lim = raise_dyn_smem_limit(k_lower_inverse_blocked<T>);
   cudaError_t e;
-  if (smem <= (size_t)COARSE_SMEM_MAX) {
-    e = cudaFuncSetAttribute(k_cholesky_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             COARSE_SMEM_MAX);
-    if (e != cudaSuccess) return e;
+  if (smem <= (size_t)chol_lim) {
     k_cholesky_blocked<T><<<1, 1024, smem, s>>>(n, (T*)A, status);
   } else {
     k_cholesky<T><<<1, 1024, 0, s>>>(n, (T*)A, status);
@@ -782,10 +794,7 @@ static cudaError_t cholinv_t(int n, void* A, void* Ainv, int* status, cudaStream
   // the buffers are swapped by copying back.
   const int nbk = (n + 31) / 32;
   const size_t ismem = ((size_t)nbk * 32 * 32 + 32 * 33) * sizeof(T);
-  if (ismem <= (size_t)COARSE_SMEM_MAX) {
-    e = cudaFuncSetAttribute(k_lower_inverse_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             COARSE_SMEM_MAX);
-    if (e != cudaSuccess) return e;
+  if (ismem <= (size_t)inv_lim) {
     k_lower_inverse_blocked<T><<<nbk, 1024, ismem, s>>>(n, (const T*)A, (T*)Ainv);
   } else {
     k_lower_inverse<T><<<nblocks((long long)n * 32, 256), 256, 0, s>>>(n, (const T*)A, (T*)Ainv);

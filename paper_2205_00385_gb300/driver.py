@@ -38,6 +38,7 @@ class IterLog:
     seconds: float
     relres: Optional[float] = None   # final recursive-residual ratio of the MGCG solve
     converged: bool = True           # False when the MGCG solve stopped at maxit
+    solve_seconds: float = 0.0       # wall time of the equilibrium solve (MGCG or CARM)
 
 
 class TopoSolver:
@@ -160,7 +161,14 @@ class TopoSolver:
     def step(self, read_compliance: bool = True) -> IterLog:
         t0 = time.perf_counter()
         self.density_phase()
+        # the solve's calls synchronise on their results (|r|, eps), so the
+        # host wall time of solve_phase, after the density phase has
+        # finished, is the solve's time
+        self.stream.synchronize()
+        ts = time.perf_counter()
         branch, eps, iters, rel, ok = self.solve_phase()
+        self.stream.synchronize()
+        t_solve = time.perf_counter() - ts
         self.update_phase()
         C = change = float("nan")
         if read_compliance:
@@ -168,7 +176,8 @@ class TopoSolver:
             with torch.cuda.stream(self.stream):
                 vals = self.scalars[:2].cpu().numpy()
             C, change = float(vals[0]), float(vals[1])
-        log = IterLog(self.k, branch, C, eps, iters, change, time.perf_counter() - t0, rel, ok)
+        log = IterLog(self.k, branch, C, eps, iters, change, time.perf_counter() - t0, rel, ok,
+                      t_solve)
         self.history.append(log)
         return log
 

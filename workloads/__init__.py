@@ -19,6 +19,12 @@ from .problems import (  # noqa: F401
     bridge3d,
     mbb2d,
     cantilever2d,
+    halfwheel2d,
+    beam3d,
+    study_halfwheel,
+    study_beam,
+    HALFWHEEL_MODELS,
+    BEAM_MODELS,
     small_problem,
     rand_vector,
     rand_density,

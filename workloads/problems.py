@@ -188,6 +188,61 @@ def bridge3d(nelx: int, nely: int, nelz: int, volfrac: float = 0.10, rmin: float
     return p.with_(**kw)
 
 
+def halfwheel2d(nelx: int, nely: int, volfrac: float = 0.5, rmin: float = 2.5, **kw) -> Problem:
+    """2D half-wheel of Sec. 4.2.1: a rectangle (aspect ratio 2 in the paper),
+    the lower-left node fully constrained, the lower-right node constrained in
+    the load direction (y), a unit downward point load at the midpoint of the
+    bottom edge."""
+    dim = 2
+    _, nn, ndof = grid_counts(dim, nelx, nely)
+    fixed = np.zeros(ndof, np.uint8)
+    fixed[dim * _node(nelx, nely, 0, 0) + 0] = 1
+    fixed[dim * _node(nelx, nely, 0, 0) + 1] = 1
+    fixed[dim * _node(nelx, nely, nelx, 0) + 1] = 1
+    f = np.zeros(ndof)
+    f[dim * _node(nelx, nely, nelx // 2, 0) + 1] = -1.0
+    nel = nelx * nely
+    p = Problem("halfwheel2d", dim, nelx, nely, 0, fixed, f, np.full(nel, volfrac), volfrac, rmin)
+    return p.with_(**kw)
+
+
+def beam3d(nelx: int, nely: int, nelz: int, volfrac: float = 0.2, rmin: float = 2.5,
+           **kw) -> Problem:
+    """3D simply supported beam of Sec. 4.2.2: a cuboid (x length, y height,
+    z depth), all DOFs of the four bottom corner nodes fixed, a unit downward
+    point load at the midpoint of the bottom face."""
+    dim = 3
+    _, nn, ndof = grid_counts(dim, nelx, nely, nelz)
+    fixed = np.zeros(ndof, np.uint8)
+    for i in (0, nelx):
+        for k in (0, nelz):
+            n = _node(nelx, nely, i, 0, k)
+            fixed[dim * n:dim * n + 3] = 1
+    f = np.zeros(ndof)
+    f[dim * _node(nelx, nely, nelx // 2, 0, nelz // 2) + 1] = -1.0
+    nel = nelx * nely * nelz
+    p = Problem("beam3d", dim, nelx, nely, nelz, fixed, f, np.full(nel, volfrac), volfrac, rmin)
+    return p.with_(**kw)
+
+
+# The reproduction studies of Sec. 4.2: MGCG and AARMR on the same problem
+# (N_on = 20, N_s = N_m = 2, MGCG rtol 1e-6, 3 grid levels; MGCG maxit 200
+# in 2D, 50 in 3D), the force-residual criterion eps_tol varied.
+HALFWHEEL_MODELS = [(320, 160), (640, 320), (840, 420), (960, 480)]
+BEAM_MODELS = [(72, 24, 48), (84, 28, 56), (96, 32, 64), (120, 40, 80)]
+
+
+def study_halfwheel(nelx: int, nely: int, eps_tol: float, n_iter: int = 100, **kw) -> Problem:
+    return halfwheel2d(nelx, nely, n_iter=n_iter, mg_levels=3, n_parm=2, n_carm=2, n_on=20,
+                       eps_tol=eps_tol, rtol=1e-6, maxit=200, **kw)
+
+
+def study_beam(nelx: int, nely: int, nelz: int, eps_tol: float, n_iter: int = 100,
+               **kw) -> Problem:
+    return beam3d(nelx, nely, nelz, n_iter=n_iter, mg_levels=3, n_parm=2, n_carm=2, n_on=20,
+                  eps_tol=eps_tol, rtol=1e-6, maxit=50, **kw)
+
+
 # --------------------------------------------------------------------------
 # The five benchmark workloads.  Parameters the paper leaves open take the
 # readings recorded with the design notes (N_s = N_m = s, N_on per workload,
