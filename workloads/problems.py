@@ -226,21 +226,36 @@ def beam3d(nelx: int, nely: int, nelz: int, volfrac: float = 0.2, rmin: float = 
 
 
 # The reproduction studies of Sec. 4.2: MGCG and AARMR on the same problem
-# (N_on = 20, N_s = N_m = 2, MGCG rtol 1e-6, 3 grid levels; MGCG maxit 200
-# in 2D, 50 in 3D), the force-residual criterion eps_tol varied.
+# (N_on = 20, N_s = N_m = 2, MGCG rtol 1e-6; MGCG maxit 200 in 2D, 50 in
+# 3D), the force-residual criterion eps_tol varied.  The paper uses 3 grid
+# levels; here the hierarchy is the deepest the grid allows (the coarsest
+# grid is solved densely), the same for both methods.
 HALFWHEEL_MODELS = [(320, 160), (640, 320), (840, 420), (960, 480)]
 BEAM_MODELS = [(72, 24, 48), (84, 28, 56), (96, 32, 64), (120, 40, 80)]
 
 
-def study_halfwheel(nelx: int, nely: int, eps_tol: float, n_iter: int = 100, **kw) -> Problem:
-    return halfwheel2d(nelx, nely, n_iter=n_iter, mg_levels=3, n_parm=2, n_carm=2, n_on=20,
-                       eps_tol=eps_tol, rtol=1e-6, maxit=200, **kw)
+def deepest_levels(*nel: int) -> int:
+    """Grid levels of the deepest 2x-coarsened hierarchy of a grid: halve
+    while every axis stays even and the halved axes keep at least 2
+    elements."""
+    levels, dims = 1, [n for n in nel if n > 0]
+    while all(n % 2 == 0 and n // 2 >= 2 for n in dims):
+        dims = [n // 2 for n in dims]
+        levels += 1
+    return levels
+
+
+def study_halfwheel(nelx: int, nely: int, eps_tol: float, n_iter: int = 100,
+                    mg_levels: int = 0, **kw) -> Problem:
+    return halfwheel2d(nelx, nely, n_iter=n_iter, mg_levels=mg_levels or deepest_levels(nelx, nely),
+                       n_parm=2, n_carm=2, n_on=20, eps_tol=eps_tol, rtol=1e-6, maxit=200, **kw)
 
 
 def study_beam(nelx: int, nely: int, nelz: int, eps_tol: float, n_iter: int = 100,
-               **kw) -> Problem:
-    return beam3d(nelx, nely, nelz, n_iter=n_iter, mg_levels=3, n_parm=2, n_carm=2, n_on=20,
-                  eps_tol=eps_tol, rtol=1e-6, maxit=50, **kw)
+               mg_levels: int = 0, **kw) -> Problem:
+    return beam3d(nelx, nely, nelz, n_iter=n_iter,
+                  mg_levels=mg_levels or deepest_levels(nelx, nely, nelz), n_parm=2, n_carm=2,
+                  n_on=20, eps_tol=eps_tol, rtol=1e-6, maxit=50, **kw)
 
 
 # --------------------------------------------------------------------------
