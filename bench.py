@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the plain float64 run of the same workload")
+    ap.add_argument("--no-mgcg-arm", action="store_true",
+                    help="skip the MGCG-only run of the same workload")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the occupancy heuristic's launch shapes")
     ap.add_argument("--tensor-cores", action="store_true",
@@ -288,6 +290,23 @@ def _timed_run(p, W, K, ws, barrier, profile=True, clocks=None, autotune=True,
     return out
 
 
+def _carm_summary(logs):
+    """Time and outcome of the timed iterations' CARM attempts (build of the
+    basis, reduced solve and eps), and the MGCG solves around them."""
+    att = [h for h in logs if h.branch in ("carm", "mgcg-fallback")]
+    mg = [h for h in logs if h.branch == "mgcg"]
+    fb = [h for h in logs if h.branch == "mgcg-fallback"]
+    if not att:
+        return None
+    return {"attempts": len(att), "accepted": sum(h.branch == "carm" for h in att),
+            "mean_build_and_solve_ms": round(1e3 * sum(h.carm_seconds for h in att) / len(att), 3),
+            "eps_min": float(min(h.eps for h in att)), "eps_max": float(max(h.eps for h in att)),
+            "mean_mgcg_solve_ms": (round(1e3 * sum(h.solve_seconds for h in mg) / len(mg), 3)
+                                   if mg else None),
+            "mean_fallback_solve_ms": (round(1e3 * sum(h.solve_seconds for h in fb) / len(fb), 3)
+                                       if fb else None)}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -341,6 +360,21 @@ def run_ours(args):
                 "compliance_rel_diff_max": float(np.max(np.abs(c32 - c64) / np.abs(c64))),
                 "note": ("each precision runs its own trajectory from the same initial design; "
                          "the difference is taken per timed iteration")}
+
+    # ---- the same workload with MGCG only (Algorithm 1 without the reanalysis) ----
+    mgcg_only = None
+    if not args.no_mgcg_arm:
+        rm = _timed_run(p.with_(n_on=10 ** 9), W, K, ws, barrier, profile=False,
+                        autotune=not args.no_autotune, tensor_cores=args.tensor_cores)
+        em = slowest_rank(max(rm["dev_s"], 1e-9), ws)
+        cm = np.array(rm["compliance"])
+        mgcg_only = {"value": round(whole_job_rate(K, ws, em), 4), "unit": UNIT,
+                     "ms_per_step": round(em / K * 1e3, 3),
+                     "cg_iterations": sum(h.cg_iters for h in rm["logs"]),
+                     "aarmr_over_mgcg": round(value / whole_job_rate(K, ws, em), 4),
+                     "final_compliance": float(cm[-1]),
+                     "final_compliance_rel_diff": float(abs(r["compliance"][-1] - cm[-1]) /
+                                                        abs(cm[-1]))}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -415,7 +449,9 @@ def run_ours(args):
                    "final_compliance": r["compliance"][-1],
                    "l2": "inputs larger than L2 (43.6 MB per float64 vector; >2 GB state)",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": roofline, "fp64_arm": fp64, "e2e": e2e, "gpu_launches": int(r["launches"]),
+        "roofline": roofline, "fp64_arm": fp64, "mgcg_only_arm": mgcg_only,
+        "carm_attempts": _carm_summary(logs),
+        "e2e": e2e, "gpu_launches": int(r["launches"]),
         "autotune": ([{k: (round(v, 2) if isinstance(v, float) else v) for k, v in q.items()}
                       for q in r["tuning"]] if r["tuning"] else None),
         "clocks": r["clocks"], "wall_s": round(r["wall_s"], 3),

@@ -39,6 +39,7 @@ class IterLog:
     relres: Optional[float] = None   # final recursive-residual ratio of the MGCG solve
     converged: bool = True           # False when the MGCG solve stopped at maxit
     solve_seconds: float = 0.0       # wall time of the equilibrium solve (MGCG or CARM)
+    carm_seconds: float = 0.0        # wall time of the CARM build and reduced solve, if tried
 
 
 class TopoSolver:
@@ -122,6 +123,7 @@ class TopoSolver:
         k = self.k
         eps = None
         iters, rel, ok = 0, None, True
+        self.last_carm_s = 0.0
         if k <= p.n_on or B.to_parm_count(ctx) < p.n_parm:
             flags = (B.TO_SOLVE_WARM_START if k > 1 else 0)
             if k > p.n_on - p.n_parm:
@@ -129,8 +131,10 @@ class TopoSolver:
             iters, rel, ok = B.to_mgcg_solve(ctx, p.rtol, p.maxit, flags, self.u)
             branch = "mgcg"
         else:
+            tc = time.perf_counter()
             B.to_carm_build(ctx, self.u)
-            eps = B.to_carm_solve(ctx, self.u, self.scalars[2:3])
+            eps = B.to_carm_solve(ctx, self.u, self.scalars[2:3])   # returns eps to the host
+            self.last_carm_s = time.perf_counter() - tc
             if eps < p.eps_tol:
                 branch = "carm"
             else:
@@ -177,7 +181,7 @@ class TopoSolver:
                 vals = self.scalars[:2].cpu().numpy()
             C, change = float(vals[0]), float(vals[1])
         log = IterLog(self.k, branch, C, eps, iters, change, time.perf_counter() - t0, rel, ok,
-                      t_solve)
+                      t_solve, self.last_carm_s)
         self.history.append(log)
         return log
 
