@@ -20,6 +20,9 @@ from .problems import (  # noqa: F401
     mbb2d,
     cantilever2d,
     halfwheel2d,
+    inverter2d,
+    study_inverter,
+    INVERTER_MODELS,
     beam3d,
     study_halfwheel,
     study_beam,

@@ -64,6 +64,9 @@ class Problem:
     carm_r1: str = "u_last"   # first CA basis vector: "u_last" or "projected_load" (Phi K_Phi^-1 Phi^T f)
     volfrac_ramp: tuple = ()  # (k0, v_end, step): from iteration k0 the volume fraction
                               # falls by `step` per iteration down to v_end
+    springs: tuple = ()       # ((dof, k), ...): linear springs to ground (Sec. 4.3)
+    out_dof: int = -1         # mechanism objective u_out = u[out_dof] (Sec. 4.3); -1: compliance
+    oc_eta: float = 0.5       # damping exponent of the OC update
     meta: dict = field(default_factory=dict)
 
     def volfrac_at(self, k: int) -> float:
@@ -225,6 +228,46 @@ def beam3d(nelx: int, nely: int, nelz: int, volfrac: float = 0.2, rmin: float = 
     return p.with_(**kw)
 
 
+def inverter2d(nelx: int, nely: int, volfrac: float = 0.3, rmin: float = 2.5,
+               k_in: float = 1.0, k_out: float = 0.1, **kw) -> Problem:
+    """2D displacement inverter of Sec. 4.3 (half model): the bottom edge is
+    the symmetry axis (y-displacements fixed), the input A is the bottom-left
+    node with a unit force in +x and a spring k_in, the output B the
+    bottom-right node with a spring k_out; the top end of the left edge
+    (nely/16 of it, at least one element) is clamped.  The objective is
+    u_out = u_x(B), minimised (B moves against the input); OC damping 0.3,
+    move limit 0.1."""
+    dim = 2
+    _, nn, ndof = grid_counts(dim, nelx, nely)
+    fixed = np.zeros(ndof, np.uint8)
+    for i in range(nelx + 1):
+        fixed[dim * _node(nelx, nely, i, 0) + 1] = 1
+    for j in range(nely - max(1, nely // 16), nely + 1):
+        n = _node(nelx, nely, 0, j)
+        fixed[dim * n:dim * n + 2] = 1
+    a = dim * _node(nelx, nely, 0, 0)
+    b = dim * _node(nelx, nely, nelx, 0)
+    f = np.zeros(ndof)
+    f[a] = 1.0
+    nel = nelx * nely
+    p = Problem("inverter2d", dim, nelx, nely, 0, fixed, f, np.full(nel, volfrac), volfrac, rmin,
+                move=0.1, springs=((a, k_in), (b, k_out)), out_dof=b, oc_eta=0.3)
+    return p.with_(**kw)
+
+
+# Sec. 4.3 (Table 1): the inverter at 320 x 160 and 640 x 320, 200 design
+# iterations, N_on = 20, N_s = N_m = 2, MGCG rtol 1e-6 and maxit 200, the
+# force-residual criterion 0.01 % and 0.1 %.
+INVERTER_MODELS = [(320, 160), (640, 320)]
+
+
+def study_inverter(nelx: int, nely: int, eps_tol: float, n_iter: int = 200,
+                   mg_levels: int = 0, **kw) -> Problem:
+    return inverter2d(nelx, nely, n_iter=n_iter,
+                      mg_levels=mg_levels or deepest_levels(nelx, nely), n_parm=2, n_carm=2,
+                      n_on=20, eps_tol=eps_tol, rtol=1e-6, maxit=200, **kw)
+
+
 # The reproduction studies of Sec. 4.2: MGCG and AARMR on the same problem
 # (N_on = 20, N_s = N_m = 2, MGCG rtol 1e-6; MGCG maxit 200 in 2D, 50 in
 # 3D), the force-residual criterion eps_tol varied.  The paper uses 3 grid
@@ -345,6 +388,10 @@ def small_problem(kind: str = "cantilever3d", **kw) -> Problem:
         base = dict(nelx=12, nely=8)
         base.update({k: kw.pop(k) for k in list(kw) if k in ("nelx", "nely")})
         return cantilever2d(base["nelx"], base["nely"], **kw)
+    if kind == "inverter2d":
+        base = dict(nelx=16, nely=8)
+        base.update({k: kw.pop(k) for k in list(kw) if k in ("nelx", "nely")})
+        return inverter2d(base["nelx"], base["nely"], **kw)
     raise ValueError(kind)
 
 
