@@ -170,6 +170,8 @@ to_status to_carm_build(to_ctx* ctx, const double* u_last);
  *   TO_TUNE_GAL1_RESID / _SMOOTH: the level-1 Galerkin operator applied
  *     from the finest moduli (3D, >= 3 levels);
  *   TO_TUNE_ACC_APPLY / _RESID: the double-float operator (TO_MIXED).
+ * For the float32 finest-grid kernels it also times a second register
+ * variant (one more resident block per SM, a few registers spilled).
  * It keeps the fastest (the occupancy heuristic's own shape when within 1 %
  * of it), applies it to every later launch of that kernel on this context,
  * drops the captured V-cycle graphs so that they are recaptured with it, and
@@ -188,6 +190,8 @@ typedef struct {
   int32_t chunk_layers;  /* chosen node layers per chunk (0: the heuristic's shape) */
   double chosen_us;      /* average launch time of the chosen shape (0 when cached) */
   double heuristic_us;   /* average launch time of the heuristic's shape (0 when cached) */
+  int32_t variant;       /* float32 finest-grid kernels (TO_TUNE_OP_*): register variant,
+                            0 = no spills, 1 = one more resident block per SM */
 } to_tune_result;
 to_status to_autotune(to_ctx* ctx, int32_t reps, to_tune_result* results, int32_t cap,
                       int32_t* count);
@@ -236,8 +240,9 @@ typedef struct {
 } to_batch_job;
 to_status to_batch_step(const to_batch_job* jobs, int32_t n, int32_t phase, void* stream);
 
-/* Options of the float32 finest-grid operator of a 3D TO_MIXED context
- * (default 0).  TO_OPERATOR_TENSOR_CORES: its products (K p of CG, the
+/* Operator and multigrid options of a context (default 0).
+ * TO_OPERATOR_TENSOR_CORES (3D TO_MIXED only): the float32 finest-grid
+ * operator's products (K p of CG, the
  * V-cycle's finest residual and smoother) run on the tensor cores (tcgen05,
  * TF32 split into two parts per operand, three products, float32
  * accumulation: about 2^-21 relative per element product) instead of the
@@ -247,6 +252,16 @@ to_status to_batch_step(const to_batch_job* jobs, int32_t n, int32_t phase, void
  * to_mgcg_solve return TO_E_TIMEOUT.  TO_E_INVALID for unknown bits or a
  * 2D context. */
 #define TO_OPERATOR_TENSOR_CORES 1
+/* TO_OPERATOR_FUSED_COARSE: the coarse end of the V-cycle (Algorithm 2) --
+ * the stored levels whose assembled stencil is at most a few MB, down to
+ * the coarsest grid and back -- runs as one launch of one thread-block
+ * cluster with hardware cluster barriers between the steps, instead of one
+ * kernel per step (the default).  The results are bit for bit the same.
+ * Measured at 192 x 96 x 96 it is slower (each step then runs on the
+ * cluster's 8-16 SMs with one memory round trip or more per step, where the
+ * one-kernel steps use the whole GPU and overlap their launches), so it is
+ * off by default.  Changing it drops the captured V-cycle graphs. */
+#define TO_OPERATOR_FUSED_COARSE 2
 to_status to_operator_options(to_ctx* ctx, int32_t flags);
 
 /* Options of to_carm_build (default 0).  TO_CARM_R1_PROJECTED_LOAD: the
@@ -284,6 +299,35 @@ to_status to_carm_solve(to_ctx* ctx, double* u, double* eps, double* eps_dev);
  * dc_e = -penal (E0-Emin) rho~_e^(penal-1) u_e^T KE u_e (Eq. 6 / 34) -> dc
  * (dev, nel). */
 to_status to_sensitivity(to_ctx* ctx, const double* u, double* compliance_dev, double* dc);
+
+/* Compliant mechanisms (Sec. 4.3, the displacement inverter).
+ *
+ * to_mesh_springs: linear springs to ground on free finest-grid DOFs (2D
+ * contexts): every product with K and K_ref (TO_OP_K, TO_OP_KREF, the CG,
+ * the V-cycle's finest level, the CARM's K_ref Phi and K R~) becomes
+ * (K + S) x with S diagonal, k[q] at dofs[q]; dK is unchanged (the springs
+ * do not depend on the design); the multigrid hierarchy includes P^T S P.
+ * dofs (host int64, n) and k (host float64 >= 0, n) are copied; n <=
+ * TO_MAX_SPRINGS; n = 0 removes them.  Takes effect at the next
+ * to_set_density.  Synchronises (reads the DOFs' masks).  TO_E_INVALID for
+ * a 3D context, a DOF out of range, repeated or fixed, or a bad k. */
+#define TO_MAX_SPRINGS 4
+to_status to_mesh_springs(to_ctx* ctx, int32_t n, const int64_t* dofs, const double* k);
+
+/* Sensitivity of an output displacement u_out = l^T u through the adjoint
+ * field lam (K lam = l): dc_e = -penal (E0-Emin) rho~_e^(penal-1)
+ * lam_e^T KE u_e -> dc (dev, nel), the prescribed DOFs taken as zero in
+ * both fields; sum_e E_e lam_e^T KE u_e -> mutual_dev (dev, 1 double).
+ * u, lam: dev float64 n.  Uses the density of the last to_set_density. */
+to_status to_sensitivity_adjoint(to_ctx* ctx, const double* u, const double* lam,
+                                 double* mutual_dev, double* dc);
+
+/* Damping exponent eta of the OC update (default 1/2, the compliance rule):
+ * rho_new = clamp(rho max(0, -dc / (lambda dv))^eta) within the move limit
+ * (0.3 for the mechanism problem).  Applies to to_oc_update and the batched
+ * update phase (not to the no-allocation entry point).  TO_E_INVALID
+ * unless 0 < eta <= 1. */
+to_status to_oc_options(to_ctx* ctx, double eta);
 
 /* Density filter (Eq. 31-32), mode TO_FILTER_DENSITY: out = (H in) / Hs;
  * or its transpose for sensitivities (Eq. 33), mode TO_FILTER_SENS:

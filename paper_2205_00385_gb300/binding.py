@@ -61,6 +61,9 @@ _SIGS = {
     "to_carm_build": [_VP, _VP],
     "to_carm_solve": [_VP, _VP, C.POINTER(C.c_double), _VP],
     "to_sensitivity": [_VP, _VP, _VP, _VP],
+    "to_mesh_springs": [_VP, C.c_int32, _VP, _VP],
+    "to_sensitivity_adjoint": [_VP, _VP, _VP, _VP, _VP],
+    "to_oc_options": [_VP, C.c_double],
     "to_filter": [_VP, C.c_int32, _VP, _VP],
     "to_oc_update": [_VP, C.c_double, C.c_double, _VP, _VP, _VP, _VP],
     "to_oc_update_noalloc": [C.c_int64, C.c_double, C.c_double, _VP, _VP, _VP, _VP, _VP],
@@ -202,7 +205,7 @@ TUNE_KERNELS = ("op_apply", "op_resid", "op_smooth", "gal1_resid", "gal1_smooth"
 
 class to_tune_result(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("candidates", C.c_int32), ("chunk_layers", C.c_int32),
-                ("chosen_us", C.c_double), ("heuristic_us", C.c_double)]
+                ("chosen_us", C.c_double), ("heuristic_us", C.c_double), ("variant", C.c_int32)]
 
 
 def to_autotune(ctx, reps=10):
@@ -212,7 +215,8 @@ def to_autotune(ctx, reps=10):
     n = C.c_int32()
     _check(load().to_autotune(ctx, reps, C.cast(res, _VP), len(TUNE_KERNELS), C.byref(n)), ctx)
     return [dict(kernel=TUNE_KERNELS[r.kernel], candidates=r.candidates,
-                 chunk_layers=r.chunk_layers, chosen_us=r.chosen_us, heuristic_us=r.heuristic_us)
+                 chunk_layers=r.chunk_layers, chosen_us=r.chosen_us, heuristic_us=r.heuristic_us,
+                 variant=r.variant)
             for r in res[:n.value]]
 
 
@@ -221,6 +225,7 @@ TO_CARM_R1_PROJECTED_LOAD = 1
 
 
 TO_OPERATOR_TENSOR_CORES = 1
+TO_OPERATOR_FUSED_COARSE = 2
 
 
 def to_operator_options(ctx, flags):
@@ -255,6 +260,27 @@ def to_carm_basis_column(ctx, j, out):
 
 def to_sensitivity(ctx, u, compliance_dev, dc):
     _check(load().to_sensitivity(ctx, _ptr(u), _ptr(compliance_dev), _ptr(dc)), ctx)
+
+
+TO_MAX_SPRINGS = 4
+
+
+def to_mesh_springs(ctx, dofs, ks):
+    """Springs to ground on free DOFs (2D): lists of DOF indices and
+    stiffnesses, copied by the library."""
+    n = len(dofs)
+    d = (C.c_int64 * max(n, 1))(*[int(x) for x in dofs])
+    k = (C.c_double * max(n, 1))(*[float(x) for x in ks])
+    _check(load().to_mesh_springs(ctx, n, C.cast(d, _VP), C.cast(k, _VP)), ctx)
+
+
+def to_sensitivity_adjoint(ctx, u, lam, mutual_dev, dc):
+    _check(load().to_sensitivity_adjoint(ctx, _ptr(u), _ptr(lam), _ptr(mutual_dev), _ptr(dc)),
+           ctx)
+
+
+def to_oc_options(ctx, eta):
+    _check(load().to_oc_options(ctx, float(eta)), ctx)
 
 
 def to_filter(ctx, mode, x, out):

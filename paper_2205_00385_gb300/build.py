@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libtopo.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["kernels_fe.cu", "kernels_pair.cu", "kernels_tc.cu", "kernels_df.cu", "kernels_mg.cu", "kernels_blas.cu", "kernels_vec.cu", "kernels_opt.cu",
+SOURCES = ["kernels_fe.cu", "kernels_pair.cu", "kernels_tc.cu", "kernels_vfuse.cu", "kernels_df.cu", "kernels_mg.cu", "kernels_blas.cu", "kernels_vec.cu", "kernels_opt.cu",
            "topo_api.cu", "batch.cu", "noalloc.cu"]
 
 

@@ -46,11 +46,45 @@ struct ApplyArgs {
                                      // column is fixed (null: mask every node)
   int zsplit = 0;      // layers per z-chunk of the column-streaming 3D kernels, set
                        // by the autotuner (0: the launcher's occupancy heuristic)
+  int variant = 0;     // register / occupancy variant of the float32 pair kernel
+                       // (0: no spills; 1: one more resident block), autotuned
   bool use_tc = false;            // float32 finest grid: the tensor-core operator
   const void* bmat = nullptr;     // its B operand (tc_pack_b), device
   int* status = nullptr;          // device word receiving TO_E_TIMEOUT from bounded waits
+  Springs springs;                // finest 2D grid: springs to ground added to K (none: n = 0)
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+
+// The coarse end of the V-cycle in one cluster launch (kernels_vfuse.cu):
+// restriction into level l0 (from level l0 - 1's residual r), the residual
+// and restriction of every level down to the coarsest, its exact solve with
+// the stored inverse, then interpolation and post-smoothing back up to level
+// l0 (result in lv[l0].z2).  Levels l0 .. L-1 must be stored (stencil)
+// levels.  Bit for bit the same as the one-kernel-per-step sequence.
+constexpr int VF_MAXL = 12;
+// a level joins the fused stretch when its assembled stencil is at most this
+// large (the cluster's 8-16 SMs stream it in a few microseconds)
+constexpr double VF_MAX_STENCIL_BYTES = 6.0e6;
+struct VFLevel {
+  GridP g;
+  const uint8_t* mask;
+  const void* S;       // assembled stencil (levels >= l0)
+  const void* dinv;
+  void* b;             // right-hand side
+  void* z;             // iterate (pre-smoothed, then corrected)
+  void* z2;            // post-smoothed result
+  void* r;             // residual
+};
+struct VFuseArgs {
+  int l0, L;
+  VFLevel lv[VF_MAXL];   // indexed by level; lv[l0 - 1] supplies the input residual
+  const void* Ainv;      // coarsest inverse, type ta
+  int nc;
+  double omega;
+};
+// cluster size the fused kernel launches with on this device (0: unavailable)
+int vcycle_coarse_cluster(int dim, int t, int ta);
+cudaError_t launch_vcycle_coarse(int dim, int t, int ta, const VFuseArgs& a, cudaStream_t s);
 // Float32 3D finest-grid operator, two element columns per thread with packed
 // f32x2 arithmetic (kernels_pair.cu); pair_apply_ok tells whether it applies.
 bool pair_apply_ok(const ApplyArgs& a);
@@ -84,7 +118,7 @@ void wht_blocks_pin_zeros(double* w64, float* w32);
 // dinv = 1 / diag(A) (1 on fixed DOFs)
 cudaError_t launch_diag(int dim, const GridP& g, const uint8_t* mask, int tc, bool expl,
                         const void* coef, const void* Kc, const void* ke, void* dinv,
-                        cudaStream_t s);
+                        cudaStream_t s, const Springs& sp = Springs());
 
 // ---- multigrid transfer and Galerkin operators (kernels_mg.cu) ----
 // b_c = Pm^T r_f; when zc is not null also the coarse level's smoothing from
@@ -232,11 +266,14 @@ cudaError_t launch_sensitivity_df(const GridP& g, const uint8_t* mask, const dou
                                   double* compliance, double* partials, unsigned* counter,
                                   cudaStream_t s);
 // wht: host pointer to the float64 Walsh blocks of KE (3D), else null
+// With v set (an adjoint field) the element term is v_e^T KE u_e instead of
+// u_e^T KE u_e (generic kernel, no Walsh blocks) and `compliance` receives
+// sum_e E_e v_e^T KE u_e.
 cudaError_t launch_sensitivity(int dim, const GridP& g, const uint8_t* mask, const double* ke,
                                const double* wht, const double* u, const double* E,
                                const double* rho, double penal, double E0, double Emin,
                                double* dc, double* compliance, double* partials,
-                               unsigned* counter, cudaStream_t s);
+                               unsigned* counter, cudaStream_t s, const double* v = nullptr);
 cudaError_t launch_oc_prep(long long nel, const double* rho, const double* dc,
                            const double* dv, double* a, double* scal, cudaStream_t s);
 cudaError_t launch_oc_step(long long nel, const double* rho, const double* a,
@@ -249,17 +286,25 @@ cudaError_t launch_oc_prep_b(long long nel, const double* rho, const double* dc,
 cudaError_t launch_oc_step_b(long long nel, const double* a, const double* lo, const double* hi,
                              const double* dv, double target, double* scal, double* partials,
                              unsigned* counter, cudaStream_t s);
-// lambda search of the OC update: the candidate factors a = rho sqrt(-dc/dv)
-// (float64 copy a64 for the final update) and the move limits and dv as
-// double-float pairs; one launch narrows [l1, l2] eight-fold in double-float
+// lambda search of the OC update: the candidate factors
+// a = rho max(0, -dc/dv)^eta (float64 copy a64 for the final update; eta
+// 1/2 for compliance) and the move limits and dv as double-float pairs; one
+// launch narrows [l1, l2] eight-fold in double-float; rho_new =
+// clamp(a lambda^-eta)
 cudaError_t launch_oc_prep_d(long long nel, const double* rho, const double* dc,
                              const double* dv, double move, double* a64, void* a2, void* lo2,
-                             void* hi2, void* dv2, double* scal, cudaStream_t s);
+                             void* hi2, void* dv2, double* scal, cudaStream_t s,
+                             double eta = 0.5);
 cudaError_t launch_oc_section(long long nel, const void* a2, const void* lo2, const void* hi2,
                               const void* dv2, double target, double* scal, double* partials,
-                              unsigned* counter, cudaStream_t s);
+                              unsigned* counter, cudaStream_t s, double eta = 0.5);
 cudaError_t launch_oc_final(long long nel, double* rho, const double* a, double move,
                             double* scal, double* change_dev, double* partials,
-                            unsigned* counter, cudaStream_t s);
+                            unsigned* counter, cudaStream_t s, double eta = 0.5);
+// Kc_E* += k w w^T for each spring: its fine DOF's interpolation weights w
+// over the corners of one coarse element E* holding it (the Galerkin product
+// P^T S P, element-wise; level 1 from the finest grid, stored matrices)
+cudaError_t launch_spring_galerkin(int dim, int t, const GridP& gc, const GridP& gf,
+                                   const Springs& sp, void* Kc, cudaStream_t s);
 
 }  // namespace topo

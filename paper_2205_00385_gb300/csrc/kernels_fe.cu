@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "mg_device.cuh"
 
 namespace topo {
 
@@ -19,7 +20,7 @@ __global__ void __launch_bounds__(128)
     k_apply(GridP g, const uint8_t* __restrict__ mask, KEP<TC, Geo<DIM>::ND> ke,
             const TC* __restrict__ coef, const TC* __restrict__ Kc,
             const TX* __restrict__ x, TY* __restrict__ y, const TX* __restrict__ b,
-            const TC* __restrict__ dinv, TC omega, TC dfix) {
+            const TC* __restrict__ dinv, TC omega, TC dfix, Springs sp) {
   constexpr int ND = Geo<DIM>::ND;
   constexpr int NPE = Geo<DIM>::NPE;
   constexpr int NB = Geo<DIM>::NB;
@@ -97,6 +98,9 @@ __global__ void __launch_bounds__(128)
   for (int ci = 0; ci < DIM; ++ci) {
     const long long d = DIM * node + ci;
     TE Ax = ((mself >> ci) & 1u) ? TE(dfix) * TE(x[d]) : TE(acc[ci]);
+    if (!((mself >> ci) & 1u))
+      for (int q = 0; q < sp.n; ++q)
+        if (sp.dof[q] == d) Ax += TE(sp.k[q]) * TE(x[d]);
     if (EPI == EPI_APPLY) {
       y[d] = TY(Ax);
     } else if (EPI == EPI_RESID) {
@@ -230,30 +234,8 @@ __device__ __forceinline__ void wht_element(const WhtBlocks<TC>& kb, const TC (&
 
 // ---------------------------------------------------------------------------
 // Coarse levels with stored Galerkin element matrices are applied from their
-// assembled form: per DOF row, the coefficients of the 3^DIM neighbouring
-// nodes' DIM components (81 in 3D).  Boundary conditions are folded in at
-// assembly (fixed columns are zero, a fixed row is the identity row), so the
-// apply is a plain stencil product:  y_r = sum_q S_r[q] x[col(r, q)].
-// Coefficient qq of neighbour plane pz couples row r = DIM n + c with
-// component qq % DIM of the neighbour n + (dx, dy, dz), qq / DIM =
-// (dx+1) + 3 (dy+1), pz = dz + 1.  Layout: each plane's 9 DIM coefficients
-// are padded to a multiple of W = 16 / sizeof(T) and stored in W-wide groups
-// group-major, S[((pz GP + qq / W) rows + r) W + qq % W], so that a row's
-// coefficients are GP 16-byte loads per plane and a warp's load of one group
-// is 512 contiguous bytes.
+// assembled stencil (StencilLayout in mg_device.cuh).
 // ---------------------------------------------------------------------------
-template <int DIM, typename T>
-struct StencilLayout {
-  static constexpr int NP = DIM == 3 ? 3 : 1;          // neighbour planes
-  static constexpr int NQP = 9 * DIM;                  // coefficients per plane
-  static constexpr int W = 16 / (int)sizeof(T);        // values per group
-  static constexpr int GP = (NQP + W - 1) / W;         // groups per plane
-  __host__ __device__ static long long index(long long rows, long long r, int pz, int qq) {
-    return ((long long)(pz * GP + qq / W) * rows + r) * W + qq % W;
-  }
-  __host__ __device__ static long long values(long long rows) { return rows * NP * GP * W; }
-};
-
 // one thread per (row, padded slot): the sum over the elements containing
 // node n and its neighbour of the packed element matrix entry
 // (DIM a_n + c, DIM a_m + c'), elements in a fixed order; padding slots are 0
@@ -302,69 +284,17 @@ __global__ void __launch_bounds__(256)
   S[SL::index(rows, r, pz, qq)] = s;
 }
 
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using V = float4;
-  __device__ static float get(const float4& v, int l) {
-    return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w;
-  }
-};
-template <>
-struct Vec16<double> {
-  using V = double2;
-  __device__ static double get(const double2& v, int l) { return l == 0 ? v.x : v.y; }
-};
-
 // y = S x with the epilogue (K x, b - K x, or the damped Jacobi sweep); one
-// thread per row; each plane's coefficient groups and neighbour values are
-// all loaded before its sums, which run in a fixed order.
+// thread per row (body in mg_device.cuh).
 template <int DIM, typename T, int EPI>
 __global__ void __launch_bounds__(256, 2)
     k_stencil_apply(GridP g, const T* __restrict__ S, const T* __restrict__ x, T* __restrict__ y,
                     const T* __restrict__ b, const T* __restrict__ dinv, T omega) {
-  using SL = StencilLayout<DIM, T>;
-  using VV = typename Vec16<T>::V;
   const long long rows = DIM * g.nn;
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   pdl_wait();
   if (r >= rows) return;
-  const long long n = r / DIM;
-  const int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny);
-  const int k = DIM == 3 ? (int)(n / ((long long)g.nnx * g.nny)) : 0;
-  // clamped neighbour indices (their coefficients are zero outside the grid)
-  int ix[3], jy[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    ix[d] = min(max(i + d - 1, 0), g.nnx - 1);
-    jy[d] = min(max(j + d - 1, 0), g.nny - 1);
-  }
-  const VV* Sv = reinterpret_cast<const VV*>(S);
-  T acc = T(0);
-#pragma unroll
-  for (int pz = 0; pz < SL::NP; ++pz) {
-    const int kz = DIM == 3 ? min(max(k + pz - 1, 0), g.nnz - 1) : 0;
-    VV sv[SL::GP];
-    T xv[SL::NQP];
-#pragma unroll
-    for (int q = 0; q < SL::GP; ++q) sv[q] = __ldg(Sv + (long long)(pz * SL::GP + q) * rows + r);
-#pragma unroll
-    for (int qq = 0; qq < SL::NQP; ++qq) {
-      const int o = qq / DIM, cp = qq % DIM;
-      const long long m = ix[o % 3] + (long long)g.nnx * (jy[o / 3] + (long long)g.nny * kz);
-      xv[qq] = x[DIM * m + cp];
-    }
-#pragma unroll
-    for (int qq = 0; qq < SL::NQP; ++qq)
-      acc = fma(Vec16<T>::get(sv[qq / SL::W], qq % SL::W), xv[qq], acc);
-  }
-  if (EPI == EPI_APPLY)
-    y[r] = acc;
-  else if (EPI == EPI_RESID)
-    y[r] = b[r] - acc;
-  else
-    y[r] = x[r] + omega * dinv[r] * (b[r] - acc);
+  stencil_row<DIM, T, EPI, false>(g, S, x, y, b, dinv, omega, r);
   pdl_launch_dependents();
 }
 
@@ -539,7 +469,8 @@ __global__ void __launch_bounds__(WX * WY, (OP == OPK_GAL1 && sizeof(TC) == 4) ?
 template <int DIM, typename TC, bool EXPL>
 __global__ void __launch_bounds__(256)
     k_diag(GridP g, const uint8_t* __restrict__ mask, KEP<TC, Geo<DIM>::ND> ke,
-           const TC* __restrict__ coef, const TC* __restrict__ Kc, TC* __restrict__ dinv) {
+           const TC* __restrict__ coef, const TC* __restrict__ Kc, TC* __restrict__ dinv,
+           Springs sp) {
   constexpr int ND = Geo<DIM>::ND;
   constexpr int NZ = DIM == 3 ? 2 : 1;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -570,6 +501,10 @@ __global__ void __launch_bounds__(256)
                        : coef[e] * ke.v[row * ND + row];
         }
       }
+  for (int q = 0; q < sp.n; ++q)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      if (sp.dof[q] == DIM * node + c) d[c] += TC(sp.k[q]);
   const unsigned m = mask[node];
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
@@ -593,7 +528,7 @@ static cudaError_t run_apply(const ApplyArgs& a, cudaStream_t s) {
   k_apply<DIM, TC, TX, TY, EPI, EXPL><<<nblocks(a.g.nn, th), th, 0, s>>>(
       a.g, a.mask, ke, static_cast<const TC*>(a.coef), static_cast<const TC*>(a.Kc),
       static_cast<const TX*>(a.x), static_cast<TY*>(a.y), static_cast<const TX*>(a.b),
-      static_cast<const TC*>(a.dinv), TC(a.omega), TC(a.dfix));
+      static_cast<const TC*>(a.dinv), TC(a.omega), TC(a.dfix), a.springs);
   return cudaGetLastError();
 }
 
@@ -741,30 +676,31 @@ void wht_blocks_pin_zeros(double* w64, float* w32) {
 
 template <int DIM, typename TC, bool EXPL>
 static cudaError_t run_diag(const GridP& g, const uint8_t* mask, const void* coef,
-                            const void* Kc, const void* kev, void* dinv, cudaStream_t s) {
+                            const void* Kc, const void* kev, void* dinv, cudaStream_t s,
+                            const Springs& sp) {
   constexpr int ND = Geo<DIM>::ND;
   KEP<TC, ND> ke;
   for (int q = 0; q < ND * ND; ++q) ke.v[q] = EXPL ? TC(0) : static_cast<const TC*>(kev)[q];
   k_diag<DIM, TC, EXPL><<<nblocks(g.nn, 256), 256, 0, s>>>(
       g, mask, ke, static_cast<const TC*>(coef), static_cast<const TC*>(Kc),
-      static_cast<TC*>(dinv));
+      static_cast<TC*>(dinv), sp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag(int dim, const GridP& g, const uint8_t* mask, int tc, bool expl,
                         const void* coef, const void* Kc, const void* ke, void* dinv,
-                        cudaStream_t s) {
+                        cudaStream_t s, const Springs& sp) {
   if (g.nn <= 0) return cudaSuccess;
   if (dim == 2) {
-    if (tc == T_F64) return expl ? run_diag<2, double, true>(g, mask, coef, Kc, ke, dinv, s)
-                                 : run_diag<2, double, false>(g, mask, coef, Kc, ke, dinv, s);
-    return expl ? run_diag<2, float, true>(g, mask, coef, Kc, ke, dinv, s)
-                : run_diag<2, float, false>(g, mask, coef, Kc, ke, dinv, s);
+    if (tc == T_F64) return expl ? run_diag<2, double, true>(g, mask, coef, Kc, ke, dinv, s, sp)
+                                 : run_diag<2, double, false>(g, mask, coef, Kc, ke, dinv, s, sp);
+    return expl ? run_diag<2, float, true>(g, mask, coef, Kc, ke, dinv, s, sp)
+                : run_diag<2, float, false>(g, mask, coef, Kc, ke, dinv, s, sp);
   }
-  if (tc == T_F64) return expl ? run_diag<3, double, true>(g, mask, coef, Kc, ke, dinv, s)
-                               : run_diag<3, double, false>(g, mask, coef, Kc, ke, dinv, s);
-  return expl ? run_diag<3, float, true>(g, mask, coef, Kc, ke, dinv, s)
-              : run_diag<3, float, false>(g, mask, coef, Kc, ke, dinv, s);
+  if (tc == T_F64) return expl ? run_diag<3, double, true>(g, mask, coef, Kc, ke, dinv, s, sp)
+                               : run_diag<3, double, false>(g, mask, coef, Kc, ke, dinv, s, sp);
+  return expl ? run_diag<3, float, true>(g, mask, coef, Kc, ke, dinv, s, sp)
+              : run_diag<3, float, false>(g, mask, coef, Kc, ke, dinv, s, sp);
 }
 
 }  // namespace topo

@@ -12,6 +12,7 @@
 
 #include "dfmath.cuh"
 #include "kernels.h"
+#include "mg_device.cuh"
 
 namespace topo {
 
@@ -31,14 +32,9 @@ __host__ __device__ __forceinline__ double wchild(int c, int a, int A) {
 }
 
 // ---------------------------------------------------------------------------
-// Restriction b_c = Pm^T r_f (Pm = M_f P M_c): coarse node (I,J,K) gathers
-// the fine nodes around (2I,2J,2K) with weights prod(1 - |d|/2).  Threads
+// Restriction and interpolation kernels (bodies in mg_device.cuh).  Threads
 // are laid out on the node grid (x lanes along I, block rows along J,
-// blockIdx.z = K), so no index division is needed.  Every fine load is
-// issued before any is used: indices are clamped into the grid and the
-// out-of-range and fixed terms are dropped by selects after the loads, so
-// the 3^DIM masks and values take one memory round trip; the terms are then
-// summed in a fixed order.
+// blockIdx.z = K), so no index division is needed.
 // ---------------------------------------------------------------------------
 constexpr int TBX = 32, TBY = 4;
 
@@ -52,127 +48,25 @@ __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
                const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc,
                const T* __restrict__ dinvc, T omega, T* __restrict__ zc) {
-  constexpr int NZ = DIM == 3 ? 3 : 1;
   const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
   const int K = DIM == 3 ? (int)blockIdx.z : 0;
   pdl_wait();
   if (I >= gc.nnx || J >= gc.nny) return;
-  unsigned m[NZ][3][3];
-  T v[NZ][3][3][DIM];
-#pragma unroll
-  for (int a = 0; a < NZ; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int i = min(max(2 * I + q - 1, 0), gf.nnx - 1);
-        const int j = min(max(2 * J + b - 1, 0), gf.nny - 1);
-        const int k = DIM == 3 ? min(max(2 * K + a - 1, 0), gf.nnz - 1) : 0;
-        const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
-        m[a][b][q] = maskf[fn];
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) v[a][b][q][c] = rf[DIM * fn + c];
-      }
-  T acc[DIM];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-#pragma unroll
-  for (int a = 0; a < NZ; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int dx = q - 1, dy = b - 1, dz = DIM == 3 ? a - 1 : 0;
-        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-        bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
-        if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
-        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
-        const unsigned mm = in ? m[a][b][q] : 7u;
-#pragma unroll
-        for (int c = 0; c < DIM; ++c)
-          acc[c] += ((mm >> c) & 1u) ? T(0) : w * v[a][b][q][c];
-      }
-  const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
-  const unsigned mc = maskc[node];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    const long long d = DIM * node + c;
-    const T bv = ((mc >> c) & 1u) ? T(0) : acc[c];
-    bc[d] = bv;
-    // the coarse level's pre-smoothing from a zero guess, z = omega D^-1 b
-    if (zc) zc[d] = omega * dinvc[d] * bv;
-  }
+  restrict_node<DIM, T, false>(gf, maskf, gc, maskc, rf, bc, dinvc, omega, zc, I, J, K);
   pdl_launch_dependents();
 }
 
-// z_f += Pm z_c: fine node (i,j,k) interpolates from coarse nodes
-// floor(i/2) .. ceil(i/2) per axis.  Threads on the fine (i, j) grid, each
-// taking the fine nodes k = 2q and 2q+1 (3D), which share the coarse plane
-// q: the coarse values of planes q and q+1 and the fine values are all
-// loaded (clamped into the grid) before any sum, and each fine node then
-// sums its own terms in a fixed order.
+// z_f += Pm z_c: threads on the fine (i, j) grid, each taking the fine nodes
+// k = 2q and 2q+1 (3D), which share the coarse plane q.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     k_prolong_add(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
                   const T* __restrict__ zc, T* __restrict__ zf) {
-  constexpr int NK = DIM == 3 ? 2 : 1;   // fine nodes per thread along z
   const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
   const int q = DIM == 3 ? (int)blockIdx.z : 0;
   pdl_wait();
   if (i >= gf.nnx || j >= gf.nny) return;
-  const int i0 = i >> 1, j0 = j >> 1;
-  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
-  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
-  // coarse values: plane q (+ q+1 for the odd fine node), 2 x 2 around (i0, j0)
-  T cv[NK][2][2][DIM];
-#pragma unroll
-  for (int a = 0; a < NK; ++a)
-#pragma unroll
-    for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int ic = min(i0 + cc, gc.nnx - 1), jc = min(j0 + bb, gc.nny - 1);
-        const int kc = DIM == 3 ? min(q + a, gc.nnz - 1) : 0;
-        const long long cn = ic + (long long)gc.nnx * (jc + (long long)gc.nny * kc);
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) cv[a][bb][cc][c] = zc[DIM * cn + c];
-      }
-  unsigned m[NK];
-  T zv[NK][DIM];
-#pragma unroll
-  for (int s = 0; s < NK; ++s) {
-    const int k = DIM == 3 ? min(2 * q + s, gf.nnz - 1) : 0;
-    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
-    m[s] = maskf[node];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) zv[s][c] = zf[DIM * node + c];
-  }
-#pragma unroll
-  for (int s = 0; s < NK; ++s) {
-    const int k = DIM == 3 ? 2 * q + s : 0;
-    if (DIM == 3 && k >= gf.nnz) break;
-    const int nk = (DIM == 3 && (k & 1)) ? 2 : 1;
-    const T w = wx * wy * ((DIM == 3 && (k & 1)) ? T(0.5) : T(1));
-    T acc[DIM];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          if (a >= NK) continue;
-          // fine node k = 2q + s reads coarse plane (k >> 1) + a = q + a
-          const bool use = a < nk && bb < nj && cc < ni;
-#pragma unroll
-          for (int c = 0; c < DIM; ++c) acc[c] += use ? w * cv[a][bb][cc][c] : T(0);
-        }
-    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c)
-      if (!((m[s] >> c) & 1u)) zf[DIM * node + c] = zv[s][c] + acc[c];
-  }
+  prolong_pair<DIM, T, false>(gf, maskf, gc, zc, zf, i, j, q);
   pdl_launch_dependents();
 }
 
@@ -679,6 +573,53 @@ static cudaError_t gal_fine_t(const GridP& gc, const GridP& gf, const void* coef
   const long long tot = gc.nel * tri_len(ND);
   k_galerkin_fine<DIM, T><<<nblocks(tot, 256), 256, 0, s>>>(gc, gf, (const T*)coef,
                                                             (const T*)Qc, (T*)Kc);
+  return cudaGetLastError();
+}
+
+// Springs in the level-1 Galerkin matrices: the spring at fine DOF (node n,
+// component c) adds k w_A w_B to entry (DIM A + c, DIM B + c) of one coarse
+// element holding n, w the 1D linear weights of n at that element's corners
+// (P^T S P; any element holding n gives the same assembled operator, since
+// n interpolates only from the corners of each element holding it).  One
+// thread per spring, springs applied in order.
+template <int DIM, typename T>
+__global__ void k_spring_galerkin(GridP gc, GridP gf, Springs sp, T* __restrict__ Kc) {
+  constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE, NT = tri_len(ND);
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int q = 0; q < sp.n; ++q) {
+    const long long node = sp.dof[q] / DIM;
+    const int c = (int)(sp.dof[q] % DIM);
+    const int i = (int)(node % gf.nnx);
+    const long long rest = node / gf.nnx;
+    const int j = (int)(rest % gf.nny);
+    const int k = DIM == 3 ? (int)(rest / gf.nny) : 0;
+    const int EX = min(i / 2, gc.nx - 1), EY = min(j / 2, gc.ny - 1);
+    const int EZ = DIM == 3 ? min(k / 2, gc.nz - 1) : 0;
+    const long long E = EX + (long long)gc.nx * (EY + (long long)gc.ny * EZ);
+    double w[NPE];
+    for (int a = 0; a < NPE; ++a) {
+      const double px = 0.5 * (i - 2 * EX), py = 0.5 * (j - 2 * EY), pz = 0.5 * (k - 2 * EZ);
+      w[a] = ((a & 1) ? px : 1.0 - px) * (((a >> 1) & 1) ? py : 1.0 - py) *
+             (DIM == 3 ? (((a >> 2) & 1) ? pz : 1.0 - pz) : 1.0);
+    }
+    for (int a = 0; a < NPE; ++a)
+      for (int b = a; b < NPE; ++b) {
+        const double v = sp.k[q] * w[a] * w[b];
+        if (v != 0.0) Kc[(size_t)E * NT + tri_idx(DIM * a + c, DIM * b + c, ND)] += T(v);
+      }
+  }
+}
+
+cudaError_t launch_spring_galerkin(int dim, int t, const GridP& gc, const GridP& gf,
+                                   const Springs& sp, void* Kc, cudaStream_t s) {
+  if (sp.n <= 0) return cudaSuccess;
+  if (dim == 2) {
+    if (t == T_F64) k_spring_galerkin<2, double><<<1, 32, 0, s>>>(gc, gf, sp, (double*)Kc);
+    else k_spring_galerkin<2, float><<<1, 32, 0, s>>>(gc, gf, sp, (float*)Kc);
+  } else {
+    if (t == T_F64) k_spring_galerkin<3, double><<<1, 32, 0, s>>>(gc, gf, sp, (double*)Kc);
+    else k_spring_galerkin<3, float><<<1, 32, 0, s>>>(gc, gf, sp, (float*)Kc);
+  }
   return cudaGetLastError();
 }
 

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(RED_THREADS)
                   const double* __restrict__ u, const double* __restrict__ E,
                   const double* __restrict__ rho, double penal, double E0, double Emin,
                   double* __restrict__ dc, double* compliance, double* partials,
-                  unsigned* counter) {
+                  unsigned* counter, const double* __restrict__ adj) {
   constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE;
   __shared__ double sh[32];
   double v[1] = {0.0};
@@ -218,14 +218,19 @@ __global__ void __launch_bounds__(RED_THREADS)
     const long long rest = e / g.nx;
     const int ey = (int)(rest % g.ny);
     const int ez = DIM == 3 ? (int)(rest / g.ny) : 0;
-    double ue[ND];
+    // ue: the field; ve: the adjoint field (the field itself for compliance)
+    double ue[ND], ve[ND];
 #pragma unroll
     for (int a = 0; a < NPE; ++a) {
       const int i = ex + (a & 1), j = ey + ((a >> 1) & 1), k = ez + ((a >> 2) & 1);
       const long long nd = i + (long long)g.nnx * (j + (long long)g.nny * (DIM == 3 ? k : 0));
       const unsigned m = mask[nd];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) ue[DIM * a + c] = ((m >> c) & 1u) ? 0.0 : u[DIM * nd + c];
+      for (int c = 0; c < DIM; ++c) {
+        const bool fx = (m >> c) & 1u;
+        ue[DIM * a + c] = fx ? 0.0 : u[DIM * nd + c];
+        ve[DIM * a + c] = fx ? 0.0 : (adj ? adj[DIM * nd + c] : u[DIM * nd + c]);
+      }
     }
     double ce = 0.0;
 #pragma unroll
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(RED_THREADS)
       double s = 0.0;
 #pragma unroll
       for (int c = 0; c < ND; ++c) s = fma(ke.v[r * ND + c], ue[c], s);
-      ce = fma(ue[r], s, ce);
+      ce = fma(ve[r], s, ce);
     }
     const double re = rho[e];
     dc[e] = -penal * (E0 - Emin) * ipow(re, penal - 1.0) * ce;
@@ -349,11 +354,20 @@ __global__ void __launch_bounds__(RED_THREADS)
 // step.  It stops at the same relative bracket of 1e-13.
 constexpr int OC_SPLIT = 8;
 
+// x^eta of the OC rule (sqrt for the compliance rule's eta = 1/2) and the
+// multiplier's factor lambda^-eta
+__device__ __forceinline__ double oc_damp(double x, double eta) {
+  return eta == 0.5 ? sqrt(x) : pow(x, eta);
+}
+__device__ __forceinline__ double oc_lam_factor(double lam, double eta) {
+  return eta == 0.5 ? 1.0 / sqrt(lam) : pow(lam, -eta);
+}
+
 __global__ void __launch_bounds__(256)
     k_oc_prep_d(long long nel, const double* __restrict__ rho, const double* __restrict__ dc,
                 const double* __restrict__ dv, double move, double* __restrict__ a64,
                 float2* __restrict__ a, float2* __restrict__ lo, float2* __restrict__ hi,
-                float2* __restrict__ dvd, double* scal) {
+                float2* __restrict__ dvd, double* scal, double eta) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e == 0) {
     scal[S_OC_L1] = 0.0;
@@ -361,7 +375,7 @@ __global__ void __launch_bounds__(256)
   }
   if (e >= nel) return;
   const double r = rho[e];
-  const double ae = r * sqrt(fmax(0.0, -dc[e] / dv[e]));
+  const double ae = r * oc_damp(fmax(0.0, -dc[e] / dv[e]), eta);
   a64[e] = ae;
   const dfl av = split_d(ae);
   const dfl lv = split_d(fmax(0.0, r - move)), hv = split_d(fmin(1.0, r + move));
@@ -385,7 +399,7 @@ __device__ __forceinline__ double oc_point(double l1, double l2, int j) {
 __global__ void __launch_bounds__(RED_THREADS)
     k_oc_section(long long nel, const float2* __restrict__ a, const float2* __restrict__ lo,
                  const float2* __restrict__ hi, const float2* __restrict__ dvd, double target,
-                 double* scal, double* partials, unsigned* counter) {
+                 double* scal, double* partials, unsigned* counter, double eta) {
   constexpr int NP = OC_SPLIT - 1;
   __shared__ double sh[NP * 32];
   __shared__ dfl s_s[NP];
@@ -393,7 +407,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (!((l2 - l1) > 1e-13 * (l1 + l2))) return;
   if (threadIdx.x < NP) {
     const double lam = oc_point(l1, l2, threadIdx.x + 1);
-    s_s[threadIdx.x] = split_d(1.0 / sqrt(lam));
+    s_s[threadIdx.x] = split_d(oc_lam_factor(lam, eta));
   }
   __syncthreads();
   dfl sv[NP], v[NP];
@@ -437,10 +451,10 @@ __global__ void __launch_bounds__(RED_THREADS)
 __global__ void __launch_bounds__(RED_THREADS)
     k_oc_final(long long nel, double* __restrict__ rho, const double* __restrict__ a,
                double move, double* scal, double* change_dev, double* partials,
-               unsigned* counter) {
+               unsigned* counter, double eta) {
   __shared__ double sh[32];
   const double lam = 0.5 * (scal[S_OC_L1] + scal[S_OC_L2]);
-  const double s = 1.0 / sqrt(lam);
+  const double s = oc_lam_factor(lam, eta);
   double v[1] = {0.0};
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nel;
        e += (long long)gridDim.x * blockDim.x) {
@@ -515,12 +529,12 @@ template <int DIM>
 static cudaError_t sens_t(const GridP& g, const uint8_t* mask, const double* kev, const double* u,
                           const double* E, const double* rho, double penal, double E0,
                           double Emin, double* dc, double* compliance, double* partials,
-                          unsigned* counter, cudaStream_t s) {
+                          unsigned* counter, cudaStream_t s, const double* v) {
   constexpr int ND = Geo<DIM>::ND;
   KEP<double, ND> ke;
   for (int q = 0; q < ND * ND; ++q) ke.v[q] = kev[q];
   k_sensitivity<DIM><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, mask, ke, u, E, rho, penal, E0, Emin,
-                                                        dc, compliance, partials, counter);
+                                                        dc, compliance, partials, counter, v);
   return cudaGetLastError();
 }
 
@@ -528,17 +542,19 @@ cudaError_t launch_sensitivity(int dim, const GridP& g, const uint8_t* mask, con
                                const double* wht, const double* u, const double* E,
                                const double* rho, double penal, double E0, double Emin,
                                double* dc, double* compliance, double* partials,
-                               unsigned* counter, cudaStream_t s) {
+                               unsigned* counter, cudaStream_t s, const double* v) {
   if (dim == 2)
-    return sens_t<2>(g, mask, ke, u, E, rho, penal, E0, Emin, dc, compliance, partials, counter, s);
-  if (wht) {
+    return sens_t<2>(g, mask, ke, u, E, rho, penal, E0, Emin, dc, compliance, partials, counter, s,
+                     v);
+  if (wht && !v) {
     WhtBlocks<double> kb;
     for (int q = 0; q < 72; ++q) (&kb.b[0][0][0])[q] = wht[q];
     k_sensitivity3_wht<<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, mask, kb, u, E, rho, penal, E0, Emin,
                                                           dc, compliance, partials, counter);
     return cudaGetLastError();
   }
-  return sens_t<3>(g, mask, ke, u, E, rho, penal, E0, Emin, dc, compliance, partials, counter, s);
+  return sens_t<3>(g, mask, ke, u, E, rho, penal, E0, Emin, dc, compliance, partials, counter, s,
+                   v);
 }
 
 cudaError_t launch_oc_prep(long long nel, const double* rho, const double* dc,
@@ -572,26 +588,27 @@ cudaError_t launch_oc_step_b(long long nel, const double* a, const double* lo, c
 
 cudaError_t launch_oc_prep_d(long long nel, const double* rho, const double* dc,
                              const double* dv, double move, double* a64, void* a2, void* lo2,
-                             void* hi2, void* dv2, double* scal, cudaStream_t s) {
+                             void* hi2, void* dv2, double* scal, cudaStream_t s, double eta) {
   k_oc_prep_d<<<nblocks(nel, 256), 256, 0, s>>>(nel, rho, dc, dv, move, a64, (float2*)a2,
-                                                (float2*)lo2, (float2*)hi2, (float2*)dv2, scal);
+                                                (float2*)lo2, (float2*)hi2, (float2*)dv2, scal,
+                                                eta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_oc_section(long long nel, const void* a2, const void* lo2, const void* hi2,
                               const void* dv2, double target, double* scal, double* partials,
-                              unsigned* counter, cudaStream_t s) {
+                              unsigned* counter, cudaStream_t s, double eta) {
   k_oc_section<<<RED_BLOCKS, RED_THREADS, 0, s>>>(nel, (const float2*)a2, (const float2*)lo2,
                                                   (const float2*)hi2, (const float2*)dv2, target,
-                                                  scal, partials, counter);
+                                                  scal, partials, counter, eta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_oc_final(long long nel, double* rho, const double* a, double move,
                             double* scal, double* change_dev, double* partials,
-                            unsigned* counter, cudaStream_t s) {
+                            unsigned* counter, cudaStream_t s, double eta) {
   k_oc_final<<<RED_BLOCKS, RED_THREADS, 0, s>>>(nel, rho, a, move, scal, change_dev, partials,
-                                                counter);
+                                                counter, eta);
   return cudaGetLastError();
 }
 

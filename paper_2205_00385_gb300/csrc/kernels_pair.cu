@@ -337,10 +337,12 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
   cp_wait<0>();
 }
 
-// resident blocks per SM the register allocation targets: K p fits four
-// without spilling; the residual and smoother epilogues keep three
-template <int EPI>
-__global__ void __launch_bounds__(PX * PY, EPI == EPI_APPLY ? 4 : 3)
+// resident blocks per SM the register allocation targets (MINB): variant 0
+// without spilling (four for K p, three for the residual and smoother
+// epilogues), variant 1 one block more with a few spilled registers; the
+// autotuner times both
+template <int EPI, int MINB>
+__global__ void __launch_bounds__(PX * PY, MINB)
     k_apply3_pair(PairArgs a, WhtPair kb) {
   __shared__ PairSmem sm;
   const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
@@ -382,32 +384,49 @@ cudaError_t launch_colfix(const GridP& g, const uint8_t* mask, uint8_t* colfix, 
   return cudaGetLastError();
 }
 
-// resident blocks of the pair kernel on the current device (cached per device)
-static long long pair_slots(int epi) {
-  static long long cache[3][64] = {};
+template <int EPI>
+constexpr int pair_minb(int variant) {
+  return (EPI == EPI_APPLY ? 4 : 3) + (variant ? 1 : 0);
+}
+
+template <int EPI, int V>
+static auto pair_kernel() {
+  return k_apply3_pair<EPI, pair_minb<EPI>(V)>;
+}
+
+// resident blocks of the pair kernel on the current device (cached per
+// device, epilogue and variant)
+static long long pair_slots(int epi, int variant) {
+  static long long cache[3][2][64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   const int e = epi == EPI_APPLY ? 0 : epi == EPI_RESID ? 1 : 2;
-  if (cache[e][dev] > 0) return cache[e][dev];
+  const int v = variant ? 1 : 0;
+  if (cache[e][v][dev] > 0) return cache[e][v][dev];
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t err;
   if (e == 0)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply3_pair<EPI_APPLY>, PX * PY, 0);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, v ? pair_kernel<EPI_APPLY, 1>() : pair_kernel<EPI_APPLY, 0>(), PX * PY, 0);
   else if (e == 1)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply3_pair<EPI_RESID>, PX * PY, 0);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, v ? pair_kernel<EPI_RESID, 1>() : pair_kernel<EPI_RESID, 0>(), PX * PY, 0);
   else
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply3_pair<EPI_SMOOTH>, PX * PY, 0);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, v ? pair_kernel<EPI_SMOOTH, 1>() : pair_kernel<EPI_SMOOTH, 0>(), PX * PY, 0);
   if (err != cudaSuccess || sms <= 0 || per_sm <= 0) return 2 * 152;
-  cache[e][dev] = (long long)sms * per_sm;
-  return cache[e][dev];
+  cache[e][v][dev] = (long long)sms * per_sm;
+  return cache[e][v][dev];
 }
 
 void pair_prepare() {
   // occupancy queries happen here, outside any stream capture
-  pair_slots(EPI_APPLY);
-  pair_slots(EPI_RESID);
-  pair_slots(EPI_SMOOTH);
+  for (int v = 0; v < 2; ++v) {
+    pair_slots(EPI_APPLY, v);
+    pair_slots(EPI_RESID, v);
+    pair_slots(EPI_SMOOTH, v);
+  }
 }
 
 bool pair_apply_ok(const ApplyArgs& a) {
@@ -439,7 +458,8 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   // z-chunks: each chunk streams its layers and recomputes one element layer
   // below it; the count is chosen to minimise waves x layers per chunk for
   // the resident-block capacity of the device
-  const long long slots = pair_slots(a.epi);
+  const int var = a.variant ? 1 : 0;
+  const long long slots = pair_slots(a.epi, var);
   const long long nxy = (long long)gx * gy;
   int best = 1;
   long long best_cost = -1;
@@ -458,9 +478,15 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   best = (a.g.nnz + p.zc - 1) / p.zc;
   dim3 grid(gx, gy, best);
   switch (a.epi) {
-    case EPI_APPLY: return launch_pdl(k_apply3_pair<EPI_APPLY>, grid, dim3(PX * PY), 0, s, p, kb);
-    case EPI_RESID: return launch_pdl(k_apply3_pair<EPI_RESID>, grid, dim3(PX * PY), 0, s, p, kb);
-    default: return launch_pdl(k_apply3_pair<EPI_SMOOTH>, grid, dim3(PX * PY), 0, s, p, kb);
+    case EPI_APPLY:
+      return var ? launch_pdl(pair_kernel<EPI_APPLY, 1>(), grid, dim3(PX * PY), 0, s, p, kb)
+                 : launch_pdl(pair_kernel<EPI_APPLY, 0>(), grid, dim3(PX * PY), 0, s, p, kb);
+    case EPI_RESID:
+      return var ? launch_pdl(pair_kernel<EPI_RESID, 1>(), grid, dim3(PX * PY), 0, s, p, kb)
+                 : launch_pdl(pair_kernel<EPI_RESID, 0>(), grid, dim3(PX * PY), 0, s, p, kb);
+    default:
+      return var ? launch_pdl(pair_kernel<EPI_SMOOTH, 1>(), grid, dim3(PX * PY), 0, s, p, kb)
+                 : launch_pdl(pair_kernel<EPI_SMOOTH, 0>(), grid, dim3(PX * PY), 0, s, p, kb);
   }
   return cudaGetLastError();
 }

@@ -1,0 +1,241 @@
+// Per-item bodies of the multigrid transfer and stored-level stencil kernels
+// (Algorithm 2: restriction P^T, interpolation P, the level operator with
+// its residual / damped-Jacobi epilogues).  The one-kernel-per-step path
+// (kernels_mg.cu, kernels_fe.cu) and the fused coarse V-cycle
+// (kernels_vfuse.cu) both call these, so the two compute the same values
+// bit for bit.
+//
+// CG selects how vectors that the calling kernel may itself have written are
+// loaded: false, a plain load (one kernel per step: the data come from
+// earlier kernels); true, ld.global.cg (cached in L2 only), for the fused
+// kernel whose CTAs exchange those vectors between phases of one launch.
+#pragma once
+
+#include "kernels.h"
+
+namespace topo {
+
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// ---------------------------------------------------------------------------
+// Assembled stencil of a stored level: per DOF row, the coefficients of the
+// 3^DIM neighbouring nodes' DIM components (81 in 3D).  Boundary conditions
+// are folded in at assembly (fixed columns are zero, a fixed row is the
+// identity row), so the apply is a plain stencil product
+//   y_r = sum_q S_r[q] x[col(r, q)].
+// Coefficient qq of neighbour plane pz couples row r = DIM n + c with
+// component qq % DIM of the neighbour n + (dx, dy, dz), qq / DIM =
+// (dx+1) + 3 (dy+1), pz = dz + 1.  Layout: each plane's 9 DIM coefficients
+// are padded to a multiple of W = 16 / sizeof(T) and stored in W-wide groups
+// group-major, S[((pz GP + qq / W) rows + r) W + qq % W], so that a row's
+// coefficients are GP 16-byte loads per plane and a warp's load of one group
+// is 512 contiguous bytes.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+struct StencilLayout {
+  static constexpr int NP = DIM == 3 ? 3 : 1;          // neighbour planes
+  static constexpr int NQP = 9 * DIM;                  // coefficients per plane
+  static constexpr int W = 16 / (int)sizeof(T);        // values per group
+  static constexpr int GP = (NQP + W - 1) / W;         // groups per plane
+  __host__ __device__ static long long index(long long rows, long long r, int pz, int qq) {
+    return ((long long)(pz * GP + qq / W) * rows + r) * W + qq % W;
+  }
+  __host__ __device__ static long long values(long long rows) { return rows * NP * GP * W; }
+};
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  __device__ static float get(const float4& v, int l) {
+    return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w;
+  }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  __device__ static double get(const double2& v, int l) { return l == 0 ? v.x : v.y; }
+};
+
+// Row r of y = S x with the epilogue (K x, b - K x, or the damped Jacobi
+// sweep); each plane's coefficient groups and neighbour values are all
+// loaded before its sums, which run in a fixed order.
+template <int DIM, typename T, int EPI, bool CG>
+__device__ __forceinline__ void stencil_row(const GridP& g, const T* __restrict__ S,
+                                            const T* __restrict__ x, T* __restrict__ y,
+                                            const T* __restrict__ b, const T* __restrict__ dinv,
+                                            T omega, long long r) {
+  using SL = StencilLayout<DIM, T>;
+  using VV = typename Vec16<T>::V;
+  const long long rows = DIM * g.nn;
+  const long long n = r / DIM;
+  const int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny);
+  const int k = DIM == 3 ? (int)(n / ((long long)g.nnx * g.nny)) : 0;
+  // clamped neighbour indices (their coefficients are zero outside the grid)
+  int ix[3], jy[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ix[d] = min(max(i + d - 1, 0), g.nnx - 1);
+    jy[d] = min(max(j + d - 1, 0), g.nny - 1);
+  }
+  const VV* Sv = reinterpret_cast<const VV*>(S);
+  T acc = T(0);
+#pragma unroll
+  for (int pz = 0; pz < SL::NP; ++pz) {
+    const int kz = DIM == 3 ? min(max(k + pz - 1, 0), g.nnz - 1) : 0;
+    VV sv[SL::GP];
+    T xv[SL::NQP];
+#pragma unroll
+    for (int q = 0; q < SL::GP; ++q) sv[q] = __ldg(Sv + (long long)(pz * SL::GP + q) * rows + r);
+#pragma unroll
+    for (int qq = 0; qq < SL::NQP; ++qq) {
+      const int o = qq / DIM, cp = qq % DIM;
+      const long long m = ix[o % 3] + (long long)g.nnx * (jy[o / 3] + (long long)g.nny * kz);
+      xv[qq] = ldv<CG>(x + DIM * m + cp);
+    }
+#pragma unroll
+    for (int qq = 0; qq < SL::NQP; ++qq)
+      acc = fma(Vec16<T>::get(sv[qq / SL::W], qq % SL::W), xv[qq], acc);
+  }
+  if (EPI == EPI_APPLY)
+    y[r] = acc;
+  else if (EPI == EPI_RESID)
+    y[r] = ldv<CG>(b + r) - acc;
+  else
+    y[r] = ldv<CG>(x + r) + omega * __ldg(dinv + r) * (ldv<CG>(b + r) - acc);
+}
+
+// ---------------------------------------------------------------------------
+// Restriction b_c = Pm^T r_f (Pm = M_f P M_c) at coarse node (I, J, K): it
+// gathers the fine nodes around (2I, 2J, 2K) with weights prod(1 - |d|/2).
+// Every fine load is issued before any is used: indices are clamped into the
+// grid and the out-of-range and fixed terms are dropped by selects after the
+// loads, so the 3^DIM masks and values take one memory round trip; the terms
+// are then summed in a fixed order.  With zc set, the coarse level is also
+// pre-smoothed from a zero guess, z = omega D^-1 b.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T, bool CG>
+__device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __restrict__ maskf,
+                                              const GridP& gc, const uint8_t* __restrict__ maskc,
+                                              const T* __restrict__ rf, T* __restrict__ bc,
+                                              const T* __restrict__ dinvc, T omega,
+                                              T* __restrict__ zc, int I, int J, int K) {
+  constexpr int NZ = DIM == 3 ? 3 : 1;
+  unsigned m[NZ][3][3];
+  T v[NZ][3][3][DIM];
+#pragma unroll
+  for (int a = 0; a < NZ; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int i = min(max(2 * I + q - 1, 0), gf.nnx - 1);
+        const int j = min(max(2 * J + b - 1, 0), gf.nny - 1);
+        const int k = DIM == 3 ? min(max(2 * K + a - 1, 0), gf.nnz - 1) : 0;
+        const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+        m[a][b][q] = maskf[fn];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) v[a][b][q][c] = ldv<CG>(rf + DIM * fn + c);
+      }
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int a = 0; a < NZ; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int dx = q - 1, dy = b - 1, dz = DIM == 3 ? a - 1 : 0;
+        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+        bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
+        if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
+        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+        const unsigned mm = in ? m[a][b][q] : 7u;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+          acc[c] += ((mm >> c) & 1u) ? T(0) : w * v[a][b][q][c];
+      }
+  const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
+  const unsigned mc = maskc[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long d = DIM * node + c;
+    const T bv = ((mc >> c) & 1u) ? T(0) : acc[c];
+    bc[d] = bv;
+    if (zc) zc[d] = omega * dinvc[d] * bv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z_f += Pm z_c for the fine nodes (i, j, 2q) and (i, j, 2q + 1) (3D; one
+// node in 2D): each interpolates from coarse nodes floor(./2) .. ceil(./2)
+// per axis.  The coarse values of planes q and q + 1 and the fine values are
+// all loaded (clamped into the grid) before any sum, and each fine node then
+// sums its own terms in a fixed order.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T, bool CG>
+__device__ __forceinline__ void prolong_pair(const GridP& gf, const uint8_t* __restrict__ maskf,
+                                             const GridP& gc, const T* __restrict__ zc,
+                                             T* __restrict__ zf, int i, int j, int q) {
+  constexpr int NK = DIM == 3 ? 2 : 1;   // fine nodes per item along z
+  const int i0 = i >> 1, j0 = j >> 1;
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
+  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
+  T cv[NK][2][2][DIM];
+#pragma unroll
+  for (int a = 0; a < NK; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const int ic = min(i0 + cc, gc.nnx - 1), jc = min(j0 + bb, gc.nny - 1);
+        const int kc = DIM == 3 ? min(q + a, gc.nnz - 1) : 0;
+        const long long cn = ic + (long long)gc.nnx * (jc + (long long)gc.nny * kc);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) cv[a][bb][cc][c] = ldv<CG>(zc + DIM * cn + c);
+      }
+  unsigned m[NK];
+  T zv[NK][DIM];
+#pragma unroll
+  for (int s = 0; s < NK; ++s) {
+    const int k = DIM == 3 ? min(2 * q + s, gf.nnz - 1) : 0;
+    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+    m[s] = maskf[node];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) zv[s][c] = ldv<CG>(zf + DIM * node + c);
+  }
+#pragma unroll
+  for (int s = 0; s < NK; ++s) {
+    const int k = DIM == 3 ? 2 * q + s : 0;
+    if (DIM == 3 && k >= gf.nnz) break;
+    const int nk = (DIM == 3 && (k & 1)) ? 2 : 1;
+    const T w = wx * wy * ((DIM == 3 && (k & 1)) ? T(0.5) : T(1));
+    T acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          if (a >= NK) continue;
+          // fine node k = 2q + s reads coarse plane (k >> 1) + a = q + a
+          const bool use = a < nk && bb < nj && cc < ni;
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) acc[c] += use ? w * cv[a][bb][cc][c] : T(0);
+        }
+    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      if (!((m[s] >> c) & 1u)) zf[DIM * node + c] = zv[s][c] + acc[c];
+  }
+}
+
+}  // namespace topo

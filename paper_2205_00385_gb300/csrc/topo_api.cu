@@ -4,6 +4,7 @@
 // bookkeeping (level geometry, PARM ring position, iteration counts); every
 // arithmetic step of the solver path runs in the library's kernels.  Device
 // memory comes exclusively from the caller's workspace.
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -435,6 +436,8 @@ const char* to_last_error(const to_ctx* ctx) {
   return ctx ? ctx->last_error.c_str() : g_last_error.c_str();
 }
 
+static int mg_t(const to_ctx* c) { return c->mixed ? T_F32 : T_F64; }
+
 to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, const double* f,
                        void* workspace, int64_t ws_bytes, void* stream, to_ctx** out) {
   std::string why;
@@ -468,9 +471,13 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->vcycle_bytes = 0.0;
   c->coarse_t = c->mixed ? T_F32 : T_F64;
   c->coarse_shift = 0.0;
-  for (int q = 0; q < 8; ++q) c->tuned_zc[q] = 0;
+  for (int q = 0; q < 8; ++q) c->tuned_zc[q] = c->tuned_var[q] = 0;
   c->carm_flags = 0;
   c->use_tc = false;
+  c->fuse_coarse = false;
+  c->vf_l0 = 0;
+  c->springs = Springs();
+  c->oc_eta = 0.5;
   c->host_rr = nullptr;
   c->rr_event = nullptr;
   c->cap_stream = nullptr;
@@ -545,6 +552,21 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
     col_prepare();
     df_prepare();
   }
+  // first level of the optional fused coarse stretch (TO_OPERATOR_FUSED_COARSE):
+  // the first stored level whose stencil is small (a few MB)
+  if (c->L >= 2 && vcycle_coarse_cluster(c->dim, mg_t(c), c->coarse_t) > 0) {
+    const int first = c->l1_implicit ? 2 : 1;
+    for (int l = first; l < c->L && l < VF_MAXL; ++l) {
+      const double sbytes = (double)stencil_values(c->dim, mg_t(c), c->lv[l].g) *
+                            (mg_t(c) == T_F64 ? 8.0 : 4.0);
+      if (l == c->L - 1 || sbytes <= VF_MAX_STENCIL_BYTES) {
+        c->vf_l0 = l;
+        break;
+      }
+    }
+    if (c->L > VF_MAXL) c->vf_l0 = 0;
+  }
+  (void)cudaGetLastError();
   for (int l = 0; l < c->L; ++l)
     INIT_TRY(launch_colfix(c->lv[l].g, c->lv[l].mask, c->lv[l].colfix, s), "column flags");
   for (int l = 0; l + 1 < c->L; ++l) {
@@ -609,7 +631,6 @@ to_status to_set_density(to_ctx* c, const double* rho_phys) {
 // ---------------------------------------------------------------------------
 // Internal solver pieces
 // ---------------------------------------------------------------------------
-static int mg_t(const to_ctx* c) { return c->mixed ? T_F32 : T_F64; }
 
 static const void* coef_for(const to_ctx* c, int op, int tc) {
   if (tc == T_F64 || tc == T_DF) return op == TO_OP_K ? (const void*)c->E64
@@ -656,9 +677,12 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.epi = epi;
   const int k = tune_kind_fine(c, tc, epi);
   a.zsplit = k >= 0 ? c->tuned_zc[k] : 0;
+  a.variant = k >= 0 ? c->tuned_var[k] : 0;
   a.use_tc = c->use_tc;
   a.bmat = c->tc_bmat;
   a.status = c->ints + I_TIMEOUT;
+  // the springs do not depend on the design: they cancel in dK
+  if (op != TO_OP_DK) a.springs = c->springs;
   return a;
 }
 
@@ -737,7 +761,7 @@ static to_status build_hierarchy(to_ctx* c) {
   const void* KE = t == T_F64 ? (const void*)c->KE64 : (const void*)c->KE32;
   const void* Qc = t == T_F64 ? (const void*)c->Qc64 : (const void*)c->Qc32;
   LAUNCH(c, launch_diag(c->dim, c->lv[0].g, c->lv[0].mask, t, false, E, nullptr, KE,
-                        c->lv[0].dinv, s), "diag 0");
+                        c->lv[0].dinv, s, c->springs), "diag 0");
   if (c->l1_implicit) {
     // level 1 stays implicit; level 2 straight from the finest moduli
     const void* R2 = t == T_F64 ? (const void*)c->R2_64 : (const void*)c->R2_32;
@@ -747,6 +771,8 @@ static to_status build_hierarchy(to_ctx* c) {
   } else {
     LAUNCH(c, launch_galerkin_fine(c->dim, t, c->lv[1].g, c->lv[0].g, E, Qc, c->lv[1].Kc, s),
            "galerkin 1");
+    LAUNCH(c, launch_spring_galerkin(c->dim, t, c->lv[1].g, c->lv[0].g, c->springs, c->lv[1].Kc,
+                                     s), "springs 1");
   }
   const int lfirst = c->l1_implicit ? 3 : 2;
   for (int l = lfirst; l < c->L; ++l)
@@ -821,21 +847,50 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
                            lv[l - 1].r, lv[l].b, smooth ? lv[l].dinv : nullptr, 0.6,
                            smooth ? lv[l].z : nullptr, s);
   };
-  LAUNCH(c, restrict_into(1), "restrict 0");
-  vb += vbytes_restrict(lv[0].n, lv[1].n, t, 1 < L - 1);
+  // levels lf .. L-1 (lf = 0: none) run as one fused cluster launch
+  const int lf = c->fuse_coarse ? c->vf_l0 : 0;
+  if (lf != 1) {
+    LAUNCH(c, restrict_into(1), "restrict 0");
+    vb += vbytes_restrict(lv[0].n, lv[1].n, t, 1 < L - 1);
+  }
   for (int l = 1; l < L - 1; ++l) {
+    if (lf && l >= lf) break;
     const ApplyArgs a = coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID);
     vb += apply_bytes(a);
     if ((st = run_op(c, a, "resid l")) != TO_OK) return st;
+    if (lf && l + 1 == lf) break;
     LAUNCH(c, restrict_into(l + 1), "restrict l");
     vb += vbytes_restrict(lv[l].n, lv[l + 1].n, t, l + 1 < L - 1);
   }
-  // coarsest grid: exact solve with the stored inverse
-  LAUNCH(c, launch_dense_gemv(c->coarse_t, t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s),
-         "coarse solve");
-  vb += vbytes_coarse(c->nc, c->coarse_t, t);
+  if (lf) {
+    VFuseArgs fa = {};
+    fa.l0 = lf;
+    fa.L = L;
+    for (int l = lf - 1; l < L; ++l)
+      fa.lv[l] = VFLevel{lv[l].g, lv[l].mask, lv[l].S, lv[l].dinv, lv[l].b, lv[l].z, lv[l].z2,
+                         lv[l].r};
+    fa.Ainv = c->Ainv;
+    fa.nc = c->nc;
+    fa.omega = 0.6;
+    LAUNCH(c, launch_vcycle_coarse(c->dim, t, c->coarse_t, fa, s), "coarse levels (fused)");
+    // the same algorithmic bytes as the separate launches
+    vb += vbytes_restrict(lv[lf - 1].n, lv[lf].n, t, lf < L - 1);
+    for (int l = lf; l < L - 1; ++l) {
+      vb += apply_bytes(coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID));
+      vb += vbytes_restrict(lv[l].n, lv[l + 1].n, t, l + 1 < L - 1);
+      vb += vbytes_prolong(lv[l].n, lv[l + 1].n, t);
+      vb += apply_bytes(coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH));
+    }
+    vb += vbytes_coarse(c->nc, c->coarse_t, t);
+  } else {
+    // coarsest grid: exact solve with the stored inverse
+    LAUNCH(c, launch_dense_gemv(c->coarse_t, t, c->nc, c->Ainv, lv[L - 1].b, lv[L - 1].z2, s),
+           "coarse solve");
+    vb += vbytes_coarse(c->nc, c->coarse_t, t);
+  }
   // upward: interpolate, post-smooth (result of level l lands in z2)
   for (int l = L - 2; l >= 1; --l) {
+    if (lf && l >= lf) continue;
     LAUNCH(c, launch_prolong_add(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].z2,
                                  lv[l].z, s), "prolong l");
     vb += vbytes_prolong(lv[l].n, lv[l + 1].n, t);
@@ -1341,7 +1396,8 @@ to_status to_carm_build(to_ctx* c, const double* u_last) {
 
 // process-wide cache of tuned chunk lengths: (device, kernel, grid) -> layers
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, long long, long long, long long>, int> g_tune_cache;
+static std::map<std::tuple<int, int, long long, long long, long long>, std::pair<int, int>>
+    g_tune_cache;   // -> (layers per chunk, register variant)
 
 to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t cap,
                       int32_t* count) {
@@ -1411,44 +1467,55 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
     const auto key = std::make_tuple(dev * 64 + kind * 4 + (c->mixed ? 1 : 0) + (c->use_tc ? 2 : 0),
                                      kind,
                                      (long long)a.g.nnx, (long long)a.g.nny, (long long)a.g.nnz);
-    to_tune_result r{kind, 0, 0, 0.0, 0.0};
+    to_tune_result r{kind, 0, 0, 0.0, 0.0, 0};
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto it = g_tune_cache.find(key);
       if (it != g_tune_cache.end()) {
-        c->tuned_zc[kind] = it->second;
-        r.chunk_layers = it->second;
+        c->tuned_zc[kind] = it->second.first;
+        c->tuned_var[kind] = it->second.second;
+        r.chunk_layers = it->second.first;
+        r.variant = it->second.second;
         if (*count < cap) results[*count] = r;
         ++*count;
         continue;
       }
     }
     a.zsplit = 0;
+    a.variant = 0;
     double h_us = 0.0;
     if ((err = time_us(a, &h_us)) != cudaSuccess) break;
     double best_us = h_us;
-    int best = 0, tried = 0;
+    int best = 0, best_var = 0, tried = 0;
     const int nnz = (int)a.g.nnz;
-    for (int nzc = 1; nzc <= nnz && nzc <= 64; ++nzc) {
-      const int zc = (nnz + nzc - 1) / nzc;
-      if (zc < 2 || (nnz + zc - 1) / zc != nzc) continue;
-      a.zsplit = zc;
-      double us = 0.0;
-      if ((err = time_us(a, &us)) != cudaSuccess) break;
-      ++tried;
-      if (us < 0.99 * best_us) {
-        best_us = us;
-        best = zc;
+    // the pair kernel (float32 finest grid) also has a second register variant
+    const bool pair = kind <= TO_TUNE_OP_SMOOTH && pair_apply_ok(a) && !a.use_tc;
+    for (int var = 0; var <= (pair ? 1 : 0) && err == cudaSuccess; ++var) {
+      for (int nzc = 1; nzc <= nnz && nzc <= 64; ++nzc) {
+        const int zc = (nnz + nzc - 1) / nzc;
+        if (zc < 2 || (nnz + zc - 1) / zc != nzc) continue;
+        a.zsplit = zc;
+        a.variant = var;
+        double us = 0.0;
+        if ((err = time_us(a, &us)) != cudaSuccess) break;
+        ++tried;
+        if (us < 0.99 * best_us) {
+          best_us = us;
+          best = zc;
+          best_var = var;
+        }
       }
     }
     if (err != cudaSuccess) break;
     c->tuned_zc[kind] = best;
+    c->tuned_var[kind] = best_var;
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
-      g_tune_cache[key] = best;
+      g_tune_cache[key] = std::make_pair(best, best_var);
     }
     r.candidates = tried;
     r.chunk_layers = best;
+    r.variant = best_var;
     r.chosen_us = best_us;
     r.heuristic_us = h_us;
     if (*count < cap) results[*count] = r;
@@ -1465,14 +1532,18 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
 
 to_status to_operator_options(to_ctx* c, int32_t flags) {
   if (!c) return fail(c, TO_E_INVALID, "NULL argument");
-  if (flags & ~TO_OPERATOR_TENSOR_CORES) return fail(c, TO_E_INVALID, "unknown operator option");
+  if (flags & ~(TO_OPERATOR_TENSOR_CORES | TO_OPERATOR_FUSED_COARSE))
+    return fail(c, TO_E_INVALID, "unknown operator option");
   const bool tc = (flags & TO_OPERATOR_TENSOR_CORES) != 0;
+  const bool fuse = (flags & TO_OPERATOR_FUSED_COARSE) != 0;
   if (tc && !c->tc_bmat) return fail(c, TO_E_INVALID, "the tensor-core operator is 3D only");
-  if (tc != c->use_tc) {
+  if (tc != c->use_tc || fuse != c->fuse_coarse) {
+    if (tc != c->use_tc)
+      for (int q = 0; q < 8; ++q) c->tuned_zc[q] = c->tuned_var[q] = 0;
     c->use_tc = tc;
+    c->fuse_coarse = fuse;
     for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
-    c->n_vgraph = 0;   // recaptured with the selected kernel
-    for (int q = 0; q < 8; ++q) c->tuned_zc[q] = 0;
+    c->n_vgraph = 0;   // recaptured with the selected kernels
   }
   return TO_OK;
 }
@@ -1575,6 +1646,50 @@ to_status to_sensitivity(to_ctx* c, const double* u, double* compliance_dev, dou
   return TO_OK;
 }
 
+to_status to_mesh_springs(to_ctx* c, int32_t n, const int64_t* dofs, const double* k) {
+  if (!c || n < 0 || (n > 0 && (!dofs || !k))) return fail(c, TO_E_INVALID, "bad arguments");
+  if (c->dim != 2) return fail(c, TO_E_INVALID, "springs are supported on 2D grids");
+  if (n > TO_MAX_SPRINGS) return fail(c, TO_E_INVALID, "too many springs");
+  Springs sp;
+  sp.n = n;
+  for (int q = 0; q < n; ++q) {
+    if (dofs[q] < 0 || dofs[q] >= c->n) return fail(c, TO_E_INVALID, "spring DOF out of range");
+    if (!(k[q] >= 0.0) || !std::isfinite(k[q])) return fail(c, TO_E_INVALID, "bad spring stiffness");
+    for (int r = 0; r < q; ++r)
+      if (dofs[r] == dofs[q]) return fail(c, TO_E_INVALID, "spring DOF repeated");
+    uint8_t m = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&m, c->lv[0].mask + dofs[q] / c->dim, 1, cudaMemcpyDeviceToHost,
+                                c->stream), "read mask");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+    if ((m >> (dofs[q] % c->dim)) & 1u) return fail(c, TO_E_INVALID, "spring on a fixed DOF");
+    sp.dof[q] = dofs[q];
+    sp.k[q] = k[q];
+  }
+  c->springs = sp;
+  c->hier_stale = true;   // diagonal and level-1 matrices include the springs
+  for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
+  c->n_vgraph = 0;        // captured launches carry the old springs
+  return TO_OK;
+}
+
+to_status to_sensitivity_adjoint(to_ctx* c, const double* u, const double* lam,
+                                 double* mutual_dev, double* dc) {
+  if (!c || !u || !lam || !mutual_dev || !dc) return fail(c, TO_E_INVALID, "NULL argument");
+  if (!c->have_density) return fail(c, TO_E_STATE, "to_set_density has not been called");
+  const to_mesh_desc& d = c->desc;
+  LAUNCH(c, launch_sensitivity(c->dim, c->lv[0].g, c->lv[0].mask, c->KE64, nullptr, u, c->E64,
+                               c->rho_phys, d.penal, d.E0, d.Emin, dc, mutual_dev, c->partials,
+                               c->counters + C_SENS, c->stream, lam), "adjoint sensitivity");
+  return TO_OK;
+}
+
+to_status to_oc_options(to_ctx* c, double eta) {
+  if (!c) return fail(c, TO_E_INVALID, "NULL argument");
+  if (!(eta > 0.0 && eta <= 1.0)) return fail(c, TO_E_INVALID, "eta must be in (0, 1]");
+  c->oc_eta = eta;
+  return TO_OK;
+}
+
 to_status to_filter(to_ctx* c, int32_t mode, const double* in, double* out) {
   if (!c || !in || !out || in == out) return fail(c, TO_E_INVALID, "bad arguments");
   if (mode != TO_FILTER_DENSITY && mode != TO_FILTER_SENS) return fail(c, TO_E_INVALID, "bad mode");
@@ -1595,12 +1710,12 @@ to_status oc_update_enqueue(to_ctx* c, double volfrac, double move, const double
   const long long nel = c->nel;
   const double target = volfrac * (double)nel;
   LAUNCH(c, launch_oc_prep_d(nel, rho, dc_f, dv_f, move, c->oc_a, c->oc_a2, c->oc_lo, c->oc_hi,
-                             c->oc_dv2, c->scal, s), "oc prep");
+                             c->oc_dv2, c->scal, s, c->oc_eta), "oc prep");
   for (int q = 0; q < 48; ++q)
     LAUNCH(c, launch_oc_section(nel, c->oc_a2, c->oc_lo, c->oc_hi, c->oc_dv2, target, c->scal,
-                                c->partials, c->counters + C_OC, s), "oc section");
+                                c->partials, c->counters + C_OC, s, c->oc_eta), "oc section");
   LAUNCH(c, launch_oc_final(nel, rho, c->oc_a, move, c->scal, change_dev, c->partials,
-                            c->counters + C_MAX, s), "oc final");
+                            c->counters + C_MAX, s, c->oc_eta), "oc final");
   return TO_OK;
 }
 
@@ -1615,7 +1730,7 @@ to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_
   const long long nel = c->nel;
   const double target = volfrac * (double)nel;
   LAUNCH(c, launch_oc_prep_d(nel, rho, dc_f, dv_f, move, c->oc_a, c->oc_a2, c->oc_lo, c->oc_hi,
-                             c->oc_dv2, c->scal, s), "oc prep");
+                             c->oc_dv2, c->scal, s, c->oc_eta), "oc prep");
   // eight-way sections run on the device; a launch is a no-op once the
   // bracket is within a relative 1e-13.  From [0, 1e9] geometric cuts reach
   // lambda's magnitude in a few sweeps (at most 7 for lambda >= 1e-40) and
@@ -1624,14 +1739,14 @@ to_status to_oc_update(to_ctx* c, double volfrac, double move, const double* dc_
   for (int chunk = 0, nsec = 24; chunk < 16; ++chunk, nsec = 8) {
     for (int q = 0; q < nsec; ++q)
       LAUNCH(c, launch_oc_section(nel, c->oc_a2, c->oc_lo, c->oc_hi, c->oc_dv2, target, c->scal,
-                                  c->partials, c->counters + C_OC, s), "oc section");
+                                  c->partials, c->counters + C_OC, s, c->oc_eta), "oc section");
     double lr[2];
     CUDA_TRY(c, cudaMemcpyAsync(lr, c->scal + S_OC_L1, 16, cudaMemcpyDeviceToHost, s), "read");
     CUDA_TRY(c, cudaStreamSynchronize(s), "sync");
     if (!((lr[1] - lr[0]) > 1e-13 * (lr[0] + lr[1]))) break;
   }
   LAUNCH(c, launch_oc_final(nel, rho, c->oc_a, move, c->scal, change_dev, c->partials,
-                            c->counters + C_MAX, s), "oc final");
+                            c->counters + C_MAX, s, c->oc_eta), "oc final");
   return TO_OK;
 }
 

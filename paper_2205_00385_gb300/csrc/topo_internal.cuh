@@ -27,6 +27,15 @@ struct GridP {
   long long nn, nel;   // node and element counts
 };
 
+// Linear springs to ground on free finest-grid DOFs (Sec. 4.3): the
+// operator becomes K + S with S diagonal, k[q] at dof[q].
+constexpr int MAX_SPRINGS = 4;
+struct Springs {
+  int n = 0;
+  long long dof[MAX_SPRINGS] = {};
+  double k[MAX_SPRINGS] = {};
+};
+
 // Symmetric element matrices of the stored coarse levels keep their upper
 // triangle, row-major packed: entry (r, c), r <= c, at tri_idx(r, c, nd);
 // tri_len(nd) = nd (nd + 1) / 2 entries per element.
@@ -349,8 +358,13 @@ struct to_ctx {
   int coarse_t;          // storage of the coarsest matrix and its inverse
   double coarse_shift;   // relative diagonal shift of the coarsest matrix
   int tuned_zc[8];       // autotuned layers per z-chunk per TO_TUNE_* kernel (0: heuristic)
+  int tuned_var[8];      // autotuned register variant per TO_TUNE_* kernel (pair kernels)
   int carm_flags;        // TO_CARM_* options of to_carm_build
   bool use_tc;           // float32 finest-grid operator on the tensor cores
+  bool fuse_coarse;      // coarse end of the V-cycle as one cluster launch (option)
+  topo::Springs springs;  // springs to ground of the finest grid (2D)
+  double oc_eta;          // damping exponent of the OC update
+  int vf_l0;             // its first level (0: no level qualifies)
   float* tc_bmat;        // its B operand (device, 2 x 1024 floats)
   VGraph vgraph[4];
   int n_vgraph;

@@ -191,6 +191,80 @@ class TopoSolver:
         return self.history
 
 
+@dataclass
+class MechLog:
+    k: int
+    objective: float                 # u_out of the state solution
+    branches: tuple                  # (state, adjoint)
+    eps: tuple
+    cg_iters: tuple
+    change: float
+    seconds: float
+    solve_seconds: float = 0.0       # wall time of both equilibrium solves
+
+
+class MechanismSolver:
+    """Compliant-mechanism job (Sec. 4.3, the displacement inverter): the
+    state system (K + S) u = f_in and the adjoint system (K + S) lam = l
+    (l the unit vector of the output DOF) as two contexts on the same mesh,
+    springs and density, each running Algorithm 1 with its own PARM.  Per
+    iteration: filter and SIMP on the state context (the adjoint context
+    gets the same physical density), both solves, the output sensitivity
+    from (u, lam), its filter and the damped OC update."""
+
+    def __init__(self, prob, device="cuda", stream=None, precision: Optional[str] = None):
+        torch = _torch()
+        if prob.out_dof < 0 or not prob.springs:
+            raise ValueError("a mechanism problem needs out_dof and springs")
+        self.prob = prob
+        l_vec = np.zeros(prob.ndof)
+        l_vec[prob.out_dof] = 1.0
+        self.state = TopoSolver(prob, device, stream, precision)
+        self.adj = TopoSolver(prob.with_(f=l_vec), device, self.state.stream, precision)
+        dofs = [d for d, _ in prob.springs]
+        ks = [k for _, k in prob.springs]
+        with torch.cuda.stream(self.state.stream):
+            for s in (self.state, self.adj):
+                B.to_mesh_springs(s.ctx, dofs, ks)
+            B.to_oc_options(self.state.ctx, prob.oc_eta)
+        self.k = 0
+        self.history: List[MechLog] = []
+
+    def close(self):
+        self.state.close()
+        self.adj.close()
+
+    def step(self) -> MechLog:
+        torch = _torch()
+        p, st, ad = self.prob, self.state, self.adj
+        t0 = time.perf_counter()
+        with torch.cuda.stream(st.stream):
+            st.density_phase()
+            B.to_set_density(ad.ctx, st.rho_phys)
+            st.stream.synchronize()
+            ts = time.perf_counter()
+            bu, eu, iu, _, _ = st.solve_phase()
+            bl, el, il, _, _ = ad.solve_phase()
+            st.stream.synchronize()
+            t_solve = time.perf_counter() - ts
+            self.k = st.k
+            B.to_sensitivity_adjoint(st.ctx, st.u, ad.u, st.scalars[3:4], st.dc)
+            B.to_filter(st.ctx, B.TO_FILTER_SENS, st.dc, st.dc_f)
+            B.to_oc_update(st.ctx, p.volfrac_at(self.k), p.move, st.dc_f, st.dv_f, st.rho,
+                           st.scalars[1:2])
+            obj = float(st.u[p.out_dof].item())
+            change = float(st.scalars[1].item())
+        log = MechLog(self.k, obj, (bu, bl), (eu, el), (iu, il), change,
+                      time.perf_counter() - t0, t_solve)
+        self.history.append(log)
+        return log
+
+    def run(self, n_iter: Optional[int] = None) -> List[MechLog]:
+        for _ in range(n_iter if n_iter is not None else self.prob.n_iter):
+            self.step()
+        return self.history
+
+
 def run_job(prob, n_iter=None, device="cuda", precision=None):
     s = TopoSolver(prob, device=device, precision=precision)
     try:
