@@ -110,6 +110,55 @@ __device__ __forceinline__ void stencil_row(const GridP& g, const T* __restrict_
     y[r] = ldv<CG>(x + r) + omega * __ldg(dinv + r) * (ldv<CG>(b + r) - acc);
 }
 
+// Products and sums rounded one by one (no contraction into FMAs), so that
+// every kernel calling these bodies computes the same bits whatever the
+// compiler does around them.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// The weighted sum of a coarse node's 3^DIM fine neighbours (masks m and
+// values v as loaded, index (a, b, q) = (dz, dy, dx) + 1), in a fixed order,
+// and the coarse node's outputs.
+template <int DIM, typename T>
+__device__ __forceinline__ void restrict_finish(const GridP& gf, const GridP& gc,
+                                                const uint8_t* __restrict__ maskc,
+                                                const unsigned (&m)[DIM == 3 ? 3 : 1][3][3],
+                                                const T (&v)[DIM == 3 ? 3 : 1][3][3][DIM],
+                                                T* __restrict__ bc, const T* __restrict__ dinvc,
+                                                T omega, T* __restrict__ zc, int I, int J, int K) {
+  constexpr int NZ = DIM == 3 ? 3 : 1;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int a = 0; a < NZ; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int dx = q - 1, dy = b - 1, dz = DIM == 3 ? a - 1 : 0;
+        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+        bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
+        if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
+        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+        const unsigned mm = in ? m[a][b][q] : 7u;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+          acc[c] = add_rn(acc[c], ((mm >> c) & 1u) ? T(0) : mul_rn(w, v[a][b][q][c]));
+      }
+  const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
+  const unsigned mc = maskc[node];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long d = DIM * node + c;
+    const T bv = ((mc >> c) & 1u) ? T(0) : acc[c];
+    bc[d] = bv;
+    if (zc) zc[d] = mul_rn(mul_rn(omega, dinvc[d]), bv);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Restriction b_c = Pm^T r_f (Pm = M_f P M_c) at coarse node (I, J, K): it
 // gathers the fine nodes around (2I, 2J, 2K) with weights prod(1 - |d|/2).
@@ -142,34 +191,7 @@ __device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[a][b][q][c] = ldv<CG>(rf + DIM * fn + c);
       }
-  T acc[DIM];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-#pragma unroll
-  for (int a = 0; a < NZ; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int dx = q - 1, dy = b - 1, dz = DIM == 3 ? a - 1 : 0;
-        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-        bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
-        if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
-        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
-        const unsigned mm = in ? m[a][b][q] : 7u;
-#pragma unroll
-        for (int c = 0; c < DIM; ++c)
-          acc[c] += ((mm >> c) & 1u) ? T(0) : w * v[a][b][q][c];
-      }
-  const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
-  const unsigned mc = maskc[node];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    const long long d = DIM * node + c;
-    const T bv = ((mc >> c) & 1u) ? T(0) : acc[c];
-    bc[d] = bv;
-    if (zc) zc[d] = omega * dinvc[d] * bv;
-  }
+  restrict_finish<DIM, T>(gf, gc, maskc, m, v, bc, dinvc, omega, zc, I, J, K);
 }
 
 // ---------------------------------------------------------------------------
@@ -179,15 +201,38 @@ __device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __
 // all loaded (clamped into the grid) before any sum, and each fine node then
 // sums its own terms in a fixed order.
 // ---------------------------------------------------------------------------
+// The interpolated value at fine node (i, j, k), one component: its own
+// value zv plus the weighted coarse values cv[a][bb][cc] at coarse nodes
+// (i/2 + cc, j/2 + bb, k/2 + a), summed in a fixed order over the parents
+// the node interpolates from (cv entries of other positions are ignored).
+template <int DIM, typename T>
+__device__ __forceinline__ T prolong_one(T zv, const T (&cv)[DIM == 3 ? 2 : 1][2][2], int i, int j,
+                                         int k) {
+  constexpr int NK = DIM == 3 ? 2 : 1;
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
+  const int nk = (DIM == 3 && (k & 1)) ? 2 : 1;
+  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
+  const T w = mul_rn(mul_rn(wx, wy), (DIM == 3 && (k & 1)) ? T(0.5) : T(1));
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < NK; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const bool use = a < nk && bb < nj && cc < ni;
+        acc = add_rn(acc, use ? mul_rn(w, cv[a][bb][cc]) : T(0));
+      }
+  return add_rn(zv, acc);
+}
+
 template <int DIM, typename T, bool CG>
 __device__ __forceinline__ void prolong_pair(const GridP& gf, const uint8_t* __restrict__ maskf,
                                              const GridP& gc, const T* __restrict__ zc,
                                              T* __restrict__ zf, int i, int j, int q) {
   constexpr int NK = DIM == 3 ? 2 : 1;   // fine nodes per item along z
   const int i0 = i >> 1, j0 = j >> 1;
-  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
-  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
-  T cv[NK][2][2][DIM];
+  T cv[DIM][NK][2][2];
 #pragma unroll
   for (int a = 0; a < NK; ++a)
 #pragma unroll
@@ -198,7 +243,7 @@ __device__ __forceinline__ void prolong_pair(const GridP& gf, const uint8_t* __r
         const int kc = DIM == 3 ? min(q + a, gc.nnz - 1) : 0;
         const long long cn = ic + (long long)gc.nnx * (jc + (long long)gc.nny * kc);
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) cv[a][bb][cc][c] = ldv<CG>(zc + DIM * cn + c);
+        for (int c = 0; c < DIM; ++c) cv[c][a][bb][cc] = ldv<CG>(zc + DIM * cn + c);
       }
   unsigned m[NK];
   T zv[NK][DIM];
@@ -214,27 +259,10 @@ __device__ __forceinline__ void prolong_pair(const GridP& gf, const uint8_t* __r
   for (int s = 0; s < NK; ++s) {
     const int k = DIM == 3 ? 2 * q + s : 0;
     if (DIM == 3 && k >= gf.nnz) break;
-    const int nk = (DIM == 3 && (k & 1)) ? 2 : 1;
-    const T w = wx * wy * ((DIM == 3 && (k & 1)) ? T(0.5) : T(1));
-    T acc[DIM];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          if (a >= NK) continue;
-          // fine node k = 2q + s reads coarse plane (k >> 1) + a = q + a
-          const bool use = a < nk && bb < nj && cc < ni;
-#pragma unroll
-          for (int c = 0; c < DIM; ++c) acc[c] += use ? w * cv[a][bb][cc][c] : T(0);
-        }
     const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
 #pragma unroll
     for (int c = 0; c < DIM; ++c)
-      if (!((m[s] >> c) & 1u)) zf[DIM * node + c] = zv[s][c] + acc[c];
+      if (!((m[s] >> c) & 1u)) zf[DIM * node + c] = prolong_one<DIM, T>(zv[s][c], cv[c], i, j, k);
   }
 }
 

@@ -237,7 +237,7 @@ def inverter2d(nelx: int, nely: int, volfrac: float = 0.3, rmin: float = 2.5,
     clamped: nely/16 of it, rounded up to whole elements of the coarsest
     multigrid level (so that the supports stay closed under the coarse-grid
     interpolation).  The objective is u_out = u_x(B), minimised (B moves
-    against the input); OC damping 0.3, move limit 0.1."""
+    against the input); OC damping 0.3, move limit 0.05."""
     dim = 2
     _, nn, ndof = grid_counts(dim, nelx, nely)
     fixed = np.zeros(ndof, np.uint8)
@@ -254,7 +254,7 @@ def inverter2d(nelx: int, nely: int, volfrac: float = 0.3, rmin: float = 2.5,
     f[a] = 1.0
     nel = nelx * nely
     p = Problem("inverter2d", dim, nelx, nely, 0, fixed, f, np.full(nel, volfrac), volfrac, rmin,
-                move=0.1, springs=((a, k_in), (b, k_out)), out_dof=b, oc_eta=0.3)
+                move=0.05, springs=((a, k_in), (b, k_out)), out_dof=b, oc_eta=0.3)
     return p.with_(**kw)
 
 
