@@ -299,6 +299,7 @@ def _carm_summary(logs):
     if not att:
         return None
     return {"attempts": len(att), "accepted": sum(h.branch == "carm" for h in att),
+            "timing_note": "host wall time of each solve, between stream synchronisations",
             "mean_build_and_solve_ms": round(1e3 * sum(h.carm_seconds for h in att) / len(att), 3),
             "eps_min": float(min(h.eps for h in att)), "eps_max": float(max(h.eps for h in att)),
             "mean_mgcg_solve_ms": (round(1e3 * sum(h.solve_seconds for h in mg) / len(mg), 3)
@@ -451,6 +452,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline, "fp64_arm": fp64, "mgcg_only_arm": mgcg_only,
         "carm_attempts": _carm_summary(logs),
+        "mgcg_us_per_cg_iteration": round(
+            1e6 * sum(h.solve_seconds - h.carm_seconds for h in logs) / max(cg, 1), 1),
         "e2e": e2e, "gpu_launches": int(r["launches"]),
         "autotune": ([{k: (round(v, 2) if isinstance(v, float) else v) for k, v in q.items()}
                       for q in r["tuning"]] if r["tuning"] else None),

@@ -122,7 +122,12 @@ to_status to_set_density(to_ctx* ctx, const double* rho_phys);
  * the next preconditioner application and waited on after it, so the
  * V-cycle runs during the round trip (its result is discarded on the
  * iteration that stops).  The first call on a context allocates 64 bytes of
- * pinned host memory for that read (released by to_destroy). */
+ * pinned host memory for that read (released by to_destroy).
+ * The first solve after to_set_density rebuilds the multigrid hierarchy; in
+ * TO_MIXED the coarsest matrix's explicit inverse is formed in float32 and
+ * checked (one small synchronising read), and a context whose float32
+ * factorisation meets a non-positive pivot (near-void designs) factors in
+ * float64 from then on. */
 to_status to_mgcg_solve(to_ctx* ctx, double rtol, int32_t maxit, int32_t flags, double* u,
                         int32_t* iters, double* relres);
 

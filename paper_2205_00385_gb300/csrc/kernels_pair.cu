@@ -141,10 +141,7 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
   const int tid = threadIdx.x;
   const int tx = tid % PX, ty = tid / PX;
   const int X0 = blockIdx.x * POX, Y0 = blockIdx.y * POY;
-  // the chunks split the node layers evenly (lengths differ by at most one),
-  // so the blocks of a wave finish together
-  const int z0 = (int)((long long)blockIdx.z * g.nnz / gridDim.z);
-  const int z1 = (int)((long long)(blockIdx.z + 1) * g.nnz / gridDim.z);
+  const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, g.nnz);
   const int i = X0 - 1 + 2 * tx, j = Y0 - 1 + ty;   // corner 0 of element A
   const long long plane = (long long)g.nnx * g.nny;
   const bool eA = i >= 0 && i < g.nx && j >= 0 && j < g.ny;

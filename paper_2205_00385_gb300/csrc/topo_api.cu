@@ -787,8 +787,30 @@ static to_status build_hierarchy(to_ctx* c) {
   const int Lc = c->L - 1;
   LAUNCH(c, launch_dense_assemble(c->dim, t, c->coarse_t, c->lv[Lc].g, c->lv[Lc].mask,
                                   c->lv[Lc].Kc, c->Adense, c->coarse_shift, s), "dense assemble");
-  LAUNCH(c, launch_cholesky_inverse(c->coarse_t, c->nc, c->Adense, c->Ainv, c->ints + I_STATUS,
-                                    s), "coarse factor");
+  if (c->coarse_t == T_F32) {
+    // float32 factorisation, checked: on high-contrast designs (near-void
+    // regions at Emin / E0 = 1e-9) the float32 coarsest matrix can lose
+    // positive definiteness; the context then factors it in float64 from
+    // here on (the V-cycles captured with the float32 product are dropped)
+    LAUNCH(c, launch_cholesky_inverse(T_F32, c->nc, c->Adense, c->Ainv, c->ints + I_COARSE, s),
+           "coarse factor");
+    int bad = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&bad, c->ints + I_COARSE, sizeof(int), cudaMemcpyDeviceToHost, s),
+             "read coarse status");
+    CUDA_TRY(c, cudaStreamSynchronize(s), "sync");
+    if (bad) {
+      CUDA_TRY(c, cudaMemsetAsync(c->ints + I_COARSE, 0, sizeof(int), s), "reset");
+      c->coarse_t = T_F64;
+      for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
+      c->n_vgraph = 0;
+      LAUNCH(c, launch_dense_assemble(c->dim, t, c->coarse_t, c->lv[Lc].g, c->lv[Lc].mask,
+                                      c->lv[Lc].Kc, c->Adense, c->coarse_shift, s),
+             "dense assemble");
+    }
+  }
+  if (c->coarse_t != T_F32)
+    LAUNCH(c, launch_cholesky_inverse(c->coarse_t, c->nc, c->Adense, c->Ainv, c->ints + I_STATUS,
+                                      s), "coarse factor");
   c->hier_stale = false;
   return TO_OK;
 }

@@ -137,7 +137,7 @@ enum SmallOff {
 // I_KCOUNT: columns accepted by the QR of the CARM basis; I_KRED: directions
 // kept by the truncated SVD of Eq. 21
 // I_TIMEOUT: a bounded device wait expired (TO_E_TIMEOUT)
-enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_KRED = 2, I_TIMEOUT = 3, I_NINTS = 16 };
+enum IntSlot { I_KCOUNT = 0, I_STATUS = 1, I_KRED = 2, I_TIMEOUT = 3, I_COARSE = 4, I_NINTS = 16 };
 
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of NV float64 values, finished by the last
