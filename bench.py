@@ -63,7 +63,11 @@ def _args():
     ap.add_argument("--tensor-cores", action="store_true",
                     help="finest-grid float32 operator on the tensor cores (tcgen05)")
     ap.add_argument("--small", action="store_true", help="48x24x24 instead (quick checks)")
-    ap.add_argument("--kernel", default=None, choices=[None, "apply"],
+    ap.add_argument("--config4", action="store_true",
+                    help="with --kernel: the 320x160x160 bridge (24.96M DOFs) instead")
+    ap.add_argument("--fused-coarse", action="store_true",
+                    help="with --kernel vcycle: the coarse levels as one cluster launch")
+    ap.add_argument("--kernel", default=None, choices=[None, "apply", "vcycle"],
                     help="time one kernel alone (profiling) instead of the design loop")
     ap.add_argument("--kernel-prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--serve-jobs", type=int, default=24,
@@ -74,7 +78,9 @@ def _args():
 
 
 def _problem(args):
-    from workloads import config3_cantilever3d, cantilever3d
+    from workloads import config3_cantilever3d, config4_bridge3d, cantilever3d
+    if getattr(args, "config4", False):
+        return config4_bridge3d()
     if args.small:
         return cantilever3d(48, 24, 24, volfrac=0.12, rmin=2.0, n_iter=30, mg_levels=4,
                             precision=args.precision, n_parm=10, n_carm=10, n_on=15,
@@ -562,10 +568,45 @@ def run_kernel_apply(args):
             "bytes_per_launch": by / n, "workload": p.name + f" {p.nelx}x{p.nely}x{p.nelz}"}
 
 
+def run_kernel_vcycle(args):
+    """Times the V-cycle (to_vcycle, uncaptured, with its float64 <-> float32
+    conversions) on the bench workload at a uniform design, for profiling:
+    W untimed, K timed calls; --fused-coarse selects the one-launch coarse
+    end."""
+    import numpy as np
+    import torch
+    from paper_2205_00385_gb300 import binding as B
+    from paper_2205_00385_gb300.driver import TopoSolver
+    p = _problem(args)
+    s = TopoSolver(p)
+    rho = torch.full((p.nel,), p.volfrac, dtype=torch.float64, device="cuda")
+    B.to_set_density(s.ctx, rho)
+    if args.fused_coarse:
+        B.to_operator_options(s.ctx, B.TO_OPERATOR_FUSED_COARSE)
+    r = torch.from_numpy(np.random.default_rng(1).standard_normal(p.ndof)).cuda()
+    z = torch.empty_like(r)
+    for _ in range(args.warmup):
+        B.to_vcycle(s.ctx, r, z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        B.to_vcycle(s.ctx, r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    s.close()
+    return {"kernel": "to_vcycle", "fused_coarse": bool(args.fused_coarse),
+            "calls": args.steps, "avg_us": 1e3 * e0.elapsed_time(e1) / args.steps,
+            "workload": p.name + f" {p.nelx}x{p.nely}x{p.nelz}"}
+
+
 def main():
     args = _args()
     if args.kernel == "apply":
         print(json.dumps(run_kernel_apply(args)), flush=True)
+        return
+    if args.kernel == "vcycle":
+        print(json.dumps(run_kernel_vcycle(args)), flush=True)
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

@@ -175,8 +175,8 @@ to_status to_carm_build(to_ctx* ctx, const double* u_last);
  *   TO_TUNE_GAL1_RESID / _SMOOTH: the level-1 Galerkin operator applied
  *     from the finest moduli (3D, >= 3 levels);
  *   TO_TUNE_ACC_APPLY / _RESID: the double-float operator (TO_MIXED).
- * For the float32 finest-grid kernels it also times a second register
- * variant (one more resident block per SM, a few registers spilled).
+ * For the float32 finest-grid kernels it also times the 16-row tile
+ * variant (TO_OPERATOR_TALL_TILES).
  * It keeps the fastest (the occupancy heuristic's own shape when within 1 %
  * of it), applies it to every later launch of that kernel on this context,
  * drops the captured V-cycle graphs so that they are recaptured with it, and
@@ -195,8 +195,8 @@ typedef struct {
   int32_t chunk_layers;  /* chosen node layers per chunk (0: the heuristic's shape) */
   double chosen_us;      /* average launch time of the chosen shape (0 when cached) */
   double heuristic_us;   /* average launch time of the heuristic's shape (0 when cached) */
-  int32_t variant;       /* float32 finest-grid kernels (TO_TUNE_OP_*): register variant,
-                            0 = no spills, 1 = one more resident block per SM */
+  int32_t variant;       /* float32 finest-grid kernels (TO_TUNE_OP_*): tile variant,
+                            0 = 8-row tiles, 1 = 16-row tiles (TO_OPERATOR_TALL_TILES) */
 } to_tune_result;
 to_status to_autotune(to_ctx* ctx, int32_t reps, to_tune_result* results, int32_t cap,
                       int32_t* count);
@@ -267,6 +267,13 @@ to_status to_batch_step(const to_batch_job* jobs, int32_t n, int32_t phase, void
  * one-kernel steps use the whole GPU and overlap their launches), so it is
  * off by default.  Changing it drops the captured V-cycle graphs. */
 #define TO_OPERATOR_FUSED_COARSE 2
+/* TO_OPERATOR_TALL_TILES: the float32 finest-grid operator (3D TO_MIXED)
+ * runs its 256-thread variant with 16-row tiles (16 element rows computed
+ * for 15 owned node rows instead of 8 for 7) in every launch; to_autotune
+ * also times that variant and may select it for a kernel on its own.  The
+ * results are bit for bit the same.  Changing it drops the captured
+ * V-cycle graphs. */
+#define TO_OPERATOR_TALL_TILES 4
 to_status to_operator_options(to_ctx* ctx, int32_t flags);
 
 /* Options of to_carm_build (default 0).  TO_CARM_R1_PROJECTED_LOAD: the

@@ -226,6 +226,7 @@ TO_CARM_R1_PROJECTED_LOAD = 1
 
 TO_OPERATOR_TENSOR_CORES = 1
 TO_OPERATOR_FUSED_COARSE = 2
+TO_OPERATOR_TALL_TILES = 4
 
 
 def to_operator_options(ctx, flags):

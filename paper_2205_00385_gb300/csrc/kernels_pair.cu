@@ -26,7 +26,7 @@
 namespace topo {
 namespace {
 
-constexpr int PX = 16, PY = 8, POX = 2 * (PX - 1), POY = PY - 1, PZC = 16;
+constexpr int PX = 16, POX = 2 * (PX - 1), PZC = 16;
 
 struct WhtPair {
   float2 b[8][3][3];   // Walsh blocks with each entry in both lanes
@@ -113,12 +113,19 @@ struct PairArgs {
   float omega, dfix;
 };
 
-// Face tile of a block: (2 PX + 1) x (PY + 1) nodes, three floats per node,
-// rows of FROW floats (odd, so the two half-warps' rows hit disjoint banks)
-constexpr int FNX = 2 * PX + 1, FNY = PY + 1, FROW = 3 * FNX, FTILE = FROW * FNY;
+// Face tile of a block of PX x PY threads: (2 PX + 1) x (PY + 1) nodes,
+// three floats per node, rows of FROW floats (odd, so the two half-warps'
+// rows hit disjoint banks).  PY is 8 or 16 (the taller tile computes 16
+// element rows for 15 owned node rows instead of 8 for 7).
+constexpr int FNX = 2 * PX + 1, FROW = 3 * FNX;
 constexpr int NSTAGE = 4;                                   // faces in flight
 static_assert((NSTAGE & (NSTAGE - 1)) == 0, "stage index uses a mask");
-static_assert(PX * PY == 128 && FNY <= 12 && FROW <= 128, "face copy: 4 warps x 3 rows x 4 lanes");
+static_assert(FROW <= 128, "face copy: 4 lanes per row segment");
+template <int PY>
+struct PairGeo {
+  static constexpr int POY = PY - 1, FNY = PY + 1, FTILE = FROW * FNY, NT = PX * PY;
+  static constexpr int NWARP = NT / 32, RPW = (FNY + NWARP - 1) / NWARP;   // face rows per warp
+};
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -130,13 +137,17 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+template <int PY>
 struct PairSmem {
-  float face[NSTAGE][FTILE];
+  float face[NSTAGE][PairGeo<PY>::FTILE];
   float4 pub[2][4][PY][PX];
 };
 
-template <int EPI, bool MASKED>
-__device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, PairSmem& sm) {
+template <int EPI, bool MASKED, int PY>
+__device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb,
+                                          PairSmem<PY>& sm) {
+  using G = PairGeo<PY>;
+  constexpr int POY = G::POY, FNY = G::FNY, FTILE = G::FTILE;
   const GridP& g = a.g;
   const int tid = threadIdx.x;
   const int tx = tid % PX, ty = tid / PX;
@@ -171,8 +182,8 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
       float* dst = sm.face[slot];
       const float* src = a.x + 3 * plane * kz;
 #pragma unroll
-      for (int rr = 0; rr < 3; ++rr) {
-        const int row = warp + 4 * rr;
+      for (int rr = 0; rr < G::RPW; ++rr) {
+        const int row = warp + G::NWARP * rr;
         if (row < FNY) {
           const int nj = Y0 - 1 + row;
           const bool rok = nj >= 0 && nj < g.nny;
@@ -187,7 +198,7 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
     } else if (kz >= z0 - 1 && kz <= z1) {
       // face outside the grid: zeros
       float* dst = sm.face[slot];
-      for (int f = tid; f < FTILE; f += PX * PY) dst[f] = 0.f;
+      for (int f = tid; f < FTILE; f += G::NT) dst[f] = 0.f;
     }
     cp_commit();
   };
@@ -337,16 +348,18 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb, 
   cp_wait<0>();
 }
 
-// resident blocks per SM the register allocation targets (MINB): variant 0
-// without spilling (four for K p, three for the residual and smoother
-// epilogues), variant 1 one block more with a few spilled registers; the
-// autotuner times both
-template <int EPI, int MINB>
+// Register / tile variants, timed by the autotuner: variant 0, 128 threads
+// (PY = 8) and the resident blocks per SM (MINB) the register allocation
+// allows without spilling (four for K p, three for the residual and
+// smoother epilogues); variant 1, 256 threads (PY = 16, less redundant
+// element work at tile edges) and two blocks per SM.
+template <int EPI, int MINB, int PY>
 __global__ void __launch_bounds__(PX * PY, MINB)
     k_apply3_pair(PairArgs a, WhtPair kb) {
-  __shared__ PairSmem sm;
+  extern __shared__ __align__(16) unsigned char pair_smem[];
+  PairSmem<PY>& sm = *reinterpret_cast<PairSmem<PY>*>(pair_smem);
   const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
-  const int i = blockIdx.x * POX - 1 + 2 * tx, j = blockIdx.y * POY - 1 + ty;
+  const int i = blockIdx.x * POX - 1 + 2 * tx, j = blockIdx.y * PairGeo<PY>::POY - 1 + ty;
   bool flag = a.colfix == nullptr;
 #pragma unroll
   for (int r = 0; r < 2; ++r)
@@ -360,9 +373,9 @@ __global__ void __launch_bounds__(PX * PY, MINB)
   // all threads of a block must take the same branch (both contain
   // __syncthreads), so the decision is block-wide
   if (__syncthreads_or(flag))
-    pair_loop<EPI, true>(a, kb, sm);
+    pair_loop<EPI, true, PY>(a, kb, sm);
   else
-    pair_loop<EPI, false>(a, kb, sm);
+    pair_loop<EPI, false, PY>(a, kb, sm);
   pdl_launch_dependents();
 }
 
@@ -384,14 +397,34 @@ cudaError_t launch_colfix(const GridP& g, const uint8_t* mask, uint8_t* colfix, 
   return cudaGetLastError();
 }
 
-template <int EPI>
-constexpr int pair_minb(int variant) {
-  return (EPI == EPI_APPLY ? 4 : 3) + (variant ? 1 : 0);
-}
+template <int EPI, int V>
+struct PairVar {
+  static constexpr int PY = V ? 16 : 8;
+  static constexpr int MINB = V ? 2 : (EPI == EPI_APPLY ? 4 : 3);
+  static constexpr int NT = PX * PY;
+  static constexpr size_t SMEM = sizeof(PairSmem<PY>);
+};
 
 template <int EPI, int V>
 static auto pair_kernel() {
-  return k_apply3_pair<EPI, pair_minb<EPI>(V)>;
+  return k_apply3_pair<EPI, PairVar<EPI, V>::MINB, PairVar<EPI, V>::PY>;
+}
+
+template <int EPI, int V>
+static int pair_occupancy() {
+  auto kern = pair_kernel<EPI, V>();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)PairVar<EPI, V>::SMEM) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PairVar<EPI, V>::NT,
+                                                    PairVar<EPI, V>::SMEM) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per_sm;
 }
 
 // resident blocks of the pair kernel on the current device (cached per
@@ -405,17 +438,13 @@ static long long pair_slots(int epi, int variant) {
   if (cache[e][v][dev] > 0) return cache[e][v][dev];
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t err;
   if (e == 0)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, v ? pair_kernel<EPI_APPLY, 1>() : pair_kernel<EPI_APPLY, 0>(), PX * PY, 0);
+    per_sm = v ? pair_occupancy<EPI_APPLY, 1>() : pair_occupancy<EPI_APPLY, 0>();
   else if (e == 1)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, v ? pair_kernel<EPI_RESID, 1>() : pair_kernel<EPI_RESID, 0>(), PX * PY, 0);
+    per_sm = v ? pair_occupancy<EPI_RESID, 1>() : pair_occupancy<EPI_RESID, 0>();
   else
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, v ? pair_kernel<EPI_SMOOTH, 1>() : pair_kernel<EPI_SMOOTH, 0>(), PX * PY, 0);
-  if (err != cudaSuccess || sms <= 0 || per_sm <= 0) return 2 * 152;
+    per_sm = v ? pair_occupancy<EPI_SMOOTH, 1>() : pair_occupancy<EPI_SMOOTH, 0>();
+  if (sms <= 0 || per_sm <= 0) return 2 * 152;
   cache[e][v][dev] = (long long)sms * per_sm;
   return cache[e][v][dev];
 }
@@ -454,11 +483,12 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   p.dinv = static_cast<const float*>(a.dinv);
   p.omega = (float)a.omega;
   p.dfix = (float)a.dfix;
-  const int gx = (a.g.nnx + POX - 1) / POX, gy = (a.g.nny + POY - 1) / POY;
+  const int var = a.variant ? 1 : 0;
+  const int poy = var ? PairGeo<16>::POY : PairGeo<8>::POY;
+  const int gx = (a.g.nnx + POX - 1) / POX, gy = (a.g.nny + poy - 1) / poy;
   // z-chunks: each chunk streams its layers and recomputes one element layer
   // below it; the count is chosen to minimise waves x layers per chunk for
   // the resident-block capacity of the device
-  const int var = a.variant ? 1 : 0;
   const long long slots = pair_slots(a.epi, var);
   const long long nxy = (long long)gx * gy;
   int best = 1;
@@ -477,17 +507,14 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   p.zc = a.zsplit > 0 ? min(a.zsplit, (int)a.g.nnz) : (a.g.nnz + best - 1) / best;
   best = (a.g.nnz + p.zc - 1) / p.zc;
   dim3 grid(gx, gy, best);
+#define PAIR_LAUNCH(E, V)                                                                   \
+  launch_pdl(pair_kernel<E, V>(), grid, dim3(PairVar<E, V>::NT), PairVar<E, V>::SMEM, s, p, kb)
   switch (a.epi) {
-    case EPI_APPLY:
-      return var ? launch_pdl(pair_kernel<EPI_APPLY, 1>(), grid, dim3(PX * PY), 0, s, p, kb)
-                 : launch_pdl(pair_kernel<EPI_APPLY, 0>(), grid, dim3(PX * PY), 0, s, p, kb);
-    case EPI_RESID:
-      return var ? launch_pdl(pair_kernel<EPI_RESID, 1>(), grid, dim3(PX * PY), 0, s, p, kb)
-                 : launch_pdl(pair_kernel<EPI_RESID, 0>(), grid, dim3(PX * PY), 0, s, p, kb);
-    default:
-      return var ? launch_pdl(pair_kernel<EPI_SMOOTH, 1>(), grid, dim3(PX * PY), 0, s, p, kb)
-                 : launch_pdl(pair_kernel<EPI_SMOOTH, 0>(), grid, dim3(PX * PY), 0, s, p, kb);
+    case EPI_APPLY: return var ? PAIR_LAUNCH(EPI_APPLY, 1) : PAIR_LAUNCH(EPI_APPLY, 0);
+    case EPI_RESID: return var ? PAIR_LAUNCH(EPI_RESID, 1) : PAIR_LAUNCH(EPI_RESID, 0);
+    default: return var ? PAIR_LAUNCH(EPI_SMOOTH, 1) : PAIR_LAUNCH(EPI_SMOOTH, 0);
   }
+#undef PAIR_LAUNCH
   return cudaGetLastError();
 }
 

@@ -475,6 +475,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->carm_flags = 0;
   c->use_tc = false;
   c->fuse_coarse = false;
+  c->tall_tiles = false;
   c->vf_l0 = 0;
   c->springs = Springs();
   c->oc_eta = 0.5;
@@ -677,7 +678,7 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.epi = epi;
   const int k = tune_kind_fine(c, tc, epi);
   a.zsplit = k >= 0 ? c->tuned_zc[k] : 0;
-  a.variant = k >= 0 ? c->tuned_var[k] : 0;
+  a.variant = (k >= 0 ? c->tuned_var[k] : 0) | (c->tall_tiles ? 1 : 0);
   a.use_tc = c->use_tc;
   a.bmat = c->tc_bmat;
   a.status = c->ints + I_TIMEOUT;
@@ -1554,10 +1555,16 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
 
 to_status to_operator_options(to_ctx* c, int32_t flags) {
   if (!c) return fail(c, TO_E_INVALID, "NULL argument");
-  if (flags & ~(TO_OPERATOR_TENSOR_CORES | TO_OPERATOR_FUSED_COARSE))
+  if (flags & ~(TO_OPERATOR_TENSOR_CORES | TO_OPERATOR_FUSED_COARSE | TO_OPERATOR_TALL_TILES))
     return fail(c, TO_E_INVALID, "unknown operator option");
   const bool tc = (flags & TO_OPERATOR_TENSOR_CORES) != 0;
   const bool fuse = (flags & TO_OPERATOR_FUSED_COARSE) != 0;
+  const bool tall = (flags & TO_OPERATOR_TALL_TILES) != 0;
+  if (tall != c->tall_tiles) {
+    c->tall_tiles = tall;
+    for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
+    c->n_vgraph = 0;   // recaptured with the selected tile
+  }
   if (tc && !c->tc_bmat) return fail(c, TO_E_INVALID, "the tensor-core operator is 3D only");
   if (tc != c->use_tc || fuse != c->fuse_coarse) {
     if (tc != c->use_tc)

@@ -362,6 +362,7 @@ struct to_ctx {
   int carm_flags;        // TO_CARM_* options of to_carm_build
   bool use_tc;           // float32 finest-grid operator on the tensor cores
   bool fuse_coarse;      // coarse end of the V-cycle as one cluster launch (option)
+  bool tall_tiles;       // float32 finest-grid operator with 16-row tiles (option)
   topo::Springs springs;  // springs to ground of the finest grid (2D)
   double oc_eta;          // damping exponent of the OC update
   int vf_l0;             // its first level (0: no level qualifies)

@@ -62,3 +62,30 @@ def test_autotune_keeps_results_and_caches(precision):
         res2 = B.to_autotune(c2.ctx, reps=3)
     assert [q["candidates"] for q in res2] == [0] * len(res2)
     assert [q["chunk_layers"] for q in res2] == [q["chunk_layers"] for q in res]
+
+
+def test_tall_tiles_give_the_same_bits():
+    """The 16-row tile variant of the float32 finest-grid operator
+    (TO_OPERATOR_TALL_TILES) computes every node's sum in the same order as
+    the 8-row one: products, V-cycles and solves are bitwise the same, on a
+    grid whose rows split unevenly into both tile heights."""
+    from paper_2205_00385_gb300 import binding as B
+    p = small_problem("cantilever3d", nelx=64, nely=40, nelz=24, mg_levels=4)
+    rho = rand_density(p.nel, 75, 0.05, 1.0)
+    x = dev(rand_vector(p.ndof, 76, fixed=p.fixed))
+    r = dev(rand_vector(p.ndof, 77, fixed=p.fixed))
+    out = []
+    with Ctx(p, precision="mixed") as c:
+        c.set_density(rho)
+        for flags in (0, B.TO_OPERATOR_TALL_TILES):
+            B.to_operator_options(c.ctx, flags)
+            y = dev(np.zeros(p.ndof))
+            B.to_apply(c.ctx, B.TO_OP_K, B.TO_PREC_FP32, x, y)
+            z = dev(np.zeros(p.ndof))
+            B.to_vcycle(c.ctx, r, z)
+            u = dev(np.zeros(p.ndof))
+            it, _, _ = B.to_mgcg_solve(c.ctx, 1e-8, 200, 0, u)
+            out.append((host(y), host(z), host(u), it))
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert out[0][3] == out[1][3]
