@@ -105,7 +105,8 @@ to_status to_set_density(to_ctx* ctx, const double* rho_phys);
 
 /* MGCG (Algorithm 2 as preconditioner of CG) for K(E) u = f.
  * u (dev, float64, n): in: initial guess if flags has TO_SOLVE_WARM_START
- *   (else ignored and zero is used); out: the solution.
+ *   (else ignored and zero is used; its entries on fixed DOFs are taken as
+ *   zero, as in the solution); out: the solution.
  * rtol: stop when ||f - K u|| / ||f|| < rtol.  In TO_FP64 the CG recursive
  *   residual is tested; in TO_MIXED (float32 operator inside CG) the
  *   recursive residual is replaced by the float64 true residual f - K u

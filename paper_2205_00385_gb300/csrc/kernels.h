@@ -52,6 +52,8 @@ struct ApplyArgs {
   const void* bmat = nullptr;     // its B operand (tc_pack_b), device
   int* status = nullptr;          // device word receiving TO_E_TIMEOUT from bounded waits
   Springs springs;                // finest 2D grid: springs to ground added to K (none: n = 0)
+  bool clean_inputs = false;      // x zero on every fixed DOF (the solver's own vectors): the
+                                  // float32 pair kernel then masks only the fixed rows' outputs
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 
@@ -183,6 +185,9 @@ cudaError_t launch_vdot(long long n, int vt, const void* a, const void* b, doubl
 // out = in with a change of storage (split, widen or copy)
 cudaError_t launch_vconvert(long long n, int tin, const void* in, int tout, void* out,
                             cudaStream_t s);
+// x = 0 on the fixed DOFs (mask per node, bit c for DOF c), storage vt
+cudaError_t launch_zero_fixed(long long nn, int dim, const uint8_t* mask, int vt, void* x,
+                              cudaStream_t s);
 // a *= 1/sqrt(*s2)
 cudaError_t launch_vscale_inv_sqrt(long long n, int vt, void* a, const double* s2,
                                    cudaStream_t s);

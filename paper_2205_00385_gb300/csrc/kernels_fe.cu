@@ -354,7 +354,9 @@ __global__ void __launch_bounds__(WX * WY, (OP == OPK_GAL1 && sizeof(TC) == 4) ?
     k_apply3_col(GridP g, GridP gf, const uint8_t* __restrict__ mask, WhtBlocks<TC> kb,
                  const TC* __restrict__ coef, int zc, const TX* __restrict__ x,
                  TY* __restrict__ y, const TX* __restrict__ b, const TC* __restrict__ dinv,
-                 TC omega, TC dfix) {
+                 TC omega, TC dfix, bool clean) {
+  // clean: x is zero on every fixed DOF, so the input masks are not loaded
+  // (the fixed rows' outputs are still set from the node masks)
   using TE = typename std::conditional<(sizeof(TY) > sizeof(TC)), double, TC>::type;
   constexpr bool GAL1 = OP == OPK_GAL1;
   __shared__ TC part[2][4][WY][WX][3];
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(WX * WY, (OP == OPK_GAL1 && sizeof(TC) == 4) ?
       const int i = ex + (q & 1), j = ey + (q >> 1);
       if (col_ok && kz >= 0 && kz < g.nnz) {
         const long long nd = i + (long long)g.nnx * j + plane * kz;
-        rmask |= ((unsigned)mask[nd] & 7u) << (3 * q);
+        if (!clean) rmask |= ((unsigned)mask[nd] & 7u) << (3 * q);
 #pragma unroll
         for (int c = 0; c < 3; ++c) raw[q][c] = x[3 * nd + c];
       } else {
@@ -609,7 +611,7 @@ static cudaError_t run_col(const ApplyArgs& a, cudaStream_t s) {
   return launch_pdl(k_apply3_col<TC, TX, TY, EPI, OP>, grid, dim3(WX * WY), 0, s, a.g, a.gf, a.mask,
                     kb, static_cast<const TC*>(a.coef), zc, static_cast<const TX*>(a.x),
                     static_cast<TY*>(a.y), static_cast<const TX*>(a.b),
-                    static_cast<const TC*>(a.dinv), TC(a.omega), TC(a.dfix));
+                    static_cast<const TC*>(a.dinv), TC(a.omega), TC(a.dfix), a.clean_inputs);
 }
 
 template <typename TC, typename TX, typename TY, int OP>

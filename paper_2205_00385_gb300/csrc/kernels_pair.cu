@@ -111,6 +111,7 @@ struct PairArgs {
   const float* b;
   const float* dinv;
   float omega, dfix;
+  bool clean_inputs;       // x (and, fused, b) zero on every fixed DOF
 };
 
 // Face tile of a block of PX x PY threads: (2 PX + 1) x (PY + 1) nodes,
@@ -143,11 +144,16 @@ struct PairSmem {
   float4 pub[2][4][PY][PX];
 };
 
-template <int EPI, bool MASKED, int PY>
+// MODE 0: no fixed DOF in the block's columns; 1: inputs and outputs masked
+// (M K M x + dfix (I - M) x for any x); 2: outputs only, for inputs that are
+// zero on the fixed DOFs (the solver's own vectors), where masking the input
+// values changes nothing and only the fixed rows' outputs need setting.
+template <int EPI, int MODE, int PY>
 __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb,
                                           PairSmem<PY>& sm) {
   using G = PairGeo<PY>;
   constexpr int POY = G::POY, FNY = G::FNY, FTILE = G::FTILE;
+  constexpr bool MASKED = MODE == 1, MASK_OUT = MODE != 0;
   const GridP& g = a.g;
   const int tid = threadIdx.x;
   const int tx = tid % PX, ty = tid / PX;
@@ -328,11 +334,11 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb,
       for (int m = 0; m < 2; ++m) {
         if (m == 1 && !own2) break;
         const long long nd = nd0 + m;
-        const unsigned mk = MASKED ? (unsigned)a.mask[nd] : 0u;
+        const unsigned mk = MASK_OUT ? (unsigned)a.mask[nd] : 0u;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const long long d = 3 * nd + c;
-          const float Ax = (MASKED && ((mk >> c) & 1u)) ? a.dfix * a.x[d] : s[m][c];
+          const float Ax = (MASK_OUT && ((mk >> c) & 1u)) ? a.dfix * a.x[d] : s[m][c];
           if (EPI == EPI_APPLY) {
             a.y[d] = Ax;
           } else if (EPI == EPI_RESID) {
@@ -372,10 +378,12 @@ __global__ void __launch_bounds__(PX * PY, MINB)
   pdl_wait();
   // all threads of a block must take the same branch (both contain
   // __syncthreads), so the decision is block-wide
-  if (__syncthreads_or(flag))
-    pair_loop<EPI, true, PY>(a, kb, sm);
+  if (!__syncthreads_or(flag))
+    pair_loop<EPI, 0, PY>(a, kb, sm);
+  else if (a.clean_inputs)
+    pair_loop<EPI, 2, PY>(a, kb, sm);
   else
-    pair_loop<EPI, false, PY>(a, kb, sm);
+    pair_loop<EPI, 1, PY>(a, kb, sm);
   pdl_launch_dependents();
 }
 
@@ -483,6 +491,7 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   p.dinv = static_cast<const float*>(a.dinv);
   p.omega = (float)a.omega;
   p.dfix = (float)a.dfix;
+  p.clean_inputs = a.clean_inputs;
   const int var = a.variant ? 1 : 0;
   const int poy = var ? PairGeo<16>::POY : PairGeo<8>::POY;
   const int gx = (a.g.nnx + POX - 1) / POX, gy = (a.g.nny + poy - 1) / poy;

@@ -679,6 +679,28 @@ cudaError_t launch_vconvert(long long n, int tin, const void* in, int tout, void
   return cudaGetLastError();
 }
 
+// x[dim node + c] = 0 where DOF c of the node is fixed; one thread per node
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_zero_fixed(long long nn, int dim, const uint8_t* __restrict__ mask, S* __restrict__ x) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  const unsigned m = mask[node];
+  if (!m) return;
+  for (int c = 0; c < dim; ++c)
+    if ((m >> c) & 1u) x[dim * node + c] = S{};
+}
+
+cudaError_t launch_zero_fixed(long long nn, int dim, const uint8_t* mask, int vt, void* x,
+                              cudaStream_t s) {
+  if (nn <= 0) return cudaSuccess;
+  if (vt == V_DF2)
+    k_zero_fixed<float2><<<nblocks(nn, 256), 256, 0, s>>>(nn, dim, mask, (float2*)x);
+  else
+    k_zero_fixed<double><<<nblocks(nn, 256), 256, 0, s>>>(nn, dim, mask, (double*)x);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vscale_inv_sqrt(long long n, int vt, void* a, const double* s2,
                                    cudaStream_t s) {
   if (vt == V_DF2)

@@ -841,8 +841,11 @@ static double vbytes_coarse(long long nc, int ta, int t) {
          2.0 * (t == T_F64 ? 8.0 : 4.0) * (double)nc;
 }
 
+// clean: the right-hand side is zero on every fixed DOF (the solver's CG
+// residual), so the finest level's vectors are too and its float32 operator
+// needs to mask only the fixed rows' outputs.
 static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int zt,
-                        bool pre = false) {
+                        bool pre = false, bool clean = false) {
   cudaStream_t s = c->stream;
   const int t = mg_t(c);
   const int L = c->L;
@@ -857,8 +860,9 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
   }
   to_status st;
   {
-    const ApplyArgs a = fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
-                                  EPI_RESID);
+    ApplyArgs a = fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
+                            EPI_RESID);
+    a.clean_inputs = clean;
     vb += apply_bytes(a);
     if ((st = run_op(c, a, "resid 0")) != TO_OK) return st;
   }
@@ -878,7 +882,8 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
   }
   for (int l = 1; l < L - 1; ++l) {
     if (lf && l >= lf) break;
-    const ApplyArgs a = coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID);
+    ApplyArgs a = coarse_args(c, l, lv[l].z, lv[l].r, lv[l].b, EPI_RESID);
+    a.clean_inputs = clean;
     vb += apply_bytes(a);
     if ((st = run_op(c, a, "resid l")) != TO_OK) return st;
     if (lf && l + 1 == lf) break;
@@ -917,15 +922,17 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
     LAUNCH(c, launch_prolong_add(c->dim, t, lv[l].g, lv[l].mask, lv[l + 1].g, lv[l + 1].z2,
                                  lv[l].z, s), "prolong l");
     vb += vbytes_prolong(lv[l].n, lv[l + 1].n, t);
-    const ApplyArgs a = coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH);
+    ApplyArgs a = coarse_args(c, l, lv[l].z, lv[l].z2, lv[l].b, EPI_SMOOTH);
+    a.clean_inputs = clean;
     vb += apply_bytes(a);
     if ((st = run_op(c, a, "postsmooth l")) != TO_OK) return st;
   }
   LAUNCH(c, launch_prolong_add(c->dim, t, lv[0].g, lv[0].mask, lv[1].g, lv[1].z2, lv[0].z, s),
          "prolong 0");
   vb += vbytes_prolong(lv[0].n, lv[1].n, t);
-  const ApplyArgs a = fine_args(c, TO_OP_K, t, t, zt, lv[0].z, zout, lv[0].b, lv[0].dinv,
-                                EPI_SMOOTH);
+  ApplyArgs a = fine_args(c, TO_OP_K, t, t, zt, lv[0].z, zout, lv[0].b, lv[0].dinv,
+                          EPI_SMOOTH);
+  a.clean_inputs = clean;
   vb += apply_bytes(a);
   ps.bytes = vb;
   c->vcycle_bytes = vb;
@@ -958,7 +965,7 @@ static to_status vcycle_graphed(to_ctx* c, const void* rin, int rin_t, void* zou
     to_status st = TO_OK;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      st = vcycle(c, rin, rin_t, zout, zt, pre);
+      st = vcycle(c, rin, rin_t, zout, zt, pre, true);
       const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
       if (e == cudaSuccess) e = e2;
     }
@@ -1159,10 +1166,17 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   const bool mixed = c->mixed;
   double* x = mixed ? c->z : u;
   const bool warm = (flags & TO_SOLVE_WARM_START) != 0;
-  if (mixed && warm)
+  if (mixed && warm) {
     LAUNCH(c, launch_vconvert(n, V_F64, u, V_DF2, x, s), "split u");
-  else if (!warm)
+    // the solution is zero on the fixed DOFs; a warm start that is not gets
+    // those entries cleared, so that every vector of the solve is (the
+    // float32 operator relies on it)
+    LAUNCH(c, launch_zero_fixed(c->nn, c->dim, c->lv[0].mask, V_DF2, x, s), "clear fixed");
+  } else if (!warm) {
     CUDA_TRY(c, cudaMemsetAsync(x, 0, n * 8, s), "zero x");
+  } else {
+    LAUNCH(c, launch_zero_fixed(c->nn, c->dim, c->lv[0].mask, V_F64, x, s), "clear fixed");
+  }
   // r = f - K x with the float64-accurate operator (the true residual)
   auto true_residual = [&](double* rr_out) -> to_status {
     to_status e;
@@ -1217,9 +1231,10 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
         if ((st = apply_accurate_vec(c, TO_OP_K, c->p, c->t, EPI_APPLY)) != TO_OK) return st;
         LAUNCH(c, launch_convert(T_D2, T_F32, n, c->t, c->q32, s), "q to float32");
       } else if (mixed) {
-        if ((st = run_op(c, fine_args(c, TO_OP_K, T_F32, T_F32, T_F32, c->p32, c->q32, nullptr,
-                                      nullptr, EPI_APPLY), "q = K p")) != TO_OK)
-          return st;
+        ApplyArgs a = fine_args(c, TO_OP_K, T_F32, T_F32, T_F32, c->p32, c->q32, nullptr,
+                                nullptr, EPI_APPLY);
+        a.clean_inputs = true;   // p is zero on the fixed DOFs
+        if ((st = run_op(c, a, "q = K p")) != TO_OK) return st;
       }
       if (mixed) {
         LAUNCH(c, launch_dot_d2f(n, c->p, c->q32, c->partials, c->counters + C_DOT,
@@ -1231,9 +1246,10 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
                "x, r update");
         pre = true;
       } else {
-        if ((st = run_op(c, fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, c->p, c->q, nullptr,
-                                      nullptr, EPI_APPLY), "q = K p")) != TO_OK)
-          return st;
+        ApplyArgs a = fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, c->p, c->q, nullptr, nullptr,
+                                EPI_APPLY);
+        a.clean_inputs = true;   // p is zero on the fixed DOFs
+        if ((st = run_op(c, a, "q = K p")) != TO_OK) return st;
         LAUNCH(c, launch_dot(n, c->p, c->q, c->partials, c->counters + C_DOT, c->scal + S_PQ, s),
                "pq");
         LAUNCH(c, launch_cg_xr(n, x, c->r, c->p, c->q, c->scal, cur, S_PQ, S_RR, c->partials,
@@ -1444,17 +1460,20 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
                                   EPI_APPLY)
                       : fine_args(c, TO_OP_K, T_F64, T_F64, T_F64, c->p, c->q, nullptr, nullptr,
                                   EPI_APPLY);
+        a->clean_inputs = true;   // timed as the solver launches it (scratch values)
         return true;
       case TO_TUNE_OP_RESID:
       case TO_TUNE_OP_SMOOTH:
         *a = fine_args(c, TO_OP_K, t, t, t, lv[0].z, lv[0].r, lv[0].b, lv[0].dinv,
                        kind == TO_TUNE_OP_RESID ? EPI_RESID : EPI_SMOOTH);
+        a->clean_inputs = true;
         return true;
       case TO_TUNE_GAL1_RESID:
       case TO_TUNE_GAL1_SMOOTH:
         if (!c->l1_implicit) return false;
         *a = coarse_args(c, 1, lv[1].z, kind == TO_TUNE_GAL1_RESID ? lv[1].r : lv[1].z2, lv[1].b,
                          kind == TO_TUNE_GAL1_RESID ? EPI_RESID : EPI_SMOOTH);
+        a->clean_inputs = true;
         return true;
       case TO_TUNE_ACC_APPLY:
       case TO_TUNE_ACC_RESID:
