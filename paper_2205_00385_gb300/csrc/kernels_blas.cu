@@ -222,51 +222,69 @@ __global__ void k_small_chol_solve(int mmax, const int* m_dev, const double* A, 
 // basis R (m columns) equals Q Rt with Q orthonormal (kq columns) and Rt
 // kq x m; with D the column norms of R, the unit-column basis R D^-1 has the
 // singular values of A = Rt D^-1, and its left singular vectors are Q U with
-// U those of A.  One warp runs one-sided (Hestenes) Jacobi on the columns of
-// A, lane r holding row r: each rotation makes a pair of columns
-// orthogonal, until every pair is orthogonal to 1e-15 of the product of
-// their norms; the column norms are then the singular values.  Directions
+// U those of A.  One-sided (Hestenes) Jacobi on the columns of A, lane r of
+// a warp holding row r: each rotation makes a pair of columns orthogonal,
+// until every pair is orthogonal to 1e-15 of the product of their norms;
+// the column norms are then the singular values.  Directions
 // with sigma <= tau sigma_1 are dropped; the kept ones, in descending order,
 // are written to U (ld MAXB), their count to ints[I_KRED] and every
 // singular value, descending, to sig.  A column of R that is zero (norm 0)
 // contributes nothing.
-__global__ void k_small_svd_trunc(int m, const int* kq_dev, const double* Rt, const double* rn,
-                                  double tau, double* U, double* sig, int* ints) {
+__global__ void __launch_bounds__(32 * MAXB / 2)
+    k_small_svd_trunc(int m, const int* kq_dev, const double* Rt, const double* rn, double tau,
+                      double* U, double* sig, int* ints) {
   __shared__ double sA[MAXB * 32];   // column j, row r at sA[32 j + r]
   __shared__ double snrm[MAXB];
   __shared__ int sord[MAXB];
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-  const int r = threadIdx.x;
+  __shared__ int s_rot;
+  if (blockIdx.x != 0) return;
+  const int r = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int kq = min(max(*kq_dev, 0), MAXB);
   m = min(max(m, 0), MAXB);
-  for (int j = 0; j < MAXB; ++j) {
+  for (int idx = threadIdx.x; idx < MAXB * 32; idx += blockDim.x) {
+    const int j = idx >> 5, rr = idx & 31;
     double v = 0.0;
-    if (j < m && r < kq && rn[j] > 0.0) v = Rt[r + (size_t)MAXB * j] / rn[j];
-    sA[32 * j + r] = v;
+    if (j < m && rr < kq && rn[j] > 0.0) v = Rt[rr + (size_t)MAXB * j] / rn[j];
+    sA[idx] = v;
   }
-  __syncwarp();
+  __syncthreads();
   auto wsum = [](double x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
   };
+  // One-sided (Hestenes) Jacobi in parallel order: the columns are paired by
+  // the round-robin tournament (position 0 fixed, the others rotating), so
+  // each of the mm - 1 steps of a sweep rotates mm / 2 disjoint pairs at once,
+  // one warp per pair, and every pair meets once per sweep.
+  const int mm = m + (m & 1);   // an odd count gets an empty partner
   for (int sweep = 0; sweep < 60; ++sweep) {
-    bool rotated = false;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double ap = sA[32 * p + r], aq = sA[32 * q + r];
-        const double alpha = wsum(ap * ap), beta = wsum(aq * aq), gamma = wsum(ap * aq);
-        if (!(fabs(gamma) > 1e-15 * sqrt(alpha * beta))) continue;
-        rotated = true;
-        const double zeta = (beta - alpha) / (2.0 * gamma);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-        sA[32 * p + r] = c * ap - sn * aq;
-        sA[32 * q + r] = sn * ap + c * aq;
-        __syncwarp();
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int step = 0; step + 1 < mm; ++step) {
+      if (w < mm / 2) {
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mm - 1); };
+        const int a = player(w), b = player(mm - 1 - w);
+        const int p = min(a, b), q = max(a, b);
+        if (q < m) {
+          const double ap = sA[32 * p + r], aq = sA[32 * q + r];
+          const double alpha = wsum(ap * ap), beta = wsum(aq * aq), gamma = wsum(ap * aq);
+          if (fabs(gamma) > 1e-15 * sqrt(alpha * beta)) {
+            const double zeta = (beta - alpha) / (2.0 * gamma);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+            sA[32 * p + r] = c * ap - sn * aq;
+            sA[32 * q + r] = sn * ap + c * aq;
+            if (r == 0) s_rot = 1;
+          }
+        }
       }
-    if (!rotated) break;
+      __syncthreads();
+    }
+    if (!s_rot) break;
+    __syncthreads();
   }
+  if (w != 0) return;
   for (int j = 0; j < MAXB; ++j) {
     const double a = sA[32 * j + r];
     const double nj = sqrt(wsum(a * a));
@@ -372,7 +390,7 @@ cudaError_t launch_small_svd_trunc(int m, const int* kq_dev, const double* Rt, c
                                    double tau, double* U, double* sig, int* ints,
                                    cudaStream_t s) {
   if (m < 1 || m > MAXB) return cudaErrorInvalidValue;
-  k_small_svd_trunc<<<1, 32, 0, s>>>(m, kq_dev, Rt, rn, tau, U, sig, ints);
+  k_small_svd_trunc<<<1, 32 * MAXB / 2, 0, s>>>(m, kq_dev, Rt, rn, tau, U, sig, ints);
   return cudaGetLastError();
 }
 

@@ -307,25 +307,28 @@ __global__ void __launch_bounds__(MD_CH)
   if (t == 0) *counter = 0u;
 }
 
-// Column case: g[i] = sum_k A[k + i*n] b[k].  Warp i of a block accumulates
-// column i (one accumulator per lane, two indices in flight), so registers
-// stay few and many loads are outstanding; lanes, warps' results and blocks
-// are summed in a fixed order.
+// Column case: g[i] = sum_k A[k + i*n] b[k].  Warp w of a block
+// accumulates column w % na over its own share of the indices, wpc = blockDim
+// / (32 na) warps per column (more warps for few columns, so that a launch
+// with one or two columns still keeps enough loads outstanding); one
+// accumulator set per lane, four indices in flight.  Lanes, the warps of a
+// column, and blocks are summed in a fixed order.
 template <typename S>
 __global__ void __launch_bounds__(32 * MAXB)
     k_gram_col(long long n, const S* __restrict__ A, int na, const int* na_dev,
                const S* __restrict__ b, double* g, double* partials, unsigned* counter) {
   using Rg = Ar<S>;
   using V = typename Rg::T;
-  __shared__ double sh[MAXB];
+  __shared__ double sh[32 * MAXB / 32];
   __shared__ bool s_last;
   const int ma = na_dev ? min(max(*na_dev, 0), na) : na;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int wpc = nw / na, ci = wi % na, sub = wi / na;
   V acc = Rg::zero(), acc2 = Rg::zero();
-  if (wi < ma) {
-    const S* col = A + (size_t)wi * n;
-    const long long stride = (long long)gridDim.x * 32;
-    long long k = (long long)blockIdx.x * 32 + lane;
+  if (ci < ma) {
+    const S* col = A + (size_t)ci * n;
+    const long long stride = (long long)gridDim.x * wpc * 32;
+    long long k = ((long long)blockIdx.x * wpc + sub) * 32 + lane;
     V acc3 = Rg::zero(), acc4 = Rg::zero();
     for (; k + 3 * stride < n; k += 4 * stride) {
       const V a0 = Rg::ld(col, k), b0 = Rg::ld(b, k);
@@ -342,10 +345,12 @@ __global__ void __launch_bounds__(32 * MAXB)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc = Rg::add(acc, Rg::shfl_down(acc, o));
   }
-  if (lane == 0) sh[wi] = wi < ma ? Rg::to_d(acc) : 0.0;
+  if (lane == 0) sh[wi] = ci < ma ? Rg::to_d(acc) : 0.0;
   __syncthreads();
   if ((int)threadIdx.x < MAXB) {
-    const double v = (int)threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    double v = 0.0;
+    if ((int)threadIdx.x < na)
+      for (int u = 0; u < wpc; ++u) v += sh[u * na + threadIdx.x];
     partials[(size_t)blockIdx.x * MAXB + threadIdx.x] = v;
   }
   __threadfence();
@@ -721,10 +726,11 @@ static void gram_t(long long n, const void* A, int na, const int* na_dev, const 
     cudaFuncSetAttribute(k_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * 2 * MAXB * MD_CH * sizeof(S)));
   });
-  if (nb == 1 && nb_dev == nullptr && !sym)
-    k_gram_col<S><<<RED_BLOCKS, 32 * na, 0, s>>>(n, (const S*)A, na, na_dev, (const S*)B, G,
-                                                 partials, counter);
-  else
+  if (nb == 1 && nb_dev == nullptr && !sym) {
+    const int wpc = na >= 8 ? 1 : 8 / na;   // warps per column
+    k_gram_col<S><<<RED_BLOCKS, 32 * na * wpc, 0, s>>>(n, (const S*)A, na, na_dev,
+                                                       (const S*)B, G, partials, counter);
+  } else
     k_gram<S><<<RED_BLOCKS, MD_CH, (size_t)2 * (na + nb) * MD_CH * sizeof(S), s>>>(
         n, (const S*)A, na, na_dev, (const S*)B, nb, nb_dev, G, ldg, partials, counter, sym);
 }
@@ -824,7 +830,7 @@ cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double
 // Each thread loads the kq entries of one index once and forms all k
 // outputs; U sits in shared memory.
 template <typename S, int KQ>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_combine_multi(long long n, const S* __restrict__ Q, int kq, const double* __restrict__ U,
                     int k, S* __restrict__ Y) {
   using Rg = Ar<S>;
@@ -840,13 +846,20 @@ __global__ void __launch_bounds__(256)
     V q[KQ];
 #pragma unroll
     for (int i = 0; i < KQ; ++i) q[i] = i < kq ? Rg::ld(Q + (size_t)i * n, idx) : Rg::zero();
-    for (int j = 0; j < k; ++j) {
-      V acc = Rg::zero();
+    // the k outputs' sums advance together (independent chains), each over
+    // i = 0 .. kq-1 in order
+    V acc[KQ];
 #pragma unroll
-      for (int i = 0; i < KQ; ++i)
-        if (i < kq) acc = Rg::fma3(su[i + KQ * j], q[i], acc);
-      Rg::st(Y + (size_t)j * n, idx, acc);
-    }
+    for (int j = 0; j < KQ; ++j) acc[j] = Rg::zero();
+#pragma unroll
+    for (int i = 0; i < KQ; ++i)
+      if (i < kq)
+#pragma unroll
+        for (int j = 0; j < KQ; ++j)
+          if (j < k) acc[j] = Rg::fma3(su[i + KQ * j], q[i], acc[j]);
+#pragma unroll
+    for (int j = 0; j < KQ; ++j)
+      if (j < k) Rg::st(Y + (size_t)j * n, idx, acc[j]);
   }
 }
 
