@@ -830,7 +830,7 @@ cudaError_t launch_gs_accept(long long n, int vt, void* R, int src, const double
 // Each thread loads the kq entries of one index once and forms all k
 // outputs; U sits in shared memory.
 template <typename S, int KQ>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256)
     k_combine_multi(long long n, const S* __restrict__ Q, int kq, const double* __restrict__ U,
                     int k, S* __restrict__ Y) {
   using Rg = Ar<S>;
@@ -846,20 +846,13 @@ __global__ void __launch_bounds__(256, 2)
     V q[KQ];
 #pragma unroll
     for (int i = 0; i < KQ; ++i) q[i] = i < kq ? Rg::ld(Q + (size_t)i * n, idx) : Rg::zero();
-    // the k outputs' sums advance together (independent chains), each over
-    // i = 0 .. kq-1 in order
-    V acc[KQ];
+    for (int j = 0; j < k; ++j) {
+      V acc = Rg::zero();
 #pragma unroll
-    for (int j = 0; j < KQ; ++j) acc[j] = Rg::zero();
-#pragma unroll
-    for (int i = 0; i < KQ; ++i)
-      if (i < kq)
-#pragma unroll
-        for (int j = 0; j < KQ; ++j)
-          if (j < k) acc[j] = Rg::fma3(su[i + KQ * j], q[i], acc[j]);
-#pragma unroll
-    for (int j = 0; j < KQ; ++j)
-      if (j < k) Rg::st(Y + (size_t)j * n, idx, acc[j]);
+      for (int i = 0; i < KQ; ++i)
+        if (i < kq) acc = Rg::fma3(su[i + KQ * j], q[i], acc);
+      Rg::st(Y + (size_t)j * n, idx, acc);
+    }
   }
 }
 
