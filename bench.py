@@ -63,7 +63,7 @@ def _args():
     ap.add_argument("--tensor-cores", action="store_true",
                     help="finest-grid float32 operator on the tensor cores (tcgen05)")
     ap.add_argument("--small", action="store_true", help="48x24x24 instead (quick checks)")
-    ap.add_argument("--config4", action="store_true",
+    ap.add_argument("--bridge320", action="store_true",
                     help="with --kernel: the 320x160x160 bridge (24.96M DOFs) instead")
     ap.add_argument("--fused-coarse", action="store_true",
                     help="with --kernel vcycle: the coarse levels as one cluster launch")
@@ -78,14 +78,14 @@ def _args():
 
 
 def _problem(args):
-    from workloads import config3_cantilever3d, config4_bridge3d, cantilever3d
-    if getattr(args, "config4", False):
-        return config4_bridge3d()
+    from workloads import cantilever3d_192x96x96, bridge3d_320x160x160, cantilever3d
+    if getattr(args, "bridge320", False):
+        return bridge3d_320x160x160()
     if args.small:
         return cantilever3d(48, 24, 24, volfrac=0.12, rmin=2.0, n_iter=30, mg_levels=4,
                             precision=args.precision, n_parm=10, n_carm=10, n_on=15,
                             eps_tol=1e-3, rtol=1e-8, maxit=200)
-    return config3_cantilever3d(args.precision)
+    return cantilever3d_192x96x96(args.precision)
 
 
 # ---------------------------------------------------------------------------
@@ -467,8 +467,8 @@ def run_ours(args):
     }
     if args.serve_jobs > 0 and ws == 1:
         from paper_2205_00385_gb300.serve import Server
-        from workloads import config5_jobs
-        jobs = config5_jobs()[:args.serve_jobs]
+        from workloads import served_job_stream
+        jobs = served_job_stream()[:args.serve_jobs]
         rep = Server(int(120 * 2 ** 30), max_active=16).run(jobs, args.serve_iters,
                                                           args.serve_time_scale)
         line["serving"] = {

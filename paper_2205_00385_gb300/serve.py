@@ -321,7 +321,7 @@ Server = BatchServer
 
 def main():
     import torch
-    from workloads import config5_jobs
+    from workloads import served_job_stream
     ap = argparse.ArgumentParser(description="Replay the served stream of optimisation jobs")
     ap.add_argument("--jobs", type=int, default=256)
     ap.add_argument("--iters", type=int, default=30)
@@ -331,7 +331,7 @@ def main():
     ap.add_argument("--precision", default="workload", choices=["workload", "mixed", "fp64"])
     a = ap.parse_args()
     torch.cuda.set_device(0)
-    jobs = config5_jobs()[:a.jobs]
+    jobs = served_job_stream()[:a.jobs]
     ap2 = a
     srv = BatchServer(int(ap2.budget_gb * 2 ** 30), ap2.max_active,
                       precision=None if ap2.precision == "workload" else ap2.precision)

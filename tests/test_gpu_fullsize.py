@@ -39,7 +39,7 @@ import pytest
 
 from gpu_helpers import Ctx, dev, host
 from oracle import aarmr, fe, filters, oc, reanalysis, sensitivity, solvers
-from workloads import (config2_cantilever3d, config3_cantilever3d, config4_bridge3d,
+from workloads import (cantilever3d_48x24x24, cantilever3d_192x96x96, bridge3d_320x160x160,
                        rand_density, rand_vector, smooth_fields)
 
 # the CARM parity tolerances of the small-grid tests, which depend on the
@@ -68,7 +68,7 @@ def design48():
     """Physical density of the oracle's 48 x 24 x 24 cantilever after 8
     design iterations with MGCG solves: a mid-optimisation design (about a
     third of the elements below 0.05, a few percent above 0.5)."""
-    p = config2_cantilever3d()
+    p = cantilever3d_48x24x24()
     t = aarmr.run(p, n_iter=8, mode="mgcg", snapshot_at=(8,))
     return t.snapshots[8]["rho_phys"]
 
@@ -85,7 +85,7 @@ def _upsample(rho, nelx, nely, nelz, k):
 
 def test_cantilever48_fp64_mgcg_against_oracle(design48):
     B = _B()
-    p = config2_cantilever3d()
+    p = cantilever3d_48x24x24()
     g, KE = _model(p)
     E = _E(p, design48)
     K = fe.stiffness(g, E, KE, p.fixed)
@@ -110,7 +110,7 @@ def test_cantilever48_fp64_mgcg_against_oracle(design48):
 
 def test_cantilever192_stiffness_products():
     B = _B()
-    p = config3_cantilever3d("mixed")
+    p = cantilever3d_192x96x96("mixed")
     g, KE = _model(p)
     r_prev = rand_density(g.nel, 41, 0.0, 1.0)
     r_now = np.clip(r_prev + rand_density(g.nel, 42, -0.2, 0.2), 0.0, 1.0)
@@ -138,7 +138,7 @@ def test_cantilever192_stiffness_products():
 def test_cantilever192_filter_sensitivity_oc():
     B = _B()
     fabs_tol = 1e-14
-    p = config3_cantilever3d("mixed")
+    p = cantilever3d_192x96x96("mixed")
     g, KE = _model(p)
     H, Hs = filters.filter_matrix(g, p.rmin)
     rho = rand_density(g.nel, 44, 0.0, 2.0 * p.volfrac)
@@ -183,7 +183,7 @@ def test_cantilever192_mgcg_solution(design48):
     float64 one (the float64 path is pinned to the oracle at 1e-10 on the
     smaller grids)."""
     B = _B()
-    p = config3_cantilever3d("mixed")
+    p = cantilever3d_192x96x96("mixed")
     g, KE = _model(p)
     rho = _upsample(design48, 48, 24, 24, 4)
     E = _E(p, rho)
@@ -255,7 +255,7 @@ def test_cantilever192_carm_parity():
     """
     from carm_cases import refine_element_field, refine_nodal_field, snapshot_48_s10
     B = _B()
-    p = config3_cantilever3d("mixed")
+    p = cantilever3d_192x96x96("mixed")
     g, KE = _model(p)
     p48, snap, _ = snapshot_48_s10()
     shape48 = (p48.nelx, p48.nely, p48.nelz)
@@ -307,7 +307,7 @@ def test_cantilever192_carm_parity():
 
 def test_bridge320_largest_workload():
     B = _B()
-    p = config4_bridge3d()
+    p = bridge3d_320x160x160()
     g, KE = _model(p)
     rng = np.random.default_rng(48)
     rows = rng.choice(g.ndof, 1 << 16, replace=False)

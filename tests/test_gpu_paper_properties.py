@@ -19,7 +19,7 @@ This file runs last (it is the newest).
 import pytest
 
 from oracle import aarmr
-from workloads import config1_mbb2d
+from workloads import mbb2d_60x20
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ N_ITER = 40
 
 
 def _problem(ns, nm):
-    return config1_mbb2d().with_(n_parm=ns, n_carm=nm, n_on=12, eps_tol=0.3)
+    return mbb2d_60x20().with_(n_parm=ns, n_carm=nm, n_on=12, eps_tol=0.3)
 
 
 def _gpu_history(p):

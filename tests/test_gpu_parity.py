@@ -444,10 +444,10 @@ def _compare_trajectories(p, n_iter, rel_c):
     return hist, ref, rho
 
 
-def test_design_loop_config1_mbb2d_fp64():
+def test_design_loop_mbb2d_60x20_fp64():
     """The 2D MBB workload (60 x 20, 50 iterations, s = 6) end to end."""
-    from workloads import config1_mbb2d
-    p = config1_mbb2d()
+    from workloads import mbb2d_60x20
+    p = mbb2d_60x20()
     hist, ref, rho = _compare_trajectories(p, p.n_iter, 1e-6)
     assert np.max(np.abs(rho - ref.rho)) < 1e-3
 

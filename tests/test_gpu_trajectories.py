@@ -2,8 +2,8 @@
 (Algorithm 1 in the design loop of Fig. 1: 40 iterations, s = 8, N_on = 20,
 eps_tol = 1e-3) on the GPU against the oracle's trajectory.
 
-The oracle's trajectory is stored in tests/golden/config2_trajectory.json,
-written by tests/golden/make_config2_trajectory.py, which calls only the
+The oracle's trajectory is stored in tests/golden/cantilever48_trajectory.json,
+written by tests/golden/make_cantilever48_trajectory.py, which calls only the
 oracle (about four minutes of host work, so it is not rerun here).
 
 Checked per iteration: the branch of Algorithm 1, the compliance, the CARM
@@ -23,12 +23,12 @@ import os
 import numpy as np
 import pytest
 
-from workloads import config2_cantilever3d
+from workloads import cantilever3d_48x24x24
 
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
-                      "config2_trajectory.json")
+                      "cantilever48_trajectory.json")
 # MGCG iteration counts: the float64 path runs the oracle's algorithm (one
 # iteration apart where the residual crosses rtol between the two); the
 # mixed path's float32 V-cycle is a different preconditioner, whose counts
@@ -44,10 +44,10 @@ def _iters_ok(precision, it, it_ref):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_design_loop_config2_cantilever48(precision):
+def test_design_loop_cantilever48(precision):
     from paper_2205_00385_gb300.driver import TopoSolver
     ref = json.load(open(GOLDEN))["history"]
-    p = config2_cantilever3d()
+    p = cantilever3d_48x24x24()
     s = TopoSolver(p, precision=precision)
     try:
         hist = s.run(p.n_iter)
@@ -60,7 +60,7 @@ def test_design_loop_config2_cantilever48(precision):
         worst["C"] = max(worst["C"], abs(h.compliance - r["compliance"]) / r["compliance"])
         if r["eps"] is not None:
             worst["eps"] = max(worst["eps"], abs(h.eps - r["eps"]) / r["eps"])
-    print(f"[trajectory config2 {precision}] worst {worst} iters "
+    print(f"[trajectory cantilever48 {precision}] worst {worst} iters "
           f"{[(h.cg_iters, r['cg_iters']) for h, r in zip(hist, ref)]}")
     assert all(h.converged for h in hist), [h.k for h in hist if not h.converged]
     assert all(_iters_ok(precision, h.cg_iters, r["cg_iters"]) for h, r in zip(hist, ref))

@@ -13,7 +13,7 @@ from workloads import rand_density, rand_vector, small_problem
 pytestmark = pytest.mark.gpu
 
 # (problem, levels): 2D fuses from level 1, 3D (level 1 implicit) from level 2;
-# the 48 x 24 x 24 grid is the config-2 hierarchy; in the 128 x 64 x 64 one
+# the 48 x 24 x 24 grid is the 4-level cantilever hierarchy; in the 128 x 64 x 64 one
 # level 2 (32 x 16 x 16) is too large to join (its stencil is above the size
 # limit), so the stretch starts at level 3
 CASES = [

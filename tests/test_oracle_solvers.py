@@ -286,8 +286,8 @@ def test_basis_sizes_the_paper_reports_as_overlapping():
     in span{phi_1}, which holds u_last (the last MGCG solution, or a Galerkin
     multiple of it).  The three design trajectories, with CARM accepted
     repeatedly, must coincide: same branches, compliances equal to rounding."""
-    from workloads import config1_mbb2d
-    base = config1_mbb2d()
+    from workloads import mbb2d_60x20
+    base = mbb2d_60x20()
     runs = {}
     for ns, nm in ((1, 1), (1, 10), (10, 1)):
         p = base.with_(n_parm=ns, n_carm=nm, n_on=12, eps_tol=0.3)

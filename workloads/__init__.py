@@ -10,11 +10,11 @@ sharing any computation.
 from .problems import (  # noqa: F401
     Problem,
     Job,
-    config1_mbb2d,
-    config2_cantilever3d,
-    config3_cantilever3d,
-    config4_bridge3d,
-    config5_jobs,
+    mbb2d_60x20,
+    cantilever3d_48x24x24,
+    cantilever3d_192x96x96,
+    bridge3d_320x160x160,
+    served_job_stream,
     cantilever3d,
     bridge3d,
     mbb2d,

@@ -312,27 +312,27 @@ def study_beam(nelx: int, nely: int, nelz: int, eps_tol: float, n_iter: int = 10
 # levels limited by 2x coarsening).
 # --------------------------------------------------------------------------
 
-def config1_mbb2d() -> Problem:
+def mbb2d_60x20() -> Problem:
     """2D MBB half-beam, 60 x 20 Q4 (2,562 DOFs), FP64, s = 6."""
     return mbb2d(60, 20, volfrac=0.5, rmin=1.5, n_iter=50, mg_levels=3, precision="fp64",
                  n_parm=6, n_carm=6, n_on=20, eps_tol=1e-3, rtol=1e-8, maxit=200)
 
 
-def config2_cantilever3d() -> Problem:
+def cantilever3d_48x24x24() -> Problem:
     """3D cantilever, 48 x 24 x 24 hex8 (91,875 DOFs), FP64, 4 levels, s = 8."""
     return cantilever3d(48, 24, 24, volfrac=0.12, rmin=1.5, n_iter=40, mg_levels=4,
                         precision="fp64", n_parm=8, n_carm=8, n_on=20, eps_tol=1e-3,
                         rtol=1e-8, maxit=200)
 
 
-def config3_cantilever3d(precision: str = "mixed") -> Problem:
+def cantilever3d_192x96x96(precision: str = "mixed") -> Problem:
     """3D cantilever, 192 x 96 x 96 hex8 (5,447,811 DOFs), 6 levels, s = 10."""
     return cantilever3d(192, 96, 96, volfrac=0.12, rmin=2.0, n_iter=30, mg_levels=6,
                         precision=precision, n_parm=10, n_carm=10, n_on=15, eps_tol=1e-3,
                         rtol=1e-8, maxit=200)
 
 
-def config4_bridge3d() -> Problem:
+def bridge3d_320x160x160() -> Problem:
     """3D MBB bridge, 320 x 160 x 160 hex8 (24,961,923 DOFs), mixed, s = 10,
     6 levels (2x coarsening allows no more), seeded +-0.05 initial noise."""
     return bridge3d(320, 160, 160, volfrac=0.10, rmin=2.5, noise=0.05, seed=2205, n_iter=20,
@@ -350,7 +350,7 @@ class Job:
     problem: Problem
 
 
-def config5_jobs(n_jobs: int = 256, rate_per_s: float = 4.0, seed: int = 385,
+def served_job_stream(n_jobs: int = 256, rate_per_s: float = 4.0, seed: int = 385,
                  n_iter: int = 30) -> List[Job]:
     """Served stream: Poisson arrivals (mean rate 4 jobs/s), cantilever or
     bridge 50/50, mesh uniform over four sizes, volfrac U[0.08, 0.3],
