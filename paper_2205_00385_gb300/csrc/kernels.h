@@ -124,10 +124,12 @@ cudaError_t launch_diag(int dim, const GridP& g, const uint8_t* mask, int tc, bo
 
 // ---- multigrid transfer and Galerkin operators (kernels_mg.cu) ----
 // b_c = Pm^T r_f; when zc is not null also the coarse level's smoothing from
-// a zero guess, zc = omega * dinvc * b_c
+// a zero guess, zc = omega * dinvc * b_c.  clean: r_f is zero on every fixed
+// DOF (the fine masks are then not read; same result)
 cudaError_t launch_restrict(int dim, int t, const GridP& gf, const uint8_t* maskf,
                             const GridP& gc, const uint8_t* maskc, const void* rf, void* bc,
-                            const void* dinvc, double omega, void* zc, cudaStream_t s);
+                            const void* dinvc, double omega, void* zc, bool clean,
+                            cudaStream_t s);
 cudaError_t launch_prolong_add(int dim, int t, const GridP& gf, const uint8_t* maskf,
                                const GridP& gc, const void* zc, void* zf, cudaStream_t s);
 // z = omega * dinv * b (smoothing from a zero initial guess); if bout != 0 the

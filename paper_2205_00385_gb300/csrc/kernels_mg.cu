@@ -43,7 +43,9 @@ __host__ __device__ constexpr int transfer_min_blocks() {
   return sizeof(T) == 4 ? 4 : 2;   // registers for all loads in flight
 }
 
-template <int DIM, typename T>
+// CLEAN: r_f is zero on every fixed DOF (restrict_node then skips the fine
+// masks, with the same result)
+template <int DIM, typename T, bool CLEAN>
 __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
                const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc,
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
   const int K = DIM == 3 ? (int)blockIdx.z : 0;
   pdl_wait();
   if (I >= gc.nnx || J >= gc.nny) return;
-  restrict_node<DIM, T, false>(gf, maskf, gc, maskc, rf, bc, dinvc, omega, zc, I, J, K);
+  restrict_node<DIM, T, false, CLEAN>(gf, maskf, gc, maskc, rf, bc, dinvc, omega, zc, I, J, K);
   pdl_launch_dependents();
 }
 
@@ -494,21 +496,22 @@ __global__ void __launch_bounds__(256)
 template <int DIM, typename T>
 static cudaError_t restrict_t(const GridP& gf, const uint8_t* mf, const GridP& gc,
                               const uint8_t* mc, const void* rf, void* bc, const void* dinvc,
-                              double omega, void* zc, cudaStream_t s) {
+                              double omega, void* zc, bool clean, cudaStream_t s) {
   if (gc.nn <= 0) return cudaSuccess;
   dim3 grid((gc.nnx + TBX - 1) / TBX, (gc.nny + TBY - 1) / TBY, DIM == 3 ? gc.nnz : 1);
-  return launch_pdl(k_restrict<DIM, T>, grid, dim3(TBX, TBY), 0, s, gf, mf, gc, mc, (const T*)rf,
-                    (T*)bc, (const T*)dinvc, T(omega), (T*)zc);
+  auto kern = clean ? k_restrict<DIM, T, true> : k_restrict<DIM, T, false>;
+  return launch_pdl(kern, grid, dim3(TBX, TBY), 0, s, gf, mf, gc, mc, (const T*)rf, (T*)bc,
+                    (const T*)dinvc, T(omega), (T*)zc);
 }
 
 cudaError_t launch_restrict(int dim, int t, const GridP& gf, const uint8_t* mf, const GridP& gc,
                             const uint8_t* mc, const void* rf, void* bc, const void* dinvc,
-                            double omega, void* zc, cudaStream_t s) {
+                            double omega, void* zc, bool clean, cudaStream_t s) {
   if (dim == 2)
-    return t == T_F64 ? restrict_t<2, double>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s)
-                      : restrict_t<2, float>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s);
-  return t == T_F64 ? restrict_t<3, double>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s)
-                    : restrict_t<3, float>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, s);
+    return t == T_F64 ? restrict_t<2, double>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, clean, s)
+                      : restrict_t<2, float>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, clean, s);
+  return t == T_F64 ? restrict_t<3, double>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, clean, s)
+                    : restrict_t<3, float>(gf, mf, gc, mc, rf, bc, dinvc, omega, zc, clean, s);
 }
 
 template <int DIM, typename T>

@@ -167,8 +167,11 @@ __device__ __forceinline__ void restrict_finish(const GridP& gf, const GridP& gc
 // loads, so the 3^DIM masks and values take one memory round trip; the terms
 // are then summed in a fixed order.  With zc set, the coarse level is also
 // pre-smoothed from a zero guess, z = omega D^-1 b.
+// CLEAN: r_f is +-0 on every fixed DOF, so the fine masks are not loaded: a
+// fixed term then adds w * (+-0) where the masked sum adds +0, and a running
+// sum that starts at +0 is never -0, so the bits are the same.
 // ---------------------------------------------------------------------------
-template <int DIM, typename T, bool CG>
+template <int DIM, typename T, bool CG, bool CLEAN = false>
 __device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __restrict__ maskf,
                                               const GridP& gc, const uint8_t* __restrict__ maskc,
                                               const T* __restrict__ rf, T* __restrict__ bc,
@@ -187,7 +190,7 @@ __device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __
         const int j = min(max(2 * J + b - 1, 0), gf.nny - 1);
         const int k = DIM == 3 ? min(max(2 * K + a - 1, 0), gf.nnz - 1) : 0;
         const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
-        m[a][b][q] = maskf[fn];
+        m[a][b][q] = CLEAN ? 0u : (unsigned)maskf[fn];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[a][b][q][c] = ldv<CG>(rf + DIM * fn + c);
       }
@@ -197,32 +200,34 @@ __device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __
 // ---------------------------------------------------------------------------
 // z_f += Pm z_c for the fine nodes (i, j, 2q) and (i, j, 2q + 1) (3D; one
 // node in 2D): each interpolates from coarse nodes floor(./2) .. ceil(./2)
-// per axis.  The coarse values of planes q and q + 1 and the fine values are
-// all loaded (clamped into the grid) before any sum, and each fine node then
-// sums its own terms in a fixed order.
+// per axis, i.e. from 2 parents along an axis where its index is odd and 1
+// where it is even.  Only the parents that exist are loaded (the y parity
+// and the z position are uniform over a warp of the one-kernel path, the x
+// parity is per lane), all before any sum, together with the fine values;
+// each fine node then sums its parents' terms in a fixed order.
 // ---------------------------------------------------------------------------
 // The interpolated value at fine node (i, j, k), one component: its own
 // value zv plus the weighted coarse values cv[a][bb][cc] at coarse nodes
-// (i/2 + cc, j/2 + bb, k/2 + a), summed in a fixed order over the parents
-// the node interpolates from (cv entries of other positions are ignored).
+// (i/2 + cc, j/2 + bb, k/2 + a), summed over the parents the node
+// interpolates from with a (z) outermost and cc (x) innermost; the entries
+// of other positions are not read.
 template <int DIM, typename T>
 __device__ __forceinline__ T prolong_one(T zv, const T (&cv)[DIM == 3 ? 2 : 1][2][2], int i, int j,
                                          int k) {
   constexpr int NK = DIM == 3 ? 2 : 1;
-  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
-  const int nk = (DIM == 3 && (k & 1)) ? 2 : 1;
-  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
-  const T w = mul_rn(mul_rn(wx, wy), (DIM == 3 && (k & 1)) ? T(0.5) : T(1));
+  const bool xo = i & 1, yo = j & 1, zo = DIM == 3 && (k & 1);
+  const T w = mul_rn(mul_rn(xo ? T(0.5) : T(1), yo ? T(0.5) : T(1)), zo ? T(0.5) : T(1));
   T acc = T(0);
 #pragma unroll
-  for (int a = 0; a < NK; ++a)
+  for (int a = 0; a < NK; ++a) {
+    if (a == 1 && !zo) break;
 #pragma unroll
-    for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const bool use = a < nk && bb < nj && cc < ni;
-        acc = add_rn(acc, use ? mul_rn(w, cv[a][bb][cc]) : T(0));
-      }
+    for (int bb = 0; bb < 2; ++bb) {
+      if (bb == 1 && !yo) break;
+      acc = add_rn(acc, mul_rn(w, cv[a][bb][0]));
+      if (xo) acc = add_rn(acc, mul_rn(w, cv[a][bb][1]));
+    }
+  }
   return add_rn(zv, acc);
 }
 
@@ -232,6 +237,8 @@ __device__ __forceinline__ void prolong_pair(const GridP& gf, const uint8_t* __r
                                              T* __restrict__ zf, int i, int j, int q) {
   constexpr int NK = DIM == 3 ? 2 : 1;   // fine nodes per item along z
   const int i0 = i >> 1, j0 = j >> 1;
+  const bool xo = i & 1, yo = j & 1;
+  const bool second = DIM == 3 && 2 * q + 1 < gf.nnz;   // node (i, j, 2q + 1) exists
   T cv[DIM][NK][2][2];
 #pragma unroll
   for (int a = 0; a < NK; ++a)
@@ -239,26 +246,25 @@ __device__ __forceinline__ void prolong_pair(const GridP& gf, const uint8_t* __r
     for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
-        const int ic = min(i0 + cc, gc.nnx - 1), jc = min(j0 + bb, gc.nny - 1);
-        const int kc = DIM == 3 ? min(q + a, gc.nnz - 1) : 0;
-        const long long cn = ic + (long long)gc.nnx * (jc + (long long)gc.nny * kc);
+        const bool need = (a == 0 || second) && (bb == 0 || yo) && (cc == 0 || xo);
+        const long long cn = (i0 + cc) + (long long)gc.nnx * ((j0 + bb) + (long long)gc.nny * (q + a));
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) cv[c][a][bb][cc] = ldv<CG>(zc + DIM * cn + c);
+        for (int c = 0; c < DIM; ++c) cv[c][a][bb][cc] = need ? ldv<CG>(zc + DIM * cn + c) : T(0);
       }
   unsigned m[NK];
   T zv[NK][DIM];
 #pragma unroll
   for (int s = 0; s < NK; ++s) {
-    const int k = DIM == 3 ? min(2 * q + s, gf.nnz - 1) : 0;
-    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+    if (s == 1 && !second) break;
+    const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * (2 * q + s));
     m[s] = maskf[node];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) zv[s][c] = ldv<CG>(zf + DIM * node + c);
   }
 #pragma unroll
   for (int s = 0; s < NK; ++s) {
+    if (s == 1 && !second) break;
     const int k = DIM == 3 ? 2 * q + s : 0;
-    if (DIM == 3 && k >= gf.nnz) break;
     const long long node = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
 #pragma unroll
     for (int c = 0; c < DIM; ++c)

@@ -867,12 +867,14 @@ static to_status vcycle(to_ctx* c, const void* rin, int rin_t, void* zout, int z
     if ((st = run_op(c, a, "resid 0")) != TO_OK) return st;
   }
   // restriction into level l also pre-smooths level l from a zero guess
-  // (except on the coarsest level, which is solved exactly)
+  // (except on the coarsest level, which is solved exactly).  The residual of
+  // a coarse level is zero on its fixed DOFs (its right-hand side and
+  // zero-guess smoothing are), that of the finest level when the input is.
   auto restrict_into = [&](int l) {
     const bool smooth = l < L - 1;
     return launch_restrict(c->dim, t, lv[l - 1].g, lv[l - 1].mask, lv[l].g, lv[l].mask,
                            lv[l - 1].r, lv[l].b, smooth ? lv[l].dinv : nullptr, 0.6,
-                           smooth ? lv[l].z : nullptr, s);
+                           smooth ? lv[l].z : nullptr, clean || l >= 2, s);
   };
   // levels lf .. L-1 (lf = 0: none) run as one fused cluster launch
   const int lf = c->fuse_coarse ? c->vf_l0 : 0;
