@@ -444,6 +444,22 @@ def run_ours(args):
                                     "moduli or assembled stencil, right-hand side, inverse "
                                     "diagonal; transfer inputs and outputs; coarsest inverse")},
                 "other_fine_apply": {"launches": n_o, "ms": round(ms_o, 3)}}
+    if p.dim == 3 and n_f:
+        # the same kernel against the FP32 pipe, which ncu shows it is bound by
+        # (issue and FMA pipe about half busy, DRAM below a tenth)
+        nodes = (p.nelx + 1) * (p.nely + 1) * (p.nelz + 1)
+        flops = 234 * p.nel + 21 * nodes
+        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        alu_ach = flops / (avg_ms / 1e3) / 1e12
+        roofline["alu"] = {
+            "bound": "alu", "pipe": "fp32", "achieved": round(alu_ach, 2), "peak": alu_peak,
+            "unit": "TFLOP/s", "frac": round(alu_ach / alu_peak, 4),
+            "flops_per_launch": flops,
+            "flops_rule": ("234 per element (the 8-point Walsh transform of the three components "
+                           "both ways, 2 x 72 adds; E scaling, 24; the 45 non-zero Walsh-block "
+                           "entries, 24 multiplies + 21 FMAs) + 21 per node (the sums of eight "
+                           "element contributions)"),
+            "peak_rule": "152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz (maximum SM clock)"}
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": W, "ms_per_step": round(elapsed / K * 1e3, 3), "higher_is_better": True,
