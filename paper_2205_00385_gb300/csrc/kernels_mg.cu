@@ -16,21 +16,6 @@
 
 namespace topo {
 
-// 1D linear weight of coarse corner A at fine corner a of child position c
-// (positions in half coarse-element units: (c + a) / 2).
-__host__ __device__ __forceinline__ double w1d(int c, int a, int A) {
-  const double pos = 0.5 * (double)(c + a);
-  return A ? pos : 1.0 - pos;
-}
-
-template <int DIM>
-__host__ __device__ __forceinline__ double wchild(int c, int a, int A) {
-  double w = 1.0;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) w *= w1d((c >> d) & 1, (a >> d) & 1, (A >> d) & 1);
-  return w;
-}
-
 // ---------------------------------------------------------------------------
 // Restriction and interpolation kernels (bodies in mg_device.cuh).  Threads
 // are laid out on the node grid (x lanes along I, block rows along J,
@@ -197,15 +182,32 @@ __global__ void __launch_bounds__(256)
 
 // Galerkin level l+1 from stored level-l element matrices.  One block of
 // ND*ND threads per coarse element; T = Kchild W in shared memory, then
-// Kc += W^T T, summed over the 2^DIM children.
+// Kc += W^T T, summed over the 2^DIM children.  W_c[a][A], the weight of
+// coarse corner A at fine corner a of child c, is the product over the axes
+// of the linear weights (c + a) / 2 (A's bit set) or (2 - c - a) / 2 (per
+// axis bits, positions in half coarse-element units); it is staged in shared
+// memory from integer arithmetic, an integer over 2^DIM, exact in any
+// floating type.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
     k_galerkin_coarse(GridP gc, GridP gf, const T* __restrict__ Kf, T* __restrict__ Kc) {
   constexpr int ND = Geo<DIM>::ND, NPE = Geo<DIM>::NPE, NT = tri_len(ND);
   __shared__ T sK[ND * ND];
   __shared__ T sT[ND * ND];
+  __shared__ T sW[NPE * NPE * NPE];   // [child][fine corner][coarse corner]
   const long long E = blockIdx.x;
   const int tid = threadIdx.x;
+  for (int q = tid; q < NPE * NPE * NPE; q += ND * ND) {
+    const int c = q / (NPE * NPE), a = (q / NPE) % NPE, A = q % NPE;
+    int num = 1;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int p = ((c >> d) & 1) + ((a >> d) & 1);
+      num *= ((A >> d) & 1) ? p : 2 - p;
+    }
+    sW[q] = T(num) / T(1 << DIM);
+  }
+  __syncthreads();
   const int EX = (int)(E % gc.nx);
   const long long rest = E / gc.nx;
   const int EY = (int)(rest % gc.ny);
@@ -221,12 +223,12 @@ __global__ void __launch_bounds__(Geo<DIM>::ND * Geo<DIM>::ND)
     // T[i][J] = sum_b K[i][(b, cj)] W_c[b][AJ]   (i = I here)
     T tv = T(0);
 #pragma unroll
-    for (int bcn = 0; bcn < NPE; ++bcn) tv += sK[I * ND + DIM * bcn + cj] * T(wchild<DIM>(c, bcn, AJ));
+    for (int bcn = 0; bcn < NPE; ++bcn) tv += sK[I * ND + DIM * bcn + cj] * sW[(c * NPE + bcn) * NPE + AJ];
     sT[tid] = tv;
     __syncthreads();
     // acc[I][J] += sum_a W_c[a][AI] T[(a, ci)][J]
 #pragma unroll
-    for (int acn = 0; acn < NPE; ++acn) acc += T(wchild<DIM>(c, acn, AI)) * sT[(DIM * acn + ci) * ND + J];
+    for (int acn = 0; acn < NPE; ++acn) acc += sW[(c * NPE + acn) * NPE + AI] * sT[(DIM * acn + ci) * ND + J];
     __syncthreads();
   }
   if (J >= I) Kc[(size_t)E * NT + tri_idx(I, J, ND)] = acc;
@@ -360,13 +362,20 @@ __global__ void __launch_bounds__(1024) k_cholesky_blocked(int n, T* __restrict_
       if (cc <= r) A[(size_t)(k0 + r) * n + k0 + cc] = Dg[r * CBP + cc];
     }
     const int m = n - k0 - kb;
+    // the panel below the diagonal block, staged by all threads (coalesced
+    // rows), then solved row by row in place
+    for (int idx = tid; idx < m * kb; idx += blockDim.x) {
+      const int r = idx / kb, cc = idx - r * kb;
+      Pn[r * CBP + cc] = A[(size_t)(k0 + kb + r) * n + k0 + cc];
+    }
+    __syncthreads();
     for (int r = tid; r < m; r += blockDim.x) {
       const size_t row = (size_t)(k0 + kb + r) * n + k0;
       T xr[CB];
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
         if (cc < kb) {
-          T s = A[row + cc];
+          T s = Pn[r * CBP + cc];
 #pragma unroll
           for (int t = 0; t < CB; ++t)
             if (t < cc) s -= xr[t] * Dg[cc * CBP + t];
@@ -377,13 +386,29 @@ __global__ void __launch_bounds__(1024) k_cholesky_blocked(int n, T* __restrict_
       }
     }
     __syncthreads();
+    // trailing update, four entries per thread and pass, with their loads
+    // issued before the sums
     const long long total = (long long)m * (m + 1) / 2;
-    for (long long p = tid; p < total; p += blockDim.x) {
-      int ii, jj;
-      tri_index(p, ii, jj);
-      T s = T(0);
-      for (int t = 0; t < kb; ++t) s += Pn[ii * CBP + t] * Pn[jj * CBP + t];
-      A[(size_t)(k0 + kb + ii) * n + k0 + kb + jj] -= s;
+    const int nt = blockDim.x;
+    for (long long p0 = tid; p0 < total; p0 += 4LL * nt) {
+      int ij[4];
+      T a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long p = p0 + (long long)u * nt;
+        int ii = 0, jj = 0;
+        if (p < total) tri_index(p, ii, jj);
+        ij[u] = (ii << 16) | jj;
+        a[u] = p < total ? A[(size_t)(k0 + kb + ii) * n + k0 + kb + jj] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (p0 + (long long)u * nt >= total) break;
+        const int ii = ij[u] >> 16, jj = ij[u] & 0xffff;
+        T s = T(0);
+        for (int t = 0; t < kb; ++t) s += Pn[ii * CBP + t] * Pn[jj * CBP + t];
+        A[(size_t)(k0 + kb + ii) * n + k0 + kb + jj] = a[u] - s;
+      }
     }
     __syncthreads();
   }
