@@ -306,9 +306,10 @@ __global__ void __launch_bounds__(1024) k_cholesky(int n, T* __restrict__ A, int
 }
 
 // Blocked right-looking Cholesky (lower, in place) by one block of 1024
-// threads: per 32-column block, the diagonal block is factored by one warp
-// in shared memory, the panel below it is solved row by row, staged in
-// shared memory, and the trailing lower triangle is updated by all threads.
+// threads: per 32-column block, the diagonal block is factored in shared
+// memory (one entry per thread in each column's update), the panel below it
+// is staged in shared memory and solved row by row, and the trailing lower
+// triangle is updated by all threads in 4 x 4 register tiles.
 constexpr int CB = 32, CBP = 33;
 
 __device__ __forceinline__ void tri_index(long long p, int& ii, int& jj) {
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(1024) k_cholesky_blocked(int n, T* __restrict_
   T* Dg = reinterpret_cast<T*>(smem_raw);   // CB x CBP
   T* Pn = Dg + CB * CBP;                    // (n) x CBP panel rows
   __shared__ int s_bad;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   if (tid == 0) s_bad = 0;
   for (int k0 = 0; k0 < n; k0 += CB) {
     const int kb = min(CB, n - k0);
@@ -335,9 +336,13 @@ __global__ void __launch_bounds__(1024) k_cholesky_blocked(int n, T* __restrict_
       Dg[r * CBP + cc] = A[(size_t)(k0 + r) * n + k0 + cc];
     }
     __syncthreads();
-    if (warp == 0) {
+    // diagonal block: per column j the pivot, the scaling of the column and
+    // the rank-1 update of the block's remaining lower triangle, one entry
+    // per thread (thread (r, cc) = (tid / 32, tid % 32))
+    {
+      const int r = tid >> 5, cc = tid & 31;
       for (int j = 0; j < kb; ++j) {
-        if (lane == 0) {
+        if (tid == 0) {
           T d = Dg[j * CBP + j];
           if (!(d > T(0))) {
             s_bad = 1;
@@ -345,18 +350,13 @@ __global__ void __launch_bounds__(1024) k_cholesky_blocked(int n, T* __restrict_
           }
           Dg[j * CBP + j] = sqrt(d);
         }
-        __syncwarp();
-        const T ljj = Dg[j * CBP + j];
-        if (lane > j && lane < kb) Dg[lane * CBP + j] /= ljj;
-        __syncwarp();
-        if (lane > j && lane < kb) {
-          const T lij = Dg[lane * CBP + j];
-          for (int jj = j + 1; jj <= lane; ++jj) Dg[lane * CBP + jj] -= lij * Dg[jj * CBP + j];
-        }
-        __syncwarp();
+        __syncthreads();
+        if (tid > j && tid < kb) Dg[tid * CBP + j] /= Dg[j * CBP + j];
+        __syncthreads();
+        if (r > j && r < kb && cc > j && cc <= r) Dg[r * CBP + cc] -= Dg[r * CBP + j] * Dg[cc * CBP + j];
+        __syncthreads();
       }
     }
-    __syncthreads();
     for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
       const int r = idx / kb, cc = idx % kb;
       if (cc <= r) A[(size_t)(k0 + r) * n + k0 + cc] = Dg[r * CBP + cc];
@@ -386,29 +386,39 @@ __global__ void __launch_bounds__(1024) k_cholesky_blocked(int n, T* __restrict_
       }
     }
     __syncthreads();
-    // trailing update, four entries per thread and pass, with their loads
-    // issued before the sums
-    const long long total = (long long)m * (m + 1) / 2;
-    const int nt = blockDim.x;
-    for (long long p0 = tid; p0 < total; p0 += 4LL * nt) {
-      int ij[4];
-      T a[4];
+    // trailing update by 4 x 4 tiles of the lower triangle, one tile per
+    // thread and pass: each entry sums its kb products in the same order as
+    // an entry-wise loop, the tile's panel rows are read once per t
+    const int mt = (m + 3) >> 2;
+    const long long tiles = (long long)mt * (mt + 1) / 2;
+    for (long long p = tid; p < tiles; p += blockDim.x) {
+      int ti, tj;
+      tri_index(p, ti, tj);
+      const int r0 = 4 * ti, c0 = 4 * tj;
+      T acc[4][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const long long p = p0 + (long long)u * nt;
-        int ii = 0, jj = 0;
-        if (p < total) tri_index(p, ii, jj);
-        ij[u] = (ii << 16) | jj;
-        a[u] = p < total ? A[(size_t)(k0 + kb + ii) * n + k0 + kb + jj] : T(0);
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+      for (int t = 0; t < kb; ++t) {
+        T pr[4], pc[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          pr[a] = r0 + a < m ? Pn[(r0 + a) * CBP + t] : T(0);
+          pc[a] = c0 + a < m ? Pn[(c0 + a) * CBP + t] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += pr[a] * pc[b];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (p0 + (long long)u * nt >= total) break;
-        const int ii = ij[u] >> 16, jj = ij[u] & 0xffff;
-        T s = T(0);
-        for (int t = 0; t < kb; ++t) s += Pn[ii * CBP + t] * Pn[jj * CBP + t];
-        A[(size_t)(k0 + kb + ii) * n + k0 + kb + jj] = a[u] - s;
-      }
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int ii = r0 + a, jj = c0 + b;
+          if (ii < m && jj <= ii) A[(size_t)(k0 + kb + ii) * n + k0 + kb + jj] -= acc[a][b];
+        }
     }
     __syncthreads();
   }
