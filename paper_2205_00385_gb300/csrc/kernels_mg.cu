@@ -17,10 +17,72 @@
 namespace topo {
 
 // ---------------------------------------------------------------------------
-// Restriction and interpolation kernels (bodies in mg_device.cuh).  Threads
-// are laid out on the node grid (x lanes along I, block rows along J,
-// blockIdx.z = K), so no index division is needed.
+// Restriction and interpolation.  Each value sums its terms in the order of
+// restrict_finish / prolong_one (mg_device.cuh), whose per-node bodies the
+// fused coarse V-cycle runs, so the bits are the same.  The restriction
+// runs one thread per coarse value: consecutive threads take consecutive
+// values of one coarse plane (its rows flattened), so a warp's fine loads
+// span few sectors and a thread holds only its 27 terms (more threads in
+// flight than one per node, which pays on the small levels).
 // ---------------------------------------------------------------------------
+constexpr int TVAL = 256;
+
+// CLEAN: r_f is zero on every fixed DOF, so the fine masks are not loaded
+// (restrict_node's CLEAN reading: the same result)
+template <int DIM, typename T, bool CLEAN>
+__global__ void __launch_bounds__(TVAL)
+    k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
+               const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc,
+               const T* __restrict__ dinvc, T omega, T* __restrict__ zc) {
+  constexpr int NZ = DIM == 3 ? 3 : 1;
+  const int rowv = DIM * gc.nnx;
+  const int pv = blockIdx.x * TVAL + threadIdx.x;
+  const int K = DIM == 3 ? (int)blockIdx.y : 0;
+  pdl_wait();
+  if (pv >= rowv * gc.nny) return;
+  const int J = pv / rowv, v = pv - J * rowv;
+  const int I = v / DIM, c = v - I * DIM;
+  unsigned m[NZ][3][3];
+  T x[NZ][3][3];
+#pragma unroll
+  for (int a = 0; a < NZ; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int i = min(max(2 * I + q - 1, 0), gf.nnx - 1);
+        const int j = min(max(2 * J + b - 1, 0), gf.nny - 1);
+        const int k = DIM == 3 ? min(max(2 * K + a - 1, 0), gf.nnz - 1) : 0;
+        const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
+        m[a][b][q] = CLEAN ? 0u : (unsigned)maskf[fn];
+        x[a][b][q] = rf[DIM * fn + c];
+      }
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < NZ; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int dx = q - 1, dy = b - 1, dz = DIM == 3 ? a - 1 : 0;
+        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+        bool in = i >= 0 && i < gf.nnx && j >= 0 && j < gf.nny;
+        if (DIM == 3) in = in && k >= 0 && k < gf.nnz;
+        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+        const unsigned mm = in ? m[a][b][q] : 7u;
+        acc = add_rn(acc, ((mm >> c) & 1u) ? T(0) : mul_rn(w, x[a][b][q]));
+      }
+  const long long node = I + (long long)gc.nnx * (J + (long long)gc.nny * K);
+  const long long d = DIM * node + c;
+  const T bv = ((maskc[node] >> c) & 1u) ? T(0) : acc;
+  bc[d] = bv;
+  if (zc) zc[d] = mul_rn(mul_rn(omega, dinvc[d]), bv);
+  pdl_launch_dependents();
+}
+
+// z_f += Pm z_c: threads on the fine (i, j) grid, each taking the fine nodes
+// k = 2q and 2q+1 (3D), which share the coarse plane q (index work shared by
+// six values; one thread per value measured 2.5x slower at the finest level).
 constexpr int TBX = 32, TBY = 4;
 
 template <typename T>
@@ -30,21 +92,6 @@ __host__ __device__ constexpr int transfer_min_blocks() {
 
 // CLEAN: r_f is zero on every fixed DOF (restrict_node then skips the fine
 // masks, with the same result)
-template <int DIM, typename T, bool CLEAN>
-__global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
-    k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
-               const uint8_t* __restrict__ maskc, const T* __restrict__ rf, T* __restrict__ bc,
-               const T* __restrict__ dinvc, T omega, T* __restrict__ zc) {
-  const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
-  const int K = DIM == 3 ? (int)blockIdx.z : 0;
-  pdl_wait();
-  if (I >= gc.nnx || J >= gc.nny) return;
-  restrict_node<DIM, T, false, CLEAN>(gf, maskf, gc, maskc, rf, bc, dinvc, omega, zc, I, J, K);
-  pdl_launch_dependents();
-}
-
-// z_f += Pm z_c: threads on the fine (i, j) grid, each taking the fine nodes
-// k = 2q and 2q+1 (3D), which share the coarse plane q.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     k_prolong_add(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,
@@ -533,9 +580,11 @@ static cudaError_t restrict_t(const GridP& gf, const uint8_t* mf, const GridP& g
                               const uint8_t* mc, const void* rf, void* bc, const void* dinvc,
                               double omega, void* zc, bool clean, cudaStream_t s) {
   if (gc.nn <= 0) return cudaSuccess;
-  dim3 grid((gc.nnx + TBX - 1) / TBX, (gc.nny + TBY - 1) / TBY, DIM == 3 ? gc.nnz : 1);
+  const long long pv = (long long)DIM * gc.nnx * gc.nny;
+  if (pv >= (1LL << 31) - TVAL || gc.nnz > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((pv + TVAL - 1) / TVAL), DIM == 3 ? gc.nnz : 1);
   auto kern = clean ? k_restrict<DIM, T, true> : k_restrict<DIM, T, false>;
-  return launch_pdl(kern, grid, dim3(TBX, TBY), 0, s, gf, mf, gc, mc, (const T*)rf, (T*)bc,
+  return launch_pdl(kern, grid, dim3(TVAL), 0, s, gf, mf, gc, mc, (const T*)rf, (T*)bc,
                     (const T*)dinvc, T(omega), (T*)zc);
 }
 
