@@ -177,7 +177,8 @@ to_status to_carm_build(to_ctx* ctx, const double* u_last);
  *     from the finest moduli (3D, >= 3 levels);
  *   TO_TUNE_ACC_APPLY / _RESID: the double-float operator (TO_MIXED).
  * For the float32 finest-grid kernels it also times the 16-row tile
- * variant (TO_OPERATOR_TALL_TILES).
+ * variant (TO_OPERATOR_TALL_TILES) and the work-list launch of either tile
+ * (TO_OPERATOR_WORK_LIST).
  * It keeps the fastest (the occupancy heuristic's own shape when within 1 %
  * of it), applies it to every later launch of that kernel on this context,
  * drops the captured V-cycle graphs so that they are recaptured with it, and
@@ -196,8 +197,9 @@ typedef struct {
   int32_t chunk_layers;  /* chosen node layers per chunk (0: the heuristic's shape) */
   double chosen_us;      /* average launch time of the chosen shape (0 when cached) */
   double heuristic_us;   /* average launch time of the heuristic's shape (0 when cached) */
-  int32_t variant;       /* float32 finest-grid kernels (TO_TUNE_OP_*): tile variant,
-                            0 = 8-row tiles, 1 = 16-row tiles (TO_OPERATOR_TALL_TILES) */
+  int32_t variant;       /* float32 finest-grid kernels (TO_TUNE_OP_*): bit 0 the tile,
+                            0 = 8-row tiles, 1 = 16-row tiles (TO_OPERATOR_TALL_TILES);
+                            bit 1 the work-list launch (TO_OPERATOR_WORK_LIST) */
 } to_tune_result;
 to_status to_autotune(to_ctx* ctx, int32_t reps, to_tune_result* results, int32_t cap,
                       int32_t* count);
@@ -275,6 +277,14 @@ to_status to_batch_step(const to_batch_job* jobs, int32_t n, int32_t phase, void
  * results are bit for bit the same.  Changing it drops the captured
  * V-cycle graphs. */
 #define TO_OPERATOR_TALL_TILES 4
+/* TO_OPERATOR_WORK_LIST: the float32 finest-grid operator (3D TO_MIXED) is
+ * launched as a work list in every launch: one CTA per resident block slot,
+ * each taking the next (tile, z-chunk) item from a device counter until
+ * none is left (the last CTA resets the counter), instead of one block per
+ * item; to_autotune also times this launch and may select it for a kernel
+ * on its own.  The results are bit for bit the same.  Changing it drops the
+ * captured V-cycle graphs. */
+#define TO_OPERATOR_WORK_LIST 8
 to_status to_operator_options(to_ctx* ctx, int32_t flags);
 
 /* Options of to_carm_build (default 0).  TO_CARM_R1_PROJECTED_LOAD: the

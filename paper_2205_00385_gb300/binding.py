@@ -227,6 +227,7 @@ TO_CARM_R1_PROJECTED_LOAD = 1
 TO_OPERATOR_TENSOR_CORES = 1
 TO_OPERATOR_FUSED_COARSE = 2
 TO_OPERATOR_TALL_TILES = 4
+TO_OPERATOR_WORK_LIST = 8
 
 
 def to_operator_options(ctx, flags):

@@ -46,8 +46,11 @@ struct ApplyArgs {
                                      // column is fixed (null: mask every node)
   int zsplit = 0;      // layers per z-chunk of the column-streaming 3D kernels, set
                        // by the autotuner (0: the launcher's occupancy heuristic)
-  int variant = 0;     // tile variant of the float32 pair kernel (0: 8-row tiles,
-                       // 1: 16-row tiles), autotuned or set by an option
+  int variant = 0;     // float32 pair kernel: bit 0 the tile variant (0: 8-row
+                       // tiles, 1: 16-row tiles), bit 1 the work-list launch (with
+                       // wl set); autotuned or set by an option
+  unsigned* wl = nullptr;         // the pair kernel's work-list counters (two, zero
+                                  // between launches), device
   bool use_tc = false;            // float32 finest grid: the tensor-core operator
   const void* bmat = nullptr;     // its B operand (tc_pack_b), device
   int* status = nullptr;          // device word receiving TO_E_TIMEOUT from bounded waits

@@ -20,6 +20,8 @@
 // 30 x 7 nodes whose surrounding columns it computes; per z-layer the
 // column partials of each owned node are summed in shared memory in a fixed
 // order (deterministic, no atomics).
+#include <algorithm>
+
 #include "kernels.h"
 #include "topo_internal.cuh"
 
@@ -112,6 +114,10 @@ struct PairArgs {
   const float* dinv;
   float omega, dfix;
   bool clean_inputs;       // x (and, fused, b) zero on every fixed DOF
+  // work-list launch (null: one block per tile and z-chunk): wl[0] hands out
+  // the items (tile x fastest, z-chunk slowest), wl[1] counts the CTAs done
+  unsigned* wl;
+  int gx, gy, nitems;
 };
 
 // Face tile of a block of PX x PY threads: (2 PX + 1) x (PY + 1) nodes,
@@ -150,15 +156,15 @@ struct PairSmem {
 // values changes nothing and only the fixed rows' outputs need setting.
 template <int EPI, int MODE, int PY>
 __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb,
-                                          PairSmem<PY>& sm) {
+                                          PairSmem<PY>& sm, int bx, int by, int bz) {
   using G = PairGeo<PY>;
   constexpr int POY = G::POY, FNY = G::FNY, FTILE = G::FTILE;
   constexpr bool MASKED = MODE == 1, MASK_OUT = MODE != 0;
   const GridP& g = a.g;
   const int tid = threadIdx.x;
   const int tx = tid % PX, ty = tid / PX;
-  const int X0 = blockIdx.x * POX, Y0 = blockIdx.y * POY;
-  const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, g.nnz);
+  const int X0 = bx * POX, Y0 = by * POY;
+  const int z0 = bz * a.zc, z1 = min(z0 + a.zc, g.nnz);
   const int i = X0 - 1 + 2 * tx, j = Y0 - 1 + ty;   // corner 0 of element A
   const long long plane = (long long)g.nnx * g.nny;
   const bool eA = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
@@ -358,32 +364,70 @@ __device__ __forceinline__ void pair_loop(const PairArgs& a, const WhtPair& kb,
 // (PY = 8) and the resident blocks per SM (MINB) the register allocation
 // allows without spilling (four for K p, three for the residual and
 // smoother epilogues); variant 1, 256 threads (PY = 16, less redundant
-// element work at tile edges) and two blocks per SM.
+// element work at tile edges) and two blocks per SM.  Either runs one block
+// per (tile, z-chunk), or as a work list (a.wl set): one CTA per resident
+// slot, each taking the next item from a counter until none is left, so
+// that CTAs whose items finish early take more and the SMs stay busy to the
+// end; the last CTA to finish resets the counters for the next launch.
+// An item computes exactly what the block of the same tile and chunk
+// computes, so both forms give the same bits.
 template <int EPI, int MINB, int PY>
 __global__ void __launch_bounds__(PX * PY, MINB)
     k_apply3_pair(PairArgs a, WhtPair kb) {
   extern __shared__ __align__(16) unsigned char pair_smem[];
+  __shared__ int s_item;
   PairSmem<PY>& sm = *reinterpret_cast<PairSmem<PY>*>(pair_smem);
   const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
-  const int i = blockIdx.x * POX - 1 + 2 * tx, j = blockIdx.y * PairGeo<PY>::POY - 1 + ty;
-  bool flag = a.colfix == nullptr;
+  // does the tile's node-column range hold a fixed DOF (set up once)
+  auto tile_flag = [&](int bx, int by) {
+    const int i = bx * POX - 1 + 2 * tx, j = by * PairGeo<PY>::POY - 1 + ty;
+    bool flag = a.colfix == nullptr;
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
-    for (int n = 0; n < 3; ++n)
-      if (a.colfix && i + n >= 0 && i + n < a.g.nnx && j + r >= 0 && j + r < a.g.nny)
-        flag |= a.colfix[(i + n) + (long long)a.g.nnx * (j + r)] != 0;
-  // (the column flags are set up once; everything below reads the vectors
-  // of preceding kernels)
-  pdl_wait();
+      for (int n = 0; n < 3; ++n)
+        if (a.colfix && i + n >= 0 && i + n < a.g.nnx && j + r >= 0 && j + r < a.g.nny)
+          flag |= a.colfix[(i + n) + (long long)a.g.nnx * (j + r)] != 0;
+    return flag;
+  };
   // all threads of a block must take the same branch (both contain
   // __syncthreads), so the decision is block-wide
-  if (!__syncthreads_or(flag))
-    pair_loop<EPI, 0, PY>(a, kb, sm);
-  else if (a.clean_inputs)
-    pair_loop<EPI, 2, PY>(a, kb, sm);
-  else
-    pair_loop<EPI, 1, PY>(a, kb, sm);
+  auto tile = [&](int bx, int by, int bz, bool flag) {
+    if (!__syncthreads_or(flag))
+      pair_loop<EPI, 0, PY>(a, kb, sm, bx, by, bz);
+    else if (a.clean_inputs)
+      pair_loop<EPI, 2, PY>(a, kb, sm, bx, by, bz);
+    else
+      pair_loop<EPI, 1, PY>(a, kb, sm, bx, by, bz);
+  };
+  if (a.wl == nullptr) {
+    const bool flag = tile_flag(blockIdx.x, blockIdx.y);
+    // (the column flags are set up once; everything below reads the vectors
+    // of preceding kernels)
+    pdl_wait();
+    tile(blockIdx.x, blockIdx.y, blockIdx.z, flag);
+  } else {
+    pdl_wait();
+    for (;;) {
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(a.wl, 1u);
+      __syncthreads();
+      const int item = s_item;
+      if (item >= a.nitems) break;
+      const int bx = item % a.gx, rest = item / a.gx;
+      const int by = rest % a.gy, bz = rest / a.gy;
+      tile(bx, by, bz, tile_flag(bx, by));
+      __syncthreads();   // shared memory (and s_item) is reused by the next item
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      // every CTA has taken its last item before it counts itself done, so
+      // the last one may reset the hand-out counter
+      if (atomicAdd(a.wl + 1, 1u) == gridDim.x - 1) {
+        atomicExch(a.wl, 0u);
+        atomicExch(a.wl + 1, 0u);
+      }
+    }
+  }
   pdl_launch_dependents();
 }
 
@@ -492,7 +536,8 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   p.omega = (float)a.omega;
   p.dfix = (float)a.dfix;
   p.clean_inputs = a.clean_inputs;
-  const int var = a.variant ? 1 : 0;
+  const int var = (a.variant & 1) ? 1 : 0;
+  const bool wl = (a.variant & 2) && a.wl != nullptr;
   const int poy = var ? PairGeo<16>::POY : PairGeo<8>::POY;
   const int gx = (a.g.nnx + POX - 1) / POX, gy = (a.g.nny + poy - 1) / poy;
   // z-chunks: each chunk streams its layers and recomputes one element layer
@@ -515,7 +560,11 @@ cudaError_t launch_apply_pair(const ApplyArgs& a, cudaStream_t s) {
   }
   p.zc = a.zsplit > 0 ? min(a.zsplit, (int)a.g.nnz) : (a.g.nnz + best - 1) / best;
   best = (a.g.nnz + p.zc - 1) / p.zc;
-  dim3 grid(gx, gy, best);
+  p.gx = gx;
+  p.gy = gy;
+  p.nitems = gx * gy * best;
+  p.wl = wl ? a.wl : nullptr;
+  dim3 grid = wl ? dim3((unsigned)std::min<long long>(slots, p.nitems)) : dim3(gx, gy, best);
 #define PAIR_LAUNCH(E, V)                                                                   \
   launch_pdl(pair_kernel<E, V>(), grid, dim3(PairVar<E, V>::NT), PairVar<E, V>::SMEM, s, p, kb)
   switch (a.epi) {

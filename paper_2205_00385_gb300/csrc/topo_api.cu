@@ -476,6 +476,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->use_tc = false;
   c->fuse_coarse = false;
   c->tall_tiles = false;
+  c->work_list = false;
   c->vf_l0 = 0;
   c->springs = Springs();
   c->oc_eta = 0.5;
@@ -678,7 +679,8 @@ static ApplyArgs fine_args(const to_ctx* c, int op, int tc, int tx, int ty, cons
   a.epi = epi;
   const int k = tune_kind_fine(c, tc, epi);
   a.zsplit = k >= 0 ? c->tuned_zc[k] : 0;
-  a.variant = (k >= 0 ? c->tuned_var[k] : 0) | (c->tall_tiles ? 1 : 0);
+  a.variant = (k >= 0 ? c->tuned_var[k] : 0) | (c->tall_tiles ? 1 : 0) | (c->work_list ? 2 : 0);
+  a.wl = c->counters + C_PAIR + 2 * (epi == EPI_APPLY ? 0 : epi == EPI_RESID ? 1 : 2);
   a.use_tc = c->use_tc;
   a.bmat = c->tc_bmat;
   a.status = c->ints + I_TIMEOUT;
@@ -1532,9 +1534,10 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
     double best_us = h_us;
     int best = 0, best_var = 0, tried = 0;
     const int nnz = (int)a.g.nnz;
-    // the pair kernel (float32 finest grid) also has a second register variant
+    // the pair kernel (float32 finest grid) also has a second register
+    // variant (bit 0) and the work-list launch of either (bit 1)
     const bool pair = kind <= TO_TUNE_OP_SMOOTH && pair_apply_ok(a) && !a.use_tc;
-    for (int var = 0; var <= (pair ? 1 : 0) && err == cudaSuccess; ++var) {
+    for (int var = 0; var <= (pair ? 3 : 0) && err == cudaSuccess; ++var) {
       for (int nzc = 1; nzc <= nnz && nzc <= 64; ++nzc) {
         const int zc = (nnz + nzc - 1) / nzc;
         if (zc < 2 || (nnz + zc - 1) / zc != nzc) continue;
@@ -1576,13 +1579,16 @@ to_status to_autotune(to_ctx* c, int32_t reps, to_tune_result* results, int32_t 
 
 to_status to_operator_options(to_ctx* c, int32_t flags) {
   if (!c) return fail(c, TO_E_INVALID, "NULL argument");
-  if (flags & ~(TO_OPERATOR_TENSOR_CORES | TO_OPERATOR_FUSED_COARSE | TO_OPERATOR_TALL_TILES))
+  if (flags & ~(TO_OPERATOR_TENSOR_CORES | TO_OPERATOR_FUSED_COARSE | TO_OPERATOR_TALL_TILES |
+                TO_OPERATOR_WORK_LIST))
     return fail(c, TO_E_INVALID, "unknown operator option");
   const bool tc = (flags & TO_OPERATOR_TENSOR_CORES) != 0;
   const bool fuse = (flags & TO_OPERATOR_FUSED_COARSE) != 0;
   const bool tall = (flags & TO_OPERATOR_TALL_TILES) != 0;
-  if (tall != c->tall_tiles) {
+  const bool wl = (flags & TO_OPERATOR_WORK_LIST) != 0;
+  if (tall != c->tall_tiles || wl != c->work_list) {
     c->tall_tiles = tall;
+    c->work_list = wl;
     for (int q = 0; q < c->n_vgraph; ++q) cudaGraphExecDestroy(c->vgraph[q].exec);
     c->n_vgraph = 0;   // recaptured with the selected tile
   }

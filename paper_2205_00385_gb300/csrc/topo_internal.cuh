@@ -363,6 +363,7 @@ struct to_ctx {
   bool use_tc;           // float32 finest-grid operator on the tensor cores
   bool fuse_coarse;      // coarse end of the V-cycle as one cluster launch (option)
   bool tall_tiles;       // float32 finest-grid operator with 16-row tiles (option)
+  bool work_list;        // float32 finest-grid operator launched as a work list (option)
   topo::Springs springs;  // springs to ground of the finest grid (2D)
   double oc_eta;          // damping exponent of the OC update
   int vf_l0;             // its first level (0: no level qualifies)
@@ -387,8 +388,9 @@ void batch_forget(const to_ctx* c);
 namespace topo {
 
 // Counter slots (ctx->counters, one per reduction site in flight)
+// C_PAIR: the float32 pair kernel's work-list counters, two per epilogue
 enum Counter { C_DOT = 0, C_MULTI = 1 /* .. +16 */, C_UPD = 20, C_OC = 21, C_SENS = 22,
-               C_MAX = 23, C_NCOUNTERS = 32 };
+               C_MAX = 23, C_PAIR = 24 /* .. +6 */, C_NCOUNTERS = 32 };
 
 // --- launch helpers (host) ---
 void note_launch(to_ctx* c);

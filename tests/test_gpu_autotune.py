@@ -89,3 +89,39 @@ def test_tall_tiles_give_the_same_bits():
     for a, b in zip(out[0][:3], out[1][:3]):
         assert np.array_equal(a, b)
     assert out[0][3] == out[1][3]
+
+
+@pytest.mark.parametrize("tall", [False, True])
+def test_work_list_launch_gives_the_same_bits(tall):
+    """The work-list launch of the float32 finest-grid operator
+    (TO_OPERATOR_WORK_LIST: one CTA per resident slot taking (tile, z-chunk)
+    items from a counter) computes each item as the one-block-per-item
+    launch does: products, V-cycles (captured graphs included, whose
+    replays reuse the counters) and whole solves are bitwise the same, on a
+    grid with more items than resident CTAs and on one with fewer."""
+    from paper_2205_00385_gb300 import binding as B
+    base = B.TO_OPERATOR_TALL_TILES if tall else 0
+    for kw, levels in ((dict(nelx=64, nely=40, nelz=24), 4), (dict(nelx=16, nely=8, nelz=8), 2)):
+        p = small_problem("cantilever3d", mg_levels=levels, **kw)
+        rho = rand_density(p.nel, 78, 0.05, 1.0)
+        x = dev(rand_vector(p.ndof, 79, fixed=p.fixed))
+        r = dev(rand_vector(p.ndof, 80, fixed=p.fixed))
+        out = []
+        with Ctx(p, precision="mixed") as c:
+            c.set_density(rho)
+            for flags in (base, base | B.TO_OPERATOR_WORK_LIST):
+                B.to_operator_options(c.ctx, flags)
+                res = []
+                for _ in range(2):   # the second call reuses the reset counters
+                    y = dev(np.zeros(p.ndof))
+                    B.to_apply(c.ctx, B.TO_OP_K, B.TO_PREC_FP32, x, y)
+                    z = dev(np.zeros(p.ndof))
+                    B.to_vcycle(c.ctx, r, z)
+                    res += [host(y), host(z)]
+                u = dev(np.zeros(p.ndof))
+                it, _, _ = B.to_mgcg_solve(c.ctx, 1e-8, 200, 0, u)
+                out.append((res, host(u), it))
+        for a, b in zip(out[0][0], out[1][0]):
+            assert np.array_equal(a, b)
+        assert np.array_equal(out[0][1], out[1][1])
+        assert out[0][2] == out[1][2] and out[0][2] > 0

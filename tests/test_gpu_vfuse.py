@@ -81,7 +81,7 @@ def test_operator_options_reject_unknown_bits():
     p = small_problem("mbb2d", nelx=16, nely=8, mg_levels=2)
     with Ctx(p, precision="fp64") as c:
         with pytest.raises(B.TopoError) as e:
-            B.to_operator_options(c.ctx, 8)
+            B.to_operator_options(c.ctx, 16)
         assert e.value.status == B.TO_E_INVALID
         with pytest.raises(B.TopoError):
             B.to_operator_options(c.ctx, B.TO_OPERATOR_TENSOR_CORES)   # 2D: no tensor-core operator
