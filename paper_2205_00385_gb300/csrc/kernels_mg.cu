@@ -27,8 +27,9 @@ namespace topo {
 // ---------------------------------------------------------------------------
 constexpr int TVAL = 256;
 
-// CLEAN: r_f is zero on every fixed DOF, so the fine masks are not loaded
-// (restrict_node's CLEAN reading: the same result)
+// CLEAN: r_f is +-0 on every fixed DOF, so the fine masks are not loaded: a
+// fixed term then adds w * (+-0) where restrict_finish adds +0, and a
+// running sum that starts at +0 is never -0, so the bits are the same.
 template <int DIM, typename T, bool CLEAN>
 __global__ void __launch_bounds__(TVAL)
     k_restrict(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,

@@ -167,11 +167,8 @@ __device__ __forceinline__ void restrict_finish(const GridP& gf, const GridP& gc
 // loads, so the 3^DIM masks and values take one memory round trip; the terms
 // are then summed in a fixed order.  With zc set, the coarse level is also
 // pre-smoothed from a zero guess, z = omega D^-1 b.
-// CLEAN: r_f is +-0 on every fixed DOF, so the fine masks are not loaded: a
-// fixed term then adds w * (+-0) where the masked sum adds +0, and a running
-// sum that starts at +0 is never -0, so the bits are the same.
 // ---------------------------------------------------------------------------
-template <int DIM, typename T, bool CG, bool CLEAN = false>
+template <int DIM, typename T, bool CG>
 __device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __restrict__ maskf,
                                               const GridP& gc, const uint8_t* __restrict__ maskc,
                                               const T* __restrict__ rf, T* __restrict__ bc,
@@ -190,7 +187,7 @@ __device__ __forceinline__ void restrict_node(const GridP& gf, const uint8_t* __
         const int j = min(max(2 * J + b - 1, 0), gf.nny - 1);
         const int k = DIM == 3 ? min(max(2 * K + a - 1, 0), gf.nnz - 1) : 0;
         const long long fn = i + (long long)gf.nnx * (j + (long long)gf.nny * k);
-        m[a][b][q] = CLEAN ? 0u : (unsigned)maskf[fn];
+        m[a][b][q] = maskf[fn];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[a][b][q][c] = ldv<CG>(rf + DIM * fn + c);
       }
