@@ -235,11 +235,12 @@ cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* p
                            unsigned* counter, double* out, cudaStream_t s);
 // x += alpha p, r -= alpha q, scal[rr] = |r|^2 with alpha = scal[num]/scal[den];
 // with b non-null also b = float(r), zpre = omega dinv b (the next V-cycle's
-// right-hand side and pre-smoothing from zero)
+// right-hand side and pre-smoothing from zero); host_rr (may be null): a
+// device-accessible pointer to pinned host memory that also receives |r|^2
 cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const float* q,
                             double* scal, int num, int den, int rr, double* partials,
                             unsigned* counter, float* b, float* zpre, const float* dinv,
-                            double omega, cudaStream_t s);
+                            double omega, cudaStream_t s, double* host_rr = nullptr);
 // p = z + beta p (num < 0: p = z), beta = scal[num]/scal[den]; p32 = float(p)
 cudaError_t launch_cg_p_d2(long long n, void* p, float* p32, const float* z, const double* scal,
                            int num, int den, cudaStream_t s);

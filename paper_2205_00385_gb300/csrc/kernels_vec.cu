@@ -563,12 +563,16 @@ __global__ void __launch_bounds__(RED_THREADS)
 // With b non-null it also starts the next V-cycle: b = r rounded to float32
 // and zpre = omega dinv b (its pre-smoothing from a zero guess), the values
 // the V-cycle's first kernel would compute.
+// With host_rr set, |r|^2 is also written there (pinned host memory mapped
+// into the device's address space), so the host reads it after an event on
+// the stream without a copy between this kernel and the next.
 template <bool PRE>
 __global__ void __launch_bounds__(RED_THREADS)
     k_cg_xr_d2(long long n, float2* __restrict__ x, float2* __restrict__ r,
                const float2* __restrict__ p, const float* __restrict__ q, double* scal, int num,
                int den, int rr, double* partials, unsigned* counter, float* __restrict__ b,
-               float* __restrict__ zpre, const float* __restrict__ dinv, float omega) {
+               float* __restrict__ zpre, const float* __restrict__ dinv, float omega,
+               double* host_rr) {
   using Rg = Ar<float2>;
   __shared__ double sh[32];
   __shared__ double s_alpha;
@@ -608,7 +612,23 @@ __global__ void __launch_bounds__(RED_THREADS)
   }
   for (; k < n; k += stride)
     step(k, Rg::ld(x, k), Rg::ld(p, k), Rg::ld(r, k), q[k], PRE ? dinv[k] : 0.f, v[0]);
-  reduce_to<float2>(df_add(df_norm(v[0]), df_norm(v[1])), scal + rr, partials, counter, sh);
+  {
+    // reduce_to's sum, with the second destination
+    typename Ar<float2>::T vv[1] = {df_add(df_norm(v[0]), df_norm(v[1]))};
+    double o1[1];
+    block_sum_v<float2, 1>(vv, o1, sh);
+    if (publish_partials<1>(o1, partials, counter)) {
+      double o[1];
+      finish_sum<1>(partials, counter, o, sh);
+      if (threadIdx.x == 0) {
+        scal[rr] = o[0];
+        if (host_rr) {
+          *reinterpret_cast<volatile double*>(host_rr) = o[0];
+          __threadfence_system();
+        }
+      }
+    }
+  }
   pdl_launch_dependents();
 }
 
@@ -890,14 +910,14 @@ cudaError_t launch_dot_d2f(long long n, const void* a, const float* b, double* p
 cudaError_t launch_cg_xr_d2(long long n, void* x, void* r, const void* p, const float* q,
                             double* scal, int num, int den, int rr, double* partials,
                             unsigned* counter, float* b, float* zpre, const float* dinv,
-                            double omega, cudaStream_t s) {
+                            double omega, cudaStream_t s, double* host_rr) {
   if (b)
     return launch_pdl(k_cg_xr_d2<true>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n, (float2*)x,
                       (float2*)r, (const float2*)p, q, scal, num, den, rr, partials, counter, b,
-                      zpre, dinv, (float)omega);
+                      zpre, dinv, (float)omega, host_rr);
   return launch_pdl(k_cg_xr_d2<false>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, n, (float2*)x,
                     (float2*)r, (const float2*)p, q, scal, num, den, rr, partials, counter,
-                    (float*)nullptr, (float*)nullptr, (const float*)nullptr, 0.f);
+                    (float*)nullptr, (float*)nullptr, (const float*)nullptr, 0.f, host_rr);
 }
 
 cudaError_t launch_cg_p_d2(long long n, void* p, float* p32, const float* z, const double* scal,

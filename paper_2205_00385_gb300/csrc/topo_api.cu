@@ -481,6 +481,7 @@ to_status to_mesh_init(const to_mesh_desc* desc, const uint8_t* fixed_mask, cons
   c->springs = Springs();
   c->oc_eta = 0.5;
   c->host_rr = nullptr;
+  c->host_rr_dev = nullptr;
   c->rr_event = nullptr;
   c->cap_stream = nullptr;
   if (!make_stencil(c->dim, desc->rmin, &c->stencil)) {
@@ -1154,11 +1155,15 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   to_status st;
   if (c->hier_stale && (st = build_hierarchy(c)) != TO_OK) return st;
   if (!c->host_rr) {
-    // 64 bytes of pinned host memory per context, so that the residual read
-    // is an asynchronous copy the host can wait on with an event
+    // 64 bytes of pinned host memory per context, mapped into the device's
+    // address space: the mixed CG update writes |r|^2 there itself, the FP64
+    // one is followed by an asynchronous copy; the host waits on an event
     void* h = nullptr;
-    CUDA_TRY(c, cudaMallocHost(&h, 64), "pinned residual slot");
+    CUDA_TRY(c, cudaHostAlloc(&h, 64, cudaHostAllocMapped), "pinned residual slot");
     c->host_rr = static_cast<double*>(h);
+    void* d = nullptr;
+    CUDA_TRY(c, cudaHostGetDevicePointer(&d, h, 0), "mapped residual slot");
+    c->host_rr_dev = static_cast<double*>(d);
   }
   if (!c->rr_event)
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->rr_event, cudaEventDisableTiming), "rr event");
@@ -1246,7 +1251,8 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
         LAUNCH(c, launch_cg_xr_d2(n, x, c->r, c->p, c->q32, c->scal, cur, S_PQ, S_RR,
                                   c->partials, c->counters + C_UPD,
                                   static_cast<float*>(c->lv[0].b), static_cast<float*>(c->lv[0].z),
-                                  static_cast<const float*>(c->lv[0].dinv), 0.6, s),
+                                  static_cast<const float*>(c->lv[0].dinv), 0.6, s,
+                                  c->host_rr_dev),
                "x, r update");
         pre = true;
       } else {
@@ -1265,13 +1271,15 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
       // its own scratch and scal[nxt], so when the loop stops (or a true
       // residual replaces r) its result is discarded (or recomputed) and
       // the iterates are the same as with the read first.
-      CUDA_TRY(c, cudaMemcpyAsync(c->host_rr, c->scal + S_RR, 8, cudaMemcpyDeviceToHost, s),
-               "read rr");
+      // (the mixed update writes it to the mapped host slot itself)
+      if (!mixed)
+        CUDA_TRY(c, cudaMemcpyAsync(c->host_rr, c->scal + S_RR, 8, cudaMemcpyDeviceToHost, s),
+                 "read rr");
       CUDA_TRY(c, cudaEventRecord(c->rr_event, s), "rr event");
       bool fresh = it < maxit;
       if (fresh && (st = precondition(nxt)) != TO_OK) return st;
       CUDA_TRY(c, cudaEventSynchronize(c->rr_event), "wait rr");
-      rr = *c->host_rr;
+      rr = *reinterpret_cast<volatile double*>(c->host_rr);
       rel = sqrt(rr) / c->fnorm;
       if (!isfinite(rel)) return fail(c, TO_E_SINGULAR, "CG breakdown (non-finite residual)");
       // Reliable updates: with a float32 operator the recursive residual

@@ -372,6 +372,7 @@ struct to_ctx {
   int n_vgraph;
   cudaStream_t cap_stream;   // private stream used only for graph capture
   double* host_rr;           // pinned host slot for the CG residual read
+  double* host_rr_dev;       // the same slot as the device addresses it (mapped)
   cudaEvent_t rr_event;      // marks that read on the context stream
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
