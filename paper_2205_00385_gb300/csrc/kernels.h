@@ -174,7 +174,7 @@ cudaError_t launch_dot(long long n, const double* a, const double* b, double* pa
 // alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q; scal[rr] = r.r
 cudaError_t launch_cg_xr(long long n, double* x, double* r, const double* p, const double* q,
                          double* scal, int num, int den, int rr, double* partials,
-                         unsigned* counter, cudaStream_t s);
+                         unsigned* counter, cudaStream_t s, double* host_rr = nullptr);
 // beta = scal[num] / scal[den]; p = z + beta p
 cudaError_t launch_cg_p(long long n, double* p, const double* z, const double* scal, int num,
                         int den, cudaStream_t s);

@@ -24,10 +24,12 @@ __global__ void __launch_bounds__(RED_THREADS)
   }
 }
 
+// host_rr (may be null): pinned host memory mapped into the device's
+// address space that also receives |r|^2
 __global__ void __launch_bounds__(RED_THREADS)
     k_cg_xr(long long n, double* __restrict__ x, double* __restrict__ r,
             const double* __restrict__ p, const double* __restrict__ q, double* scal, int num,
-            int den, int rr, double* partials, unsigned* counter) {
+            int den, int rr, double* partials, unsigned* counter, double* host_rr) {
   __shared__ double sh[32];
   const double alpha = scal[num] / scal[den];
   double v[1] = {0.0};
@@ -42,7 +44,13 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (publish_partials<1>(v, partials, counter)) {
     double o[1];
     finish_sum<1>(partials, counter, o, sh);
-    if (threadIdx.x == 0) scal[rr] = o[0];
+    if (threadIdx.x == 0) {
+      scal[rr] = o[0];
+      if (host_rr) {
+        *reinterpret_cast<volatile double*>(host_rr) = o[0];
+        __threadfence_system();
+      }
+    }
   }
 }
 
@@ -339,9 +347,9 @@ cudaError_t launch_dot(long long n, const double* a, const double* b, double* pa
 
 cudaError_t launch_cg_xr(long long n, double* x, double* r, const double* p, const double* q,
                          double* scal, int num, int den, int rr, double* partials,
-                         unsigned* counter, cudaStream_t s) {
+                         unsigned* counter, cudaStream_t s, double* host_rr) {
   k_cg_xr<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, scal, num, den, rr, partials,
-                                             counter);
+                                             counter, host_rr);
   return cudaGetLastError();
 }
 

@@ -1156,8 +1156,8 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
   if (c->hier_stale && (st = build_hierarchy(c)) != TO_OK) return st;
   if (!c->host_rr) {
     // 64 bytes of pinned host memory per context, mapped into the device's
-    // address space: the mixed CG update writes |r|^2 there itself, the FP64
-    // one is followed by an asynchronous copy; the host waits on an event
+    // address space: the CG update kernel writes |r|^2 there itself and the
+    // host waits on an event recorded after it
     void* h = nullptr;
     CUDA_TRY(c, cudaHostAlloc(&h, 64, cudaHostAllocMapped), "pinned residual slot");
     c->host_rr = static_cast<double*>(h);
@@ -1263,7 +1263,7 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
         LAUNCH(c, launch_dot(n, c->p, c->q, c->partials, c->counters + C_DOT, c->scal + S_PQ, s),
                "pq");
         LAUNCH(c, launch_cg_xr(n, x, c->r, c->p, c->q, c->scal, cur, S_PQ, S_RR, c->partials,
-                               c->counters + C_UPD, s), "x, r update");
+                               c->counters + C_UPD, s, c->host_rr_dev), "x, r update");
       }
       // |r|^2 goes to the host, and the next preconditioner application is
       // enqueued before the host waits for it: the V-cycle runs while the
@@ -1271,10 +1271,7 @@ to_status to_mgcg_solve(to_ctx* c, double rtol, int32_t maxit, int32_t flags, do
       // its own scratch and scal[nxt], so when the loop stops (or a true
       // residual replaces r) its result is discarded (or recomputed) and
       // the iterates are the same as with the read first.
-      // (the mixed update writes it to the mapped host slot itself)
-      if (!mixed)
-        CUDA_TRY(c, cudaMemcpyAsync(c->host_rr, c->scal + S_RR, 8, cudaMemcpyDeviceToHost, s),
-                 "read rr");
+      // (the update kernel writes it into the mapped host slot itself)
       CUDA_TRY(c, cudaEventRecord(c->rr_event, s), "rr event");
       bool fresh = it < maxit;
       if (fresh && (st = precondition(nxt)) != TO_OK) return st;
