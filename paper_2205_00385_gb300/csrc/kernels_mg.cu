@@ -91,8 +91,6 @@ __host__ __device__ constexpr int transfer_min_blocks() {
   return sizeof(T) == 4 ? 4 : 2;   // registers for all loads in flight
 }
 
-// CLEAN: r_f is zero on every fixed DOF (restrict_node then skips the fine
-// masks, with the same result)
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TBX * TBY, transfer_min_blocks<T>())
     k_prolong_add(GridP gf, const uint8_t* __restrict__ maskf, GridP gc,

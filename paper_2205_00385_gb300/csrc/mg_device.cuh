@@ -1,9 +1,11 @@
 // Per-item bodies of the multigrid transfer and stored-level stencil kernels
 // (Algorithm 2: restriction P^T, interpolation P, the level operator with
-// its residual / damped-Jacobi epilogues).  The one-kernel-per-step path
-// (kernels_mg.cu, kernels_fe.cu) and the fused coarse V-cycle
-// (kernels_vfuse.cu) both call these, so the two compute the same values
-// bit for bit.
+// its residual / damped-Jacobi epilogues).  The fused coarse V-cycle
+// (kernels_vfuse.cu) calls all of them, the one-kernel-per-step
+// interpolation and stencil apply (kernels_mg.cu, kernels_fe.cu) call
+// theirs, and the one-kernel restriction (kernels_mg.cu, one thread per
+// value) repeats restrict_finish's per-term arithmetic in the same order,
+// so the two paths compute the same values bit for bit.
 //
 // CG selects how vectors that the calling kernel may itself have written are
 // loaded: false, a plain load (one kernel per step: the data come from
