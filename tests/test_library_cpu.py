@@ -41,6 +41,30 @@ def test_library_exports_every_declared_symbol():
     assert sorted(B.exported_symbols()) == _declared()
 
 
+def _header_constants():
+    """Integer constants of include/topo.h: #define TO_X <int> and the
+    TO_X = <int> entries of its enums."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    vals = {k: int(v) for k, v in re.findall(r"#define\s+(TO_[A-Z_0-9]+)\s+(-?\d+)\s*$", src,
+                                             flags=re.M)}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for k, v in re.findall(r"(TO_[A-Z_0-9]+)\s*=\s*(-?\d+)", body):
+            vals[k] = int(v)
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """Every TO_* integer the Python binding defines has the header's value
+    (option bits, enums, limits, status codes)."""
+    from paper_2205_00385_gb300 import binding as B
+    hdr = _header_constants()
+    assert len(hdr) >= 30
+    shared = [k for k in hdr if hasattr(B, k)]
+    assert "TO_OPERATOR_WORK_LIST" in shared and "TO_PREC_DF" in shared
+    for k in shared:
+        assert getattr(B, k) == hdr[k], k
+
+
 def test_workspace_bytes_and_validation():
     B, _ = _lib()
     d = B.make_desc(3, (192, 96, 96), rmin=2.0, mg_levels=6, precision=B.TO_MIXED,
